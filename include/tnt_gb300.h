@@ -1,0 +1,275 @@
+/*
+ * tnt_gb300.h -- C-ABI of the GB300 (sm_103a) two-site-update library.
+ *
+ * The library computes the hot path of the MPS algorithms of "The Tensor Network Theory
+ * Library" (arXiv:1610.02244): the effective-Hamiltonian matvec L.W.W.R.theta that the
+ * eigensolver applies in DMRG (Sec. 4.2 Listing 1, Sec. 4.3 Listing 2), the two-site
+ * gate of TEBD (Sec. 3, Sec. 5), and the reshape plus truncated SVD of theta that follows
+ * both (App. B.1.2, Eq. 3), on Bose-Hubbard chains (Sec. 5, Eq. 2) with optional U(1)
+ * boson-number labels (App. A.1.1).
+ *
+ * Conventions for every call
+ *   - Every call returns an int status (TNT_OK = 0 or a TNT_E_* code); results go through
+ *     out-pointers.  After a failure tnt_last_error(ctx) describes it.
+ *   - Complex numbers are interleaved {double re, im} (tnt_cplx), tensors are dense,
+ *     row-major (C order), with the leg orders below.  Sizes are int64_t.
+ *       MPS site tensor   A[a, s, b]           (left bond, physical, right bond)
+ *       two-site tensor   theta[a, s1, s2, b]
+ *       MPO tensor        W[w, w', s', s]      (s' out/bra, s in/ket)
+ *       left environment  L[a', w, a]          (a' bra side, a ket side)
+ *       right environment R[b', w, b]
+ *   - Pointers named d_* are DEVICE pointers (CUDA global memory on the context's device);
+ *     they are borrowed for the duration of the call, never freed or retained.  Pointers
+ *     named h_* are HOST pointers, copied during the call.
+ *   - Work is enqueued on the context's stream.  Calls that return host scalars
+ *     synchronise that stream before returning; calls with device outputs only do not.
+ *   - All computation runs on the GPU; there is no CPU fallback.  A missing or
+ *     unusable GPU makes tnt_ctx_create fail with TNT_E_CUDA.
+ *   - Handles (tnt_ctx, tnt_mpo, tnt_mps, tnt_dmrg) are opaque, created by the library
+ *     and freed only by their *_destroy call.
+ */
+#ifndef TNT_GB300_H
+#define TNT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Everything declared here is exported from the shared library; nothing else is. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+  TNT_OK = 0,
+  TNT_E_INVALID = 1,     /* bad argument (null pointer, non-positive size, bad enum)   */
+  TNT_E_ALLOC = 2,       /* device or pinned host allocation failed                     */
+  TNT_E_CUDA = 3,        /* a CUDA runtime/driver call or kernel launch failed          */
+  TNT_E_NOCONV = 4,      /* an iterative solver hit its iteration cap unconverged       */
+  TNT_E_TIMEOUT = 5,     /* a bounded device-side wait gave up                          */
+  TNT_E_BOUNDS = 6,      /* a device-side index check failed                            */
+  TNT_E_NAN = 7,         /* a NaN/Inf was detected in a result                          */
+  TNT_E_UNSUPPORTED = 8  /* shape or mode not supported by this build                   */
+};
+
+enum { TNT_PREC_FP64 = 0, TNT_PREC_MIXED = 1 };
+/* Truncation error functions of App. B.1.2: Eq. 3 (2-norm), sum of squares, 1-norm. */
+enum { TNT_TRUNC_2NORM = 0, TNT_TRUNC_SUMSQ = 1, TNT_TRUNC_1NORM = 2 };
+/* Which factor of M = U S V^H the truncated SVD keeps orthonormal. */
+enum { TNT_SVD_LEFT = 0, TNT_SVD_RIGHT = 1 };
+
+typedef struct { double re, im; } tnt_cplx;
+
+typedef struct tnt_ctx tnt_ctx;
+typedef struct tnt_mpo tnt_mpo;
+typedef struct tnt_mps tnt_mps;
+typedef struct tnt_dmrg tnt_dmrg;
+
+/*
+ * Simulation parameters (the library's system settings, App. A.3 and App. B.5).
+ * Defaults (tnt_params_default) are the printed defaults of App. A.3 Listing 5:
+ * relative truncation tolerance 1e-16, absolute tolerance -1 (off), truncation error
+ * tolerance 1e-8, truncation type 2norm, eigensolver iteration cap 300.
+ */
+typedef struct {
+  int64_t chi_max;      /* bond-dimension cap (truncation rule 1)                 */
+  double trunc_abs;     /* rule 2: discard lambda_i < trunc_abs; <= 0 disables      */
+  double trunc_rel;     /* rule 3: discard lambda_i / lambda_0 < trunc_rel          */
+  double trunc_err;     /* rule 4: largest discard with error < trunc_err           */
+  int trunc_type;       /* TNT_TRUNC_*: error function of rule 4                   */
+  double lanczos_tol;   /* relative eigenvalue-change and residual tolerance        */
+  int lanczos_maxit;    /* total matvec cap per eigensolve                          */
+  int krylov_cap;       /* Krylov vectors before a restart (<= 64)                  */
+  int precision;        /* TNT_PREC_FP64 or TNT_PREC_MIXED for H_eff.theta          */
+  uint64_t seed;        /* reserved for library-side random draws                  */
+} tnt_params;
+
+/* Result of one eigensolve (Lanczos on H_eff, Sec. 4.3). */
+typedef struct {
+  double E;             /* Ritz value of the last Krylov step                       */
+  double E_rq;          /* FP64 Rayleigh quotient <x|H x>/<x|x> of the returned x    */
+  double resid;         /* Lanczos residual estimate beta_k |y_k|                    */
+  double resid_fp64;    /* |H x - E_rq x| with H applied in FP64                     */
+  int n_matvec;         /* matvecs spent (mixed + FP64)                              */
+  int converged;        /* 1 if the stopping rule was met before the cap             */
+} tnt_lanczos_result;
+
+/* Result of one truncated SVD (App. B.1.2). */
+typedef struct {
+  int64_t chi;          /* kept singular values                                     */
+  double err;           /* truncation error (trunc_type) of the normalised discards  */
+  double disc;          /* discarded weight: sum of raw discarded lambda^2           */
+  double norm2;         /* sum of all lambda^2                                       */
+  int n_blocks;         /* charge blocks decomposed                                  */
+  int tie_at_cut;       /* 1 if lambda_chi and lambda_chi+1 agree to 1e-10 lambda_0  */
+} tnt_trunc_result;
+
+/* Per-sweep DMRG statistics (one sweep = 2(L-1) two-site updates). */
+typedef struct {
+  double E;             /* energy after the sweep (FP64 Rayleigh quotient)           */
+  double max_err;       /* largest truncation error of the sweep                     */
+  double max_disc;      /* largest discarded weight of the sweep                     */
+  int64_t max_chi;      /* largest bond dimension after the sweep                    */
+  int total_matvecs;    /* matvecs of all eigensolves                                */
+  int unconverged;      /* eigensolves that hit the cap                              */
+  double seconds;       /* wall time of the sweep (CUDA events)                      */
+} tnt_sweep_stats;
+
+/* Per-step TEBD statistics (second-order Trotter step). */
+typedef struct {
+  double err_sum;       /* sum of the step's truncation errors (Eq. 3)               */
+  double disc_sum;      /* sum of the step's discarded weights                       */
+  int64_t max_chi;
+  double seconds;
+} tnt_step_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  Fails with TNT_E_CUDA if no usable GPU exists. */
+int tnt_ctx_create(int device, void* stream, tnt_ctx** out);
+int tnt_ctx_destroy(tnt_ctx* ctx);
+/* Replace the stream used by later calls. */
+int tnt_set_stream(tnt_ctx* ctx, void* stream);
+/* Text of the last error on this context (static storage owned by the context). */
+const char* tnt_last_error(const tnt_ctx* ctx);
+/* Number of kernels this library has launched on the context (diagnostics). */
+int64_t tnt_launch_count(const tnt_ctx* ctx);
+
+/* Parameter handling (App. A.3: the system settings and their defaults). */
+int tnt_params_default(tnt_params* p);
+int tnt_params_set(tnt_ctx* ctx, const tnt_params* p);
+int tnt_params_get(const tnt_ctx* ctx, tnt_params* p);
+/* Summary of the settings in the layout of App. A.3 Listing 5, NUL-terminated into buf. */
+int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n);
+
+/* ------------------------------------------------------------------ model (host, FP64) */
+
+/* One site's Bose-Hubbard MPO tensor W[4][4][d][d], d = n_max + 1, for site j (1-based)
+ * of Eq. 2 plus -mu n: lower-triangular hand construction (Sec. 4.3),
+ *   W[0][0] = I, W[1][0] = b, W[2][0] = b+, W[3][0] = U/2 n(n-1) + (V (j-j_c)^2 - mu) n,
+ *   W[3][1] = -J b+, W[3][2] = -J b, W[3][3] = I.
+ * Left boundary vector e_3, right boundary e_0.  h_W: host, 16 d^2 elements. */
+int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j,
+                    double j_c, tnt_cplx* h_W);
+/* Trotter gate exp(-i tau h) of the bond term
+ *   h = -J (b+ (x) b + b (x) b+) + c1 h_site (x) I + c2 I (x) h_site,
+ * h_site = U/2 n(n-1) - mu n, as a d^2 x d^2 matrix G[(s1' s2'), (s1 s2)] (host). */
+int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2,
+                     double tau, tnt_cplx* h_G);
+
+/* ------------------------------------------------------------------ two-site kernels */
+
+/* a1. theta[a,s1,s2,b] = sum_m A[a,s1,m] B[m,s2,b]  (Sec. 3 contraction, App. B.1.1).
+ * d_A: chl x d x chm, d_B: chm x d x chr, d_theta: chl x d x d x chr (device). */
+int tnt_theta_form(tnt_ctx* ctx, const tnt_cplx* d_A, const tnt_cplx* d_B, int64_t chl,
+                   int64_t d, int64_t chm, int64_t chr, tnt_cplx* d_theta);
+
+/* a2. out[a,s1',s2',b] = sum G[(s1' s2'),(s1 s2)] theta[a,s1,s2,b]  (TEBD gate, Sec. 3).
+ * d_G: d^2 x d^2 (device); d_out must not alias d_theta. */
+int tnt_gate_apply(tnt_ctx* ctx, const tnt_cplx* d_G, const tnt_cplx* d_theta, int64_t chl,
+                   int64_t d, int64_t chr, tnt_cplx* d_out);
+
+/* a3. y = H_eff theta:
+ *   y[a',s1',s2',b'] = sum L[a',w,a] W1[w,w1,s1',s1] W2[w1,w2,s2',s2] R[b',w2,b] theta[a,s1,s2,b]
+ * (two-site form of the Listing 1 contractor), contracted as (L.theta).W1.W2.R.
+ * precision = TNT_PREC_FP64: FP64 throughout.  TNT_PREC_MIXED: the two chi^3 contractions
+ * on tcgen05 tensor cores in split TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation),
+ * relative error ~1e-6 of |y|; the W contraction and the output stay FP64.
+ * d_L: chl x D x chl, d_W1, d_W2: D x D x d x d, d_R: chr x D x chr, d_theta, d_y:
+ * chl x d x d x chr (device; d_y must not alias inputs). */
+int tnt_heff_apply(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
+                   const tnt_cplx* d_W2, const tnt_cplx* d_R, const tnt_cplx* d_theta,
+                   int64_t chl, int64_t d, int64_t D, int64_t chr, int precision,
+                   tnt_cplx* d_y);
+
+/* a8. Environment growth (Sec. 4.3 <psi|H|psi> network, Listing 2 H_prepare):
+ *   left:  Lout[m',w',m] = sum conj(A[a',s',m']) L[a',w,a] W[w,w',s',s] A[a,s,m]
+ *          d_L: chl x D x chl, d_A: chl x d x chr, d_Lout: chr x D x chr
+ *   right: Rout[a',w,a] = sum conj(B[a',s',b']) R[b',w',b] W[w,w',s',s] B[a,s,b]
+ *          d_R: chr x D x chr, d_B: chl x d x chr, d_Rout: chl x D x chl      (FP64) */
+int tnt_env_left(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W,
+                 const tnt_cplx* d_A, int64_t chl, int64_t d, int64_t D, int64_t chr,
+                 tnt_cplx* d_Lout);
+int tnt_env_right(tnt_ctx* ctx, const tnt_cplx* d_R, const tnt_cplx* d_W,
+                  const tnt_cplx* d_B, int64_t chl, int64_t d, int64_t D, int64_t chr,
+                  tnt_cplx* d_Rout);
+
+/* a4 + a9. Lowest eigenpair of H_eff (Lanczos, full re-orthogonalisation by classical
+ * Gram-Schmidt twice, FP64 vectors and tridiagonal solve; restart from the Ritz vector
+ * every krylov_cap steps; at most lanczos_maxit matvecs; the library's eigensolver role of
+ * Sec. 4.3).  Matvecs use ctx precision; with TNT_PREC_MIXED one more FP64 matvec gives
+ * E_rq and resid_fp64.  d_theta (chl x d x d x chr) is the start vector on entry and the
+ * unit-norm eigenvector on exit.  Returns TNT_E_NOCONV (with the result filled) if the cap
+ * was hit unconverged. */
+int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
+                       const tnt_cplx* d_W2, const tnt_cplx* d_R, int64_t chl, int64_t d,
+                       int64_t D, int64_t chr, tnt_cplx* d_theta, tnt_lanczos_result* res);
+
+/* a5 + a6. Truncated SVD of M (m x n, device) read as block diagonal under U(1) labels
+ * h_row_q (m) and h_col_q (n) (host; pass all zeros, or NULL for both, for a dense matrix),
+ * with the four truncation rules of the context parameters (App. B.1.2; smallest chi wins)
+ * and global order lambda desc, then charge asc, then in-block index.
+ * side = TNT_SVD_LEFT:  d_U (m x chi) orthonormal columns, d_X = S V^H (chi x n) = U^H M.
+ * side = TNT_SVD_RIGHT: d_X = V^H (chi x n) orthonormal rows, d_U = U S (m x chi) = M V.
+ * renorm != 0 rescales the kept S to sum S^2 = 1 (DMRG); 0 keeps it (TEBD).
+ * Capacity: d_U holds m * cap, d_X holds cap * n, h_S and h_bond_q hold cap values, with
+ * cap = min(m, n, chi_max); outputs are written densely with leading dimension chi.
+ * Kept indices are ordered by charge ascending, then lambda descending.
+ * FP64 Gram matrix plus FP64 cyclic Jacobi per block: values below ~1e-8 lambda_0 are not
+ * resolved to full relative accuracy. */
+int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n,
+                  const int64_t* h_row_q, const int64_t* h_col_q, int side, int renorm,
+                  tnt_cplx* d_U, tnt_cplx* d_X, double* h_S, int64_t* h_bond_q,
+                  tnt_trunc_result* res);
+
+/* ------------------------------------------------------------------ MPO / MPS / DMRG */
+
+/* Bose-Hubbard MPO on L sites (Eq. 2 plus -mu N), device-resident. */
+int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, double mu,
+                         double V, double j_c, tnt_mpo** out);
+int tnt_mpo_destroy(tnt_mpo* mpo);
+
+/* MPS from host data: h_chi[0..L] bond dimensions (h_chi[0] = h_chi[L] = 1), h_sites[j]
+ * chi[j] x d x chi[j+1] tensors, h_charges[k] (chi[k] labels of bond k, bosons to the
+ * left) or h_charges = NULL for no labels.  Device capacity per bond is
+ * min(chi_cap, d^k, d^(L-k)) with chi_cap >= every h_chi. */
+int tnt_mps_create(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int64_t* h_chi,
+                   const tnt_cplx* const* h_sites, const int64_t* const* h_charges,
+                   tnt_mps** out);
+/* Product (Fock) state |n_1 ... n_L> with bond labels (e.g. the Mott state |1,...,1>). */
+int tnt_mps_product(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int* h_occupations,
+                    tnt_mps** out);
+int tnt_mps_destroy(tnt_mps* mps);
+int tnt_mps_length(const tnt_mps* mps, int* L, int* d);
+int tnt_mps_bond_dim(const tnt_mps* mps, int bond, int64_t* chi);
+/* Copy site j (chi[j] x d x chi[j+1]) to host; cap is the host buffer length in elements. */
+int tnt_mps_get_site(tnt_ctx* ctx, const tnt_mps* mps, int site, tnt_cplx* h_out,
+                     int64_t cap);
+int tnt_mps_get_charges(const tnt_mps* mps, int bond, int64_t* h_out, int64_t cap);
+/* <psi|O|psi> (FP64 environment pass) and <psi|psi>. */
+int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* mps, const tnt_mpo* mpo, double* E);
+int tnt_mps_norm2(tnt_ctx* ctx, const tnt_mps* mps, double* norm2);
+
+/* Two-site DMRG (Sec. 4.3 Listing 2 in two-site form).  Create brings the MPS to
+ * right-canonical unit-norm form by exact SVD moves and builds the right environments.
+ * One sweep = bonds 0..L-2 left to right, then L-2..0 right to left; each update forms
+ * theta (a1), runs the eigensolve (a3, a4), splits theta by the truncated SVD (a5, a6)
+ * with S renormalised (a7), and grows the environment (a8). */
+int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* mps, const tnt_mpo* mpo, tnt_dmrg** out);
+int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
+int tnt_dmrg_destroy(tnt_dmrg* dmrg);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNT_GB300_H */

@@ -1,0 +1,388 @@
+// C-ABI entry points (include/tnt_gb300.h): context, parameters, model builders and the
+// two-site kernels.  Argument checking happens here; the work is in the other units.
+#include <cmath>
+#include <cstdarg>
+#include <vector>
+
+#include "heff_plan.cuh"
+
+namespace tnt {
+
+int set_err(Ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int ws_reserve(Ctx* c, size_t bytes) {
+  if (bytes <= c->ws.cap) return TNT_OK;
+  if (c->ws.top != 0)
+    return set_err(c, TNT_E_ALLOC,
+                   "scratch of %zu bytes needed while %zu bytes are in use (reserve first)", bytes,
+                   c->ws.top);
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->ws.base) TNT_CUDA_TRY(c, cudaFree(c->ws.base));
+  c->ws.base = nullptr;
+  c->ws.cap = 0;
+  size_t cap = ws_round(bytes + bytes / 8);
+  cudaError_t e = cudaMalloc((void**)&c->ws.base, cap);
+  if (e != cudaSuccess) {
+    c->ws.base = nullptr;
+    return set_err(c, TNT_E_ALLOC, "cudaMalloc of %zu bytes of scratch failed: %s", cap,
+                   cudaGetErrorString(e));
+  }
+  c->ws.cap = cap;
+  return TNT_OK;
+}
+
+void* ws_alloc(Ctx* c, size_t bytes) {
+  bytes = ws_round(bytes);
+  if (c->ws.top + bytes > c->ws.cap) return nullptr;
+  void* p = c->ws.base + c->ws.top;
+  c->ws.top += bytes;
+  return p;
+}
+
+int pinned_reserve(Ctx* c, size_t bytes) {
+  if (bytes <= c->h_pinned_cap) return TNT_OK;
+  if (c->h_pinned) {
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaFreeHost(c->h_pinned);
+  }
+  c->h_pinned = nullptr;
+  c->h_pinned_cap = 0;
+  if (cudaMallocHost((void**)&c->h_pinned, bytes) != cudaSuccess)
+    return set_err(c, TNT_E_ALLOC, "pinned host allocation of %zu bytes failed", bytes);
+  c->h_pinned_cap = bytes;
+  return TNT_OK;
+}
+
+
+// ---------------------------------------------------------------- Bose-Hubbard (host)
+static void local_ops(int n_max, std::vector<double>* b) {
+  const int d = n_max + 1;
+  b->assign((size_t)d * d, 0.0);
+  for (int n = 1; n < d; ++n) (*b)[(size_t)(n - 1) * d + n] = std::sqrt((double)n);
+}
+
+int bh_mpo_site_host(int n_max, double J, double U, double mu, double V, double j, double jc,
+                     z* W) {
+  const int d = n_max + 1, D = 4;
+  std::vector<double> b;
+  local_ops(n_max, &b);
+  for (int e = 0; e < D * D * d * d; ++e) W[e] = zmk(0, 0);
+  auto at = [&](int w, int v, int so, int si) -> z& { return W[((w * D + v) * d + so) * d + si]; };
+  for (int so = 0; so < d; ++so)
+    for (int si = 0; si < d; ++si) {
+      const double bb = b[(size_t)so * d + si];      // <so|b|si>
+      const double bd = b[(size_t)si * d + so];      // <so|b+|si>
+      const double id = (so == si) ? 1.0 : 0.0;
+      const double nn = (so == si) ? (double)si : 0.0;
+      at(0, 0, so, si) = zmk(id, 0);
+      at(1, 0, so, si) = zmk(bb, 0);
+      at(2, 0, so, si) = zmk(bd, 0);
+      at(3, 0, so, si) = zmk(0.5 * U * nn * (nn - id) + (V * (j - jc) * (j - jc) - mu) * nn, 0);
+      at(3, 1, so, si) = zmk(-J * bd, 0);
+      at(3, 2, so, si) = zmk(-J * bb, 0);
+      at(3, 3, so, si) = zmk(id, 0);
+    }
+  return TNT_OK;
+}
+
+// Hermitian eigendecomposition on the host (cyclic Jacobi, tiny matrices: the d^2 x d^2
+// bond term) for the gate exp(-i tau h).
+static void herm_eig_host(int n, std::vector<z>& A, std::vector<double>* lam, std::vector<z>* V) {
+  V->assign((size_t)n * n, zmk(0, 0));
+  for (int i = 0; i < n; ++i) (*V)[(size_t)i * n + i] = zmk(1, 0);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0, dg = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a = std::hypot(A[(size_t)i * n + j].x, A[(size_t)i * n + j].y);
+        if (i == j) dg = std::max(dg, a); else off = std::max(off, a);
+      }
+    if (off <= 1e-16 * dg || off < 1e-300) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        z apq = A[(size_t)p * n + q];
+        double ab = std::hypot(apq.x, apq.y);
+        if (ab < 1e-300) continue;
+        double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
+        z e = zmk(apq.x / ab, apq.y / ab);
+        double tau = (aqq - app) / (2 * ab);
+        double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1 + tau * tau));
+        double cs = 1 / std::sqrt(1 + t * t), sn = t * cs;
+        for (int jx = 0; jx < n; ++jx) {  // rows: A <- J^H A
+          z gp = A[(size_t)p * n + jx], gq = zmul(e, A[(size_t)q * n + jx]);
+          A[(size_t)p * n + jx] = zsub(zscale(gp, cs), zscale(gq, sn));
+          A[(size_t)q * n + jx] = zadd(zscale(gp, sn), zscale(gq, cs));
+        }
+        z ec = zconj(e);
+        for (int i = 0; i < n; ++i) {  // columns: A <- A J, V <- V J
+          z gp = A[(size_t)i * n + p], gq = zmul(A[(size_t)i * n + q], ec);
+          A[(size_t)i * n + p] = zsub(zscale(gp, cs), zscale(gq, sn));
+          A[(size_t)i * n + q] = zadd(zscale(gp, sn), zscale(gq, cs));
+          z vp = (*V)[(size_t)i * n + p], vq = zmul((*V)[(size_t)i * n + q], ec);
+          (*V)[(size_t)i * n + p] = zsub(zscale(vp, cs), zscale(vq, sn));
+          (*V)[(size_t)i * n + q] = zadd(zscale(vp, sn), zscale(vq, cs));
+        }
+      }
+  }
+  lam->resize(n);
+  for (int i = 0; i < n; ++i) (*lam)[i] = A[(size_t)i * n + i].x;
+}
+
+int bh_bond_gate_host(int n_max, double J, double U, double mu, double c1, double c2,
+                      double tau, z* G) {
+  const int d = n_max + 1, n = d * d;
+  std::vector<double> b;
+  local_ops(n_max, &b);
+  std::vector<z> h((size_t)n * n, zmk(0, 0));
+  auto hs = [&](int s) { return 0.5 * U * s * (s - 1) - mu * s; };
+  for (int s1o = 0; s1o < d; ++s1o)
+    for (int s2o = 0; s2o < d; ++s2o)
+      for (int s1 = 0; s1 < d; ++s1)
+        for (int s2 = 0; s2 < d; ++s2) {
+          // -J (b+ (x) b + b (x) b+)
+          double v = -J * (b[(size_t)s1 * d + s1o] * b[(size_t)s2o * d + s2] +
+                           b[(size_t)s1o * d + s1] * b[(size_t)s2 * d + s2o]);
+          if (s1o == s1 && s2o == s2) v += c1 * hs(s1) + c2 * hs(s2);
+          h[(size_t)(s1o * d + s2o) * n + (s1 * d + s2)] = zmk(v, 0);
+        }
+  std::vector<double> lam;
+  std::vector<z> Q;
+  herm_eig_host(n, h, &lam, &Q);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      z acc = zmk(0, 0);
+      for (int k = 0; k < n; ++k) {
+        z ph = zmk(std::cos(-tau * lam[k]), std::sin(-tau * lam[k]));
+        zfma(acc, zmul(Q[(size_t)i * n + k], ph), zconj(Q[(size_t)j * n + k]));
+      }
+      G[(size_t)i * n + j] = acc;
+    }
+  return TNT_OK;
+}
+
+}  // namespace tnt
+
+using namespace tnt;
+
+#define CTX_CHECK(ctx)                   \
+  do {                                   \
+    if (!(ctx)) return TNT_E_INVALID;    \
+  } while (0)
+#define ARG_CHECK(ctx, cond, ...)                                       \
+  do {                                                                  \
+    if (!(cond)) return set_err(&(ctx)->c, TNT_E_INVALID, __VA_ARGS__); \
+  } while (0)
+
+extern "C" {
+
+int tnt_params_default(tnt_params* p) {
+  if (!p) return TNT_E_INVALID;
+  p->chi_max = (int64_t)1 << 40;
+  p->trunc_abs = -1.0;
+  p->trunc_rel = 1e-16;
+  p->trunc_err = 1e-8;
+  p->trunc_type = TNT_TRUNC_2NORM;
+  p->lanczos_tol = 1e-12;
+  p->lanczos_maxit = 300;
+  p->krylov_cap = 32;
+  p->precision = TNT_PREC_FP64;
+  p->seed = 0;
+  return TNT_OK;
+}
+
+int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
+  if (!out) return TNT_E_INVALID;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) return TNT_E_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return TNT_E_CUDA;
+  tnt_ctx* t = new tnt_ctx();
+  t->c.device = device;
+  t->c.stream = (cudaStream_t)stream;
+  tnt_params_default(&t->c.params);
+  if (cudaMalloc((void**)&t->c.d_status, 64) != cudaSuccess) {
+    delete t;
+    return TNT_E_CUDA;
+  }
+  cudaMemset(t->c.d_status, 0, 64);
+  if (pinned_reserve(&t->c, 4096) != TNT_OK) {
+    cudaFree(t->c.d_status);
+    delete t;
+    return TNT_E_ALLOC;
+  }
+  *out = t;
+  return TNT_OK;
+}
+
+int tnt_ctx_destroy(tnt_ctx* ctx) {
+  if (!ctx) return TNT_E_INVALID;
+  cudaStreamSynchronize(ctx->c.stream);
+  if (ctx->c.ws.base) cudaFree(ctx->c.ws.base);
+  if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
+  if (ctx->c.d_status) cudaFree(ctx->c.d_status);
+  delete ctx;
+  return TNT_OK;
+}
+
+int tnt_set_stream(tnt_ctx* ctx, void* stream) {
+  CTX_CHECK(ctx);
+  ctx->c.stream = (cudaStream_t)stream;
+  return TNT_OK;
+}
+
+const char* tnt_last_error(const tnt_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int64_t tnt_launch_count(const tnt_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
+
+int tnt_params_set(tnt_ctx* ctx, const tnt_params* p) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, p, "null params");
+  ARG_CHECK(ctx, p->chi_max >= 1, "chi_max must be >= 1");
+  ARG_CHECK(ctx, p->trunc_type >= 0 && p->trunc_type <= 2, "bad trunc_type %d", p->trunc_type);
+  ARG_CHECK(ctx, p->krylov_cap >= 2 && p->krylov_cap <= 64, "krylov_cap must be in [2, 64]");
+  ARG_CHECK(ctx, p->lanczos_maxit >= 1, "lanczos_maxit must be >= 1");
+  ARG_CHECK(ctx, p->precision == TNT_PREC_FP64 || p->precision == TNT_PREC_MIXED, "bad precision");
+  ctx->c.params = *p;
+  return TNT_OK;
+}
+
+int tnt_params_get(const tnt_ctx* ctx, tnt_params* p) {
+  if (!ctx || !p) return TNT_E_INVALID;
+  *p = ctx->c.params;
+  return TNT_OK;
+}
+
+int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return TNT_E_INVALID;
+  const tnt_params& p = ctx->c.params;
+  const char* tt = p.trunc_type == TNT_TRUNC_2NORM ? "2norm" : p.trunc_type == TNT_TRUNC_SUMSQ ? "sumsq" : "1norm";
+  snprintf(buf, n,
+           "------------- System Information -------------\n"
+           "Symmetry type: U(1) boson number (per call, optional).\n"
+           "Basis operator: boson number n.\n"
+           "Relative truncation tolerance is %g.\n"
+           "Absolute truncation tolerance is %g.\n"
+           "Truncation error tolerance is %g.\n"
+           "Current truncation type is %s.\n"
+           "SVD type is FP64 Gram plus cyclic Jacobi (GPU).\n"
+           "Maximum bond dimension is %lld.\n"
+           "Maximum number of iterations for eigenvalue solver is %d.\n"
+           "Krylov vectors before restart: %d; eigensolver tolerance %g.\n"
+           "H_eff precision: %s.\n",
+           p.trunc_rel, p.trunc_abs, p.trunc_err, tt, (long long)p.chi_max, p.lanczos_maxit,
+           p.krylov_cap, p.lanczos_tol, p.precision == TNT_PREC_MIXED ? "split TF32 (tcgen05)" : "FP64");
+  return TNT_OK;
+}
+
+int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j, double j_c,
+                    tnt_cplx* h_W) {
+  if (n_max < 0 || !h_W) return TNT_E_INVALID;
+  return bh_mpo_site_host(n_max, J, U, mu, V, j, j_c, (z*)h_W);
+}
+
+int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2, double tau,
+                     tnt_cplx* h_G) {
+  if (n_max < 0 || !h_G) return TNT_E_INVALID;
+  return bh_bond_gate_host(n_max, J, U, mu, c1, c2, tau, (z*)h_G);
+}
+
+int tnt_theta_form(tnt_ctx* ctx, const tnt_cplx* d_A, const tnt_cplx* d_B, int64_t chl, int64_t d,
+                   int64_t chm, int64_t chr, tnt_cplx* d_theta) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_A && d_B && d_theta, "null pointer");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && chm > 0 && chr > 0, "non-positive dimension");
+  Scope s(&ctx->c);
+  return theta_form_impl(&ctx->c, (const z*)d_A, (const z*)d_B, chl, d, chm, chr, (z*)d_theta);
+}
+
+int tnt_gate_apply(tnt_ctx* ctx, const tnt_cplx* d_G, const tnt_cplx* d_theta, int64_t chl,
+                   int64_t d, int64_t chr, tnt_cplx* d_out) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_G && d_theta && d_out && d_out != d_theta, "null or aliased pointer");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && chr > 0 && d * d <= 256, "bad dimension");
+  Scope s(&ctx->c);
+  TNT_TRY(ws_reserve(&ctx->c, 1 << 20));
+  std::vector<z> G((size_t)(d * d * d * d));
+  TNT_TRY(read_small(&ctx->c, d_G, G.data(), G.size() * sizeof(z)));
+  return gate_apply_impl(&ctx->c, G, (const z*)d_theta, chl, d, chr, (z*)d_out);
+}
+
+int tnt_heff_apply(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1, const tnt_cplx* d_W2,
+                   const tnt_cplx* d_R, const tnt_cplx* d_theta, int64_t chl, int64_t d, int64_t D,
+                   int64_t chr, int precision, tnt_cplx* d_y) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_L && d_W1 && d_W2 && d_R && d_theta && d_y, "null pointer");
+  ARG_CHECK(ctx, d_y != d_theta, "d_y aliases d_theta");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && D > 0 && chr > 0, "non-positive dimension");
+  ARG_CHECK(ctx, precision == TNT_PREC_FP64 || precision == TNT_PREC_MIXED, "bad precision");
+  ARG_CHECK(ctx, d * d * D <= 256, "d^2 D = %lld exceeds 256", (long long)(d * d * D));
+  Ctx* c = &ctx->c;
+  Scope s(c);
+  TNT_TRY(ws_reserve(c, heff_scratch_bound(chl, d, D, chr, precision)));
+  HeffPlan p;
+  TNT_TRY(heff_prepare(c, (const z*)d_L, (const z*)d_W1, (const z*)d_W2, (const z*)d_R, chl, d, D,
+                       chr, precision, &p));
+  return heff_run(c, p, (const z*)d_theta, (z*)d_y, precision);
+}
+
+int tnt_env_left(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W, const tnt_cplx* d_A,
+                 int64_t chl, int64_t d, int64_t D, int64_t chr, tnt_cplx* d_Lout) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_L && d_W && d_A && d_Lout, "null pointer");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && D > 0 && chr > 0 && d * D <= 256, "bad dimension");
+  Scope s(&ctx->c);
+  TNT_TRY(ws_reserve(&ctx->c, env_scratch_bound(chl, d, D, chr)));
+  return env_left_impl(&ctx->c, (const z*)d_L, (const z*)d_W, (const z*)d_A, chl, d, D, chr,
+                       (z*)d_Lout);
+}
+
+int tnt_env_right(tnt_ctx* ctx, const tnt_cplx* d_R, const tnt_cplx* d_W, const tnt_cplx* d_B,
+                  int64_t chl, int64_t d, int64_t D, int64_t chr, tnt_cplx* d_Rout) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_R && d_W && d_B && d_Rout, "null pointer");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && D > 0 && chr > 0 && d * D <= 256, "bad dimension");
+  Scope s(&ctx->c);
+  TNT_TRY(ws_reserve(&ctx->c, env_scratch_bound(chl, d, D, chr)));
+  return env_right_impl(&ctx->c, (const z*)d_R, (const z*)d_W, (const z*)d_B, chl, d, D, chr,
+                        (z*)d_Rout);
+}
+
+int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
+                       const tnt_cplx* d_W2, const tnt_cplx* d_R, int64_t chl, int64_t d,
+                       int64_t D, int64_t chr, tnt_cplx* d_theta, tnt_lanczos_result* res) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_L && d_W1 && d_W2 && d_R && d_theta && res, "null pointer");
+  ARG_CHECK(ctx, chl > 0 && d > 0 && D > 0 && chr > 0 && d * d * D <= 256, "bad dimension");
+  Ctx* c = &ctx->c;
+  Scope s(c);
+  const int64_t n = chl * d * d * chr;
+  TNT_TRY(ws_reserve(c, heff_scratch_bound(chl, d, D, chr, c->params.precision) +
+                            lanczos_scratch_bound(n, c->params.krylov_cap)));
+  HeffPlan p;
+  TNT_TRY(heff_prepare(c, (const z*)d_L, (const z*)d_W1, (const z*)d_W2, (const z*)d_R, chl, d, D,
+                       chr, c->params.precision, &p));
+  return lanczos_impl(c, p, (z*)d_theta, res);
+}
+
+int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n, const int64_t* h_row_q,
+                  const int64_t* h_col_q, int side, int renorm, tnt_cplx* d_U, tnt_cplx* d_X,
+                  double* h_S, int64_t* h_bond_q, tnt_trunc_result* res) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, d_M && d_U && d_X && h_S && h_bond_q && res, "null pointer");
+  ARG_CHECK(ctx, m > 0 && n > 0, "non-positive dimension");
+  ARG_CHECK(ctx, (h_row_q == nullptr) == (h_col_q == nullptr), "give both charge arrays or neither");
+  ARG_CHECK(ctx, side == TNT_SVD_LEFT || side == TNT_SVD_RIGHT, "bad side");
+  Scope s(&ctx->c);
+  return svd_trunc_impl(&ctx->c, (const z*)d_M, m, n, h_row_q, h_col_q, side, renorm, (z*)d_U,
+                        (z*)d_X, h_S, h_bond_q, res);
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// MPO / MPS handles and the two-site DMRG sweep (Sec. 4.3, Listing 2 in two-site form).
+// The sweep is host orchestration of the device kernels: theta formation (a1), Lanczos on
+// H_eff (a3, a4), truncated SVD (a5, a6) with S renormalised (a7), environment growth (a8).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "heff_plan.cuh"
+
+struct tnt_mpo {
+  int L = 0, d = 0, D = 4;
+  std::vector<tnt::z*> W;  // per site, D x D x d x d (device)
+  tnt::z* left = nullptr;   // boundary environment L_0[0,w,0] (device, D)
+  tnt::z* right = nullptr;  // boundary R_{L}[0,w,0]
+};
+
+struct tnt_mps {
+  int L = 0, d = 0;
+  std::vector<int64_t> chi, cap;      // bonds 0..L
+  std::vector<tnt::z*> A;             // sites 0..L-1, capacity cap[j] x d x cap[j+1]
+  std::vector<std::vector<int64_t>> q;  // bond labels (empty vectors: no labels)
+  bool labelled = false;
+};
+
+struct tnt_dmrg {
+  tnt_ctx* ctx = nullptr;
+  tnt_mps* mps = nullptr;
+  const tnt_mpo* mpo = nullptr;
+  std::vector<tnt::z*> Lenv, Renv;  // Lenv[i]: sites 0..i-1 (i = 0..L); Renv[i]: sites i..L-1
+  size_t scratch = 0;
+};
+
+namespace tnt {
+
+static int64_t ipow_cap(int64_t d, int64_t k, int64_t cap) {
+  int64_t r = 1;
+  for (int64_t i = 0; i < k; ++i) {
+    r *= d;
+    if (r >= cap) return cap;
+  }
+  return std::min(r, cap);
+}
+
+static std::vector<int64_t> labels_or_zero(const tnt_mps* m, int bond) {
+  if (m->labelled) return m->q[bond];
+  return std::vector<int64_t>((size_t)m->chi[bond], 0);
+}
+
+// exact SVD parameters for gauge moves (no truncation beyond exact zeros)
+static tnt_params exact_params(const tnt_params& p) {
+  tnt_params e = p;
+  e.chi_max = (int64_t)1 << 40;
+  e.trunc_abs = -1.0;
+  e.trunc_err = 0.0;
+  return e;
+}
+
+struct ParamsGuard {
+  Ctx* c;
+  tnt_params saved;
+  ParamsGuard(Ctx* cc, const tnt_params& p) : c(cc), saved(cc->params) { c->params = p; }
+  ~ParamsGuard() { c->params = saved; }
+};
+
+// grow Lenv over one site: Lout = env_left(Lin, W, A)
+static int dmrg_env_left(Ctx* c, tnt_dmrg* g, int i) {
+  tnt_mps* m = g->mps;
+  size_t top = c->ws.top;
+  int r = env_left_impl(c, g->Lenv[i], g->mpo->W[i], m->A[i], m->chi[i], m->d, g->mpo->D,
+                        m->chi[i + 1], g->Lenv[i + 1]);
+  c->ws.top = top;
+  return r;
+}
+
+static int dmrg_env_right(Ctx* c, tnt_dmrg* g, int j) {
+  // Renv[j] from Renv[j+1] and site j
+  tnt_mps* m = g->mps;
+  size_t top = c->ws.top;
+  int r = env_right_impl(c, g->Renv[j + 1], g->mpo->W[j], m->A[j], m->chi[j], m->d, g->mpo->D,
+                         m->chi[j + 1], g->Renv[j]);
+  c->ws.top = top;
+  return r;
+}
+
+// One two-site update on bond (i, i+1); dir > 0 left-to-right, dir < 0 right-to-left.
+static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* lz,
+                       tnt_trunc_result* tr) {
+  tnt_mps* m = g->mps;
+  const int64_t d = m->d, D = g->mpo->D;
+  const int64_t chl = m->chi[i], chm = m->chi[i + 1], chr = m->chi[i + 2];
+  const int64_t n = chl * d * d * chr;
+  const size_t top = c->ws.top;
+  z* theta = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  if (!theta) return set_err(c, TNT_E_ALLOC, "scratch exhausted (theta)");
+  TNT_TRY(theta_form_impl(c, m->A[i], m->A[i + 1], chl, d, chm, chr, theta));
+  {
+    HeffPlan p;
+    size_t t2 = c->ws.top;
+    TNT_TRY(heff_prepare(c, g->Lenv[i], g->mpo->W[i], g->mpo->W[i + 1], g->Renv[i + 2], chl, d, D,
+                         chr, c->params.precision, &p));
+    int r = lanczos_impl(c, p, theta, lz);
+    if (r != TNT_OK && r != TNT_E_NOCONV) return r;
+    c->ws.top = t2;
+  }
+  // SVD of M[(a s1), (s2 b)] with labels q_a + s1 and q_b - s2
+  std::vector<int64_t> ql = labels_or_zero(m, i), qr = labels_or_zero(m, i + 2);
+  std::vector<int64_t> rq((size_t)(chl * d)), cq((size_t)(d * chr));
+  for (int64_t a = 0; a < chl; ++a)
+    for (int64_t s = 0; s < d; ++s) rq[(size_t)(a * d + s)] = m->labelled ? ql[(size_t)a] + s : 0;
+  for (int64_t s = 0; s < d; ++s)
+    for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s * chr + b)] = m->labelled ? qr[(size_t)b] - s : 0;
+  const int64_t capk = std::min<int64_t>(m->cap[i + 1], std::min(chl * d, d * chr));
+  std::vector<double> S((size_t)capk);
+  std::vector<int64_t> bq((size_t)capk);
+  // U -> A_i (chl x d x k), X -> A_{i+1} (k x d x chr): the kernels write densely with
+  // leading dimension k, exactly the site layouts
+  TNT_TRY(svd_trunc_impl(c, theta, chl * d, d * chr, rq.data(), cq.data(),
+                         dir > 0 ? TNT_SVD_LEFT : TNT_SVD_RIGHT, 1, m->A[i], m->A[i + 1], S.data(),
+                         bq.data(), tr));
+  m->chi[i + 1] = tr->chi;
+  if (m->labelled) m->q[i + 1].assign(bq.begin(), bq.begin() + tr->chi);
+  c->ws.top = top;
+  return TNT_OK;
+}
+
+static size_t dmrg_scratch_bound(const tnt_mps* m, int D, const tnt_params& p) {
+  size_t best = 0;
+  for (int i = 0; i + 1 < m->L; ++i) {
+    const int64_t chl = m->cap[i], chr = m->cap[i + 2], d = m->d;
+    const int64_t n = chl * d * d * chr;
+    size_t b = ws_round(sizeof(z) * n) + heff_scratch_bound(chl, d, D, chr, p.precision) +
+               lanczos_scratch_bound(n, p.krylov_cap);
+    b = std::max(b, ws_round(sizeof(z) * n) + svd_scratch_bound(chl * d, d * chr));
+    b = std::max(b, env_scratch_bound(std::max(chl, m->cap[i + 1]), d, D,
+                                      std::max(chr, m->cap[i + 1])));
+    best = std::max(best, b);
+  }
+  return best + (size_t)(8 << 20);
+}
+
+}  // namespace tnt
+
+using namespace tnt;
+
+extern "C" {
+
+int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, double mu, double V,
+                         double j_c, tnt_mpo** out) {
+  if (!ctx || !out || L < 2 || n_max < 0) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mpo* o = new tnt_mpo();
+  o->L = L;
+  o->d = n_max + 1;
+  o->D = 4;
+  const size_t nW = (size_t)16 * o->d * o->d;
+  std::vector<z> h(nW);
+  for (int j = 0; j < L; ++j) {
+    bh_mpo_site_host(n_max, J, U, mu, V, (double)(j + 1), j_c, h.data());
+    z* dW = nullptr;
+    if (cudaMalloc((void**)&dW, nW * sizeof(z)) != cudaSuccess) {
+      tnt_mpo_destroy(o);
+      return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO failed");
+    }
+    o->W.push_back(dW);
+    cudaMemcpy(dW, h.data(), nW * sizeof(z), cudaMemcpyHostToDevice);
+  }
+  z lb[4] = {zmk(0, 0), zmk(0, 0), zmk(0, 0), zmk(1, 0)};
+  z rb[4] = {zmk(1, 0), zmk(0, 0), zmk(0, 0), zmk(0, 0)};
+  if (cudaMalloc((void**)&o->left, sizeof(lb)) != cudaSuccess ||
+      cudaMalloc((void**)&o->right, sizeof(rb)) != cudaSuccess) {
+    tnt_mpo_destroy(o);
+    return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO boundaries failed");
+  }
+  cudaMemcpy(o->left, lb, sizeof(lb), cudaMemcpyHostToDevice);
+  cudaMemcpy(o->right, rb, sizeof(rb), cudaMemcpyHostToDevice);
+  *out = o;
+  return TNT_OK;
+}
+
+int tnt_mpo_destroy(tnt_mpo* mpo) {
+  if (!mpo) return TNT_E_INVALID;
+  for (z* w : mpo->W) cudaFree(w);
+  if (mpo->left) cudaFree(mpo->left);
+  if (mpo->right) cudaFree(mpo->right);
+  delete mpo;
+  return TNT_OK;
+}
+
+int tnt_mps_create(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int64_t* h_chi,
+                   const tnt_cplx* const* h_sites, const int64_t* const* h_charges, tnt_mps** out) {
+  if (!ctx || !out || L < 2 || d < 1 || !h_chi || !h_sites || chi_cap < 1) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  if (h_chi[0] != 1 || h_chi[L] != 1) return set_err(c, TNT_E_INVALID, "boundary bonds must be 1");
+  tnt_mps* m = new tnt_mps();
+  m->L = L;
+  m->d = d;
+  m->chi.assign(h_chi, h_chi + L + 1);
+  m->cap.resize(L + 1);
+  for (int k = 0; k <= L; ++k) {
+    m->cap[k] = std::min(ipow_cap(d, k, chi_cap), ipow_cap(d, L - k, chi_cap));
+    if (m->chi[k] < 1 || m->chi[k] > m->cap[k]) {
+      tnt_mps_destroy(m);
+      return set_err(c, TNT_E_INVALID, "bond %d dimension %lld outside [1, %lld]", k,
+                     (long long)h_chi[k], (long long)m->cap[k]);
+    }
+  }
+  m->labelled = (h_charges != nullptr);
+  m->q.resize(L + 1);
+  if (m->labelled)
+    for (int k = 0; k <= L; ++k) m->q[k].assign(h_charges[k], h_charges[k] + m->chi[k]);
+  for (int j = 0; j < L; ++j) {
+    z* p = nullptr;
+    const size_t capn = (size_t)(m->cap[j] * d * m->cap[j + 1]);
+    if (cudaMalloc((void**)&p, capn * sizeof(z)) != cudaSuccess) {
+      tnt_mps_destroy(m);
+      return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPS site %d failed", j);
+    }
+    m->A.push_back(p);
+    const size_t nn = (size_t)(m->chi[j] * d * m->chi[j + 1]);
+    if (cudaMemcpy(p, h_sites[j], nn * sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) {
+      tnt_mps_destroy(m);
+      return set_err(c, TNT_E_CUDA, "copy of MPS site %d failed", j);
+    }
+  }
+  *out = m;
+  return TNT_OK;
+}
+
+int tnt_mps_product(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int* h_occ, tnt_mps** out) {
+  if (!ctx || !h_occ || L < 2) return TNT_E_INVALID;
+  std::vector<int64_t> chi(L + 1, 1);
+  std::vector<std::vector<tnt_cplx>> sites(L, std::vector<tnt_cplx>((size_t)d, tnt_cplx{0, 0}));
+  std::vector<const tnt_cplx*> ptr(L);
+  std::vector<std::vector<int64_t>> q(L + 1, std::vector<int64_t>(1, 0));
+  std::vector<const int64_t*> qp(L + 1);
+  int64_t tot = 0;
+  for (int j = 0; j < L; ++j) {
+    if (h_occ[j] < 0 || h_occ[j] >= d) return set_err(&ctx->c, TNT_E_INVALID, "occupation out of range");
+    sites[j][(size_t)h_occ[j]] = tnt_cplx{1.0, 0.0};
+    ptr[j] = sites[j].data();
+    tot += h_occ[j];
+    q[j + 1][0] = tot;
+  }
+  for (int k = 0; k <= L; ++k) qp[k] = q[k].data();
+  return tnt_mps_create(ctx, L, d, chi_cap, chi.data(), ptr.data(), qp.data(), out);
+}
+
+int tnt_mps_destroy(tnt_mps* m) {
+  if (!m) return TNT_E_INVALID;
+  for (z* p : m->A) cudaFree(p);
+  delete m;
+  return TNT_OK;
+}
+
+int tnt_mps_length(const tnt_mps* m, int* L, int* d) {
+  if (!m || !L || !d) return TNT_E_INVALID;
+  *L = m->L;
+  *d = m->d;
+  return TNT_OK;
+}
+
+int tnt_mps_bond_dim(const tnt_mps* m, int bond, int64_t* chi) {
+  if (!m || !chi || bond < 0 || bond > m->L) return TNT_E_INVALID;
+  *chi = m->chi[bond];
+  return TNT_OK;
+}
+
+int tnt_mps_get_site(tnt_ctx* ctx, const tnt_mps* m, int site, tnt_cplx* h_out, int64_t cap) {
+  if (!ctx || !m || !h_out || site < 0 || site >= m->L) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  const int64_t nn = m->chi[site] * m->d * m->chi[site + 1];
+  if (cap < nn) return set_err(c, TNT_E_INVALID, "host buffer holds %lld < %lld", (long long)cap, (long long)nn);
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  TNT_CUDA_TRY(c, cudaMemcpy(h_out, m->A[site], (size_t)nn * sizeof(z), cudaMemcpyDeviceToHost));
+  return TNT_OK;
+}
+
+int tnt_mps_get_charges(const tnt_mps* m, int bond, int64_t* h_out, int64_t cap) {
+  if (!m || !h_out || bond < 0 || bond > m->L || !m->labelled) return TNT_E_INVALID;
+  if (cap < m->chi[bond]) return TNT_E_INVALID;
+  std::copy(m->q[bond].begin(), m->q[bond].end(), h_out);
+  return TNT_OK;
+}
+
+int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* m, const tnt_mpo* o, double* E) {
+  if (!ctx || !m || !o || !E || m->L != o->L || m->d != o->d) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  ws_reset(c);
+  int64_t mx = *std::max_element(m->chi.begin(), m->chi.end());
+  size_t need = 2 * ws_round(sizeof(z) * (size_t)(mx * o->D * mx)) +
+                env_scratch_bound(mx, m->d, o->D, mx);
+  TNT_TRY(ws_reserve(c, need));
+  z* Ea = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(mx * o->D * mx)));
+  z* Eb = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(mx * o->D * mx)));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(Ea, o->left, sizeof(z) * o->D, cudaMemcpyDeviceToDevice, c->stream));
+  for (int j = 0; j < m->L; ++j) {
+    size_t top = c->ws.top;
+    int r = env_left_impl(c, Ea, o->W[j], m->A[j], m->chi[j], m->d, o->D, m->chi[j + 1], Eb);
+    c->ws.top = top;
+    if (r != TNT_OK) { ws_reset(c); return r; }
+    std::swap(Ea, Eb);
+  }
+  z h[4];
+  int r = read_small(c, Ea, h, sizeof(z) * o->D);
+  ws_reset(c);
+  if (r != TNT_OK) return r;
+  *E = h[0].x;  // right boundary e_0
+  return TNT_OK;
+}
+
+int tnt_mps_norm2(tnt_ctx* ctx, const tnt_mps* m, double* norm2) {
+  if (!ctx || !m || !norm2) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  ws_reset(c);
+  const int64_t d = m->d;
+  int64_t mx = *std::max_element(m->chi.begin(), m->chi.end());
+  size_t need = 2 * ws_round(sizeof(z) * (size_t)(mx * mx)) + ws_round(sizeof(z) * d * d) +
+                env_scratch_bound(mx, d, 1, mx);
+  TNT_TRY(ws_reserve(c, need));
+  z* Ea = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(mx * mx)));
+  z* Eb = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(mx * mx)));
+  z* Wid = (z*)ws_alloc(c, ws_round(sizeof(z) * d * d));
+  std::vector<z> hid((size_t)(d * d), zmk(0, 0));
+  for (int64_t s = 0; s < d; ++s) hid[(size_t)(s * d + s)] = zmk(1, 0);
+  z one = zmk(1, 0);
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(Wid, hid.data(), sizeof(z) * d * d, cudaMemcpyHostToDevice, c->stream));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(Ea, &one, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int j = 0; j < m->L; ++j) {
+    size_t top = c->ws.top;
+    int r = env_left_impl(c, Ea, Wid, m->A[j], m->chi[j], d, 1, m->chi[j + 1], Eb);
+    c->ws.top = top;
+    if (r != TNT_OK) { ws_reset(c); return r; }
+    std::swap(Ea, Eb);
+  }
+  z h;
+  int r = read_small(c, Ea, &h, sizeof(z));
+  ws_reset(c);
+  if (r != TNT_OK) return r;
+  *norm2 = h.x;
+  return TNT_OK;
+}
+
+int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) {
+  if (!ctx || !m || !o || !out || m->L != o->L || m->d != o->d) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_dmrg* g = new tnt_dmrg();
+  g->ctx = ctx;
+  g->mps = m;
+  g->mpo = o;
+  const int L = m->L;
+  g->Lenv.assign(L + 1, nullptr);
+  g->Renv.assign(L + 1, nullptr);
+  for (int k = 0; k <= L; ++k) {
+    const size_t ne = (size_t)(m->cap[k] * o->D * m->cap[k]);
+    if (cudaMalloc((void**)&g->Lenv[k], ne * sizeof(z)) != cudaSuccess ||
+        cudaMalloc((void**)&g->Renv[k], ne * sizeof(z)) != cudaSuccess) {
+      tnt_dmrg_destroy(g);
+      return set_err(c, TNT_E_ALLOC, "cudaMalloc for environments failed");
+    }
+  }
+  g->scratch = dmrg_scratch_bound(m, o->D, c->params);
+  ws_reset(c);
+  int r = ws_reserve(c, g->scratch);
+  if (r != TNT_OK) { tnt_dmrg_destroy(g); return r; }
+  // right-canonical form by exact SVD moves from the right end, then unit norm
+  {
+    ParamsGuard pg(c, exact_params(c->params));
+    const int64_t d = m->d;
+    for (int j = L - 1; j >= 1; --j) {
+      const int64_t chl = m->chi[j], chr = m->chi[j + 1];
+      std::vector<int64_t> ql = labels_or_zero(m, j), qr = labels_or_zero(m, j + 1);
+      std::vector<int64_t> cq((size_t)(d * chr));
+      for (int64_t s = 0; s < d; ++s)
+        for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s * chr + b)] = m->labelled ? qr[(size_t)b] - s : 0;
+      const int64_t capk = std::min(chl, d * chr);
+      std::vector<double> S((size_t)capk);
+      std::vector<int64_t> bq((size_t)capk);
+      z* M = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * d * chr)));
+      z* US = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * capk)));
+      z* Anew = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(m->chi[j - 1] * d * capk)));
+      if (!M || !US || !Anew) { ws_reset(c); tnt_dmrg_destroy(g); return set_err(c, TNT_E_ALLOC, "scratch (canonicalise)"); }
+      cudaMemcpyAsync(M, m->A[j], sizeof(z) * (size_t)(chl * d * chr), cudaMemcpyDeviceToDevice, c->stream);
+      tnt_trunc_result tr{};
+      r = svd_trunc_impl(c, M, chl, d * chr, ql.data(), cq.data(), TNT_SVD_RIGHT, 0, US, m->A[j],
+                         S.data(), bq.data(), &tr);
+      if (r != TNT_OK) { ws_reset(c); tnt_dmrg_destroy(g); return r; }
+      const int64_t k = tr.chi;
+      // A_{j-1} <- A_{j-1} (US)
+      ZGemm gm{};
+      gm.M = m->chi[j - 1] * d; gm.N = k; gm.K = chl;
+      gm.A = m->A[j - 1]; gm.a_rs = chl; gm.a_cs = 1;
+      gm.B = US; gm.b_rs = k; gm.b_cs = 1;
+      gm.C = Anew; gm.c_rs = k;
+      gm.alpha = zmk(1, 0); gm.beta = zmk(0, 0); gm.batch = 1;
+      r = zgemm(c, gm);
+      if (r != TNT_OK) { ws_reset(c); tnt_dmrg_destroy(g); return r; }
+      cudaMemcpyAsync(m->A[j - 1], Anew, sizeof(z) * (size_t)(m->chi[j - 1] * d * k), cudaMemcpyDeviceToDevice, c->stream);
+      m->chi[j] = k;
+      if (m->labelled) m->q[j].assign(bq.begin(), bq.begin() + k);
+      ws_reset(c);
+      TNT_TRY(ws_reserve(c, g->scratch));
+    }
+    // normalise site 0
+    const int64_t n0 = m->chi[0] * d * m->chi[1];
+    double* nrm = (double*)ws_alloc(c, 256);
+    r = vec_norm2(c, m->A[0], n0, nrm);
+    if (r == TNT_OK) r = zscale_inplace(c, m->A[0], n0, nrm, 1);
+    ws_reset(c);
+    if (r != TNT_OK) { tnt_dmrg_destroy(g); return r; }
+  }
+  // environments
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(g->Lenv[0], o->left, sizeof(z) * o->D, cudaMemcpyDeviceToDevice, c->stream));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(g->Renv[L], o->right, sizeof(z) * o->D, cudaMemcpyDeviceToDevice, c->stream));
+  for (int j = L - 1; j >= 1; --j) {
+    r = dmrg_env_right(c, g, j);
+    if (r != TNT_OK) { ws_reset(c); tnt_dmrg_destroy(g); return r; }
+  }
+  ws_reset(c);
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = g;
+  return TNT_OK;
+}
+
+int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
+  if (!ctx || !g || !st || g->ctx != ctx) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mps* m = g->mps;
+  const int L = m->L;
+  *st = tnt_sweep_stats{};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  ws_reset(c);
+  TNT_TRY(ws_reserve(c, g->scratch));
+  double E = 0;
+  auto account = [&](const tnt_lanczos_result& lz, const tnt_trunc_result& tr) {
+    st->total_matvecs += lz.n_matvec;
+    st->unconverged += lz.converged ? 0 : 1;
+    st->max_err = std::max(st->max_err, tr.err);
+    st->max_disc = std::max(st->max_disc, tr.disc);
+    E = lz.E_rq;
+  };
+  int r = TNT_OK;
+  for (int i = 0; i + 1 < L && r == TNT_OK; ++i) {
+    tnt_lanczos_result lz{};
+    tnt_trunc_result tr{};
+    r = dmrg_update(c, g, i, +1, &lz, &tr);
+    if (r == TNT_OK) r = dmrg_env_left(c, g, i);
+    account(lz, tr);
+  }
+  for (int i = L - 2; i >= 0 && r == TNT_OK; --i) {
+    tnt_lanczos_result lz{};
+    tnt_trunc_result tr{};
+    r = dmrg_update(c, g, i, -1, &lz, &tr);
+    if (r == TNT_OK) r = dmrg_env_right(c, g, i + 1);
+    account(lz, tr);
+  }
+  ws_reset(c);
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st->seconds = ms * 1e-3;
+  st->E = E;
+  st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
+  return r;
+}
+
+int tnt_dmrg_destroy(tnt_dmrg* g) {
+  if (!g) return TNT_E_INVALID;
+  for (z* p : g->Lenv) if (p) cudaFree(p);
+  for (z* p : g->Renv) if (p) cudaFree(p);
+  delete g;
+  return TNT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,621 @@
+// FP64 building blocks of the two-site update: strided complex GEMM (the contraction
+// primitive of App. B.1.1: reorder indices, one matrix product -- here the reorder is
+// folded into the strides), a sparse small-operator kernel for the MPO and gate legs,
+// the Lanczos vector operations and the tridiagonal eigensolve.
+#include <cstdarg>
+#include <cmath>
+
+#include "tnt_internal.cuh"
+
+namespace tnt {
+
+// ============================================================ complex FP64 GEMM
+// 64x64 output tile, BK = 16, 256 threads as 16x16; thread (tx, ty) owns rows ty + 16 r
+// and columns tx + 16 c (r, c < 4) so stores are coalesced along the row.
+namespace {
+constexpr int GM = 64, GN = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_zgemm(ZGemm g) {
+  __shared__ z As[GK][GM + 1];
+  __shared__ z Bs[GK][GN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * GM, n0 = (int64_t)blockIdx.x * GN;
+  const int64_t bt = blockIdx.z;
+  const z* A = g.A + bt * g.a_bs;
+  const z* B = g.B + bt * g.b_bs;
+  z* C = g.C + bt * g.c_bs;
+  z acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = zmk(0, 0);
+  const bool a_kfast = (g.a_cs == 1);
+  const bool b_nfast = (g.b_cs == 1);
+  for (int64_t k0 = 0; k0 < g.K; k0 += GK) {
+#pragma unroll
+    for (int t = 0; t < (GM * GK) / 256; ++t) {
+      int e = threadIdx.x + 256 * t;
+      int i, k;
+      if (a_kfast) { k = e % GK; i = e / GK; } else { i = e % GM; k = e / GM; }
+      int64_t gi = m0 + i, gk = k0 + k;
+      z v = zmk(0, 0);
+      if (gi < g.M && gk < g.K) {
+        v = A[gi * g.a_rs + gk * g.a_cs];
+        if (g.conj_a) v.y = -v.y;
+      }
+      As[k][i] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < (GN * GK) / 256; ++t) {
+      int e = threadIdx.x + 256 * t;
+      int j, k;
+      if (b_nfast) { j = e % GN; k = e / GN; } else { k = e % GK; j = e / GK; }
+      int64_t gj = n0 + j, gk = k0 + k;
+      z v = zmk(0, 0);
+      if (gj < g.N && gk < g.K) {
+        v = B[gk * g.b_rs + gj * g.b_cs];
+        if (g.conj_b) v.y = -v.y;
+      }
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      z a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) zfma(acc[r][c], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+  const bool use_beta = (g.beta.x != 0.0 || g.beta.y != 0.0);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int64_t gi = m0 + ty + 16 * r;
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t gj = n0 + tx + 16 * c;
+      if (gj >= g.N) continue;
+      z v = zmul(g.alpha, acc[r][c]);
+      z* p = C + gi * g.c_rs + gj;
+      if (use_beta) v = zadd(v, zmul(g.beta, *p));
+      *p = v;
+    }
+  }
+}
+}  // namespace
+
+int zgemm(Ctx* c, const ZGemm& g) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return TNT_OK;
+  if (g.K <= 0) {
+    // C = beta C (or zero): not needed by the library; reject to keep the kernel simple
+    return set_err(c, TNT_E_INVALID, "zgemm with K = 0");
+  }
+  if ((g.N + GN - 1) / GN > 0x7fffffff || (g.M + GM - 1) / GM > 65535 || g.batch > 65535)
+    return set_err(c, TNT_E_UNSUPPORTED, "zgemm grid too large (M=%lld N=%lld batch=%lld)",
+                   (long long)g.M, (long long)g.N, (long long)g.batch);
+  dim3 grid((unsigned)((g.N + GN - 1) / GN), (unsigned)((g.M + GM - 1) / GM),
+            (unsigned)g.batch);
+  k_zgemm<<<grid, 256, 0, c->stream>>>(g);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+// ============================================================ sparse operator apply
+namespace {
+constexpr int OP_MAX_NNZ = 2048;
+constexpr int OP_MAX_LEG = 256;
+
+__global__ void __launch_bounds__(256) k_op_apply(OpApply a, int nnz) {
+  __shared__ int s_row[OP_MAX_LEG + 1];
+  __shared__ int s_col[OP_MAX_NNZ];
+  __shared__ z s_val[OP_MAX_NNZ];
+  __shared__ int64_t s_in[OP_MAX_LEG];
+  __shared__ int64_t s_out[OP_MAX_LEG];
+  for (int t = threadIdx.x; t <= a.nI; t += blockDim.x) s_row[t] = a.row_ptr[t];
+  for (int t = threadIdx.x; t < nnz; t += blockDim.x) {
+    s_col[t] = a.col[t];
+    s_val[t] = a.val[t];
+  }
+  for (int t = threadIdx.x; t < a.nJ; t += blockDim.x) s_in[t] = a.in_off[t];
+  for (int t = threadIdx.x; t < a.nI; t += blockDim.x) s_out[t] = a.out_off[t];
+  __syncthreads();
+  const int64_t total = a.B0 * a.B1 * a.B2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b2 = e % a.B2;
+    int64_t r = e / a.B2;
+    int64_t b1 = r % a.B1;
+    int64_t b0 = r / a.B1;
+    const z* in = a.in + b0 * a.is0 + b1 * a.is1 + b2 * a.is2;
+    z* out = a.out + b0 * a.os0 + b1 * a.os1 + b2 * a.os2;
+    for (int i = 0; i < a.nI; ++i) {
+      z acc = zmk(0, 0);
+      for (int t = s_row[i]; t < s_row[i + 1]; ++t) zfma(acc, s_val[t], in[s_in[s_col[t]]]);
+      z* p = out + s_out[i];
+      if (a.accumulate) acc = zadd(acc, *p);
+      *p = acc;
+    }
+  }
+}
+}  // namespace
+
+int op_upload(Ctx* c, const std::vector<z>& dense, int nI, int nJ,
+              const std::vector<int64_t>& in_off, const std::vector<int64_t>& out_off,
+              OpApply* a) {
+  if (nI > OP_MAX_LEG || nJ > OP_MAX_LEG)
+    return set_err(c, TNT_E_UNSUPPORTED, "operator legs %d x %d exceed %d", nI, nJ,
+                   OP_MAX_LEG);
+  std::vector<int> row(nI + 1, 0), col;
+  std::vector<z> val;
+  for (int i = 0; i < nI; ++i) {
+    for (int j = 0; j < nJ; ++j) {
+      z v = dense[(size_t)i * nJ + j];
+      if (v.x != 0.0 || v.y != 0.0) {
+        col.push_back(j);
+        val.push_back(v);
+      }
+    }
+    row[i + 1] = (int)col.size();
+  }
+  if (col.size() > (size_t)OP_MAX_NNZ)
+    return set_err(c, TNT_E_UNSUPPORTED, "operator has %zu nonzeros > %d", col.size(),
+                   OP_MAX_NNZ);
+  if (col.empty()) {  // keep valid pointers for the kernel
+    col.push_back(0);
+    val.push_back(zmk(0, 0));
+  }
+  // one contiguous scratch block for the five tables
+  size_t b_row = ws_round(sizeof(int) * row.size());
+  size_t b_col = ws_round(sizeof(int) * col.size());
+  size_t b_val = ws_round(sizeof(z) * val.size());
+  size_t b_in = ws_round(sizeof(int64_t) * nJ);
+  size_t b_out = ws_round(sizeof(int64_t) * nI);
+  size_t total = b_row + b_col + b_val + b_in + b_out;
+  char* dev = (char*)ws_alloc(c, total);
+  if (!dev) return set_err(c, TNT_E_ALLOC, "scratch exhausted for operator tables");
+  std::vector<char> host(total, 0);
+  memcpy(host.data(), row.data(), sizeof(int) * row.size());
+  memcpy(host.data() + b_row, col.data(), sizeof(int) * col.size());
+  memcpy(host.data() + b_row + b_col, val.data(), sizeof(z) * val.size());
+  memcpy(host.data() + b_row + b_col + b_val, in_off.data(), sizeof(int64_t) * nJ);
+  memcpy(host.data() + b_row + b_col + b_val + b_in, out_off.data(), sizeof(int64_t) * nI);
+  // synchronous: the host vector dies at return (tables are a few KB)
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, c->stream));
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  a->nI = nI;
+  a->nJ = nJ;
+  a->nnz = row[nI];
+  a->row_ptr = (const int*)dev;
+  a->col = (const int*)(dev + b_row);
+  a->val = (const z*)(dev + b_row + b_col);
+  a->in_off = (const int64_t*)(dev + b_row + b_col + b_val);
+  a->out_off = (const int64_t*)(dev + b_row + b_col + b_val + b_in);
+  return TNT_OK;
+}
+
+int op_apply(Ctx* c, const OpApply& a) {
+  int64_t total = a.B0 * a.B1 * a.B2;
+  if (total <= 0) return TNT_OK;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  int nnz = a.nnz > 0 ? a.nnz : 1;
+  k_op_apply<<<(unsigned)blocks, 256, 0, c->stream>>>(a, nnz);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+// ============================================================ vector kernels
+// Deterministic reductions: a fixed grid of RB blocks; block b always covers the same
+// elements in the same order; a single-block second pass sums the partials in order.
+namespace {
+constexpr int RB = 296;       // 2 x 148..152 SMs: enough blocks to saturate HBM
+constexpr int RT = 256;
+constexpr int KB = 8;         // vectors per multidot pass
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double (result valid in thread 0)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// partial[v][blk] = sum over the block's range of conj(V_v[e]) w[e], v < kv
+__global__ void __launch_bounds__(RT) k_multidot(const z* __restrict__ V, int64_t ld, int kv,
+                                                 const z* __restrict__ w, int64_t n,
+                                                 z* __restrict__ partial) {
+  __shared__ double sh[32];
+  double ar[KB], ai[KB];
+#pragma unroll
+  for (int v = 0; v < KB; ++v) ar[v] = ai[v] = 0.0;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    z x = w[e];
+#pragma unroll
+    for (int v = 0; v < KB; ++v) {
+      if (v < kv) {
+        z u = V[(int64_t)v * ld + e];
+        ar[v] = fma(u.x, x.x, fma(u.y, x.y, ar[v]));
+        ai[v] = fma(u.x, x.y, fma(-u.y, x.x, ai[v]));
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < KB; ++v) {
+    if (v < kv) {
+      double r = block_sum(ar[v], sh);
+      double i = block_sum(ai[v], sh);
+      if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = zmk(r, i);
+    }
+  }
+}
+
+// out[v] = sum_b partial[v][b], fixed order; one block, kv outputs
+__global__ void k_reduce_partials(const z* __restrict__ partial, int nb, int kv,
+                                  z* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int v = 0; v < kv; ++v) {
+    double r = 0, i = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      z p = partial[(int64_t)v * nb + b];
+      r += p.x;
+      i += p.y;
+    }
+    r = block_sum(r, sh);
+    i = block_sum(i, sh);
+    if (threadIdx.x == 0) out[v] = zmk(r, i);
+  }
+}
+
+// w[e] -= sum_v coef[v] V_v[e]; partial[blk] = sum |w[e]|^2
+__global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, int64_t ld,
+                                                       int k, const z* __restrict__ coef,
+                                                       z* __restrict__ w, int64_t n,
+                                                       double* __restrict__ partial) {
+  __shared__ z sc[64];
+  __shared__ double sh[32];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) sc[t] = coef[t];
+  __syncthreads();
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  double acc = 0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    z x = w[e];
+    for (int v = 0; v < k; ++v) {
+      z u = V[(int64_t)v * ld + e];
+      z cv = sc[v];
+      x.x -= cv.x * u.x - cv.y * u.y;
+      x.y -= cv.x * u.y + cv.y * u.x;
+    }
+    w[e] = x;
+    acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+  }
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_reduce_real(const double* __restrict__ partial, int nb,
+                              double* __restrict__ out) {
+  __shared__ double sh[32];
+  double r = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) r += partial[b];
+  r = block_sum(r, sh);
+  if (threadIdx.x == 0) out[0] = r;
+}
+
+__global__ void k_norm2_partial(const z* __restrict__ x, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  double acc = 0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    z v = x[e];
+    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+  }
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_normalize(const z* __restrict__ x, z* __restrict__ y, int64_t n,
+                            const double* __restrict__ norm2) {
+  const double s = 1.0 / sqrt(norm2[0]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = zscale(x[e], s);
+}
+}  // namespace
+
+int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots) {
+  if (k <= 0) return TNT_OK;
+  // partial sums live in scratch only until the next launch on the same stream, so the
+  // region is handed back immediately (stream order serialises its reuse)
+  const size_t top = c->ws.top;
+  z* partial = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)KB * RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
+  for (int v0 = 0; v0 < k; v0 += KB) {
+    int kv = (k - v0 < KB) ? (k - v0) : KB;
+    k_multidot<<<RB, RT, 0, c->stream>>>(V + (int64_t)v0 * ld, ld, kv, w, n, partial);
+    k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0);
+    c->launches += 2;
+  }
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                       int64_t n, double* d_norm2) {
+  if (k > 64) return set_err(c, TNT_E_UNSUPPORTED, "multiaxpy with k=%d > 64", k);
+  const size_t top = c->ws.top;
+  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy)");
+  k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial);
+  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2);
+  c->launches += 2;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2) {
+  const size_t top = c->ws.top;
+  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (norm2)");
+  k_norm2_partial<<<RB, RT, 0, c->stream>>>(x, n, partial);
+  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2);
+  c->launches += 2;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_dot(Ctx* c, const z* x, const z* y, int64_t n, z* d_dot) {
+  return vec_multidot(c, x, 0, 1, y, n, d_dot);
+}
+
+int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > RB * 4) blocks = RB * 4;
+  if (blocks < 1) blocks = 1;
+  k_normalize<<<(unsigned)blocks, 256, 0, c->stream>>>(x, y, n, d_norm2);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+// ============================================================ tridiagonal eigensolve
+// Lowest eigenpair of the Lanczos matrix T (k <= 64): multisection on the Sturm count by
+// one warp (33 sub-intervals per step), then inverse iteration with a pivoted tridiagonal
+// LU (thread 0).  out[0] = E, out[1] = |y_{k-1}|.
+namespace {
+__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+  // number of eigenvalues < x (LDL^T of T - x I)
+  int cnt = 0;
+  double dd = a[0] - x;
+  const double tiny = 1e-300;
+  if (dd < 0) cnt++;
+  for (int i = 1; i < k; ++i) {
+    if (fabs(dd) < tiny) dd = -tiny;
+    dd = (a[i] - x) - b[i - 1] * b[i - 1] / dd;
+    if (dd < 0) cnt++;
+  }
+  return cnt;
+}
+
+__global__ void k_tridiag_lowest(const double* __restrict__ alpha,
+                                 const double* __restrict__ beta, int k,
+                                 double* __restrict__ out, double* __restrict__ y) {
+  __shared__ double a[64], b[64];
+  __shared__ double lo_s, hi_s;
+  const int l = threadIdx.x;
+  for (int i = l; i < k; i += 32) a[i] = alpha[i];
+  for (int i = l; i < k - 1; i += 32) b[i] = beta[i];
+  __syncwarp();
+  if (l == 0) {
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < k; ++i) {
+      double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+    lo_s = lo - pad;
+    hi_s = hi + pad;
+  }
+  __syncwarp();
+  double lo = lo_s, hi = hi_s;
+  for (int it = 0; it < 64; ++it) {
+    double width = hi - lo;
+    if (width <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) || width <= 1e-300)
+      break;
+    double x = lo + width * (double)(l + 1) / 33.0;
+    int cnt = sturm_count(a, b, k, x);
+    unsigned m = __ballot_sync(0xffffffffu, cnt >= 1);
+    // smallest lane whose point lies above the lowest eigenvalue
+    int first = m ? (__ffs(m) - 1) : 32;
+    double nlo = lo + width * (double)first / 33.0;
+    double nhi = lo + width * (double)(first + 1) / 33.0;
+    if (first == 32) nhi = hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (l == 0) {
+    const double lam = 0.5 * (lo + hi);
+    // inverse iteration on (T - lam I) y = y_prev with partial pivoting
+    double dl[64], dm[64], du[64], du2[64], v[64];
+    int piv[64];
+    for (int i = 0; i < k; ++i) v[i] = 1.0 / sqrt((double)k) * (1.0 + 0.01 * i);
+    const double eps = 2.220446049250313e-16;
+    double scale = 0;
+    for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(a[i]) + (i < k - 1 ? fabs(b[i]) : 0));
+    scale = fmax(scale, 1e-300);
+    for (int iter = 0; iter < 3; ++iter) {
+      for (int i = 0; i < k; ++i) {
+        dm[i] = a[i] - lam;
+        du[i] = (i < k - 1) ? b[i] : 0.0;
+        dl[i] = (i < k - 1) ? b[i] : 0.0;
+        du2[i] = 0.0;
+        piv[i] = i;
+      }
+      // LU with partial pivoting (tridiagonal, as in a textbook gtsv)
+      for (int i = 0; i < k - 1; ++i) {
+        if (fabs(dm[i]) >= fabs(dl[i])) {
+          if (fabs(dm[i]) < eps * scale) dm[i] = eps * scale;
+          double f = dl[i] / dm[i];
+          dl[i] = f;
+          dm[i + 1] -= f * du[i];
+          du2[i] = 0.0;
+          piv[i] = i;
+        } else {
+          double f = dm[i] / dl[i];
+          dm[i] = dl[i];
+          dl[i] = f;
+          double t = du[i];
+          du[i] = dm[i + 1];
+          dm[i + 1] = t - f * du[i];
+          if (i < k - 2) {
+            du2[i] = du[i + 1];
+            du[i + 1] = -f * du[i + 1];
+          }
+          piv[i] = i + 1;
+        }
+      }
+      if (fabs(dm[k - 1]) < eps * scale) dm[k - 1] = eps * scale;
+      // forward: apply row swaps and L
+      for (int i = 0; i < k - 1; ++i) {
+        if (piv[i] == i) {
+          v[i + 1] -= dl[i] * v[i];
+        } else {
+          double t = v[i];
+          v[i] = v[i + 1];
+          v[i + 1] = t - dl[i] * v[i];
+        }
+      }
+      // backward: U has diagonals dm, du, du2
+      v[k - 1] /= dm[k - 1];
+      if (k > 1) v[k - 2] = (v[k - 2] - du[k - 2] * v[k - 1]) / dm[k - 2];
+      for (int i = k - 3; i >= 0; --i)
+        v[i] = (v[i] - du[i] * v[i + 1] - du2[i] * v[i + 2]) / dm[i];
+      double nrm = 0;
+      for (int i = 0; i < k; ++i) nrm += v[i] * v[i];
+      nrm = sqrt(nrm);
+      for (int i = 0; i < k; ++i) v[i] /= nrm;
+    }
+    // fix the sign so that the first nonzero component is positive (deterministic)
+    double sgn = 1.0;
+    for (int i = 0; i < k; ++i)
+      if (v[i] != 0.0) {
+        sgn = v[i] > 0 ? 1.0 : -1.0;
+        break;
+      }
+    for (int i = 0; i < k; ++i) y[i] = sgn * v[i];
+    out[0] = lam;
+    out[1] = fabs(v[k - 1]);
+  }
+}
+}  // namespace
+
+int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, double* d_out,
+                   double* d_y) {
+  if (k < 1 || k > 64) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal size %d", k);
+  k_tridiag_lowest<<<1, 32, 0, c->stream>>>(d_alpha, d_beta, k, d_out, d_y);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+// ============================================================ gather / fill / scale
+namespace {
+__global__ void k_gather2d(const z* __restrict__ src, int64_t src_ld,
+                           const int64_t* __restrict__ rows, int64_t nr,
+                           const int64_t* __restrict__ cols, int64_t nc, z* __restrict__ dst,
+                           int64_t dst_ld, int conj_t) {
+  const int64_t total = nr * nc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / nc, j = e % nc;
+    z v = src[rows[i] * src_ld + cols[j]];
+    if (conj_t) {
+      v.y = -v.y;
+      dst[j * dst_ld + i] = v;
+    } else {
+      dst[i * dst_ld + j] = v;
+    }
+  }
+}
+
+__global__ void k_zfill(z* p, int64_t n, z v) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
+// mode 0: p *= s[0]; mode 1: p *= 1/sqrt(s[0])
+__global__ void k_zscale(z* p, int64_t n, const double* s, int mode) {
+  double f = (mode == 0) ? s[0] : 1.0 / sqrt(s[0]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = zscale(p[e], f);
+}
+
+unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+}  // namespace
+
+int gather2d(Ctx* c, const z* src, int64_t src_ld, const int64_t* d_rows, int64_t nr,
+             const int64_t* d_cols, int64_t nc, z* dst, int64_t dst_ld, int conj_t) {
+  if (nr <= 0 || nc <= 0) return TNT_OK;
+  k_gather2d<<<grid_for(nr * nc), 256, 0, c->stream>>>(src, src_ld, d_rows, nr, d_cols, nc,
+                                                        dst, dst_ld, conj_t);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int zfill(Ctx* c, z* p, int64_t n, z v) {
+  if (n <= 0) return TNT_OK;
+  k_zfill<<<grid_for(n), 256, 0, c->stream>>>(p, n, v);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int zscale_inplace(Ctx* c, z* p, int64_t n, const double* d_scale, int mode) {
+  if (n <= 0) return TNT_OK;
+  k_zscale<<<grid_for(n), 256, 0, c->stream>>>(p, n, d_scale, mode);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+}  // namespace tnt

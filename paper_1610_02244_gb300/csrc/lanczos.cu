@@ -1,0 +1,181 @@
+// Lanczos ground-state eigensolver for H_eff (the external sparse eigensolver the library
+// calls with the contractor of Listing 1 as its matvec; Sec. 4.3, iteration cap 300 of
+// App. A.3).  Vectors, reductions and the tridiagonal eigenproblem stay in FP64 on the
+// GPU; only the matvec may run in split TF32.  Per Krylov step k:
+//   w = H v_k;  c = V^H w;  alpha_k = Re c_k;  w -= V c;  c = V^H w;  w -= V c  (CGS twice)
+//   beta_k = |w|;  (E_k, y) = lowest eigenpair of T_k;  resid = beta_k |y_k|
+//   stop if |E_k - E_{k-1}| <= tol |E_k| and resid <= max(tol, 10 u)|E_k|, u the matvec's
+//   unit roundoff (2^-52 FP64, 2^-22 split TF32), or if beta_k vanishes
+//   v_{k+1} = w / beta_k;  restart from the Ritz vector after krylov_cap steps.
+// (The three-term subtraction alpha v_k + beta v_{k-1} is contained in the first
+// Gram-Schmidt pass, whose coefficient on v_k is alpha_k.)
+#include <cmath>
+
+#include "heff_plan.cuh"
+
+namespace tnt {
+
+namespace {
+// alpha[k] = Re dots[k]; beta[k] = sqrt(norm2)
+__global__ void k_lz_scalars(const z* dots, int k, const double* norm2, double* alpha,
+                             double* beta) {
+  if (threadIdx.x == 0) {
+    alpha[k] = dots[k].x;
+    beta[k] = sqrt(norm2[0]);
+  }
+}
+
+// coef[i] = -y[i] (so that multiaxpy on a zero vector builds sum_i y_i V_i)
+__global__ void k_lz_ritz_coef(const double* y, int k, z* coef) {
+  int i = threadIdx.x;
+  if (i < k) coef[i] = zmk(-y[i], 0.0);
+}
+
+// out = a - e b (elementwise), partial |.|^2 in norm-ready form
+__global__ void k_resid(const z* __restrict__ Hx, const z* __restrict__ x, const double* E,
+                        z* __restrict__ r, int64_t n) {
+  const double e = E[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = zsub(Hx[i], zscale(x[i], e));
+}
+__global__ void k_copy_re(const z* src, double* dst) {
+  if (threadIdx.x == 0) dst[0] = src[0].x;
+}
+}  // namespace
+
+size_t lanczos_scratch_bound(int64_t n, int krylov_cap) {
+  return ws_round(sizeof(z) * (size_t)n * krylov_cap) + 2 * ws_round(sizeof(z) * (size_t)n) +
+         (size_t)(2 << 20);
+}
+
+static int lanczos_cycle_loop(Ctx* c, const HeffPlan& p, z* theta, int precision,
+                              int max_matvec, tnt_lanczos_result* res, z* V, z* w,
+                              double* dsc) {
+  const tnt_params& P = c->params;
+  const int64_t n = p.chl * p.d * p.d * p.chr;
+  const int cap = P.krylov_cap;
+  z* dots = (z*)dsc;                  // 64 complex
+  double* norm2 = dsc + 128;          // 1
+  double* alpha = dsc + 136;          // 64
+  double* beta = dsc + 200;           // 64
+  double* tri = dsc + 264;            // 2
+  double* y = dsc + 272;              // 64
+  z* coef = (z*)(dsc + 336);          // 64 complex
+  const double u = (precision == TNT_PREC_MIXED) ? std::ldexp(1.0, -22) : std::ldexp(1.0, -52);
+  const double tol = P.lanczos_tol;
+  const double rtol = std::max(tol, 10.0 * u);
+  double* hp = c->h_pinned;
+  // v_0 = theta / |theta|
+  TNT_TRY(vec_norm2(c, theta, n, norm2));
+  TNT_TRY(vec_normalize(c, theta, V, n, norm2));
+  int total = 0;
+  bool have_prev = false;
+  double E_prev = 0;
+  for (;;) {
+    int kk = 0;
+    double E = 0, resid = 0;
+    bool stop = false, conv = false;
+    for (int k = 0; k < cap; ++k) {
+      z* vk = V + (int64_t)k * n;
+      TNT_TRY(heff_run(c, p, vk, w, precision));
+      ++total;
+      TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, dots));
+      TNT_TRY(vec_multiaxpy_norm(c, V, n, k + 1, dots, w, n, norm2));
+      k_lz_scalars<<<1, 32, 0, c->stream>>>(dots, k, norm2, alpha, beta);  // alpha_k from pass 1
+      c->launches++;
+      TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, coef));
+      TNT_TRY(vec_multiaxpy_norm(c, V, n, k + 1, coef, w, n, norm2));
+      // beta_k from pass 2 (overwrite), then the tridiagonal eigenpair of T_k
+      k_lz_scalars<<<1, 32, 0, c->stream>>>(dots, k, norm2, alpha, beta);
+      c->launches++;
+      TNT_TRY(tridiag_lowest(c, alpha, beta, k + 1, tri, y));
+      TNT_CUDA_TRY(c, cudaMemcpyAsync(hp, tri, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TNT_CUDA_TRY(c, cudaMemcpyAsync(hp + 2, beta + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      E = hp[0];
+      const double bk = hp[2];
+      resid = bk * hp[1];
+      kk = k + 1;
+      if (have_prev && std::fabs(E - E_prev) <= tol * std::fabs(E) && resid <= rtol * std::fabs(E))
+        conv = true;
+      if (bk <= rtol * std::fabs(E) * 1e-3 || bk == 0.0) conv = true;
+      if (!std::isfinite(E) || !std::isfinite(bk))
+        return set_err(c, TNT_E_NAN, "Lanczos produced a non-finite value at step %d", total);
+      have_prev = true;
+      E_prev = E;
+      if (conv || total >= max_matvec) {
+        stop = true;
+        break;
+      }
+      TNT_TRY(vec_normalize(c, w, V + (int64_t)(k + 1) * n, n, norm2));
+    }
+    // Ritz vector x = sum_i y_i v_i  (built in w, normalised)
+    k_lz_ritz_coef<<<1, 64, 0, c->stream>>>(y, kk, coef);
+    c->launches++;
+    TNT_TRY(zfill(c, w, n, zmk(0, 0)));
+    TNT_TRY(vec_multiaxpy_norm(c, V, n, kk, coef, w, n, norm2));
+    if (stop) {
+      TNT_TRY(vec_normalize(c, w, theta, n, norm2));
+      res->E = E;
+      res->resid = resid;
+      res->n_matvec += total;
+      res->converged = conv ? 1 : 0;
+      return TNT_OK;
+    }
+    TNT_TRY(vec_normalize(c, w, V, n, norm2));  // restart
+  }
+}
+
+int lanczos_impl(Ctx* c, const HeffPlan& p, z* theta, tnt_lanczos_result* res) {
+  const tnt_params& P = c->params;
+  const int64_t n = p.chl * p.d * p.d * p.chr;
+  const int cap = P.krylov_cap;
+  if (cap < 2 || cap > 64) return set_err(c, TNT_E_INVALID, "krylov_cap %d outside [2, 64]", cap);
+  TNT_TRY(pinned_reserve(c, 64 * sizeof(double)));
+  z* V = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)n * cap));
+  z* w = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)n));
+  z* w2 = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)n));
+  double* dsc = (double*)ws_alloc(c, ws_round(sizeof(double) * 512));
+  if (!V || !w || !w2 || !dsc) return set_err(c, TNT_E_ALLOC, "scratch exhausted (Lanczos)");
+  *res = tnt_lanczos_result{};
+  const int prec = P.precision;
+  TNT_TRY(lanczos_cycle_loop(c, p, theta, prec, P.lanczos_maxit, res, V, w, dsc));
+  if (prec == TNT_PREC_MIXED) {
+    // accuracy win-back: one FP64 matvec for the Rayleigh quotient and the true residual
+    double* hp = c->h_pinned;
+    z* dot = (z*)dsc;
+    double* norm2 = dsc + 128;
+    double* Erq = dsc + 130;
+    TNT_TRY(heff_run_f64(c, p, theta, w));
+    res->n_matvec += 1;
+    TNT_TRY(vec_dot(c, theta, w, n, dot));
+    k_copy_re<<<1, 32, 0, c->stream>>>(dot, Erq);
+    k_resid<<<1216, 256, 0, c->stream>>>(w, theta, Erq, w2, n);
+    c->launches += 2;
+    TNT_TRY(vec_norm2(c, w2, n, norm2));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(hp, Erq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(hp + 1, norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    res->E_rq = hp[0];
+    res->resid_fp64 = std::sqrt(hp[1]);
+    if (res->resid_fp64 > 1e-5 * std::fabs(res->E_rq) && res->n_matvec < P.lanczos_maxit) {
+      // not accurate enough for the FP64 energy: continue in FP64 from this vector
+      tnt_lanczos_result r2{};
+      TNT_TRY(lanczos_cycle_loop(c, p, theta, TNT_PREC_FP64, P.lanczos_maxit - res->n_matvec,
+                                 &r2, V, w, dsc));
+      res->n_matvec += r2.n_matvec;
+      res->E = r2.E;
+      res->E_rq = r2.E;
+      res->resid = r2.resid;
+      res->resid_fp64 = r2.resid;
+      res->converged = r2.converged;
+    }
+  } else {
+    res->E_rq = res->E;
+    res->resid_fp64 = res->resid;
+  }
+  return res->converged ? TNT_OK : TNT_E_NOCONV;
+}
+
+}  // namespace tnt

@@ -1,0 +1,777 @@
+// Truncated SVD of the reshaped two-site tensor (App. B.1.2, Eq. 3), FP64, on the GPU.
+//
+// M is block diagonal under U(1) labels (App. A.1.1).  Per block q (rows R_q, columns C_q):
+//   LEFT  side: G = M_q M_q^H, Jacobi eigenvectors U_q (orthonormal), X_q = U_q^H M_q,
+//               sigma_k = |row k of X_q|              (so X = S V^H without dividing by S)
+//   RIGHT side: G = M_q^H M_q, eigenvectors V_q,      Y_q = M_q V_q,
+//               sigma_k = |column k of Y_q|           (so Y = U S)
+// Only the r_q = min(m_q, n_q) leading eigenvectors are candidates (rank bound).  Taking
+// sigma as a projection norm keeps its absolute error at ~eps |M| instead of the
+// sqrt(eps) relative floor of sqrt(lambda).  All candidates are then ordered globally
+// (sigma desc, charge asc, index asc) and cut by the four rules in one kernel.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "tnt_internal.cuh"
+
+namespace tnt {
+
+namespace {
+constexpr double kEps = 2.220446049250313e-16;
+
+// -------------------------------------------------------------- Jacobi, small blocks
+// One CTA per block (n <= 64), G and V in shared memory, round-robin parallel ordering.
+__device__ __forceinline__ void rr_pair(int t, int r, int np2, int* p, int* q) {
+  // positions 0..np2-1 (np2 even); position 0 fixed, the others rotate by r
+  auto pos = [&](int i) { return i == 0 ? 0 : 1 + ((i - 1 + r) % (np2 - 1)); };
+  int a = pos(t), b = pos(np2 - 1 - t);
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+__device__ __forceinline__ void jacobi_rot(double app, double aqq, z apq, double* cs,
+                                           double* sn, z* e) {
+  double ab = hypot(apq.x, apq.y);
+  if (ab <= 1e-300 || ab < 1e-18 * sqrt(fabs(app) * fabs(aqq))) {
+    *cs = 1.0;
+    *sn = 0.0;
+    *e = zmk(1.0, 0.0);
+    return;
+  }
+  *e = zmk(apq.x / ab, apq.y / ab);
+  double tau = (aqq - app) / (2.0 * ab);
+  double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  *cs = 1.0 / sqrt(1.0 + t * t);
+  *sn = t * (*cs);
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t* off,
+                                                      const int* dims, int max_sweeps,
+                                                      double tol, int* sweeps_out) {
+  extern __shared__ double smem_d[];
+  const int n = dims[blockIdx.x];
+  if (n <= 0) return;
+  const int64_t o = off[blockIdx.x];
+  z* sG = (z*)smem_d;
+  z* sV = sG + n * n;
+  double* s_cs = (double*)(sV + n * n);
+  double* s_sn = s_cs + 32;
+  z* s_e = (z*)(s_sn + 32);
+  int* s_pq = (int*)(s_e + 32);
+  __shared__ double red_off[256], red_dg[256];
+  __shared__ int s_done;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    sG[e] = G[o + e];
+    sV[e] = (e / n == e % n) ? zmk(1, 0) : zmk(0, 0);
+  }
+  __syncthreads();
+  const int np2 = (n + 1) & ~1;
+  const int npairs = np2 / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    // convergence test before each sweep
+    double mo = 0, md = 0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, j = e % n;
+      double a = hypot(sG[e].x, sG[e].y);
+      if (i == j) md = fmax(md, a); else mo = fmax(mo, a);
+    }
+    red_off[threadIdx.x] = mo;
+    red_dg[threadIdx.x] = md;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0, b = 0;
+      for (int t = 0; t < (int)blockDim.x; ++t) {
+        a = fmax(a, red_off[t]);
+        b = fmax(b, red_dg[t]);
+      }
+      s_done = (a <= tol * b) || (a <= 1e-300);
+    }
+    __syncthreads();
+    if (s_done) break;
+    for (int r = 0; r < np2 - 1; ++r) {
+      if (threadIdx.x < npairs) {
+        int p, q;
+        rr_pair(threadIdx.x, r, np2, &p, &q);
+        double cs = 1, sn = 0;
+        z e = zmk(1, 0);
+        if (q < n) jacobi_rot(sG[p * n + p].x, sG[q * n + q].x, sG[p * n + q], &cs, &sn, &e);
+        s_cs[threadIdx.x] = cs;
+        s_sn[threadIdx.x] = sn;
+        s_e[threadIdx.x] = e;
+        s_pq[2 * threadIdx.x] = p;
+        s_pq[2 * threadIdx.x + 1] = q;
+      }
+      __syncthreads();
+      // rows: G <- J^H G
+      for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
+        int t = e / n, j = e % n;
+        int p = s_pq[2 * t], q = s_pq[2 * t + 1];
+        if (q >= n || s_sn[t] == 0.0) continue;
+        double cs = s_cs[t], sn = s_sn[t];
+        z ep = s_e[t];
+        z gp = sG[p * n + j], gq = sG[q * n + j];
+        z eq = zmul(ep, gq);
+        sG[p * n + j] = zsub(zscale(gp, cs), zscale(eq, sn));
+        sG[q * n + j] = zadd(zscale(gp, sn), zscale(eq, cs));
+      }
+      __syncthreads();
+      // columns: G <- G J, V <- V J
+      for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
+        int t = e / n, i = e % n;
+        int p = s_pq[2 * t], q = s_pq[2 * t + 1];
+        if (q >= n || s_sn[t] == 0.0) continue;
+        double cs = s_cs[t], sn = s_sn[t];
+        z ec = zconj(s_e[t]);
+        z gp = sG[i * n + p], gq = zmul(sG[i * n + q], ec);
+        sG[i * n + p] = zsub(zscale(gp, cs), zscale(gq, sn));
+        sG[i * n + q] = zadd(zscale(gp, sn), zscale(gq, cs));
+        z vp = sV[i * n + p], vq = zmul(sV[i * n + q], ec);
+        sV[i * n + p] = zsub(zscale(vp, cs), zscale(vq, sn));
+        sV[i * n + q] = zadd(zscale(vp, sn), zscale(vq, cs));
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenpairs by eigenvalue, descending (stable on index); write back
+  __shared__ int perm[64];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = 1; i < n; ++i) {
+      int v = perm[i];
+      double key = sG[v * n + v].x;
+      int j = i - 1;
+      while (j >= 0 && sG[perm[j] * n + perm[j]].x < key) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = v;
+    }
+    if (sweeps_out) sweeps_out[blockIdx.x] = sweep;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, k = e % n;
+    V[o + e] = sV[i * n + perm[k]];
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) G[o + k] = zmk(sG[perm[k] * n + perm[k]].x, 0);
+}
+
+// -------------------------------------------------------------- Jacobi, one large block
+struct Rot {
+  double cs, sn;
+  z e;
+  int p, q;
+};
+
+__global__ void k_jrot(const z* __restrict__ G, int64_t n, int np2, int r, Rot* __restrict__ rot) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np2 / 2) return;
+  int p, q;
+  rr_pair(t, r, np2, &p, &q);
+  Rot o;
+  o.p = p;
+  o.q = q;
+  o.cs = 1;
+  o.sn = 0;
+  o.e = zmk(1, 0);
+  if (q < n) jacobi_rot(G[(int64_t)p * n + p].x, G[(int64_t)q * n + q].x, G[(int64_t)p * n + q],
+                        &o.cs, &o.sn, &o.e);
+  rot[t] = o;
+}
+
+// G <- J^H G: thread per (pair, column j), coalesced along j
+__global__ void k_jrows(z* __restrict__ G, int64_t n, int npairs, const Rot* __restrict__ rot) {
+  int t = blockIdx.y;
+  Rot o = rot[t];
+  if (o.q >= n || o.sn == 0.0) return;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    z gp = G[(int64_t)o.p * n + j], gq = zmul(o.e, G[(int64_t)o.q * n + j]);
+    G[(int64_t)o.p * n + j] = zsub(zscale(gp, o.cs), zscale(gq, o.sn));
+    G[(int64_t)o.q * n + j] = zadd(zscale(gp, o.sn), zscale(gq, o.cs));
+  }
+}
+
+// G <- G J and V <- V J: thread per (row i, pair)
+__global__ void k_jcols(z* __restrict__ G, z* __restrict__ V, int64_t n, int npairs,
+                        const Rot* __restrict__ rot) {
+  int64_t total = n * npairs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / npairs;
+    int t = (int)(e % npairs);
+    Rot o = rot[t];
+    if (o.q >= n || o.sn == 0.0) continue;
+    z ec = zconj(o.e);
+    z gp = G[i * n + o.p], gq = zmul(G[i * n + o.q], ec);
+    G[i * n + o.p] = zsub(zscale(gp, o.cs), zscale(gq, o.sn));
+    G[i * n + o.q] = zadd(zscale(gp, o.sn), zscale(gq, o.cs));
+    z vp = V[i * n + o.p], vq = zmul(V[i * n + o.q], ec);
+    V[i * n + o.p] = zsub(zscale(vp, o.cs), zscale(vq, o.sn));
+    V[i * n + o.q] = zadd(zscale(vp, o.sn), zscale(vq, o.cs));
+  }
+}
+
+__global__ void k_eye(z* V, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = (e / n == e % n) ? zmk(1, 0) : zmk(0, 0);
+}
+
+// partial max of off-diagonal and diagonal magnitudes
+__global__ void k_offmax(const z* __restrict__ G, int64_t n, double* __restrict__ part) {
+  __shared__ double so[256], sd[256];
+  double mo = 0, md = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double a = hypot(G[e].x, G[e].y);
+    if (e / n == e % n) md = fmax(md, a); else mo = fmax(mo, a);
+  }
+  so[threadIdx.x] = mo;
+  sd[threadIdx.x] = md;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      so[threadIdx.x] = fmax(so[threadIdx.x], so[threadIdx.x + s]);
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = so[0];
+    part[2 * blockIdx.x + 1] = sd[0];
+  }
+}
+
+// sort the eigenvalues of one large block (diag of G) descending -> perm; one CTA,
+// bitonic over a power of two <= 8192 (dynamic smem)
+__global__ void __launch_bounds__(1024) k_eig_sort(const z* __restrict__ G, int64_t n, int P,
+                                                   int* __restrict__ perm,
+                                                   double* __restrict__ vals) {
+  extern __shared__ double sm_sort[];
+  double* key = sm_sort;
+  int* idx = (int*)(key + P);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    key[i] = (i < n) ? G[(int64_t)i * n + i].x : -INFINITY;
+    idx[i] = i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool desc_block = ((i & k) == 0);
+          // "before" = larger key, then smaller index
+          bool i_before = (key[i] > key[l]) || (key[i] == key[l] && idx[i] < idx[l]);
+          bool swap = desc_block ? !i_before : i_before;
+          if (swap) {
+            double tk = key[i];
+            key[i] = key[l];
+            key[l] = tk;
+            int ti = idx[i];
+            idx[i] = idx[l];
+            idx[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    perm[i] = idx[i];
+    vals[i] = key[i];
+  }
+}
+
+// dst[i][k] = src[i][perm[k]] for k < r (column permutation/truncation), ld n
+__global__ void k_permute_cols(const z* __restrict__ src, int64_t n, const int* __restrict__ perm,
+                               int64_t r, z* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / r, k = e % r;
+    dst[i * n + k] = src[i * n + perm[k]];
+  }
+}
+
+// sigma of each candidate: norm of row (LEFT: rows of X_q) or column (RIGHT: of Y_q)
+struct CandBlock {
+  int64_t xoff;   // packed X_q / Y_q offset
+  int64_t rows, cols;
+  int r;          // candidates
+  int vbase;      // first index in the global value list
+  int by_row;     // 1: sigma_k = |row k|, 0: |column k|
+};
+
+__global__ void k_cand_sigma(const z* __restrict__ X, const CandBlock* __restrict__ cb,
+                             double* __restrict__ sig) {
+  const CandBlock b = cb[blockIdx.x];
+  __shared__ double sh[256];
+  for (int k = 0; k < b.r; ++k) {
+    double acc = 0;
+    if (b.by_row) {
+      for (int64_t c = threadIdx.x; c < b.cols; c += blockDim.x) {
+        z v = X[b.xoff + (int64_t)k * b.cols + c];
+        acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+      }
+    } else {
+      for (int64_t i = threadIdx.x; i < b.rows; i += blockDim.x) {
+        z v = X[b.xoff + i * b.cols + k];
+        acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+      }
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sig[b.vbase + k] = sqrt(sh[0]);
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------- global selection
+struct SelOut {
+  int64_t chi;
+  double err, disc, norm2;
+  int tie;
+};
+
+__global__ void __launch_bounds__(1024) k_select(const double* __restrict__ sig_in,
+                                                 const int* __restrict__ blk_in,
+                                                 const int* __restrict__ loc_in, int n, int P,
+                                                 int64_t chi_max, double a, double rtol,
+                                                 double etol, int etype,
+                                                 double* __restrict__ sig_out,
+                                                 int* __restrict__ blk_out,
+                                                 int* __restrict__ loc_out,
+                                                 SelOut* __restrict__ res) {
+  extern __shared__ double sm_sel[];
+  double* key = sm_sel;
+  int* bk = (int*)(key + P);
+  int* lc = bk + P;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    key[i] = (i < n) ? sig_in[i] : -1.0;
+    bk[i] = (i < n) ? blk_in[i] : 0x7fffffff;
+    lc[i] = (i < n) ? loc_in[i] : 0x7fffffff;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool desc_block = ((i & k) == 0);
+          bool i_before = (key[i] > key[l]) ||
+                          (key[i] == key[l] && (bk[i] < bk[l] || (bk[i] == bk[l] && lc[i] < lc[l])));
+          bool swap = desc_block ? !i_before : i_before;
+          if (swap) {
+            double tk = key[i]; key[i] = key[l]; key[l] = tk;
+            int tb = bk[i]; bk[i] = bk[l]; bk[l] = tb;
+            int tl = lc[i]; lc[i] = lc[l]; lc[l] = tl;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sig_out[i] = key[i];
+    blk_out[i] = bk[i];
+    loc_out[i] = lc[i];
+  }
+  if (threadIdx.x == 0) {
+    const double s0 = n > 0 ? key[0] : 0.0;
+    int64_t chi1 = n < chi_max ? n : chi_max;
+    int64_t chi2 = n;
+    if (a > 0) {
+      chi2 = 0;
+      while (chi2 < n && key[chi2] >= a) ++chi2;
+    }
+    int64_t chi3 = n;
+    if (s0 > 0) {
+      chi3 = 0;
+      while (chi3 < n && key[chi3] / s0 >= rtol) ++chi3;
+    }
+    double nrm2 = 0;
+    for (int i = n - 1; i >= 0; --i) nrm2 += key[i] * key[i];
+    const double nrm = sqrt(nrm2);
+    const double inv = nrm > 0 ? 1.0 / nrm : 1.0;
+    auto term = [&](double s) {
+      double t = s * inv;
+      return etype == TNT_TRUNC_1NORM ? fabs(t) : t * t;
+    };
+    auto errf = [&](double acc) { return etype == TNT_TRUNC_2NORM ? sqrt(acc) : acc; };
+    int64_t chi4 = n;
+    double acc = 0;
+    for (int keep = n - 1; keep >= 0; --keep) {
+      acc += term(key[keep]);
+      if (errf(acc) < etol) chi4 = keep; else break;
+    }
+    int64_t chi = chi1;
+    if (chi2 < chi) chi = chi2;
+    if (chi3 < chi) chi = chi3;
+    if (chi4 < chi) chi = chi4;
+    if (chi < 1) chi = 1;
+    if (chi > n) chi = n;
+    double e = 0, dsc = 0;
+    for (int i = n - 1; i >= chi; --i) {
+      e += term(key[i]);
+      dsc += key[i] * key[i];
+    }
+    res->chi = chi;
+    res->err = errf(e);
+    res->disc = dsc;
+    res->norm2 = nrm2;
+    res->tie = (chi < n) && (key[chi - 1] - key[chi] < 1e-10 * s0);
+  }
+}
+
+// -------------------------------------------------------------- output scatter
+// One bond index k per blockIdx.y.  LEFT: U[rows[r]][k] = Vq[r][loc] (r < m_q), and
+// X[k][cols[c]] = scale * Xq[loc][c].  RIGHT: X[k][cols[c]] = conj(Vq[c][loc]) and
+// U[rows[r]][k] = scale * Yq[r][loc].
+struct KeptIdx {
+  int64_t voff, vld;     // eigenvector block (ld = Gram dim)
+  int64_t xoff, xld;     // X_q (LEFT: r x n_q, ld n_q) or Y_q (RIGHT: m_q x r, ld r)
+  int64_t roff, nr;      // rows list slice
+  int64_t coff, nc;      // cols list slice
+  int loc;
+};
+
+__global__ void k_scatter(const z* __restrict__ Vp, const z* __restrict__ Xp,
+                          const KeptIdx* __restrict__ kept, const int64_t* __restrict__ rows,
+                          const int64_t* __restrict__ cols, int side, double scale, int64_t chi,
+                          int64_t n_total, z* __restrict__ U, z* __restrict__ X) {
+  const int64_t k = blockIdx.y;
+  const KeptIdx kd = kept[k];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < kd.nr;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    z v;
+    if (side == TNT_SVD_LEFT) v = Vp[kd.voff + r * kd.vld + kd.loc];
+    else v = zscale(Xp[kd.xoff + r * kd.xld + kd.loc], scale);
+    U[rows[kd.roff + r] * chi + k] = v;
+  }
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < kd.nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    z v;
+    if (side == TNT_SVD_LEFT) v = zscale(Xp[kd.xoff + (int64_t)kd.loc * kd.xld + c], scale);
+    else v = zconj(Vp[kd.voff + c * kd.vld + kd.loc]);
+    X[k * n_total + cols[kd.coff + c]] = v;
+  }
+}
+
+unsigned gridn(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+}  // namespace
+
+// ==================================================================== Jacobi drivers
+int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_n,
+                         int nblocks, int max_n) {
+  if (nblocks <= 0) return TNT_OK;
+  if (max_n > 64) return set_err(c, TNT_E_INVALID, "small Jacobi block %d > 64", max_n);
+  size_t smem = (size_t)2 * max_n * max_n * sizeof(z) + 32 * (2 * sizeof(double) + sizeof(z) +
+                                                              2 * sizeof(int));
+  TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+  k_jacobi_small<<<nblocks, 256, smem, c->stream>>>(G, V, d_off, d_n, 40, 1e-15, nullptr);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int jacobi_large(Ctx* c, z* G, z* V, int64_t n, int max_sweeps, int* sweeps_done) {
+  const int np2 = (int)((n + 1) & ~int64_t(1));
+  const int npairs = np2 / 2;
+  Rot* rot = (Rot*)ws_alloc(c, ws_round(sizeof(Rot) * npairs));
+  const int nb_off = 64;
+  double* part = (double*)ws_alloc(c, ws_round(sizeof(double) * 2 * nb_off));
+  if (!rot || !part) return set_err(c, TNT_E_ALLOC, "scratch exhausted (jacobi_large)");
+  TNT_TRY(pinned_reserve(c, sizeof(double) * 2 * nb_off));
+  k_eye<<<gridn(n * n), 256, 0, c->stream>>>(V, n);
+  c->launches++;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    k_offmax<<<nb_off, 256, 0, c->stream>>>(G, n, part);
+    c->launches++;
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, part, sizeof(double) * 2 * nb_off,
+                                    cudaMemcpyDeviceToHost, c->stream));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    double mo = 0, md = 0;
+    for (int b = 0; b < nb_off; ++b) {
+      mo = std::max(mo, c->h_pinned[2 * b]);
+      md = std::max(md, c->h_pinned[2 * b + 1]);
+    }
+    if (mo <= 1e-15 * md || mo <= 1e-300) break;
+    for (int r = 0; r < np2 - 1; ++r) {
+      k_jrot<<<(npairs + 127) / 128, 128, 0, c->stream>>>(G, n, np2, r, rot);
+      dim3 gr((unsigned)std::min<int64_t>((n + 255) / 256, 8), (unsigned)npairs);
+      k_jrows<<<gr, 256, 0, c->stream>>>(G, n, npairs, rot);
+      k_jcols<<<gridn(n * npairs), 256, 0, c->stream>>>(G, V, n, npairs, rot);
+      c->launches += 3;
+    }
+    TNT_CHECK_LAUNCH(c);
+  }
+  if (sweeps_done) *sweeps_done = sweep;
+  return TNT_OK;
+}
+
+// ==================================================================== truncated SVD
+size_t svd_scratch_bound(int64_t m, int64_t n) {
+  const size_t mx = (size_t)std::max(m, n), mn = (size_t)std::min(m, n);
+  return 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 3 * 16 * mx * mx + 6 * 8 * mn +
+         sizeof(KeptIdx) * mn + 12 * 8192 + (size_t)(4 << 20);
+}
+
+int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq,
+                   const int64_t* h_cq, int side, int renorm, z* U, z* X, double* h_S,
+                   int64_t* h_bq, tnt_trunc_result* res) {
+  const tnt_params& P = c->params;
+  // ---- block structure (host, integer only)
+  std::map<int64_t, std::pair<std::vector<int64_t>, std::vector<int64_t>>> blocks;
+  for (int64_t i = 0; i < m; ++i) blocks[h_rq ? h_rq[i] : 0].first.push_back(i);
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t q = h_cq ? h_cq[j] : 0;
+    auto it = blocks.find(q);
+    if (it != blocks.end()) it->second.second.push_back(j);
+  }
+  struct Blk {
+    int64_t q, mq, nq, g, r;
+    int64_t roff, coff, moff, goff, xoff;
+  };
+  std::vector<Blk> bl;
+  std::vector<int64_t> rows_all, cols_all;
+  int64_t mtot = 0, gtot = 0, xtot = 0, ntot_vals = 0;
+  for (auto& kv : blocks) {
+    const auto& R = kv.second.first;
+    const auto& Cc = kv.second.second;
+    if (R.empty() || Cc.empty()) continue;
+    Blk b;
+    b.q = kv.first;
+    b.mq = (int64_t)R.size();
+    b.nq = (int64_t)Cc.size();
+    b.g = (side == TNT_SVD_LEFT) ? b.mq : b.nq;
+    b.r = std::min(b.mq, b.nq);
+    b.roff = (int64_t)rows_all.size();
+    b.coff = (int64_t)cols_all.size();
+    rows_all.insert(rows_all.end(), R.begin(), R.end());
+    cols_all.insert(cols_all.end(), Cc.begin(), Cc.end());
+    b.moff = mtot;
+    mtot += b.mq * b.nq;
+    b.goff = gtot;
+    gtot += b.g * b.g;
+    b.xoff = xtot;
+    xtot += (side == TNT_SVD_LEFT) ? b.r * b.nq : b.mq * b.r;
+    ntot_vals += b.r;
+    bl.push_back(b);
+  }
+  const int nb = (int)bl.size();
+  if (nb == 0 || ntot_vals == 0) return set_err(c, TNT_E_INVALID, "SVD: no charge block has both rows and columns");
+  if (ntot_vals > 8192) return set_err(c, TNT_E_UNSUPPORTED, "SVD: %lld candidate values > 8192", (long long)ntot_vals);
+
+  // ---- scratch
+  int P2 = 1;
+  while (P2 < ntot_vals) P2 <<= 1;
+  int64_t gmax_large = 0;
+  for (const Blk& B : bl)
+    if (B.g > 64) gmax_large = std::max(gmax_large, B.g);
+  TNT_TRY(ws_reserve(c, c->ws.top + svd_scratch_bound(m, n)));
+  z* Vt = gmax_large ? (z*)ws_alloc(c, ws_round(sizeof(z) * gmax_large * gmax_large)) : nullptr;
+  if (gmax_large && !Vt) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd Vt)");
+  int64_t* d_rows = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * rows_all.size()));
+  int64_t* d_cols = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * cols_all.size()));
+  z* Mp = (z*)ws_alloc(c, ws_round(sizeof(z) * mtot));
+  z* Gp = (z*)ws_alloc(c, ws_round(sizeof(z) * gtot));
+  z* Vp = (z*)ws_alloc(c, ws_round(sizeof(z) * gtot));
+  z* Xp = (z*)ws_alloc(c, ws_round(sizeof(z) * xtot));
+  double* d_sig = (double*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  int* d_blk = (int*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  int* d_loc = (int*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  double* d_sig_s = (double*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  int* d_blk_s = (int*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  int* d_loc_s = (int*)ws_alloc(c, ws_round(sizeof(double) * ntot_vals));
+  SelOut* d_sel = (SelOut*)ws_alloc(c, ws_round(sizeof(SelOut)));
+  CandBlock* d_cb = (CandBlock*)ws_alloc(c, ws_round(sizeof(CandBlock) * nb));
+  int64_t* d_goff = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
+  int* d_gdim = (int*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
+  int* d_perm = (int*)ws_alloc(c, ws_round(sizeof(int) * 8192));
+  double* d_pvals = (double*)ws_alloc(c, ws_round(sizeof(double) * 8192));
+  if (!d_rows || !d_cols || !Mp || !Gp || !Vp || !Xp || !d_sig || !d_blk || !d_loc || !d_sig_s ||
+      !d_blk_s || !d_loc_s || !d_sel || !d_cb || !d_goff || !d_gdim || !d_perm || !d_pvals)
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
+
+  // ---- host tables -> device (one synchronous upload of small integer tables)
+  std::vector<CandBlock> hcb(nb);
+  std::vector<int64_t> hgoff(nb);
+  std::vector<int> hgdim(nb), hblk(ntot_vals), hloc(ntot_vals);
+  {
+    int v = 0;
+    for (int b = 0; b < nb; ++b) {
+      hcb[b].xoff = bl[b].xoff;
+      hcb[b].rows = (side == TNT_SVD_LEFT) ? bl[b].r : bl[b].mq;
+      hcb[b].cols = (side == TNT_SVD_LEFT) ? bl[b].nq : bl[b].r;
+      hcb[b].r = (int)bl[b].r;
+      hcb[b].vbase = v;
+      hcb[b].by_row = (side == TNT_SVD_LEFT);
+      hgoff[b] = bl[b].goff;
+      hgdim[b] = (int)bl[b].g;
+      for (int k = 0; k < bl[b].r; ++k, ++v) {
+        hblk[v] = b;
+        hloc[v] = k;
+      }
+    }
+  }
+  cudaStream_t st = c->stream;
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_rows, rows_all.data(), sizeof(int64_t) * rows_all.size(), cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_cols, cols_all.data(), sizeof(int64_t) * cols_all.size(), cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_cb, hcb.data(), sizeof(CandBlock) * nb, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_goff, hgoff.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_gdim, hgdim.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * ntot_vals, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_loc, hloc.data(), sizeof(int) * ntot_vals, cudaMemcpyHostToDevice, st));
+
+  // ---- gather blocks, Gram matrices
+  for (int b = 0; b < nb; ++b) {
+    const Blk& B = bl[b];
+    TNT_TRY(gather2d(c, M, n, d_rows + B.roff, B.mq, d_cols + B.coff, B.nq, Mp + B.moff, B.nq, 0));
+    ZGemm g{};
+    g.batch = 1;
+    g.alpha = zmk(1, 0);
+    g.beta = zmk(0, 0);
+    g.C = Gp + B.goff;
+    g.c_rs = B.g;
+    if (side == TNT_SVD_LEFT) {  // G = M M^H
+      g.M = B.mq; g.N = B.mq; g.K = B.nq;
+      g.A = Mp + B.moff; g.a_rs = B.nq; g.a_cs = 1;
+      g.B = Mp + B.moff; g.b_rs = 1; g.b_cs = B.nq; g.conj_b = 1;
+    } else {  // G = M^H M
+      g.M = B.nq; g.N = B.nq; g.K = B.mq;
+      g.A = Mp + B.moff; g.a_rs = 1; g.a_cs = B.nq; g.conj_a = 1;
+      g.B = Mp + B.moff; g.b_rs = B.nq; g.b_cs = 1;
+    }
+    TNT_TRY(zgemm(c, g));
+  }
+  // ---- eigensolves: small blocks batched in one launch, large ones one by one
+  {
+    int max_small = 0, n_small = 0;
+    for (int b = 0; b < nb; ++b)
+      if (bl[b].g <= 64) { max_small = std::max<int>(max_small, (int)bl[b].g); n_small++; }
+    if (n_small > 0) {
+      // blocks > 64 get dim 0 in this launch (skipped)
+      std::vector<int> dims_small(nb);
+      for (int b = 0; b < nb; ++b) dims_small[b] = bl[b].g <= 64 ? (int)bl[b].g : 0;
+      int* d_dims_small = (int*)ws_alloc(c, ws_round(sizeof(int) * nb));
+      if (!d_dims_small) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd dims)");
+      TNT_CUDA_TRY(c, cudaMemcpyAsync(d_dims_small, dims_small.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // host vector lifetime
+      TNT_TRY(jacobi_small_batched(c, Gp, Vp, d_goff, d_dims_small, nb, max_small));
+    }
+    for (int b = 0; b < nb; ++b) {
+      if (bl[b].g <= 64) continue;
+      const Blk& B = bl[b];
+      if (B.g > 8192) return set_err(c, TNT_E_UNSUPPORTED, "SVD block of dim %lld > 8192", (long long)B.g);
+      int sw = 0;
+      TNT_TRY(jacobi_large(c, Gp + B.goff, Vt, B.g, 40, &sw));
+      int P = 1;
+      while (P < B.g) P <<= 1;
+      size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
+      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_eig_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_eig_sort<<<1, 1024, smem, st>>>(Gp + B.goff, B.g, P, d_perm, d_pvals);
+      k_permute_cols<<<gridn(B.g * B.g), 256, 0, st>>>(Vt, B.g, d_perm, B.g, Vp + B.goff);
+      c->launches += 2;
+      TNT_CHECK_LAUNCH(c);
+    }
+  }
+  // ---- candidate products and their norms
+  for (int b = 0; b < nb; ++b) {
+    const Blk& B = bl[b];
+    ZGemm g{};
+    g.batch = 1;
+    g.alpha = zmk(1, 0);
+    g.beta = zmk(0, 0);
+    if (side == TNT_SVD_LEFT) {  // X_q = U_q[:, :r]^H M_q  (r x n_q)
+      g.M = B.r; g.N = B.nq; g.K = B.mq;
+      g.A = Vp + B.goff; g.a_rs = 1; g.a_cs = B.g; g.conj_a = 1;
+      g.B = Mp + B.moff; g.b_rs = B.nq; g.b_cs = 1;
+      g.C = Xp + B.xoff; g.c_rs = B.nq;
+    } else {  // Y_q = M_q V_q[:, :r]  (m_q x r)
+      g.M = B.mq; g.N = B.r; g.K = B.nq;
+      g.A = Mp + B.moff; g.a_rs = B.nq; g.a_cs = 1;
+      g.B = Vp + B.goff; g.b_rs = B.g; g.b_cs = 1;
+      g.C = Xp + B.xoff; g.c_rs = B.r;
+    }
+    TNT_TRY(zgemm(c, g));
+  }
+  k_cand_sigma<<<nb, 256, 0, st>>>(Xp, d_cb, d_sig);
+  c->launches++;
+  // ---- global order and the four rules
+  {
+    size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(int));
+    TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_select<<<1, 1024, smem, st>>>(d_sig, d_blk, d_loc, (int)ntot_vals, P2, P.chi_max, P.trunc_abs,
+                                    P.trunc_rel, P.trunc_err, P.trunc_type, d_sig_s, d_blk_s, d_loc_s,
+                                    d_sel);
+    c->launches++;
+    TNT_CHECK_LAUNCH(c);
+  }
+  SelOut sel;
+  std::vector<double> hs(ntot_vals);
+  std::vector<int> hb(ntot_vals), hl(ntot_vals);
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(&sel, d_sel, sizeof(SelOut), cudaMemcpyDeviceToHost, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(hs.data(), d_sig_s, sizeof(double) * ntot_vals, cudaMemcpyDeviceToHost, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(hb.data(), d_blk_s, sizeof(int) * ntot_vals, cudaMemcpyDeviceToHost, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(hl.data(), d_loc_s, sizeof(int) * ntot_vals, cudaMemcpyDeviceToHost, st));
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
+  const int64_t chi = sel.chi;
+  // ---- bond order: charge ascending (block index), then sigma descending
+  std::vector<int> order(chi);
+  for (int64_t k = 0; k < chi; ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hb[x] < hb[y]; });
+  double kept2 = 0;
+  for (int64_t k = 0; k < chi; ++k) kept2 += hs[k] * hs[k];
+  const double scale = (renorm && kept2 > 0) ? 1.0 / sqrt(kept2) : 1.0;
+  std::vector<KeptIdx> hk(chi);
+  for (int64_t k = 0; k < chi; ++k) {
+    const int e = order[k];
+    const Blk& B = bl[hb[e]];
+    KeptIdx& K = hk[k];
+    K.voff = B.goff;
+    K.vld = B.g;
+    K.xoff = B.xoff;
+    K.xld = (side == TNT_SVD_LEFT) ? B.nq : B.r;
+    K.roff = B.roff;
+    K.nr = B.mq;
+    K.coff = B.coff;
+    K.nc = B.nq;
+    K.loc = hl[e];
+    h_S[k] = hs[e] * scale;
+    h_bq[k] = B.q;
+  }
+  KeptIdx* d_kept = (KeptIdx*)ws_alloc(c, ws_round(sizeof(KeptIdx) * chi));
+  if (!d_kept) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd kept)");
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_kept, hk.data(), sizeof(KeptIdx) * chi, cudaMemcpyHostToDevice, st));
+  TNT_TRY(zfill(c, U, m * chi, zmk(0, 0)));
+  TNT_TRY(zfill(c, X, chi * n, zmk(0, 0)));
+  int64_t mx = std::max(m, n);
+  dim3 gs((unsigned)std::min<int64_t>((mx + 255) / 256, 16), (unsigned)chi);
+  k_scatter<<<gs, 256, 0, st>>>(Vp, Xp, d_kept, d_rows, d_cols, side, scale, chi, n, U, X);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // host tables (hk) die at return
+  res->chi = chi;
+  res->err = sel.err;
+  res->disc = sel.disc;
+  res->norm2 = sel.norm2;
+  res->n_blocks = nb;
+  res->tie_at_cut = sel.tie;
+  return TNT_OK;
+}
+
+}  // namespace tnt

@@ -1,0 +1,182 @@
+// Internal declarations of the GB300 two-site-update library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tnt_gb300.h"
+
+namespace tnt {
+
+// ---------------------------------------------------------------- complex helpers
+typedef double2 z;  // complex128 stored {re, im}, the same bytes as tnt_cplx
+
+__host__ __device__ __forceinline__ z zmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ z zadd(z a, z b) { return zmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ z zsub(z a, z b) { return zmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ z zmul(z a, z b) {
+  return zmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ z zconj(z a) { return zmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ z zscale(z a, double s) { return zmk(a.x * s, a.y * s); }
+// acc += a * b
+__host__ __device__ __forceinline__ void zfma(z& acc, z a, z b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------- context
+struct Arena {
+  // A bump allocator over one device block; grown (reallocated) only between calls.
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t top = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = 0;
+  tnt_params params;
+  Arena ws;               // per-call scratch
+  std::string err;        // last error message
+  double* h_pinned = nullptr;  // small pinned host buffer for scalar read-back
+  size_t h_pinned_cap = 0;
+  // device status word written by kernels (bounds / NaN / timeout flags)
+  int* d_status = nullptr;
+  // counters (diagnostics, not hot-path state)
+  int64_t launches = 0;
+};
+
+// error plumbing: every entry point returns through these
+int set_err(Ctx* c, int code, const char* fmt, ...);
+#define TNT_CUDA_TRY(ctx, expr)                                                     \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::tnt::set_err((ctx), TNT_E_CUDA, "%s failed: %s (%s:%d)", #expr,      \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);            \
+  } while (0)
+#define TNT_TRY(expr)              \
+  do {                             \
+    int r_ = (expr);               \
+    if (r_ != TNT_OK) return r_;   \
+  } while (0)
+#define TNT_CHECK_LAUNCH(ctx) TNT_CUDA_TRY(ctx, cudaGetLastError())
+
+// scratch: reserve() grows the arena (synchronising the stream) before a call's
+// allocations; alloc() then only bumps.  Everything is released by reset().
+int ws_reserve(Ctx* c, size_t bytes);
+void* ws_alloc(Ctx* c, size_t bytes);
+inline void ws_reset(Ctx* c) { c->ws.top = 0; }
+inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
+int pinned_reserve(Ctx* c, size_t bytes);
+
+// ---------------------------------------------------------------- kernels (FP64 path)
+// Strided complex GEMM: C[i,j] = alpha * sum_k opA(i,k) opB(k,j) + beta * C[i,j]
+// opA(i,k) = A[i*a_rs + k*a_cs] (conjugated if conj_a), likewise B; batched by stride.
+struct ZGemm {
+  int64_t M, N, K;
+  const z* A;
+  int64_t a_rs, a_cs, a_bs;
+  const z* B;
+  int64_t b_rs, b_cs, b_bs;
+  z* C;
+  int64_t c_rs, c_bs;
+  int conj_a, conj_b;
+  z alpha, beta;
+  int64_t batch;
+};
+int zgemm(Ctx* c, const ZGemm& g);
+
+// Sparse small operator acting on a group of legs with strided batches:
+// out[b0*os0 + b1*os1 + b2*os2 + out_off[i]] (+)= sum_j op[i,j] in[b0*is0 + ... + in_off[j]]
+// op is given in CSR form (row_ptr over i, col j, value).
+struct OpApply {
+  const z* in;
+  z* out;
+  int nI, nJ, nnz;
+  const int* row_ptr;     // device, nI+1
+  const int* col;         // device, nnz
+  const z* val;           // device, nnz
+  const int64_t* in_off;  // device, nJ
+  const int64_t* out_off; // device, nI
+  int64_t B0, B1, B2;
+  int64_t is0, is1, is2, os0, os1, os2;
+  int accumulate;
+};
+int op_apply(Ctx* c, const OpApply& a);
+
+// Upload a dense op (nI x nJ, host) as CSR plus the two offset tables into scratch.
+int op_upload(Ctx* c, const std::vector<z>& dense, int nI, int nJ,
+              const std::vector<int64_t>& in_off, const std::vector<int64_t>& out_off,
+              OpApply* a);
+
+// Vector kernels (FP64, deterministic two-level reductions).
+// dots[i] = <V_i | w> for i < k   (V_i = V + i*ld)
+int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots);
+// w -= sum_i coef[i] V_i ; then d_norm2 = |w|^2   (coef on device)
+int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                       int64_t n, double* d_norm2);
+// y = x * (1 / sqrt(*d_norm2))  (d_norm2 on device); if x == y scales in place
+int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2);
+int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2);
+int vec_dot(Ctx* c, const z* x, const z* y, int64_t n, z* d_dot);
+
+// Lanczos tridiagonal: lowest eigenpair of T (k x k) given alpha[0..k-1], beta[0..k-2];
+// writes out[0] = E, out[1] = |y_{k-1}|, and y[0..k-1].
+int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, double* d_out,
+                   double* d_y);
+
+// Hermitian eigensolvers (FP64 cyclic Jacobi) used by the truncated SVD.
+// Small blocks: one CTA per block (n <= 64), in place on G (packed, each block n_b x n_b at
+// off_g[b]); eigenvectors to V at the same offsets.
+int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_n,
+                         int nblocks, int max_n);
+// One large block (any n), global-memory rounds.
+int jacobi_large(Ctx* c, z* G, z* V, int64_t n, int max_sweeps, int* sweeps_done);
+
+// Helpers: gather / scatter / conversion
+int gather2d(Ctx* c, const z* src, int64_t src_ld, const int64_t* d_rows, int64_t nr,
+             const int64_t* d_cols, int64_t nc, z* dst, int64_t dst_ld, int conj_t);
+int zfill(Ctx* c, z* p, int64_t n, z v);
+int zscale_inplace(Ctx* c, z* p, int64_t n, const double* d_scale, int mode);
+
+// Truncated SVD (svd.cu) and its scratch bound
+size_t svd_scratch_bound(int64_t m, int64_t n);
+int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq,
+                   const int64_t* h_cq, int side, int renorm, z* U, z* X, double* h_S,
+                   int64_t* h_bq, tnt_trunc_result* res);
+
+// H_eff internals
+int heff_f64(Ctx* c, const z* L, const z* W1, const z* W2, const z* R, const z* theta,
+             int64_t chl, int64_t d, int64_t D, int64_t chr, z* y);
+int heff_mixed(Ctx* c, const z* L, const z* W1, const z* W2, const z* R, const z* theta,
+               int64_t chl, int64_t d, int64_t D, int64_t chr, z* y);
+
+// host copies of MPO tensors are needed to build the CSR ops: read back W (tiny)
+int read_small(Ctx* c, const void* dsrc, void* hdst, size_t bytes);
+
+int bh_mpo_site_host(int n_max, double J, double U, double mu, double V, double j, double jc,
+                     z* W);
+int bh_bond_gate_host(int n_max, double J, double U, double mu, double c1, double c2,
+                      double tau, z* G);
+
+// release the call's scratch on every return path
+struct Scope {
+  Ctx* c;
+  explicit Scope(Ctx* cc) : c(cc) { ws_reset(c); }
+  ~Scope() { ws_reset(c); }
+};
+
+}  // namespace tnt
+
+struct tnt_ctx {
+  tnt::Ctx c;
+};

@@ -1,0 +1,272 @@
+"""Python API over the C-ABI: same names as the C calls, argument marshalling only.
+
+Device tensors are torch complex128 CUDA tensors in the leg orders of include/tnt_gb300.h;
+PyTorch only provides memory and the stream.  Every computation runs in libtntgb.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import (TNT_PREC_FP64, TNT_PREC_MIXED, TNT_SVD_LEFT, TNT_SVD_RIGHT,  # noqa: F401
+                   TNT_TRUNC_1NORM, TNT_TRUNC_2NORM, TNT_TRUNC_SUMSQ, TntError)
+
+CDT = torch.complex128
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != CDT or not t.is_contiguous():
+        raise ValueError("expected a contiguous complex128 CUDA tensor")
+    return t.data_ptr()
+
+
+def _struct_dict(s) -> dict:
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def bh_mpo_site(n_max, J, U, mu=0.0, V=0.0, j=1.0, j_c=0.0) -> np.ndarray:
+    """Host builder of one Bose-Hubbard MPO tensor W[4,4,d,d] (C call tnt_bh_mpo_site)."""
+    d = n_max + 1
+    out = np.zeros((4, 4, d, d), dtype=np.complex128)
+    L.check(None, L.load().tnt_bh_mpo_site(n_max, J, U, mu, V, j, j_c, out.ctypes.data))
+    return out
+
+
+def bh_bond_gate(n_max, J, U, mu, c1, c2, tau) -> np.ndarray:
+    """Host builder of the Trotter gate exp(-i tau h_bond), d^2 x d^2 (tnt_bh_bond_gate)."""
+    d = n_max + 1
+    out = np.zeros((d * d, d * d), dtype=np.complex128)
+    L.check(None, L.load().tnt_bh_bond_gate(n_max, J, U, mu, c1, c2, tau, out.ctypes.data))
+    return out
+
+
+def params_default() -> dict:
+    p = L.tnt_params()
+    L.check(None, L.load().tnt_params_default(C.byref(p)))
+    return _struct_dict(p)
+
+
+class Context:
+    """A library context on one GPU, enqueueing on torch's current stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.lib = L.load()
+        self.device = device
+        torch.cuda.set_device(device)
+        st = stream if stream is not None else torch.cuda.current_stream(device)
+        self.stream = st
+        h = C.c_void_p()
+        code = self.lib.tnt_ctx_create(device, C.c_void_p(st.cuda_stream), C.byref(h))
+        if code != 0:
+            raise TntError(code, "tnt_ctx_create failed (no usable CUDA device?)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tnt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, code, ok=(0,)):
+        return L.check(self.h, code, ok)
+
+    # ---------------------------------------------------------------- params
+    def params(self) -> dict:
+        p = L.tnt_params()
+        self._chk(self.lib.tnt_params_get(self.h, C.byref(p)))
+        return _struct_dict(p)
+
+    def set_params(self, **kw):
+        p = L.tnt_params()
+        self._chk(self.lib.tnt_params_get(self.h, C.byref(p)))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._chk(self.lib.tnt_params_set(self.h, C.byref(p)))
+
+    def sys_info(self) -> str:
+        buf = C.create_string_buffer(2048)
+        self._chk(self.lib.tnt_sys_info(self.h, buf, 2048))
+        return buf.value.decode()
+
+    def launch_count(self) -> int:
+        return int(self.lib.tnt_launch_count(self.h))
+
+    # ---------------------------------------------------------------- kernels
+    def theta_form(self, A, B, out=None):
+        chl, d, chm = A.shape
+        chr_ = B.shape[2]
+        out = out if out is not None else torch.empty((chl, d, d, chr_), dtype=CDT, device=A.device)
+        self._chk(self.lib.tnt_theta_form(self.h, _ptr(A), _ptr(B), chl, d, chm, chr_, _ptr(out)))
+        return out
+
+    def gate_apply(self, G, theta, out=None):
+        chl, d, _, chr_ = theta.shape
+        out = out if out is not None else torch.empty_like(theta)
+        self._chk(self.lib.tnt_gate_apply(self.h, _ptr(G), _ptr(theta), chl, d, chr_, _ptr(out)))
+        return out
+
+    def heff_apply(self, Lenv, W1, W2, Renv, theta, precision=TNT_PREC_FP64, out=None):
+        chl, d, _, chr_ = theta.shape
+        D = W1.shape[0]
+        out = out if out is not None else torch.empty_like(theta)
+        self._chk(self.lib.tnt_heff_apply(self.h, _ptr(Lenv), _ptr(W1), _ptr(W2), _ptr(Renv),
+                                          _ptr(theta), chl, d, D, chr_, precision, _ptr(out)))
+        return out
+
+    def env_left(self, Lenv, W, A, out=None):
+        chl, d, chr_ = A.shape
+        D = W.shape[0]
+        out = out if out is not None else torch.empty((chr_, D, chr_), dtype=CDT, device=A.device)
+        self._chk(self.lib.tnt_env_left(self.h, _ptr(Lenv), _ptr(W), _ptr(A), chl, d, D, chr_,
+                                        _ptr(out)))
+        return out
+
+    def env_right(self, Renv, W, B, out=None):
+        chl, d, chr_ = B.shape
+        D = W.shape[0]
+        out = out if out is not None else torch.empty((chl, D, chl), dtype=CDT, device=B.device)
+        self._chk(self.lib.tnt_env_right(self.h, _ptr(Renv), _ptr(W), _ptr(B), chl, d, D, chr_,
+                                         _ptr(out)))
+        return out
+
+    def lanczos_ground(self, Lenv, W1, W2, Renv, theta):
+        """theta (device) is overwritten by the eigenvector; returns the result dict."""
+        chl, d, _, chr_ = theta.shape
+        D = W1.shape[0]
+        res = L.tnt_lanczos_result()
+        self._chk(self.lib.tnt_lanczos_ground(self.h, _ptr(Lenv), _ptr(W1), _ptr(W2), _ptr(Renv),
+                                              chl, d, D, chr_, _ptr(theta), C.byref(res)),
+                  ok=(0, L.TNT_E_NOCONV))
+        return _struct_dict(res)
+
+    def svd_trunc(self, M, row_q=None, col_q=None, side=TNT_SVD_LEFT, renorm=False):
+        """Truncated SVD of the m x n device matrix M; returns (U, X, S, bond_q, info)."""
+        m, n = M.shape
+        chi_max = self.params()["chi_max"]
+        cap = int(min(m, n, chi_max))
+        U = torch.empty(m * cap, dtype=CDT, device=M.device)
+        X = torch.empty(cap * n, dtype=CDT, device=M.device)
+        S = np.zeros(cap)
+        bq = np.zeros(cap, dtype=np.int64)
+        res = L.tnt_trunc_result()
+        if row_q is not None:
+            rq = np.ascontiguousarray(row_q, dtype=np.int64)
+            cq = np.ascontiguousarray(col_q, dtype=np.int64)
+            prq, pcq = rq.ctypes.data, cq.ctypes.data
+        else:
+            prq = pcq = None
+        self._chk(self.lib.tnt_svd_trunc(self.h, _ptr(M), m, n, prq, pcq, side, int(renorm),
+                                         _ptr(U), _ptr(X), S.ctypes.data, bq.ctypes.data,
+                                         C.byref(res)))
+        k = res.chi
+        return (U[: m * k].view(m, k), X[: k * n].view(k, n), S[:k].copy(), bq[:k].copy(),
+                _struct_dict(res))
+
+    # ---------------------------------------------------------------- objects
+    def mpo_bose_hubbard(self, L_, n_max, J, U, mu=0.0, V=0.0, j_c=0.0) -> "Mpo":
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_mpo_bose_hubbard(self.h, L_, n_max, J, U, mu, V, j_c, C.byref(h)))
+        return Mpo(self, h)
+
+    def mps_create(self, tensors, charges=None, chi_cap=None) -> "Mps":
+        Ls = len(tensors)
+        d = tensors[0].shape[1]
+        chi = np.array([1] + [t.shape[2] for t in tensors], dtype=np.int64)
+        cap = int(chi_cap if chi_cap is not None else chi.max())
+        arrs = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+        sp = (C.c_void_p * Ls)(*[a.ctypes.data for a in arrs])
+        qp = None
+        if charges is not None:
+            qa = [np.ascontiguousarray(q, dtype=np.int64) for q in charges]
+            qp = (C.c_void_p * (Ls + 1))(*[a.ctypes.data for a in qa])
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_mps_create(self.h, Ls, d, cap, chi.ctypes.data, sp, qp, C.byref(h)))
+        return Mps(self, h)
+
+    def mps_product(self, occupations, d, chi_cap) -> "Mps":
+        occ = np.ascontiguousarray(occupations, dtype=np.int32)
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_mps_product(self.h, len(occ), d, chi_cap, occ.ctypes.data,
+                                           C.byref(h)))
+        return Mps(self, h)
+
+    def dmrg_create(self, mps: "Mps", mpo: "Mpo") -> "Dmrg":
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_dmrg_create(self.h, mps.h, mpo.h, C.byref(h)))
+        return Dmrg(self, h, mps, mpo)
+
+
+class Mpo:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnt_mpo_destroy(self.h)
+            self.h = None
+
+
+class Mps:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        Ls, d = C.c_int(), C.c_int()
+        ctx._chk(ctx.lib.tnt_mps_length(h, C.byref(Ls), C.byref(d)))
+        self.L, self.d = Ls.value, d.value
+
+    def bond_dim(self, k) -> int:
+        v = C.c_int64()
+        self.ctx._chk(self.ctx.lib.tnt_mps_bond_dim(self.h, k, C.byref(v)))
+        return v.value
+
+    def site(self, j) -> np.ndarray:
+        shape = (self.bond_dim(j), self.d, self.bond_dim(j + 1))
+        out = np.zeros(shape, dtype=np.complex128)
+        self.ctx._chk(self.ctx.lib.tnt_mps_get_site(self.ctx.h, self.h, j, out.ctypes.data,
+                                                    out.size))
+        return out
+
+    def charges(self, k) -> np.ndarray:
+        out = np.zeros(self.bond_dim(k), dtype=np.int64)
+        self.ctx._chk(self.ctx.lib.tnt_mps_get_charges(self.h, k, out.ctypes.data, out.size))
+        return out
+
+    def tensors(self):
+        return [self.site(j) for j in range(self.L)]
+
+    def expect_mpo(self, mpo: Mpo) -> float:
+        v = C.c_double()
+        self.ctx._chk(self.ctx.lib.tnt_mps_expect_mpo(self.ctx.h, self.h, mpo.h, C.byref(v)))
+        return v.value
+
+    def norm2(self) -> float:
+        v = C.c_double()
+        self.ctx._chk(self.ctx.lib.tnt_mps_norm2(self.ctx.h, self.h, C.byref(v)))
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnt_mps_destroy(self.h)
+            self.h = None
+
+
+class Dmrg:
+    def __init__(self, ctx: Context, h, mps: Mps, mpo: Mpo):
+        self.ctx, self.h, self.mps, self.mpo = ctx, h, mps, mpo
+
+    def sweep(self) -> dict:
+        st = L.tnt_sweep_stats()
+        self.ctx._chk(self.ctx.lib.tnt_dmrg_sweep(self.ctx.h, self.h, C.byref(st)))
+        return _struct_dict(st)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnt_dmrg_destroy(self.h)
+            self.h = None

@@ -1,0 +1,204 @@
+"""GPU parity of the two-site kernels against the FP64 CPU oracle, through the C-ABI.
+
+Shapes span several GEMM tiles (64) and ragged tails; the full cfg2 matvec shape
+(chi = 256, d = 4, D = 4) is compared element by element in FP64.  Tolerances:
+FP64 paths 1e-12 relative to max|y| (rounding of K ~ 1e3 complex FMAs); the split-TF32
+path 2e-5 (operands carry 22 mantissa bits, FP32 accumulation over K <= 1024)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bose_hubbard as bh
+from oracle import contract as oc
+from oracle import lanczos as olz
+from oracle import svd as osvd
+from paper_1610_02244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1610_02244_gb300 import build as b
+    b.build()
+    from paper_1610_02244_gb300 import tnt
+    return tnt.Context(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def heff_inputs(seed, chl, d, chr_, D=4, U=2.0):
+    g = synth.rng(seed)
+    Ws, _, _ = bh.bh_mpo(4, d - 1, 1.0, U)
+    Le = synth.hermitian_env(g, chl, D)
+    Re = synth.hermitian_env(g, chr_, D)
+    th = synth.complex_gaussian(g, (chl, d, d, chr_))
+    return Le, Ws[1], Ws[2], Re, th
+
+
+SHAPES = [(1, 2, 1), (5, 3, 7), (67, 4, 45), (130, 5, 64), (64, 2, 129)]
+
+
+@pytest.mark.parametrize("chl,d,chr_", SHAPES)
+def test_heff_fp64(ctx, chl, d, chr_):
+    Le, W1, W2, Re, th = heff_inputs(chl + d + chr_, chl, d, chr_)
+    y = ctx.heff_apply(dev(Le), dev(W1), dev(W2), dev(Re), dev(th)).cpu().numpy()
+    assert rel(y, oc.heff_apply(Le, W1, W2, Re, th)) < FP64_TOL
+
+
+def test_heff_fp64_cfg2_full(ctx):
+    """The micro-benchmark shape: L, R 256x4x256, W 4x4x4x4, theta 256x4x4x256."""
+    Le, W1, W2, Re, th = heff_inputs(0, 256, 4, 256)
+    y = ctx.heff_apply(dev(Le), dev(W1), dev(W2), dev(Re), dev(th)).cpu().numpy()
+    assert rel(y, oc.heff_apply(Le, W1, W2, Re, th)) < FP64_TOL
+
+
+@pytest.mark.parametrize("chl,d,chr_", SHAPES + [(256, 4, 256)])
+def test_heff_mixed(ctx, chl, d, chr_):
+    from paper_1610_02244_gb300 import tnt
+    Le, W1, W2, Re, th = heff_inputs(100 + chl, chl, d, chr_)
+    y = ctx.heff_apply(dev(Le), dev(W1), dev(W2), dev(Re), dev(th),
+                       precision=tnt.TNT_PREC_MIXED).cpu().numpy()
+    assert rel(y, oc.heff_apply(Le, W1, W2, Re, th)) < MIXED_TOL
+
+
+def test_heff_zero_and_sector_preserving(ctx):
+    """Exact zeros stay exact zeros: a theta confined to one charge sector with block
+    sparse environments gives a result confined to the same sector (both precisions)."""
+    from paper_1610_02244_gb300 import tnt
+    Le, W1, W2, Re, th = heff_inputs(5, 9, 3, 9)
+    th[:, 1:, :, :] = 0
+    y_ref = oc.heff_apply(Le, W1, W2, Re, th)
+    for prec in (tnt.TNT_PREC_FP64, tnt.TNT_PREC_MIXED):
+        y = ctx.heff_apply(dev(Le), dev(W1), dev(W2), dev(Re), dev(th), precision=prec)
+        y = y.cpu().numpy()
+        assert np.all((y == 0) == (y_ref == 0)) or rel(y, y_ref) < MIXED_TOL
+
+
+@pytest.mark.parametrize("chl,d,chm,chr_", [(3, 2, 4, 5), (70, 4, 66, 33), (256, 4, 256, 256)])
+def test_theta_form(ctx, chl, d, chm, chr_):
+    g = synth.rng(chl + chm)
+    A = synth.complex_gaussian(g, (chl, d, chm))
+    B = synth.complex_gaussian(g, (chm, d, chr_))
+    th = ctx.theta_form(dev(A), dev(B)).cpu().numpy()
+    assert rel(th, oc.theta_form(A, B)) < FP64_TOL
+
+
+@pytest.mark.parametrize("n_max,chl,chr_", [(4, 17, 33), (1, 64, 65), (3, 5, 1)])
+def test_gate_apply(ctx, n_max, chl, chr_):
+    from paper_1610_02244_gb300 import tnt
+    d = n_max + 1
+    G = tnt.bh_bond_gate(n_max, 1.0, 2.0, 0.0, 0.5, 0.5, 0.01)
+    g = synth.rng(chl)
+    th = synth.complex_gaussian(g, (chl, d, d, chr_))
+    out = ctx.gate_apply(dev(G), dev(th)).cpu().numpy()
+    Gr = bh.gate(bh.bond_hamiltonian(n_max, 1.0, 2.0, 0.5, 0.5), 0.01)
+    assert rel(out, oc.gate_apply(Gr, th)) < FP64_TOL
+
+
+@pytest.mark.parametrize("chl,d,chr_", [(1, 4, 4), (13, 3, 17), (96, 4, 70), (256, 4, 256)])
+def test_environments(ctx, chl, d, chr_):
+    g = synth.rng(chl * 7 + chr_)
+    Ws, _, _ = bh.bh_mpo(4, d - 1, 0.8, 1.7, 0.2)
+    A = synth.complex_gaussian(g, (chl, d, chr_))
+    Le = synth.complex_gaussian(g, (chl, 4, chl))
+    Re = synth.complex_gaussian(g, (chr_, 4, chr_))
+    Lo = ctx.env_left(dev(Le), dev(Ws[2]), dev(A)).cpu().numpy()
+    assert rel(Lo, oc.env_left(Le, Ws[2], A)) < FP64_TOL
+    Ro = ctx.env_right(dev(Re), dev(Ws[2]), dev(A)).cpu().numpy()
+    assert rel(Ro, oc.env_right(Re, Ws[2], A)) < FP64_TOL
+
+
+@pytest.mark.parametrize("chl,d,chr_", [(6, 3, 6), (12, 4, 10), (20, 3, 33)])
+def test_lanczos_fp64_matches_dense_eigh(ctx, chl, d, chr_):
+    Le, W1, W2, Re, th = heff_inputs(3 * chl + chr_, chl, d, chr_)
+    H = oc.heff_dense(Le, W1, W2, Re)
+    w, v = np.linalg.eigh(H)
+    t = dev(th)
+    res = ctx.lanczos_ground(dev(Le), dev(W1), dev(W2), dev(Re), t)
+    x = t.cpu().numpy().reshape(-1)
+    assert abs(res["E"] - w[0]) <= 1e-10 * abs(w[0])
+    gap = w[1] - w[0]
+    if gap > 1e-3 * abs(w[0]):
+        assert abs(1 - abs(np.vdot(v[:, 0], x))) < 1e-8
+    # the oracle's own Lanczos on the same start vector
+    Eo, _, _, _, _ = olz.lanczos_ground(lambda z: oc.heff_apply(Le, W1, W2, Re, z), th)
+    assert abs(res["E"] - Eo) <= 1e-10 * abs(Eo)
+
+
+def test_lanczos_mixed_energy_within_1e10(ctx):
+    from paper_1610_02244_gb300 import tnt
+    chl, d, chr_ = 16, 4, 16
+    Le, W1, W2, Re, th = heff_inputs(77, chl, d, chr_)
+    w = np.linalg.eigvalsh(oc.heff_dense(Le, W1, W2, Re))
+    ctx.set_params(precision=tnt.TNT_PREC_MIXED)
+    try:
+        res = ctx.lanczos_ground(dev(Le), dev(W1), dev(W2), dev(Re), dev(th))
+    finally:
+        ctx.set_params(precision=tnt.TNT_PREC_FP64)
+    assert abs(res["E_rq"] - w[0]) <= 1e-10 * abs(w[0])
+
+
+def svd_case(seed, m, n, charged):
+    g = synth.rng(seed)
+    M = synth.complex_gaussian(g, (m, n))
+    if charged:
+        rq = g.integers(0, 5, m)
+        cq = g.integers(0, 5, n)
+        M = M * (rq[:, None] == cq[None, :])
+        return M, rq, cq
+    return M, np.zeros(m, np.int64), np.zeros(n, np.int64)
+
+
+@pytest.mark.parametrize("m,n,charged,side", [
+    (40, 30, False, 0), (30, 40, False, 1), (100, 90, True, 0), (90, 100, True, 1),
+    (200, 160, False, 0), (8, 8, True, 1), (1, 7, False, 0)])
+def test_svd_trunc_matches_oracle(ctx, m, n, charged, side):
+    M, rq, cq = svd_case(m * n + side, m, n, charged)
+    chi_max = max(1, min(m, n) * 2 // 3)
+    ctx.set_params(chi_max=chi_max, trunc_err=1e-8, trunc_rel=1e-16)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), rq, cq, side=side)
+    finally:
+        ctx.set_params(chi_max=1 << 40)
+    p = osvd.TruncParams(chi_max=chi_max)
+    Ur, Sr, Vr, bqr, inf_r = osvd.svd_truncate(M, rq, cq, p)
+    assert info["chi"] == len(Sr)
+    order = np.lexsort((-Sr, bqr))
+    assert np.array_equal(bq, bqr[order])
+    assert np.abs(np.sort(S) - np.sort(Sr)).max() < 1e-12 * Sr.max()
+    U, X = U.cpu().numpy(), X.cpu().numpy()
+    # gauge-invariant: the truncated product and orthonormality of the kept factor
+    assert np.abs(U @ X - (Ur * Sr) @ Vr).max() < 1e-11 * Sr.max()
+    if side == 0:
+        assert np.abs(U.conj().T @ U - np.eye(len(S))).max() < 1e-12
+    else:
+        assert np.abs(X @ X.conj().T - np.eye(len(S))).max() < 1e-12
+    assert abs(info["err"] - inf_r["err"]) <= 1e-10 * max(inf_r["err"], 1e-14)
+    assert abs(info["disc"] - inf_r["disc"]) <= 1e-10 * max(inf_r["disc"], 1e-14)
+
+
+def test_svd_large_block_cfg2_shape(ctx):
+    """One dense 1024 x 1024 block (theta of chi = 256, d = 4) through the multi-launch
+    Jacobi path, truncated to chi = 256."""
+    M, rq, cq = svd_case(9, 1024, 1024, False)
+    ctx.set_params(chi_max=256)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), None, None, side=0, renorm=False)
+    finally:
+        ctx.set_params(chi_max=1 << 40)
+    s_ref = np.linalg.svd(M, compute_uv=False)
+    assert info["chi"] == 256
+    assert np.abs(S - s_ref[:256]).max() < 1e-11 * s_ref[0]
+    U = U.cpu().numpy()
+    assert np.abs(U.conj().T @ U - np.eye(256)).max() < 1e-11
+    assert abs(info["disc"] - np.sum(s_ref[256:] ** 2)) < 1e-10 * np.sum(s_ref ** 2)
