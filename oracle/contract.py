@@ -16,10 +16,15 @@ from __future__ import annotations
 import numpy as np
 
 
+def contract2(spec: str, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """One pairwise contraction, evaluated as a matrix product (BLAS) by numpy.einsum."""
+    return np.einsum(spec, a, b, optimize=True)
+
+
 def theta_form(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     """theta[a,s1,s2,b] = sum_m A[a,s1,m] B[m,s2,b]: the two-site object, contracted over
     the shared bond (Sec. 3 contraction; App. B.1.1)."""
-    return np.einsum("asm,mtb->astb", A, B)
+    return contract2("asm,mtb->astb", A, B)
 
 
 def gate_apply(G: np.ndarray, theta: np.ndarray) -> np.ndarray:
@@ -27,7 +32,7 @@ def gate_apply(G: np.ndarray, theta: np.ndarray) -> np.ndarray:
     Sec. 3 Trotterised update, Sec. 5 time evolution example)."""
     d = theta.shape[1]
     G4 = G.reshape(d, d, d, d)  # [s1', s2', s1, s2]
-    return np.einsum("xyst,astb->axyb", G4, theta)
+    return contract2("xyst,astb->axyb", G4, theta)
 
 
 def heff_apply(L: np.ndarray, W1: np.ndarray, W2: np.ndarray, R: np.ndarray,
@@ -43,10 +48,10 @@ def heff_apply(L: np.ndarray, W1: np.ndarray, W2: np.ndarray, R: np.ndarray,
       T3 = T2 . W2     (sum over w1, s2)
       y  = T3 . R      (sum over w2, b)
     """
-    T1 = np.einsum("pwa,astb->pwstb", L, theta)          # [a', w, s1, s2, b]
-    T2 = np.einsum("pwstb,wvxs->pxvtb", T1, W1)          # [a', s1', w1, s2, b]
-    T3 = np.einsum("pxvtb,vuyt->pxyub", T2, W2)          # [a', s1', s2', w2, b]
-    return np.einsum("pxyub,qub->pxyq", T3, R)           # [a', s1', s2', b']
+    T1 = contract2("pwa,astb->pwstb", L, theta)          # [a', w, s1, s2, b]
+    T2 = contract2("pwstb,wvxs->pxvtb", T1, W1)          # [a', s1', w1, s2, b]
+    T3 = contract2("pxvtb,vuyt->pxyub", T2, W2)          # [a', s1', s2', w2, b]
+    return contract2("pxyub,qub->pxyq", T3, R)           # [a', s1', s2', b']
 
 
 def heff_dense(L, W1, W2, R) -> np.ndarray:
@@ -62,17 +67,17 @@ def env_left(Lenv: np.ndarray, W: np.ndarray, A: np.ndarray) -> np.ndarray:
     Grows <psi|H|psi> by one site from the left: the environment H_prepare builds for the
     next site (Listing 2; Sec. 4.3 network of <psi|O|psi>).
     """
-    X = np.einsum("pwa,asm->pwsm", Lenv, A)              # ket side
-    Y = np.einsum("pwsm,wvts->ptvm", X, W)               # MPO
-    return np.einsum("ptn,ptvm->nvm", A.conj(), Y)       # bra side
+    X = contract2("pwa,asm->pwsm", Lenv, A)              # ket side
+    Y = contract2("pwsm,wvts->ptvm", X, W)               # MPO
+    return contract2("ptn,ptvm->nvm", A.conj(), Y)       # bra side
 
 
 def env_right(Renv: np.ndarray, W: np.ndarray, B: np.ndarray) -> np.ndarray:
     """R_next[a',w,a] = sum conj(B[a',s',b']) R[b',w',b] W[w,w',s',s] B[a,s,b] (mirror of
     env_left)."""
-    X = np.einsum("asb,qvb->asqv", B, Renv)              # ket side
-    Y = np.einsum("asqv,wvts->awtq", X, W)               # MPO
-    return np.einsum("ptq,awtq->pwa", B.conj(), Y)       # bra side
+    X = contract2("asb,qvb->asqv", B, Renv)              # ket side
+    Y = contract2("asqv,wvts->awtq", X, W)               # MPO
+    return contract2("ptq,awtq->pwa", B.conj(), Y)       # bra side
 
 
 def boundary_left(vec: np.ndarray) -> np.ndarray:
@@ -89,7 +94,7 @@ def mps_to_state(tensors) -> np.ndarray:
     psi_j = tTr[ (x)_nu T^(nu) ] of Sec. 3, Eq. 1 for a chain."""
     psi = tensors[0]  # [1, s, b]
     for A in tensors[1:]:
-        psi = np.einsum("xsm,mtb->xstb", psi, A)
+        psi = contract2("xsm,mtb->xstb", psi, A)
         psi = psi.reshape(psi.shape[0], -1, psi.shape[-1])
     return psi.reshape(-1)
 
