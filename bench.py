@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the two-site update at the H_eff.theta micro-benchmark shape.
+
+Workload (synthetic, seeded): left/right environments 256 x 4 x 256 with i.i.d. complex
+Gaussian entries (Hermitian MPO-channel pairing so that H_eff is Hermitian), the
+Bose-Hubbard MPO tensor (d = 4, D = 4, J = 1, U = 2, mu = 0), site tensors A, B of
+256 x 4 x 256 with i.i.d. complex Gaussian entries.
+
+One step = one two-site DMRG update on that data, every row of the hot path:
+  theta = A.B (a1); Lanczos on H_eff with 32 Krylov steps, FP64 vectors, CGS2 (a3, a4),
+  plus one FP64 matvec for the Rayleigh quotient when the matvecs are split TF32 (a9);
+  truncated SVD of theta as a 1024 x 1024 matrix to chi = 256, S renormalised
+  (a5, a6, a7); left-environment growth with the new site tensor (a8).
+metric: useful H_eff.theta FLOP/s of the update = (matvecs x 18.25 GFLOP) / update time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHI, D_PHYS, D_MPO = 256, 4, 4
+J, U, MU = 1.0, 2.0, 0.0
+KRYLOV = 32
+CHI_MAX = 256
+METRIC = "DMRG s/sweep & H_eff·θ TFLOP/s, mixed vs FP64 on GB300 at |ΔE|≤1e-10"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense ratio (profiling recipe table)
+FP64_PER_BF16 = 1.25 / 2250.0  # nominal FP64 1.25 TFLOP/s against 2.25 PFLOP/s bf16
+
+
+def matvec_cmacs(chl, d, D, chr_):
+    """Complex multiply-adds of one H_eff.theta in the (L.theta).W1.W2.R order."""
+    return D * d * d * chl * chr_ * (chl + chr_) + 2 * D * D * d ** 3 * chl * chr_
+
+
+FLOP_MATVEC = 8 * matvec_cmacs(CHI, D_PHYS, D_MPO, CHI)   # 18.25e9
+N_THETA = CHI * D_PHYS * D_PHYS * CHI
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def synth_inputs(seed=0):
+    from paper_1610_02244_gb300 import synth, tnt
+    g = synth.rng(seed)
+    Le = synth.hermitian_env(g, CHI, D_MPO)
+    Re = synth.hermitian_env(g, CHI, D_MPO)
+    A = synth.complex_gaussian(g, (CHI, D_PHYS, CHI))
+    B = synth.complex_gaussian(g, (CHI, D_PHYS, CHI))
+    W = tnt.bh_mpo_site(D_PHYS - 1, J, U, MU, 0.0, 2.0, 0.0)
+    return {"L": Le, "R": Re, "A": A, "B": B, "W": W}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def dist_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- the oracle (CPU)
+def oracle_sample(inp, n_matvec=2):
+    """Time the FP64 CPU oracle on a bounded sample of one update: n_matvec H_eff.theta
+    applications, one truncated SVD of the 1024 x 1024 theta and one environment growth,
+    scaled to a full update (33 matvecs)."""
+    from oracle import contract as oc
+    from oracle import svd as osvd
+    Le, Re, A, B, W = inp["L"], inp["R"], inp["A"], inp["B"], inp["W"]
+    t0 = time.perf_counter()
+    th = oc.theta_form(A, B)
+    t_theta = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x = th
+    for _ in range(n_matvec):
+        x = oc.heff_apply(Le, W, W, Re, x)
+        x = x / np.linalg.norm(x)
+    t_mv = (time.perf_counter() - t0) / n_matvec
+    t0 = time.perf_counter()
+    U, S, Vh, bq, info = osvd.svd_truncate(th.reshape(CHI * D_PHYS, -1),
+                                           np.zeros(CHI * D_PHYS, np.int64),
+                                           np.zeros(CHI * D_PHYS, np.int64),
+                                           osvd.TruncParams(chi_max=CHI_MAX))
+    t_svd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oc.env_left(Le, W, U.reshape(CHI, D_PHYS, -1))
+    t_env = time.perf_counter() - t0
+    n_full = KRYLOV + 1
+    t_update = t_theta + n_full * t_mv + t_svd + t_env
+    return {"t_update_est": t_update, "t_matvec": t_mv, "t_svd": t_svd,
+            "t_theta": t_theta, "t_env": t_env, "n_matvec": n_full,
+            "sample": f"theta, {n_matvec} matvecs, 1 SVD (1024^2), 1 env growth; "
+                      f"update time = theta + {n_full} x matvec + SVD + env"}
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    inp = synth_inputs(0)
+    if args.warmup > 0:  # one untimed sample warms BLAS and the caches
+        oracle_sample(inp, n_matvec=1)
+    vals, times = [], []
+    for _ in range(args.steps):
+        s = oracle_sample(inp, n_matvec=1)
+        vals.append(s["n_matvec"] * FLOP_MATVEC / s["t_update_est"] / 1e12)
+        times.append(s["t_update_est"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, "f64"),
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": threads_used(),
+                             "kind": "oracle", "sample": s["sample"]},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, dtype):
+    return {"workload": "two-site DMRG update, Bose-Hubbard MPO, chi=256 d=4 D=4 "
+                        "(L,R 256x4x256, theta 256x4x4x256), 32 Krylov steps, SVD to chi=256",
+            "chi": CHI, "d": D_PHYS, "D": D_MPO, "krylov_steps": KRYLOV, "chi_max": CHI_MAX,
+            "precision": args.precision, "matvec_dtype": dtype,
+            "l2": "inputs larger than L2 (Krylov basis 32 x 16 MiB per step)"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import tnt
+    b.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = tnt.Context(local)
+    prec = tnt.TNT_PREC_MIXED if args.precision == "mixed" else tnt.TNT_PREC_FP64
+    ctx.set_params(chi_max=CHI_MAX, krylov_cap=KRYLOV, lanczos_maxit=KRYLOV, precision=prec,
+                   lanczos_tol=1e-12)
+    inp = synth_inputs(1000 + rank)
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in inp.items()}
+    theta = torch.empty((CHI, D_PHYS, D_PHYS, CHI), dtype=torch.complex128, device=dev)
+    Lnew = torch.empty((CHI, D_MPO, CHI), dtype=torch.complex128, device=dev)
+    stats = {}
+
+    def step(tin):
+        ctx.theta_form(tin["A"], tin["B"], out=theta)
+        res = ctx.lanczos_ground(tin["L"], tin["W"], tin["W"], tin["R"], theta)
+        Uo, X, S, bq, info = ctx.svd_trunc(theta.view(CHI * D_PHYS, D_PHYS * CHI),
+                                           side=tnt.TNT_SVD_LEFT, renorm=True)
+        k = info["chi"]
+        ctx.env_left(tin["L"], tin["W"], Uo.reshape(CHI, D_PHYS, k),
+                     out=Lnew if k == CHI else None)
+        stats["res"], stats["info"] = res, info
+        return Uo, X, res
+
+    st = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+
+    # phase breakdown (one untimed step, events on the library's stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev[0].record(st)
+    ctx.theta_form(t["A"], t["B"], out=theta)
+    ev[1].record(st)
+    res = ctx.lanczos_ground(t["L"], t["W"], t["W"], t["R"], theta)
+    ev[2].record(st)
+    Uo, X, S, bq, info = ctx.svd_trunc(theta.view(CHI * D_PHYS, D_PHYS * CHI),
+                                       side=tnt.TNT_SVD_LEFT, renorm=True)
+    ev[3].record(st)
+    ctx.env_left(t["L"], t["W"], Uo.reshape(CHI, D_PHYS, info["chi"]))
+    ev[4].record(st)
+    torch.cuda.synchronize()
+    phases = {n: ev[i].elapsed_time(ev[i + 1])
+              for i, n in enumerate(["theta_ms", "lanczos_ms", "svd_ms", "env_ms"])}
+
+    # dominant kernel class by summed device time over one step
+    classes = ["cgemm_tf32x3", "zgemm_f64", "op_apply", "op_mixed", "split_theta",
+               "multidot", "multiaxpy", "jacobi_small", "jacobi_round"]
+    per_class = {}
+    for cls in classes:
+        ctx.profile_select(cls)
+        step(t)
+        ms, n = ctx.profile_read()
+        per_class[cls] = (ms, n)
+    ctx.profile_select(None)
+    dom = max(per_class, key=lambda k: per_class[k][0])
+
+    # timed region: K steps, dominant class timed live with events on the same stream
+    ctx.profile_select(dom)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nmv = 0
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            step(t)
+            nmv += stats["res"]["n_matvec"]
+        e1.record(st)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms_total = e0.elapsed_time(e1)
+    dom_ms, dom_n = ctx.profile_read()
+    ctx.profile_select(None)
+    launches = ctx.launch_count() - launches0
+    ms_step = dist_max(ms_total / args.steps, ws)
+    flops_step = nmv / args.steps * FLOP_MATVEC
+    value = ws * flops_step / (ms_step * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    hin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in inp.items()}
+    hout_u = torch.empty((CHI * D_PHYS * CHI,), dtype=torch.complex128).pin_memory()
+    hout_x = torch.empty((CHI * D_PHYS * CHI,), dtype=torch.complex128).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in hin.values())
+    d2h = 2 * hout_u.numel() * hout_u.element_size() + 8
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        tin = {k: v.to(dev, non_blocking=True) for k, v in hin.items()}
+        Uo, X, r = step(tin)
+        hout_u[: Uo.numel()].copy_(Uo.reshape(-1), non_blocking=True)
+        hout_x[: X.numel()].copy_(X.reshape(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        _ = r["E_rq"]
+    t_e2e = dist_max((time.perf_counter() - t0) / e2e_steps, ws)
+    e2e = ws * flops_step / t_e2e / 1e12
+
+    line = None
+    if rank == 0:
+        peaks, src = load_peaks()
+        roof = roofline(dom, dom_ms, dom_n, args, peaks, src, nmv / args.steps)
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            s = oracle_sample(inp, n_matvec=2)
+            cpu = {"value": s["n_matvec"] * FLOP_MATVEC / s["t_update_est"] / 1e12,
+                   "unit": "TFLOP/s", "cores": threads_used(), "kind": "oracle",
+                   "sample": s["sample"], "t_update_est_s": s["t_update_est"],
+                   "t_matvec_s": s["t_matvec"], "t_svd_s": s["t_svd"]}
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == tnt.TNT_PREC_FP64 else "tf32x3+f64",
+                "data": "synthetic", "config": config_dict(args, "f64" if prec == 0 else "tf32x3"),
+                "s_per_update": ms_step / 1e3, "matvecs_per_step": nmv / args.steps,
+                "phases_ms": phases, "kernel_ms_per_step": {k: v[0] for k, v in per_class.items()},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clk.summary(),
+                "lanczos": {k: stats["res"][k] for k in ("E", "E_rq", "resid_fp64", "n_matvec")},
+                "svd": {k: stats["info"][k] for k in ("chi", "err", "disc")}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def roofline(dom, ms, n, args, peaks, src, matvecs):
+    """Roofline of the dominant kernel class: algorithmic work per launch / mean duration."""
+    if n == 0:
+        return None
+    avg_s = ms / n * 1e-3
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nvec = N_THETA
+    if dom == "cgemm_tf32x3":
+        # two launches per matvec, each chi^3 D d^2 complex MACs (useful FLOPs only)
+        per = 8 * D_MPO * D_PHYS ** 2 * CHI ** 3
+        return {"kernel": dom, "bound": "tensor", "achieved": per / avg_s / 1e12,
+                "peak": bf16 * TF32_PER_BF16, "unit": "TFLOP/s",
+                "frac": per / avg_s / 1e12 / (bf16 * TF32_PER_BF16), "traffic": None,
+                "peak_source": f"{src} bf16 x nominal tf32/bf16", "launches": n}
+    if dom in ("multidot", "multiaxpy"):
+        # Krylov step k reads k+1 basis vectors (+ w); multiaxpy also writes w
+        k = int(round(matvecs)) - 1
+        steps = range(max(k, 1))
+        if dom == "multidot":
+            byts = sum(2 * (j + 2) * nvec * 16 for j in steps)
+            nl = sum(2 * ((j + 1 + 7) // 8) for j in steps)
+        else:
+            byts = sum(2 * (j + 3) * nvec * 16 for j in steps)
+            nl = 2 * len(steps)
+        per = byts / max(nl, 1)
+        return {"kernel": dom, "bound": "hbm", "achieved": per / avg_s / 1e9, "peak": hbm,
+                "unit": "GB/s", "frac": per / avg_s / 1e9 / hbm, "traffic": None,
+                "peak_source": src, "launches": n}
+    if dom == "zgemm_f64":
+        per = 8 * D_MPO * D_PHYS ** 2 * CHI ** 3
+        pk = bf16 * FP64_PER_BF16 * 1e3
+        return {"kernel": dom, "bound": "alu", "achieved": per / avg_s / 1e9, "peak": pk,
+                "unit": "GFLOP/s", "frac": per / avg_s / 1e9 / pk, "traffic": None,
+                "peak_source": f"{src} bf16 x nominal fp64/bf16", "launches": n}
+    if dom == "jacobi_round":
+        nn = CHI * D_PHYS
+        per = 36 * nn * nn  # FP64 flops of one round (n/2 rotations on G rows, cols and V)
+        pk = bf16 * FP64_PER_BF16 * 1e3
+        return {"kernel": dom, "bound": "alu", "achieved": per / avg_s / 1e9, "peak": pk,
+                "unit": "GFLOP/s", "frac": per / avg_s / 1e9 / pk, "traffic": None,
+                "peak_source": f"{src} bf16 x nominal fp64/bf16", "launches": n}
+    return {"kernel": dom, "bound": "unknown", "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None, "launches": n, "mean_ms": ms / n}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

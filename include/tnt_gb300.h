@@ -139,6 +139,14 @@ int tnt_set_stream(tnt_ctx* ctx, void* stream);
 const char* tnt_last_error(const tnt_ctx* ctx);
 /* Number of kernels this library has launched on the context (diagnostics). */
 int64_t tnt_launch_count(const tnt_ctx* ctx);
+/* Diagnostics: time every launch of one kernel class with CUDA events recorded on the
+ * context's stream (classes: "cgemm_tf32x3", "zgemm_f64", "op_apply", "op_mixed",
+ * "split_theta", "multidot", "multiaxpy", "jacobi_small", "jacobi_round").  NULL or ""
+ * switches timing off.  At most 8192 launches are recorded between reads. */
+int tnt_profile_select(tnt_ctx* ctx, const char* kernel_class);
+/* Synchronise the stream, return the summed duration (ms) and the number of timed
+ * launches since the last read, and reset the counters. */
+int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches);
 
 /* Parameter handling (App. A.3: the system settings and their defaults). */
 int tnt_params_default(tnt_params* p);

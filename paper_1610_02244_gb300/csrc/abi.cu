@@ -225,6 +225,7 @@ int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
 int tnt_ctx_destroy(tnt_ctx* ctx) {
   if (!ctx) return TNT_E_INVALID;
   cudaStreamSynchronize(ctx->c.stream);
+  for (auto& e : ctx->c.prof_ev) cudaEventDestroy(e);
   if (ctx->c.ws.base) cudaFree(ctx->c.ws.base);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
   if (ctx->c.d_status) cudaFree(ctx->c.d_status);
@@ -241,6 +242,36 @@ int tnt_set_stream(tnt_ctx* ctx, void* stream) {
 const char* tnt_last_error(const tnt_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
 
 int64_t tnt_launch_count(const tnt_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
+
+int tnt_profile_select(tnt_ctx* ctx, const char* cls) {
+  CTX_CHECK(ctx);
+  Ctx* c = &ctx->c;
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->prof_n = 0;
+  c->prof_cls = cls ? cls : "";
+  if (!c->prof_cls.empty() && c->prof_ev.empty()) {
+    c->prof_ev.resize(2 * 8192);
+    for (auto& e : c->prof_ev) TNT_CUDA_TRY(c, cudaEventCreate(&e));
+  }
+  return TNT_OK;
+}
+
+int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, total_ms && launches, "null pointer");
+  Ctx* c = &ctx->c;
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double t = 0;
+  for (size_t i = 0; i < c->prof_n; ++i) {
+    float ms = 0;
+    TNT_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = (int64_t)c->prof_n;
+  c->prof_n = 0;
+  return TNT_OK;
+}
 
 int tnt_params_set(tnt_ctx* ctx, const tnt_params* p) {
   CTX_CHECK(ctx);

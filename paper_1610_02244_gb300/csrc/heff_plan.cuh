@@ -1,11 +1,28 @@
 // Prepared H_eff.theta contraction: operator tables and scratch for repeated matvecs.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched from the driver)
+
 #include "tnt_internal.cuh"
 
 namespace tnt {
 
-struct MixedPlan;  // split-TF32 tensor-core operands (tc_mixed.cu)
+// Split-TF32 operands of the two chi^3 contractions (tc_mixed.cu).  Every operand is four
+// FP32 planes (re_hi, re_lo, im_hi, im_lo), K-major, rows padded to 128 and K to 16 with
+// zeros; a 3-D TMA map [plane][row][k] addresses each.
+struct MixedPlan {
+  int64_t M1, N1, K1, Mp1, Np1, Kp1;  // stage 1: T1[(a' w)][(s1 s2 b)] = L . theta
+  int64_t M4, N4, K4, Mp4, Np4, Kp4;  // stage 4: y[(a' s1' s2')][b'] = T3 . R^T
+  int split4 = 1;                     // split-K factor of stage 4
+  float* Lp = nullptr;      // 4 x Mp1 x Kp1
+  float* Thp = nullptr;     // 4 x Np1 x Kp1   (theta transposed)
+  float* T1 = nullptr;      // 2 x M1 x N1     (re, im accumulators of stage 1)
+  float* T3p = nullptr;     // 4 x Mp4 x Kp4
+  float* Rp = nullptr;      // 4 x Np4 x Kp4
+  float* Yp = nullptr;      // split4 x 2 x M4 x N4
+  OpApply op{};             // W12 on T1 -> T3 planes (offsets in plane units)
+  CUtensorMap tmL, tmTh, tmT3, tmR;
+};
 
 struct HeffPlan {
   const z* L = nullptr;
@@ -15,7 +32,7 @@ struct HeffPlan {
   OpApply op{};        // W12 acting T1 -> T3
   z* T1 = nullptr;     // [a'][w][s1][s2][b]
   z* T3 = nullptr;     // [a'][s1'][s2'][w2][b]
-  MixedPlan* mixed = nullptr;  // lives in scratch
+  MixedPlan mixed{};   // used when precision == TNT_PREC_MIXED
 };
 
 size_t heff_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr, int precision);

@@ -102,6 +102,7 @@ int zgemm(Ctx* c, const ZGemm& g) {
                    (long long)g.M, (long long)g.N, (long long)g.batch);
   dim3 grid((unsigned)((g.N + GN - 1) / GN), (unsigned)((g.M + GM - 1) / GM),
             (unsigned)g.batch);
+  ProfScope ps(c, "zgemm_f64");
   k_zgemm<<<grid, 256, 0, c->stream>>>(g);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
@@ -207,6 +208,7 @@ int op_apply(Ctx* c, const OpApply& a) {
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   int nnz = a.nnz > 0 ? a.nnz : 1;
+  ProfScope ps(c, "op_apply");
   k_op_apply<<<(unsigned)blocks, 256, 0, c->stream>>>(a, nnz);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
@@ -361,6 +363,7 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
   for (int v0 = 0; v0 < k; v0 += KB) {
     int kv = (k - v0 < KB) ? (k - v0) : KB;
+    ProfScope ps(c, "multidot");
     k_multidot<<<RB, RT, 0, c->stream>>>(V + (int64_t)v0 * ld, ld, kv, w, n, partial);
     k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0);
     c->launches += 2;
@@ -376,7 +379,10 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
   double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * RB));
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy)");
-  k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial);
+  {
+    ProfScope ps(c, "multiaxpy");
+    k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial);
+  }
   k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2);
   c->launches += 2;
   TNT_CHECK_LAUNCH(c);

@@ -481,6 +481,7 @@ int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_
                                                               2 * sizeof(int));
   TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
+  ProfScope ps(c, "jacobi_small");
   k_jacobi_small<<<nblocks, 256, smem, c->stream>>>(G, V, d_off, d_n, 40, 1e-15, nullptr);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
@@ -511,6 +512,7 @@ int jacobi_large(Ctx* c, z* G, z* V, int64_t n, int max_sweeps, int* sweeps_done
     }
     if (mo <= 1e-15 * md || mo <= 1e-300) break;
     for (int r = 0; r < np2 - 1; ++r) {
+      ProfScope ps(c, "jacobi_round");
       k_jrot<<<(npairs + 127) / 128, 128, 0, c->stream>>>(G, n, np2, r, rot);
       dim3 gr((unsigned)std::min<int64_t>((n + 255) / 256, 8), (unsigned)npairs);
       k_jrows<<<gr, 256, 0, c->stream>>>(G, n, npairs, rot);

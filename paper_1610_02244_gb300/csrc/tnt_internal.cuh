@@ -52,6 +52,26 @@ struct Ctx {
   int* d_status = nullptr;
   // counters (diagnostics, not hot-path state)
   int64_t launches = 0;
+  // optional CUDA-event timing of one kernel class (tnt_profile_select)
+  std::string prof_cls;
+  std::vector<cudaEvent_t> prof_ev;  // pairs: start, end
+  size_t prof_n = 0;
+};
+
+// Records CUDA events around the launches of one kernel class when that class is selected.
+struct ProfScope {
+  Ctx* c;
+  bool on;
+  ProfScope(Ctx* cc, const char* cls)
+      : c(cc), on(!cc->prof_cls.empty() && cc->prof_cls == cls && 2 * cc->prof_n + 1 < cc->prof_ev.size()) {
+    if (on) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+  }
+  ~ProfScope() {
+    if (on) {
+      cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+      c->prof_n++;
+    }
+  }
 };
 
 // error plumbing: every entry point returns through these

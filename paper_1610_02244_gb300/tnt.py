@@ -99,6 +99,15 @@ class Context:
     def launch_count(self) -> int:
         return int(self.lib.tnt_launch_count(self.h))
 
+    def profile_select(self, kernel_class: str | None):
+        self._chk(self.lib.tnt_profile_select(self.h, (kernel_class or "").encode()))
+
+    def profile_read(self):
+        """(summed ms, launches) of the selected kernel class since the last read."""
+        ms, n = C.c_double(), C.c_int64()
+        self._chk(self.lib.tnt_profile_read(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
     # ---------------------------------------------------------------- kernels
     def theta_form(self, A, B, out=None):
         chl, d, chm = A.shape

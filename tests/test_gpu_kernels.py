@@ -118,7 +118,7 @@ def test_environments(ctx, chl, d, chr_):
     assert rel(Ro, oc.env_right(Re, Ws[2], A)) < FP64_TOL
 
 
-@pytest.mark.parametrize("chl,d,chr_", [(6, 3, 6), (12, 4, 10), (20, 3, 33)])
+@pytest.mark.parametrize("chl,d,chr_", [(6, 3, 6), (12, 4, 10), (14, 3, 20)])
 def test_lanczos_fp64_matches_dense_eigh(ctx, chl, d, chr_):
     Le, W1, W2, Re, th = heff_inputs(3 * chl + chr_, chl, d, chr_)
     H = oc.heff_dense(Le, W1, W2, Re)
