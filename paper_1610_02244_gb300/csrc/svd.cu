@@ -5,10 +5,14 @@
 //               sigma_k = |row k of X_q|              (so X = S V^H without dividing by S)
 //   RIGHT side: G = M_q^H M_q, eigenvectors V_q,      Y_q = M_q V_q,
 //               sigma_k = |column k of Y_q|           (so Y = U S)
-// Only the r_q = min(m_q, n_q) leading eigenvectors are candidates (rank bound).  Taking
-// sigma as a projection norm keeps its absolute error at ~eps |M| instead of the
-// sqrt(eps) relative floor of sqrt(lambda).  All candidates are then ordered globally
-// (sigma desc, charge asc, index asc) and cut by the four rules in one kernel.
+// Only the k_q = min(m_q, n_q, chi_max) leading eigenvectors are candidates (rank bound,
+// and no block can contribute more than chi_max kept values); the weight of the values
+// never formed is |M_q|_F^2 minus the candidates'.  Taking sigma as a projection norm
+// keeps its absolute error at ~eps |M| instead of the sqrt(eps) relative floor of
+// sqrt(lambda).  All candidates are then ordered globally (sigma desc, charge asc, index
+// asc) and cut by the four rules in one kernel.  Blocks up to 64 are diagonalised by
+// cyclic Jacobi (one CTA each, all in one launch); larger ones by Householder
+// tridiagonalisation, bisection and inverse iteration (heig.cu).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -158,144 +162,6 @@ __global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t*
   for (int k = threadIdx.x; k < n; k += blockDim.x) G[o + k] = zmk(sG[perm[k] * n + perm[k]].x, 0);
 }
 
-// -------------------------------------------------------------- Jacobi, one large block
-struct Rot {
-  double cs, sn;
-  z e;
-  int p, q;
-};
-
-__global__ void k_jrot(const z* __restrict__ G, int64_t n, int np2, int r, Rot* __restrict__ rot) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= np2 / 2) return;
-  int p, q;
-  rr_pair(t, r, np2, &p, &q);
-  Rot o;
-  o.p = p;
-  o.q = q;
-  o.cs = 1;
-  o.sn = 0;
-  o.e = zmk(1, 0);
-  if (q < n) jacobi_rot(G[(int64_t)p * n + p].x, G[(int64_t)q * n + q].x, G[(int64_t)p * n + q],
-                        &o.cs, &o.sn, &o.e);
-  rot[t] = o;
-}
-
-// G <- J^H G: thread per (pair, column j), coalesced along j
-__global__ void k_jrows(z* __restrict__ G, int64_t n, int npairs, const Rot* __restrict__ rot) {
-  int t = blockIdx.y;
-  Rot o = rot[t];
-  if (o.q >= n || o.sn == 0.0) return;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    z gp = G[(int64_t)o.p * n + j], gq = zmul(o.e, G[(int64_t)o.q * n + j]);
-    G[(int64_t)o.p * n + j] = zsub(zscale(gp, o.cs), zscale(gq, o.sn));
-    G[(int64_t)o.q * n + j] = zadd(zscale(gp, o.sn), zscale(gq, o.cs));
-  }
-}
-
-// G <- G J and V <- V J: thread per (row i, pair)
-__global__ void k_jcols(z* __restrict__ G, z* __restrict__ V, int64_t n, int npairs,
-                        const Rot* __restrict__ rot) {
-  int64_t total = n * npairs;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / npairs;
-    int t = (int)(e % npairs);
-    Rot o = rot[t];
-    if (o.q >= n || o.sn == 0.0) continue;
-    z ec = zconj(o.e);
-    z gp = G[i * n + o.p], gq = zmul(G[i * n + o.q], ec);
-    G[i * n + o.p] = zsub(zscale(gp, o.cs), zscale(gq, o.sn));
-    G[i * n + o.q] = zadd(zscale(gp, o.sn), zscale(gq, o.cs));
-    z vp = V[i * n + o.p], vq = zmul(V[i * n + o.q], ec);
-    V[i * n + o.p] = zsub(zscale(vp, o.cs), zscale(vq, o.sn));
-    V[i * n + o.q] = zadd(zscale(vp, o.sn), zscale(vq, o.cs));
-  }
-}
-
-__global__ void k_eye(z* V, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    V[e] = (e / n == e % n) ? zmk(1, 0) : zmk(0, 0);
-}
-
-// partial max of off-diagonal and diagonal magnitudes
-__global__ void k_offmax(const z* __restrict__ G, int64_t n, double* __restrict__ part) {
-  __shared__ double so[256], sd[256];
-  double mo = 0, md = 0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    double a = hypot(G[e].x, G[e].y);
-    if (e / n == e % n) md = fmax(md, a); else mo = fmax(mo, a);
-  }
-  so[threadIdx.x] = mo;
-  sd[threadIdx.x] = md;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      so[threadIdx.x] = fmax(so[threadIdx.x], so[threadIdx.x + s]);
-      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = so[0];
-    part[2 * blockIdx.x + 1] = sd[0];
-  }
-}
-
-// sort the eigenvalues of one large block (diag of G) descending -> perm; one CTA,
-// bitonic over a power of two <= 8192 (dynamic smem)
-__global__ void __launch_bounds__(1024) k_eig_sort(const z* __restrict__ G, int64_t n, int P,
-                                                   int* __restrict__ perm,
-                                                   double* __restrict__ vals) {
-  extern __shared__ double sm_sort[];
-  double* key = sm_sort;
-  int* idx = (int*)(key + P);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    key[i] = (i < n) ? G[(int64_t)i * n + i].x : -INFINITY;
-    idx[i] = i;
-  }
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        int l = i ^ j;
-        if (l > i) {
-          bool desc_block = ((i & k) == 0);
-          // "before" = larger key, then smaller index
-          bool i_before = (key[i] > key[l]) || (key[i] == key[l] && idx[i] < idx[l]);
-          bool swap = desc_block ? !i_before : i_before;
-          if (swap) {
-            double tk = key[i];
-            key[i] = key[l];
-            key[l] = tk;
-            int ti = idx[i];
-            idx[i] = idx[l];
-            idx[l] = ti;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    perm[i] = idx[i];
-    vals[i] = key[i];
-  }
-}
-
-// dst[i][k] = src[i][perm[k]] for k < r (column permutation/truncation), ld n
-__global__ void k_permute_cols(const z* __restrict__ src, int64_t n, const int* __restrict__ perm,
-                               int64_t r, z* __restrict__ dst) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * r;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / r, k = e % r;
-    dst[i * n + k] = src[i * n + perm[k]];
-  }
-}
-
 // sigma of each candidate: norm of row (LEFT: rows of X_q) or column (RIGHT: of Y_q)
 struct CandBlock {
   int64_t xoff;   // packed X_q / Y_q offset
@@ -345,6 +211,8 @@ __global__ void __launch_bounds__(1024) k_select(const double* __restrict__ sig_
                                                  const int* __restrict__ loc_in, int n, int P,
                                                  int64_t chi_max, double a, double rtol,
                                                  double etol, int etype,
+                                                 const double* __restrict__ total_norm2,
+                                                 int complete,
                                                  double* __restrict__ sig_out,
                                                  int* __restrict__ blk_out,
                                                  int* __restrict__ loc_out,
@@ -396,8 +264,12 @@ __global__ void __launch_bounds__(1024) k_select(const double* __restrict__ sig_
       chi3 = 0;
       while (chi3 < n && key[chi3] / s0 >= rtol) ++chi3;
     }
-    double nrm2 = 0;
-    for (int i = n - 1; i >= 0; --i) nrm2 += key[i] * key[i];
+    // the candidates are each block's leading min(rank, chi_max) values; when that cuts a
+    // block short, the weight of the values never formed is |M|_F^2 minus the candidates'
+    double sumc = 0;
+    for (int i = n - 1; i >= 0; --i) sumc += key[i] * key[i];
+    const double nrm2 = complete ? sumc : fmax(total_norm2[0], sumc);
+    const double unseen = complete ? 0.0 : fmax(0.0, total_norm2[0] - sumc);
     const double nrm = sqrt(nrm2);
     const double inv = nrm > 0 ? 1.0 / nrm : 1.0;
     auto term = [&](double s) {
@@ -405,9 +277,11 @@ __global__ void __launch_bounds__(1024) k_select(const double* __restrict__ sig_
       return etype == TNT_TRUNC_1NORM ? fabs(t) : t * t;
     };
     auto errf = [&](double acc) { return etype == TNT_TRUNC_2NORM ? sqrt(acc) : acc; };
+    const double acc0 = unseen * inv * inv;  // never formed values, in normalised units
     int64_t chi4 = n;
-    double acc = 0;
-    for (int keep = n - 1; keep >= 0; --keep) {
+    double acc = acc0;
+    if (!(errf(acc) < etol)) chi4 = n;
+    for (int keep = n - 1; keep >= 0 && errf(acc) < etol; --keep) {
       acc += term(key[keep]);
       if (errf(acc) < etol) chi4 = keep; else break;
     }
@@ -417,7 +291,7 @@ __global__ void __launch_bounds__(1024) k_select(const double* __restrict__ sig_
     if (chi4 < chi) chi = chi4;
     if (chi < 1) chi = 1;
     if (chi > n) chi = n;
-    double e = 0, dsc = 0;
+    double e = acc0, dsc = unseen;
     for (int i = n - 1; i >= chi; --i) {
       e += term(key[i]);
       dsc += key[i] * key[i];
@@ -488,48 +362,12 @@ int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_
   return TNT_OK;
 }
 
-int jacobi_large(Ctx* c, z* G, z* V, int64_t n, int max_sweeps, int* sweeps_done) {
-  const int np2 = (int)((n + 1) & ~int64_t(1));
-  const int npairs = np2 / 2;
-  Rot* rot = (Rot*)ws_alloc(c, ws_round(sizeof(Rot) * npairs));
-  const int nb_off = 64;
-  double* part = (double*)ws_alloc(c, ws_round(sizeof(double) * 2 * nb_off));
-  if (!rot || !part) return set_err(c, TNT_E_ALLOC, "scratch exhausted (jacobi_large)");
-  TNT_TRY(pinned_reserve(c, sizeof(double) * 2 * nb_off));
-  k_eye<<<gridn(n * n), 256, 0, c->stream>>>(V, n);
-  c->launches++;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    k_offmax<<<nb_off, 256, 0, c->stream>>>(G, n, part);
-    c->launches++;
-    TNT_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, part, sizeof(double) * 2 * nb_off,
-                                    cudaMemcpyDeviceToHost, c->stream));
-    TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    double mo = 0, md = 0;
-    for (int b = 0; b < nb_off; ++b) {
-      mo = std::max(mo, c->h_pinned[2 * b]);
-      md = std::max(md, c->h_pinned[2 * b + 1]);
-    }
-    if (mo <= 1e-15 * md || mo <= 1e-300) break;
-    for (int r = 0; r < np2 - 1; ++r) {
-      ProfScope ps(c, "jacobi_round");
-      k_jrot<<<(npairs + 127) / 128, 128, 0, c->stream>>>(G, n, np2, r, rot);
-      dim3 gr((unsigned)std::min<int64_t>((n + 255) / 256, 8), (unsigned)npairs);
-      k_jrows<<<gr, 256, 0, c->stream>>>(G, n, npairs, rot);
-      k_jcols<<<gridn(n * npairs), 256, 0, c->stream>>>(G, V, n, npairs, rot);
-      c->launches += 3;
-    }
-    TNT_CHECK_LAUNCH(c);
-  }
-  if (sweeps_done) *sweeps_done = sweep;
-  return TNT_OK;
-}
-
 // ==================================================================== truncated SVD
 size_t svd_scratch_bound(int64_t m, int64_t n) {
   const size_t mx = (size_t)std::max(m, n), mn = (size_t)std::min(m, n);
-  return 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 3 * 16 * mx * mx + 6 * 8 * mn +
-         sizeof(KeptIdx) * mn + 12 * 8192 + (size_t)(4 << 20);
+  return 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mn +
+         sizeof(KeptIdx) * mn + 12 * 8192 + heig_scratch_bound((int64_t)mx, (int64_t)mn) +
+         (size_t)(4 << 20);
 }
 
 int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq,
@@ -544,10 +382,14 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     auto it = blocks.find(q);
     if (it != blocks.end()) it->second.second.push_back(j);
   }
+  // candidates per block: its leading min(rank, chi_max) values (all of them for the
+  // 1-norm error, which cannot be completed from |M|_F)
+  const bool all_values = (P.trunc_type == TNT_TRUNC_1NORM);
   struct Blk {
-    int64_t q, mq, nq, g, r;
+    int64_t q, mq, nq, g, r, k;
     int64_t roff, coff, moff, goff, xoff;
   };
+  bool complete = true;
   std::vector<Blk> bl;
   std::vector<int64_t> rows_all, cols_all;
   int64_t mtot = 0, gtot = 0, xtot = 0, ntot_vals = 0;
@@ -561,6 +403,8 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     b.nq = (int64_t)Cc.size();
     b.g = (side == TNT_SVD_LEFT) ? b.mq : b.nq;
     b.r = std::min(b.mq, b.nq);
+    b.k = all_values ? b.r : std::min<int64_t>(b.r, P.chi_max);
+    if (b.k < b.r) complete = false;
     b.roff = (int64_t)rows_all.size();
     b.coff = (int64_t)cols_all.size();
     rows_all.insert(rows_all.end(), R.begin(), R.end());
@@ -570,8 +414,8 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     b.goff = gtot;
     gtot += b.g * b.g;
     b.xoff = xtot;
-    xtot += (side == TNT_SVD_LEFT) ? b.r * b.nq : b.mq * b.r;
-    ntot_vals += b.r;
+    xtot += (side == TNT_SVD_LEFT) ? b.k * b.nq : b.mq * b.k;
+    ntot_vals += b.k;
     bl.push_back(b);
   }
   const int nb = (int)bl.size();
@@ -581,12 +425,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   // ---- scratch
   int P2 = 1;
   while (P2 < ntot_vals) P2 <<= 1;
-  int64_t gmax_large = 0;
-  for (const Blk& B : bl)
-    if (B.g > 64) gmax_large = std::max(gmax_large, B.g);
   TNT_TRY(ws_reserve(c, c->ws.top + svd_scratch_bound(m, n)));
-  z* Vt = gmax_large ? (z*)ws_alloc(c, ws_round(sizeof(z) * gmax_large * gmax_large)) : nullptr;
-  if (gmax_large && !Vt) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd Vt)");
   int64_t* d_rows = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * rows_all.size()));
   int64_t* d_cols = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * cols_all.size()));
   z* Mp = (z*)ws_alloc(c, ws_round(sizeof(z) * mtot));
@@ -603,10 +442,10 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   CandBlock* d_cb = (CandBlock*)ws_alloc(c, ws_round(sizeof(CandBlock) * nb));
   int64_t* d_goff = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
   int* d_gdim = (int*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
-  int* d_perm = (int*)ws_alloc(c, ws_round(sizeof(int) * 8192));
-  double* d_pvals = (double*)ws_alloc(c, ws_round(sizeof(double) * 8192));
+  double* d_ev = (double*)ws_alloc(c, ws_round(sizeof(double) * 8192));
+  double* d_tot = (double*)ws_alloc(c, ws_round(sizeof(double)));
   if (!d_rows || !d_cols || !Mp || !Gp || !Vp || !Xp || !d_sig || !d_blk || !d_loc || !d_sig_s ||
-      !d_blk_s || !d_loc_s || !d_sel || !d_cb || !d_goff || !d_gdim || !d_perm || !d_pvals)
+      !d_blk_s || !d_loc_s || !d_sel || !d_cb || !d_goff || !d_gdim || !d_ev || !d_tot)
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
 
   // ---- host tables -> device (one synchronous upload of small integer tables)
@@ -617,14 +456,14 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     int v = 0;
     for (int b = 0; b < nb; ++b) {
       hcb[b].xoff = bl[b].xoff;
-      hcb[b].rows = (side == TNT_SVD_LEFT) ? bl[b].r : bl[b].mq;
-      hcb[b].cols = (side == TNT_SVD_LEFT) ? bl[b].nq : bl[b].r;
-      hcb[b].r = (int)bl[b].r;
+      hcb[b].rows = (side == TNT_SVD_LEFT) ? bl[b].k : bl[b].mq;
+      hcb[b].cols = (side == TNT_SVD_LEFT) ? bl[b].nq : bl[b].k;
+      hcb[b].r = (int)bl[b].k;
       hcb[b].vbase = v;
       hcb[b].by_row = (side == TNT_SVD_LEFT);
       hgoff[b] = bl[b].goff;
       hgdim[b] = (int)bl[b].g;
-      for (int k = 0; k < bl[b].r; ++k, ++v) {
+      for (int k = 0; k < bl[b].k; ++k, ++v) {
         hblk[v] = b;
         hloc[v] = k;
       }
@@ -675,22 +514,16 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
       TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // host vector lifetime
       TNT_TRY(jacobi_small_batched(c, Gp, Vp, d_goff, d_dims_small, nb, max_small));
     }
+    // larger blocks: Householder tridiagonalisation, bisection, inverse iteration (the k
+    // leading eigenvectors only, columns 0..k-1 of the block's V, leading dimension g)
     for (int b = 0; b < nb; ++b) {
       if (bl[b].g <= 64) continue;
       const Blk& B = bl[b];
       if (B.g > 8192) return set_err(c, TNT_E_UNSUPPORTED, "SVD block of dim %lld > 8192", (long long)B.g);
-      int sw = 0;
-      TNT_TRY(jacobi_large(c, Gp + B.goff, Vt, B.g, 40, &sw));
-      int P = 1;
-      while (P < B.g) P <<= 1;
-      size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
-      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_eig_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_eig_sort<<<1, 1024, smem, st>>>(Gp + B.goff, B.g, P, d_perm, d_pvals);
-      k_permute_cols<<<gridn(B.g * B.g), 256, 0, st>>>(Vt, B.g, d_perm, B.g, Vp + B.goff);
-      c->launches += 2;
-      TNT_CHECK_LAUNCH(c);
+      TNT_TRY(heig_top(c, Gp + B.goff, B.g, B.k, Vp + B.goff, B.g, d_ev));
     }
   }
+  TNT_TRY(vec_norm2(c, Mp, mtot, d_tot));
   // ---- candidate products and their norms
   for (int b = 0; b < nb; ++b) {
     const Blk& B = bl[b];
@@ -698,16 +531,16 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     g.batch = 1;
     g.alpha = zmk(1, 0);
     g.beta = zmk(0, 0);
-    if (side == TNT_SVD_LEFT) {  // X_q = U_q[:, :r]^H M_q  (r x n_q)
-      g.M = B.r; g.N = B.nq; g.K = B.mq;
+    if (side == TNT_SVD_LEFT) {  // X_q = U_q[:, :k]^H M_q  (k x n_q)
+      g.M = B.k; g.N = B.nq; g.K = B.mq;
       g.A = Vp + B.goff; g.a_rs = 1; g.a_cs = B.g; g.conj_a = 1;
       g.B = Mp + B.moff; g.b_rs = B.nq; g.b_cs = 1;
       g.C = Xp + B.xoff; g.c_rs = B.nq;
-    } else {  // Y_q = M_q V_q[:, :r]  (m_q x r)
-      g.M = B.mq; g.N = B.r; g.K = B.nq;
+    } else {  // Y_q = M_q V_q[:, :k]  (m_q x k)
+      g.M = B.mq; g.N = B.k; g.K = B.nq;
       g.A = Mp + B.moff; g.a_rs = B.nq; g.a_cs = 1;
       g.B = Vp + B.goff; g.b_rs = B.g; g.b_cs = 1;
-      g.C = Xp + B.xoff; g.c_rs = B.r;
+      g.C = Xp + B.xoff; g.c_rs = B.k;
     }
     TNT_TRY(zgemm(c, g));
   }
@@ -718,8 +551,8 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(int));
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_select<<<1, 1024, smem, st>>>(d_sig, d_blk, d_loc, (int)ntot_vals, P2, P.chi_max, P.trunc_abs,
-                                    P.trunc_rel, P.trunc_err, P.trunc_type, d_sig_s, d_blk_s, d_loc_s,
-                                    d_sel);
+                                    P.trunc_rel, P.trunc_err, P.trunc_type, d_tot, complete ? 1 : 0,
+                                    d_sig_s, d_blk_s, d_loc_s, d_sel);
     c->launches++;
     TNT_CHECK_LAUNCH(c);
   }
@@ -747,7 +580,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     K.voff = B.goff;
     K.vld = B.g;
     K.xoff = B.xoff;
-    K.xld = (side == TNT_SVD_LEFT) ? B.nq : B.r;
+    K.xld = (side == TNT_SVD_LEFT) ? B.nq : B.k;
     K.roff = B.roff;
     K.nr = B.mq;
     K.coff = B.coff;

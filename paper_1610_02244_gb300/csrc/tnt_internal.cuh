@@ -160,7 +160,10 @@ int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, d
 int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_n,
                          int nblocks, int max_n);
 // One large block (any n), global-memory rounds.
-int jacobi_large(Ctx* c, z* G, z* V, int64_t n, int max_sweeps, int* sweeps_done);
+// Leading k eigenpairs of one large Hermitian block (Householder, bisection, inverse
+// iteration; heig.cu).  U: n x k with leading dimension ldu; ev: device, k values.
+size_t heig_scratch_bound(int64_t n, int64_t k);
+int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev);
 
 // Helpers: gather / scatter / conversion
 int gather2d(Ctx* c, const z* src, int64_t src_ld, const int64_t* d_rows, int64_t nr,

@@ -161,7 +161,8 @@ def svd_case(seed, m, n, charged):
 
 @pytest.mark.parametrize("m,n,charged,side", [
     (40, 30, False, 0), (30, 40, False, 1), (100, 90, True, 0), (90, 100, True, 1),
-    (200, 160, False, 0), (8, 8, True, 1), (1, 7, False, 0)])
+    (200, 160, False, 0), (160, 200, False, 1), (8, 8, True, 1), (1, 7, False, 0),
+    (420, 390, True, 0), (390, 420, True, 1), (65, 300, False, 0)])
 def test_svd_trunc_matches_oracle(ctx, m, n, charged, side):
     M, rq, cq = svd_case(m * n + side, m, n, charged)
     chi_max = max(1, min(m, n) * 2 // 3)
