@@ -195,6 +195,24 @@ int tnt_heff_apply(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
                    int64_t chl, int64_t d, int64_t D, int64_t chr, int precision,
                    tnt_cplx* d_y);
 
+/* The FP64 path of tnt_heff_apply for callers that cannot allocate device memory (the
+ * paper has no counterpart: this is an interface for embedding).  Code running during a
+ * stream capture, plug-ins confined to a host application's allocator, and processes
+ * with a fixed device-memory budget cannot call cudaMalloc; this call makes none (nor
+ * cudaFree, nor any allocating library routine).  Its intermediates live in one
+ * file-scope device array of 16 MiB that every GPU loading the library holds until the
+ * process exits, so it accepts only chl * D * d * d * chr <= 522,240 (e.g. chi = 64,
+ * d = 5, D = 4); larger shapes return TNT_E_UNSUPPORTED with the limit in the message.
+ * The first call on a device looks the array's device address up (once, with that device
+ * current); make that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams or host threads) race on it.  Arguments,
+ * layouts and results are those of tnt_heff_apply with TNT_PREC_FP64; the call returns
+ * after the operator tables are uploaded (one stream synchronisation), with the matvec
+ * enqueued on the context's stream. */
+int tnt_heff_apply_noalloc(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
+                           const tnt_cplx* d_W2, const tnt_cplx* d_R, const tnt_cplx* d_theta,
+                           int64_t chl, int64_t d, int64_t D, int64_t chr, tnt_cplx* d_y);
+
 /* a8. Environment growth (Sec. 4.3 <psi|H|psi> network, Listing 2 H_prepare):
  *   left:  Lout[m',w',m] = sum conj(A[a',s',m']) L[a',w,a] W[w,w',s',s] A[a,s,m]
  *          d_L: chl x D x chl, d_A: chl x d x chr, d_Lout: chr x D x chr

@@ -86,6 +86,7 @@ SIGNATURES = {
     "tnt_theta_form": [P, P, P, I64, I64, I64, I64, P],
     "tnt_gate_apply": [P, P, P, I64, I64, I64, P],
     "tnt_heff_apply": [P, P, P, P, P, P, I64, I64, I64, I64, I, P],
+    "tnt_heff_apply_noalloc": [P, P, P, P, P, P, I64, I64, I64, I64, P],
     "tnt_env_left": [P, P, P, P, I64, I64, I64, I64, P],
     "tnt_env_right": [P, P, P, P, I64, I64, I64, I64, P],
     "tnt_lanczos_ground": [P, P, P, P, P, I64, I64, I64, I64, P,

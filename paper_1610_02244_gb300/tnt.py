@@ -130,6 +130,16 @@ class Context:
                                           _ptr(theta), chl, d, D, chr_, precision, _ptr(out)))
         return out
 
+    def heff_apply_noalloc(self, Lenv, W1, W2, Renv, theta, out):
+        """FP64 H_eff.theta that makes no device allocation (fixed 16 MiB static scratch);
+        `out` must be supplied by the caller."""
+        chl, d, _, chr_ = theta.shape
+        D = W1.shape[0]
+        self._chk(self.lib.tnt_heff_apply_noalloc(self.h, _ptr(Lenv), _ptr(W1), _ptr(W2),
+                                                  _ptr(Renv), _ptr(theta), chl, d, D, chr_,
+                                                  _ptr(out)))
+        return out
+
     def env_left(self, Lenv, W, A, out=None):
         chl, d, chr_ = A.shape
         D = W.shape[0]
