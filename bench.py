@@ -277,14 +277,11 @@ def run_ours(args, ws, rank, local):
               for i, n in enumerate(["theta_ms", "lanczos_ms", "svd_ms", "env_ms"])}
 
     # dominant kernel class by summed device time over one step
-    classes = ["cgemm_tf32x3", "zgemm_f64", "op_apply", "op_mixed", "split_theta",
-               "multidot", "multiaxpy", "jacobi_small", "jacobi_round"]
     per_class = {}
-    for cls in classes:
+    for cls in CLASSES:
         ctx.profile_select(cls)
         step(t)
-        ms, n = ctx.profile_read()
-        per_class[cls] = (ms, n)
+        per_class[cls] = ctx.profile_read()
     ctx.profile_select(None)
     dom = max(per_class, key=lambda k: per_class[k][0])
 
@@ -305,7 +302,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
     barrier(ws)
     ms_total = e0.elapsed_time(e1)
-    dom_ms, dom_n = ctx.profile_read()
+    dom_ms, dom_n, dom_work = ctx.profile_read()
     ctx.profile_select(None)
     launches = ctx.launch_count() - launches0
     ms_step = dist_max(ms_total / args.steps, ws)
@@ -335,7 +332,8 @@ def run_ours(args, ws, rank, local):
     line = None
     if rank == 0:
         peaks, src = load_peaks()
-        roof = roofline(dom, dom_ms, dom_n, args, peaks, src, nmv / args.steps)
+        roof = roofline(dom, dom_ms, dom_n, dom_work, peaks, src)
+        kernel_roofs = {k: roofline(k, *v, peaks, src) for k, v in per_class.items() if v[1] > 0}
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             s = oracle_sample(inp, n_matvec=2)
@@ -350,6 +348,7 @@ def run_ours(args, ws, rank, local):
                 "data": "synthetic", "config": config_dict(args, "f64" if prec == 0 else "tf32x3"),
                 "s_per_update": ms_step / 1e3, "matvecs_per_step": nmv / args.steps,
                 "phases_ms": phases, "kernel_ms_per_step": {k: v[0] for k, v in per_class.items()},
+                "kernel_rooflines": kernel_roofs,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -361,50 +360,42 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
-def roofline(dom, ms, n, args, peaks, src, matvecs):
-    """Roofline of the dominant kernel class: algorithmic work per launch / mean duration."""
-    if n == 0:
+# kernel class -> (bound, what its work counts).  The library sums, per launch, the
+# algorithmic work: useful complex-product FLOPs (8 M N K; the split-TF32 repeats are not
+# counted) for the GEMM classes, FP64 FLOPs for the eigensolver, bytes read plus written
+# for the memory-bound vector and conversion kernels.
+CLASSES = {
+    "cgemm_tf32x3": ("tensor", "flop"), "zgemm_f64": ("alu", "flop"), "op_apply": ("alu", "flop"),
+    "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("hbm", "byte"),
+    "multiaxpy": ("hbm", "byte"), "jacobi_small": ("alu", None), "heig_tridiag": ("alu", "flop"),
+    "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
+}
+
+
+def roofline(cls, ms, n, work, peaks, src):
+    """Roofline of one kernel class: algorithmic work per launch / mean launch duration."""
+    if n == 0 or ms <= 0:
         return None
-    avg_s = ms / n * 1e-3
+    bound, unit = CLASSES[cls]
+    secs = ms * 1e-3
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    nvec = N_THETA
-    if dom == "cgemm_tf32x3":
-        # two launches per matvec, each chi^3 D d^2 complex MACs (useful FLOPs only)
-        per = 8 * D_MPO * D_PHYS ** 2 * CHI ** 3
-        return {"kernel": dom, "bound": "tensor", "achieved": per / avg_s / 1e12,
-                "peak": bf16 * TF32_PER_BF16, "unit": "TFLOP/s",
-                "frac": per / avg_s / 1e12 / (bf16 * TF32_PER_BF16), "traffic": None,
-                "peak_source": f"{src} bf16 x nominal tf32/bf16", "launches": n}
-    if dom in ("multidot", "multiaxpy"):
-        # Krylov step k reads k+1 basis vectors (+ w); multiaxpy also writes w
-        k = int(round(matvecs)) - 1
-        steps = range(max(k, 1))
-        if dom == "multidot":
-            byts = sum(2 * (j + 2) * nvec * 16 for j in steps)
-            nl = sum(2 * ((j + 1 + 7) // 8) for j in steps)
-        else:
-            byts = sum(2 * (j + 3) * nvec * 16 for j in steps)
-            nl = 2 * len(steps)
-        per = byts / max(nl, 1)
-        return {"kernel": dom, "bound": "hbm", "achieved": per / avg_s / 1e9, "peak": hbm,
-                "unit": "GB/s", "frac": per / avg_s / 1e9 / hbm, "traffic": None,
-                "peak_source": src, "launches": n}
-    if dom == "zgemm_f64":
-        per = 8 * D_MPO * D_PHYS ** 2 * CHI ** 3
-        pk = bf16 * FP64_PER_BF16 * 1e3
-        return {"kernel": dom, "bound": "alu", "achieved": per / avg_s / 1e9, "peak": pk,
-                "unit": "GFLOP/s", "frac": per / avg_s / 1e9 / pk, "traffic": None,
-                "peak_source": f"{src} bf16 x nominal fp64/bf16", "launches": n}
-    if dom == "jacobi_round":
-        nn = CHI * D_PHYS
-        per = 36 * nn * nn  # FP64 flops of one round (n/2 rotations on G rows, cols and V)
-        pk = bf16 * FP64_PER_BF16 * 1e3
-        return {"kernel": dom, "bound": "alu", "achieved": per / avg_s / 1e9, "peak": pk,
-                "unit": "GFLOP/s", "frac": per / avg_s / 1e9 / pk, "traffic": None,
-                "peak_source": f"{src} bf16 x nominal fp64/bf16", "launches": n}
-    return {"kernel": dom, "bound": "unknown", "achieved": None, "peak": None, "unit": None,
-            "frac": None, "traffic": None, "launches": n, "mean_ms": ms / n}
+    base = {"kernel": cls, "bound": bound, "launches": n, "mean_ms": ms / n, "traffic": None}
+    if unit is None or work <= 0:
+        return dict(base, achieved=None, peak=None, unit=None, frac=None)
+    if bound == "tensor":
+        pk = bf16 * TF32_PER_BF16
+        ach = work / secs / 1e12
+        return dict(base, achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                    peak_source=f"{src} bf16 burst x nominal tf32/bf16 ratio")
+    if bound == "hbm":
+        pk = peaks.get("hbm_gbs", 6800.0)
+        ach = work / secs / 1e9
+        return dict(base, achieved=ach, peak=pk, unit="GB/s", frac=ach / pk,
+                    peak_source=f"{src} copy bandwidth")
+    pk = bf16 * FP64_PER_BF16 * 1e3  # FP64 FLOP/s
+    ach = work / secs / 1e9
+    return dict(base, achieved=ach, peak=pk, unit="GFLOP/s", frac=ach / pk,
+                peak_source=f"{src} bf16 burst x nominal fp64/bf16 ratio")
 
 
 def main():

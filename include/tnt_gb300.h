@@ -140,13 +140,16 @@ const char* tnt_last_error(const tnt_ctx* ctx);
 /* Number of kernels this library has launched on the context (diagnostics). */
 int64_t tnt_launch_count(const tnt_ctx* ctx);
 /* Diagnostics: time every launch of one kernel class with CUDA events recorded on the
- * context's stream (classes: "cgemm_tf32x3", "zgemm_f64", "op_apply", "op_mixed",
- * "split_theta", "multidot", "multiaxpy", "jacobi_small", "jacobi_round").  NULL or ""
- * switches timing off.  At most 8192 launches are recorded between reads. */
+ * context's stream, and sum its algorithmic work.  Classes and their work unit:
+ *   "cgemm_tf32x3" (useful FLOPs 8 M N K of the complex product), "zgemm_f64" (8 M N K),
+ *   "op_apply" (FLOPs), "op_mixed", "split_theta", "multidot", "multiaxpy" (bytes read
+ *   plus written), "jacobi_small" (none), "heig_tridiag" (FLOPs), "heig_tridiag_eig"
+ *   (none), "heig_backtransform" (FLOPs).
+ * NULL or "" switches timing off.  At most 16384 launches are recorded between reads. */
 int tnt_profile_select(tnt_ctx* ctx, const char* kernel_class);
-/* Synchronise the stream, return the summed duration (ms) and the number of timed
- * launches since the last read, and reset the counters. */
-int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches);
+/* Synchronise the stream; return the summed duration (ms), the number of timed launches
+ * and their summed work since the last read; reset the counters. */
+int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches, double* work);
 
 /* Parameter handling (App. A.3: the system settings and their defaults). */
 int tnt_params_default(tnt_params* p);
@@ -226,7 +229,8 @@ int tnt_env_right(tnt_ctx* ctx, const tnt_cplx* d_R, const tnt_cplx* d_W,
                   tnt_cplx* d_Rout);
 
 /* a4 + a9. Lowest eigenpair of H_eff (Lanczos, full re-orthogonalisation by classical
- * Gram-Schmidt twice, FP64 vectors and tridiagonal solve; restart from the Ritz vector
+ * Gram-Schmidt, repeated once when the first pass cancelled more than 99% of the vector,
+ * FP64 vectors and tridiagonal solve; restart from the Ritz vector
  * every krylov_cap steps; at most lanczos_maxit matvecs; the library's eigensolver role of
  * Sec. 4.3).  Matvecs use ctx precision; with TNT_PREC_MIXED one more FP64 matvec gives
  * E_rq and resid_fp64.  d_theta (chl x d x d x chr) is the start vector on entry and the

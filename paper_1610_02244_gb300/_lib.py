@@ -76,7 +76,7 @@ SIGNATURES = {
     "tnt_last_error": [P],
     "tnt_launch_count": [P],
     "tnt_profile_select": [P, C.c_char_p],
-    "tnt_profile_read": [P, PD, PI64],
+    "tnt_profile_read": [P, PD, PI64, PD],
     "tnt_params_default": [C.POINTER(tnt_params)],
     "tnt_params_set": [P, C.POINTER(tnt_params)],
     "tnt_params_get": [P, C.POINTER(tnt_params)],

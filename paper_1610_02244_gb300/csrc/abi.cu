@@ -248,17 +248,18 @@ int tnt_profile_select(tnt_ctx* ctx, const char* cls) {
   Ctx* c = &ctx->c;
   TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->prof_n = 0;
+  c->prof_work = 0;
   c->prof_cls = cls ? cls : "";
   if (!c->prof_cls.empty() && c->prof_ev.empty()) {
-    c->prof_ev.resize(2 * 8192);
+    c->prof_ev.resize(2 * 16384);
     for (auto& e : c->prof_ev) TNT_CUDA_TRY(c, cudaEventCreate(&e));
   }
   return TNT_OK;
 }
 
-int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches) {
+int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches, double* work) {
   CTX_CHECK(ctx);
-  ARG_CHECK(ctx, total_ms && launches, "null pointer");
+  ARG_CHECK(ctx, total_ms && launches && work, "null pointer");
   Ctx* c = &ctx->c;
   TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   double t = 0;
@@ -269,7 +270,9 @@ int tnt_profile_read(tnt_ctx* ctx, double* total_ms, int64_t* launches) {
   }
   *total_ms = t;
   *launches = (int64_t)c->prof_n;
+  *work = c->prof_work;
   c->prof_n = 0;
+  c->prof_work = 0;
   return TNT_OK;
 }
 

@@ -5,11 +5,13 @@
 //      reflector H_j = I - tau v v^H maps the part below the diagonal to beta e_1 (beta
 //      real), and the trailing block is updated as A <- H_j^H A H_j through
 //      p = tau A v, w = p - (tau/2)(p^H v) v, A <- A - v w^H - w v^H.
-//   2. Bisection on Sturm counts of T for eigenvalues n-1, ..., n-k (one thread each).
-//   3. Inverse iteration on T - lambda I (pivoted tridiagonal LU, three sweeps, shifts of
-//      coincident eigenvalues separated by 10 eps |T|).
+//   2. Multisection on Sturm counts of T for eigenvalues n-1, ..., n-k (one warp each),
+//      to full precision.
+//   3. Inverse iteration on T - lambda I (pivoted tridiagonal LU, three sweeps); inside a
+//      cluster of eigenvalues closer than 1e3 eps |T| the shifts are separated by 10 eps |T|
+//      and each iterate is re-orthogonalised against the cluster's earlier vectors.
 //   4. Back-transformation U = H_0 H_1 ... H_{n-2} Y.
-//   5. One Newton-Schulz step U <- U (3 I - U^H U) / 2 in FP64 to restore orthonormality
+//   5. Two Newton-Schulz steps U <- U (3 I - U^H U) / 2 in FP64 to restore orthonormality
 //      lost to close eigenvalues.
 // All arithmetic is FP64.  The cost is O(n^3) once, against O(sweeps n^3) for Jacobi.
 #include <cmath>
@@ -39,24 +41,83 @@ __device__ double block_sum_all(double v, double* sh) {
   return r;
 }
 
-// reflector of column j from row j of the (Hermitian, fully stored) trailing matrix
-__global__ void k_hh_reflector(const z* __restrict__ G, int64_t n, int64_t j, z* __restrict__ Hv,
-                               z* __restrict__ tau, double* __restrict__ d,
-                               double* __restrict__ e) {
-  __shared__ double sh[32];
+// ---------------------------------------------------------------- persistent reduction
+// All columns in one cooperative launch.  Per column j (trailing size m = n - j - 1):
+//   barrier; p = tau A v (one warp per row, all blocks), per-block partial of p^H v;
+//   barrier; every block sums the partials (same order everywhere), updates the rows it
+//   owns (r = b, b + nb, ...); block 0 updates row 0 first and then forms the reflector
+//   of column j + 1 from that row.
+// The grid barrier spins on a generation counter with a %globaltimer limit; if any wait
+// expires, an abort flag makes every block leave at its next barrier.
+struct TriArgs {
+  z* G;
+  int64_t n;
+  z* Hv;
+  z* tau;
+  double* d;
+  double* e;
+  z* p;
+  z* part;             // nb partial sums of p^H v
+  unsigned* bar;       // [0] arrivals, [1] generation
+  int* abort_flag;
+  int* status;
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// returns false if the CTA must stop (a wait expired here or elsewhere)
+__device__ bool grid_barrier(const TriArgs& a) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = a.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(a.bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      a.bar[0] = 0;
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      const uint64_t t0 = gtime();
+      while (*gen == g) {
+        if (*(volatile int*)a.abort_flag) { ok = 0; break; }
+        if (gtime() - t0 > 2000000000ull) {
+          atomicOr(a.status, 2);
+          atomicExch(a.abort_flag, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)a.abort_flag) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// reflector of column j from row j of the trailing matrix (one block)
+__device__ void tri_reflector(const TriArgs& a, int64_t j, double* sh) {
   __shared__ double s_xn2;
-  const int64_t m = n - j - 1;
-  const z* row = G + j * n + j + 1;  // x_r = conj(row[r])
+  const int64_t n = a.n, m = n - j - 1;
+  const z* row = a.G + j * n + j + 1;  // x_r = conj(row[r])
   double acc = 0;
   for (int64_t r = 1 + threadIdx.x; r < m; r += blockDim.x) {
-    const z v = row[r];
+    const z v = __ldcg(row + r);
     acc = fma(v.x, v.x, fma(v.y, v.y, acc));
   }
   acc = block_sum_all(acc, sh);
   if (threadIdx.x == 0) s_xn2 = acc;
   __syncthreads();
   const double xn2 = s_xn2;
-  const z alpha = m > 0 ? zconj(row[0]) : zmk(0, 0);
+  const z alpha = m > 0 ? zconj(__ldcg(row)) : zmk(0, 0);
   double beta;
   z t, scale;
   if (m == 0 || (xn2 == 0.0 && alpha.y == 0.0)) {
@@ -67,92 +128,136 @@ __global__ void k_hh_reflector(const z* __restrict__ G, int64_t n, int64_t j, z*
     const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
     beta = alpha.x >= 0 ? -nrm : nrm;
     t = zmk((beta - alpha.x) / beta, -alpha.y / beta);
-    const z den = zmk(alpha.x - beta, alpha.y);  // 1 / (alpha - beta)
+    const z den = zmk(alpha.x - beta, alpha.y);
     const double dd = den.x * den.x + den.y * den.y;
     scale = zmk(den.x / dd, -den.y / dd);
   }
-  z* v = Hv + j * n;
+  z* v = a.Hv + j * n;
   for (int64_t r = threadIdx.x; r < m; r += blockDim.x)
-    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(row[r]), scale);
+    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(__ldcg(row + r)), scale);
   if (threadIdx.x == 0) {
-    tau[j] = t;
-    d[j] = G[j * n + j].x;
-    if (m > 0) e[j] = beta;
+    a.tau[j] = t;
+    a.d[j] = __ldcg(a.G + j * n + j).x;
+    if (m > 0) a.e[j] = beta;
   }
+  __syncthreads();
 }
 
-// p = tau A v (A = trailing block), one warp per row; partial[b] = sum over the block's
-// rows of conj(p_r) v_r
-__global__ void k_hh_gemv(const z* __restrict__ G, int64_t n, int64_t j, const z* __restrict__ Hv,
-                          const z* __restrict__ tau, z* __restrict__ p, z* __restrict__ partial) {
-  __shared__ double shr[8], shi[8];
-  const int64_t m = n - j - 1;
-  const z* v = Hv + j * n;
-  const z t = tau[j];
+constexpr int TRI_THREADS = 512;
+constexpr int TRI_WARPS = TRI_THREADS / 32;
+constexpr int64_t TRI_CACHE = 4096;  // v and w of up to this many rows in shared memory
+
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
+  extern __shared__ z sm_vw[];  // [TRI_CACHE] v, then [TRI_CACHE] w
+  z* sv = sm_vw;
+  z* sw = sm_vw + TRI_CACHE;
+  __shared__ double sh[32];
+  __shared__ double shr[TRI_WARPS], shi[TRI_WARPS];
+  __shared__ z s_cf;
+  const int64_t n = a.n;
+  const int nb = gridDim.x, b = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double pr = 0, pi = 0;
-  for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < m; r += (int64_t)gridDim.x * 8) {
-    const z* a = G + (j + 1 + r) * n + j + 1;
-    double sr = 0, si = 0;
-    for (int64_t c = lane; c < m; c += 32) {
-      const z x = a[c], y = v[c];
-      sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
-      si = fma(x.x, y.y, fma(x.y, y.x, si));
+  if (b == 0) tri_reflector(a, 0, sh);
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    const int64_t m = n - j - 1;
+    const z* v = a.Hv + j * n;
+    if (!grid_barrier(a)) return;
+    const bool cached = (m <= TRI_CACHE);
+    if (cached) {
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x) sv[c] = __ldcg(v + c);
+      __syncthreads();
     }
-    sr = warp_sum_d(sr);
-    si = warp_sum_d(si);
+    const z t = __ldcg(a.tau + j);
+    // p = tau A v
+    double pr = 0, pi = 0;
+    for (int64_t r = (int64_t)b * TRI_WARPS + warp; r < m; r += (int64_t)nb * TRI_WARPS) {
+      const z* row = a.G + (j + 1 + r) * n + j + 1;
+      double sr = 0, si = 0;
+      if (cached) {
+#pragma unroll 4
+        for (int64_t c = lane; c < m; c += 32) {
+          const z x = __ldcg(row + c), y = sv[c];
+          sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+          si = fma(x.x, y.y, fma(x.y, y.x, si));
+        }
+      } else {
+#pragma unroll 4
+        for (int64_t c = lane; c < m; c += 32) {
+          const z x = __ldcg(row + c), y = __ldcg(v + c);
+          sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+          si = fma(x.x, y.y, fma(x.y, y.x, si));
+        }
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) {
+        const z pv = zmul(t, zmk(sr, si));
+        a.p[r] = pv;
+        const z vr = cached ? sv[r] : __ldcg(v + r);
+        pr += pv.x * vr.x + pv.y * vr.y;
+        pi += pv.x * vr.y - pv.y * vr.x;
+      }
+    }
     if (lane == 0) {
-      const z pv = zmul(t, zmk(sr, si));
-      p[r] = pv;
-      const z vr = v[r];
-      pr += pv.x * vr.x + pv.y * vr.y;  // conj(p) v
-      pi += pv.x * vr.y - pv.y * vr.x;
+      shr[warp] = pr;
+      shi[warp] = pi;
     }
-  }
-  if (lane == 0) {
-    shr[warp] = pr;
-    shi[warp] = pi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int i = 0; i < 8; ++i) {
-      a += shr[i];
-      b += shi[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0, sb = 0;
+      for (int q = 0; q < TRI_WARPS; ++q) {
+        sa += shr[q];
+        sb += shi[q];
+      }
+      a.part[b] = zmk(sa, sb);
     }
-    partial[blockIdx.x] = zmk(a, b);
-  }
-}
-
-// A <- A - v w^H - w v^H with w = p - (tau s / 2) v, s = p^H v (sum of partials)
-__global__ void k_hh_update(z* __restrict__ G, int64_t n, int64_t j, const z* __restrict__ Hv,
-                            const z* __restrict__ tau, const z* __restrict__ p,
-                            const z* __restrict__ partial, int nparts) {
-  __shared__ z s_c;
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int i = 0; i < nparts; ++i) {
-      a += partial[i].x;
-      b += partial[i].y;
+    if (!grid_barrier(a)) return;
+    if (threadIdx.x == 0) {
+      double sa = 0, sb = 0;
+      for (int q = 0; q < nb; ++q) {
+        const z pq = __ldcg(a.part + q);
+        sa += pq.x;
+        sb += pq.y;
+      }
+      const z ts = zmul(t, zmk(sa, sb));
+      s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
     }
-    const z ts = zmul(tau[j], zmk(a, b));
-    s_c = zmk(-0.5 * ts.x, -0.5 * ts.y);
-  }
-  __syncthreads();
-  const z cf = s_c;
-  const int64_t m = n - j - 1;
-  const z* v = Hv + j * n;
-  const int64_t tot = m * m;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / m, c = e % m;
-    const z vr = v[r], vc = v[c];
-    const z wr = zadd(p[r], zmul(cf, vr)), wc = zadd(p[c], zmul(cf, vc));
-    z* a = G + (j + 1 + r) * n + j + 1 + c;
-    z x = *a;
-    x = zsub(x, zmul(vr, zconj(wc)));
-    x = zsub(x, zmul(wr, zconj(vc)));
-    *a = x;
+    __syncthreads();
+    const z cf = s_cf;
+    if (cached) {  // w = p + cf v once per block, not once per element
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x)
+        sw[c] = zadd(__ldcg(a.p + c), zmul(cf, sv[c]));
+      __syncthreads();
+    }
+    // A <- A - v w^H - w v^H on the rows this block owns (w = p + cf v)
+    for (int64_t r = b; r < m; r += nb) {
+      const z vr = cached ? sv[r] : __ldcg(v + r);
+      const z wr = cached ? sw[r] : zadd(__ldcg(a.p + r), zmul(cf, vr));
+      z* row = a.G + (j + 1 + r) * n + j + 1;
+      if (cached) {
+#pragma unroll 2
+        for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
+          const z vc = sv[c], wc = sw[c];
+          z x = __ldcg(row + c);
+          x = zsub(x, zmul(vr, zconj(wc)));
+          x = zsub(x, zmul(wr, zconj(vc)));
+          row[c] = x;
+        }
+      } else {
+        for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
+          const z vc = __ldcg(v + c);
+          const z wc = zadd(__ldcg(a.p + c), zmul(cf, vc));
+          z x = __ldcg(row + c);
+          x = zsub(x, zmul(vr, zconj(wc)));
+          x = zsub(x, zmul(wr, zconj(vc)));
+          row[c] = x;
+        }
+      }
+      if (r == 0) {  // block 0: row j + 1 is final, form the next reflector from it
+        __syncthreads();
+        tri_reflector(a, j + 1, sh);
+      }
+    }
   }
 }
 
@@ -168,114 +273,177 @@ __device__ int sturm_lt(const double* d, const double* e, int64_t n, double x, d
   return cnt;
 }
 
-// eigenvalue of ascending index n-1-i for i < k, by bisection; ev[i] descending
+// eigenvalue of ascending index n-1-i for i < k; ev[i] descending.  One warp per
+// eigenvalue: the 32 lanes evaluate Sturm counts at 32 interior points, shrinking the
+// bracket 33-fold per step, to full precision (about 11 steps).  The values serve only as
+// shifts (singular values are taken later as FP64 projection norms), and each SM's few
+// FP64 units favour short dependent chains over many of them.
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e, int64_t n,
                          int64_t k, double* __restrict__ ev, double* __restrict__ tnorm_out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double lo = d[0], hi = d[0], tn = 0, emax2 = 0;
-  for (int64_t r = 0; r < n; ++r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = blockIdx.x;
+  double lo = INFINITY, hi = -INFINITY, tn = 0, emax2 = 0;
+  for (int64_t r = lane; r < n; r += 32) {
     const double rad = (r > 0 ? fabs(e[r - 1]) : 0.0) + (r < n - 1 ? fabs(e[r]) : 0.0);
     lo = fmin(lo, d[r] - rad);
     hi = fmax(hi, d[r] + rad);
     tn = fmax(tn, fabs(d[r]) + rad);
     if (r < n - 1) emax2 = fmax(emax2, e[r] * e[r]);
   }
-  if (i == 0 && tnorm_out) tnorm_out[0] = tn;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+  }
+  if (i == 0 && lane == 0 && tnorm_out) tnorm_out[0] = tn;
   if (i >= k) return;
   const double pivmin = fmax(1e-300, EPS * EPS * fmax(emax2, 1e-300)) + 1e-300;
   const int64_t idx = n - 1 - i;
   const double pad = 2 * EPS * tn + 1e-300;
   lo -= pad;
   hi += pad;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2 * EPS * fmax(fabs(lo), fabs(hi)) + 1e-300 || mid <= lo || mid >= hi) break;
-    if (sturm_lt(d, e, n, mid, pivmin) <= idx) lo = mid; else hi = mid;
+  const double tol = 1e-300;  // full precision: the shifts must resolve close eigenvalues
+  for (int it = 0; it < 64; ++it) {
+    const double width = hi - lo;
+    if (width <= fmax(tol, 4 * EPS * fmax(fabs(lo), fabs(hi)))) break;
+    const double x = lo + width * (double)(lane + 1) / 33.0;
+    const unsigned below = __ballot_sync(0xffffffffu, sturm_lt(d, e, n, x, pivmin) <= idx);
+    const int p = __popc(below);  // points left of eigenvalue idx (counts are monotone)
+    const double nlo = p > 0 ? lo + width * (double)p / 33.0 : lo;
+    const double nhi = p < 32 ? lo + width * (double)(p + 1) / 33.0 : hi;
+    lo = nlo;
+    hi = nhi;
   }
-  ev[i] = 0.5 * (lo + hi);
+  if (lane == 0) ev[i] = 0.5 * (lo + hi);
 }
 
-// inverse iteration, one thread per eigenvalue; work arrays interleaved by thread:
-// element r of thread i at [r * k + i]
-__global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e, int64_t n,
-                          const double* __restrict__ ev, int64_t k, const double* __restrict__ tnorm,
-                          double* __restrict__ work, double* __restrict__ Y) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k) return;
+// inverse iteration on T - lambda I.  Eigenvalues closer than 1e3 eps |T| form a cluster,
+// handled by one block in order: thread 0 factors and solves (the recurrences are
+// serial), then the block re-orthogonalises the new iterate against the cluster's
+// earlier vectors (classical Gram-Schmidt, twice) after every solve, so coincident
+// eigenvalues still give independent vectors.  Wider gaps give iterates accurate to
+// eps |T| / gap, which the final Newton-Schulz steps absorb.  Work arrays live in shared
+// memory when they fit (smem_ok), else in the cluster head's slice of gwork.
+constexpr int IV_THREADS = 128;
+constexpr int IV_CHUNK = 1024;  // earlier cluster members handled per Gram-Schmidt chunk
+
+__global__ void __launch_bounds__(IV_THREADS) k_inviter(
+    const double* __restrict__ d, const double* __restrict__ e, int64_t n,
+    const double* __restrict__ ev, int64_t k, const double* __restrict__ tnorm,
+    double* __restrict__ gwork, double* __restrict__ Y, int smem_ok) {
+  extern __shared__ double sm_iv[];
+  __shared__ double sdot[IV_CHUNK];
+  __shared__ double sh[32];
+  const int64_t i0 = blockIdx.x;
   const double tn = fmax(tnorm[0], 1e-300);
-  double lam = ev[i];
-  // separate coincident shifts (descending order): keep a gap of 10 eps |T|
-  for (int64_t t = i; t > 0; --t) {
-    if (ev[t - 1] - ev[t] >= 10 * EPS * tn) break;
-    lam = fmin(lam, ev[t - 1] - 10 * EPS * tn * (double)(i - t + 1));
-  }
+  const double ortol = 1e3 * EPS * tn;
+  if (i0 > 0 && ev[i0 - 1] - ev[i0] < ortol) return;  // not the head of its cluster
+  int64_t i1 = i0 + 1;
+  while (i1 < k && ev[i1 - 1] - ev[i1] < ortol) ++i1;
+  double* work = smem_ok ? sm_iv : gwork + i0 * (6 * n);
   double* dl = work;
-  double* dm = work + n * k;
-  double* du = work + 2 * n * k;
-  double* du2 = work + 3 * n * k;
-  double* y = work + 4 * n * k;
-  int8_t* piv = (int8_t*)(work + 5 * n * k);
-#define W(a, r) a[(r) * k + i]
-  // start vector: deterministic, free of structure
-  uint32_t h = 2166136261u ^ (uint32_t)(i * 2654435761u);
-  for (int64_t r = 0; r < n; ++r) {
-    h ^= (uint32_t)r;
-    h *= 16777619u;
-    W(y, r) = 0.5 + (double)(h & 0xffff) / 65536.0;
-  }
+  double* dm = work + n;
+  double* du = work + 2 * n;
+  double* du2 = work + 3 * n;
+  double* y = work + 4 * n;
+  int8_t* piv = (int8_t*)(work + 5 * n);
   const double small = EPS * tn;
-  // LU with partial pivoting of T - lam I (tridiagonal, textbook)
-  for (int64_t r = 0; r < n; ++r) {
-    W(dm, r) = d[r] - lam;
-    W(du, r) = r < n - 1 ? e[r] : 0.0;
-    W(dl, r) = r < n - 1 ? e[r] : 0.0;
-    W(du2, r) = 0.0;
-  }
-  for (int64_t r = 0; r < n - 1; ++r) {
-    const double a = W(dm, r), b = W(dl, r);
-    if (fabs(a) >= fabs(b)) {
-      const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
-      W(dm, r) = aa;
-      const double f = b / aa;
-      W(dl, r) = f;
-      W(dm, r + 1) -= f * W(du, r);
-      piv[r * k + i] = 0;
-    } else {
-      const double f = a / b;
-      W(dm, r) = b;
-      W(dl, r) = f;
-      const double t = W(du, r);
-      W(du, r) = W(dm, r + 1);
-      W(dm, r + 1) = t - f * W(du, r);
-      if (r < n - 2) {
-        W(du2, r) = W(du, r + 1);
-        W(du, r + 1) = -f * W(du, r + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nwarps = IV_THREADS / 32;
+  double lam_prev = 0;
+  for (int64_t i = i0; i < i1; ++i) {
+    if (tid == 0) {
+      // shifts strictly decreasing inside a cluster, at least 10 eps |T| apart
+      double lam = ev[i];
+      if (i > i0) lam = fmin(lam, lam_prev - 10 * EPS * tn);
+      lam_prev = lam;
+      uint32_t h = 2166136261u ^ (uint32_t)(i * 2654435761u);
+      for (int64_t r = 0; r < n; ++r) {  // deterministic start vector, free of structure
+        h ^= (uint32_t)r;
+        h *= 16777619u;
+        y[r] = 0.5 + (double)(h & 0xffff) / 65536.0;
       }
-      piv[r * k + i] = 1;
-    }
-  }
-  if (fabs(W(dm, n - 1)) < small) W(dm, n - 1) = W(dm, n - 1) < 0 ? -small : small;
-  for (int sweep = 0; sweep < 3; ++sweep) {
-    for (int64_t r = 0; r < n - 1; ++r) {
-      if (piv[r * k + i] == 0) {
-        W(y, r + 1) -= W(dl, r) * W(y, r);
-      } else {
-        const double t = W(y, r);
-        W(y, r) = W(y, r + 1);
-        W(y, r + 1) = t - W(dl, r) * W(y, r);
+      // LU with partial pivoting of T - lam I (tridiagonal, textbook)
+      for (int64_t r = 0; r < n; ++r) {
+        dm[r] = d[r] - lam;
+        du[r] = r < n - 1 ? e[r] : 0.0;
+        dl[r] = r < n - 1 ? e[r] : 0.0;
+        du2[r] = 0.0;
       }
+      for (int64_t r = 0; r < n - 1; ++r) {
+        const double a = dm[r], b = dl[r];
+        if (fabs(a) >= fabs(b)) {
+          const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
+          dm[r] = aa;
+          const double f = b / aa;
+          dl[r] = f;
+          dm[r + 1] -= f * du[r];
+          piv[r] = 0;
+        } else {
+          const double f = a / b;
+          dm[r] = b;
+          dl[r] = f;
+          const double t = du[r];
+          du[r] = dm[r + 1];
+          dm[r + 1] = t - f * du[r];
+          if (r < n - 2) {
+            du2[r] = du[r + 1];
+            du[r + 1] = -f * du[r + 1];
+          }
+          piv[r] = 1;
+        }
+      }
+      if (fabs(dm[n - 1]) < small) dm[n - 1] = dm[n - 1] < 0 ? -small : small;
     }
-    W(y, n - 1) /= W(dm, n - 1);
-    if (n > 1) W(y, n - 2) = (W(y, n - 2) - W(du, n - 2) * W(y, n - 1)) / W(dm, n - 2);
-    for (int64_t r = n - 3; r >= 0; --r)
-      W(y, r) = (W(y, r) - W(du, r) * W(y, r + 1) - W(du2, r) * W(y, r + 2)) / W(dm, r);
-    double nrm = 0;
-    for (int64_t r = 0; r < n; ++r) nrm = fma(W(y, r), W(y, r), nrm);
-    nrm = 1.0 / sqrt(nrm);
-    for (int64_t r = 0; r < n; ++r) W(y, r) *= nrm;
+    __syncthreads();
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      if (tid == 0) {
+        for (int64_t r = 0; r < n - 1; ++r) {
+          if (piv[r] == 0) {
+            y[r + 1] -= dl[r] * y[r];
+          } else {
+            const double t = y[r];
+            y[r] = y[r + 1];
+            y[r + 1] = t - dl[r] * y[r];
+          }
+        }
+        y[n - 1] /= dm[n - 1];
+        if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dm[n - 2];
+        for (int64_t r = n - 3; r >= 0; --r)
+          y[r] = (y[r] - du[r] * y[r + 1] - du2[r] * y[r + 2]) / dm[r];
+      }
+      __syncthreads();
+      for (int pass = 0; pass < 2 && i > i0; ++pass) {
+        for (int64_t q0 = i0; q0 < i; q0 += IV_CHUNK) {
+          const int64_t q1 = min(i, q0 + IV_CHUNK);
+          for (int64_t q = q0 + warp; q < q1; q += nwarps) {  // one warp per dot product
+            const double* yq = Y + q * n;
+            double acc = 0;
+            for (int64_t r = lane; r < n; r += 32) acc = fma(y[r], yq[r], acc);
+            acc = warp_sum_d(acc);
+            if (lane == 0) sdot[q - q0] = acc;
+          }
+          __syncthreads();
+          for (int64_t r = tid; r < n; r += IV_THREADS) {
+            double v = y[r];
+            for (int64_t q = q0; q < q1; ++q) v = fma(-sdot[q - q0], Y[q * n + r], v);
+            y[r] = v;
+          }
+          __syncthreads();
+        }
+      }
+      double acc = 0;
+      for (int64_t r = tid; r < n; r += IV_THREADS) acc = fma(y[r], y[r], acc);
+      acc = block_sum_all(acc, sh);
+      const double inv = 1.0 / sqrt(acc);
+      for (int64_t r = tid; r < n; r += IV_THREADS) y[r] *= inv;
+      __syncthreads();
+    }
+    for (int64_t r = tid; r < n; r += IV_THREADS) Y[i * n + r] = y[r];
+    __syncthreads();
   }
-  for (int64_t r = 0; r < n; ++r) Y[i * n + r] = W(y, r);
-#undef W
 }
 
 // U[:, i] = H_0 ... H_{n-2} y_i; one CTA per eigenvector, the vector in shared memory
@@ -373,58 +541,94 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * n * k));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * n * k));
   z* S = (z*)ws_alloc(c, ws_round(sizeof(z) * k * k));
-  if (!Hv || !tau || !p || !d || !e || !tn || !part || !work || !Y || !U0 || !S) {
+  unsigned* bar = (unsigned*)ws_alloc(c, 256);
+  if (!Hv || !tau || !p || !d || !e || !tn || !part || !work || !Y || !U0 || !S || !bar) {
     c->ws.top = top;
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (heig_top n=%lld k=%lld)", (long long)n, (long long)k);
   }
   cudaStream_t st = c->stream;
   {
-    ProfScope ps(c, "heig_tridiag");
-    for (int64_t j = 0; j < n; ++j) {
-      k_hh_reflector<<<1, 256, 0, st>>>(G, n, j, Hv, tau, d, e);
-      const int64_t m = n - j - 1;
-      if (m <= 0) break;
-      const int nb = (int)std::min<int64_t>((m + 7) / 8, 1216);
-      k_hh_gemv<<<nb, 256, 0, st>>>(G, n, j, Hv, tau, p, part);
-      k_hh_update<<<gsz(m * m), 256, 0, st>>>(G, n, j, Hv, tau, p, part, nb);
-      c->launches += 3;
+    const double nn = (double)n;
+    ProfScope ps(c, "heig_tridiag", 24.0 * (nn - 1) * nn * (2 * nn - 1) / 6.0);
+    const size_t tri_smem = 2 * TRI_CACHE * sizeof(z);
+    static int nsm = 0, occ = 0;
+    if (!nsm) {
+      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_persistent,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
+      TNT_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+      TNT_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_persistent,
+                                                                    TRI_THREADS, tri_smem));
     }
+    if (occ < 1) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal kernel cannot be resident");
+    TNT_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 256, st));
+    TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status};
+    void* args[] = {&ta};
+    const int nb = std::min(nsm, 1216);
+    TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
+                                                dim3(TRI_THREADS), args, tri_smem, st));
     c->launches += 1;
-    TNT_CHECK_LAUNCH(c);
+  }
+  {
+    int h_status = 0;
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(&h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (h_status & 2) {
+      cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
+      c->ws.top = top;
+      return set_err(c, TNT_E_TIMEOUT, "tridiagonal reduction: a grid barrier wait expired");
+    }
   }
   {
     ProfScope ps(c, "heig_tridiag_eig");
-    k_bisect<<<(unsigned)((k + 127) / 128), 128, 0, st>>>(d, e, n, k, ev, tn);
-    k_inviter<<<(unsigned)((k + 63) / 64), 64, 0, st>>>(d, e, n, ev, k, tn, work, Y);
+    k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, n, k, ev, tn);
+    const size_t iv_smem = (size_t)n * (5 * sizeof(double) + 1);
+    const int smem_ok = iv_smem <= (size_t)180 * 1024;
+    if (smem_ok)
+      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)iv_smem));
+    k_inviter<<<(unsigned)k, IV_THREADS, smem_ok ? iv_smem : 0, st>>>(d, e, n, ev, k, tn, work, Y,
+                                                                     smem_ok);
     c->launches += 2;
     TNT_CHECK_LAUNCH(c);
   }
   {
-    ProfScope ps(c, "heig_backtransform");
+    ProfScope ps(c, "heig_backtransform", 8.0 * (double)n * (double)n * (double)k);
     const size_t smem = sizeof(z) * n;
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_backtransform<<<(unsigned)k, 256, smem, st>>>(Y, Hv, tau, n, U0, k);
     c->launches++;
     TNT_CHECK_LAUNCH(c);
   }
-  // Newton-Schulz: S = U0^H U0; S <- 1.5 I - 0.5 S; U = U0 S
-  ZGemm g{};
-  g.M = k; g.N = k; g.K = n;
-  g.A = U0; g.a_rs = 1; g.a_cs = k; g.conj_a = 1;
-  g.B = U0; g.b_rs = k; g.b_cs = 1;
-  g.C = S; g.c_rs = k;
-  g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
-  int r = zgemm(c, g);
-  if (r == TNT_OK) {
+  // two Newton-Schulz steps: S = X^H X; S <- 1.5 I - 0.5 S; X <- X S  (U0 -> U -> U0 -> U)
+  int r = TNT_OK;
+  z* src = U0;
+  int64_t lds = k;
+  for (int step = 0; step < 2 && r == TNT_OK; ++step) {
+    z* dst = (step == 0) ? U : U0;
+    const int64_t ldd = (step == 0) ? ldu : k;
+    ZGemm g{};
+    g.M = k; g.N = k; g.K = n;
+    g.A = src; g.a_rs = 1; g.a_cs = lds; g.conj_a = 1;
+    g.B = src; g.b_rs = lds; g.b_cs = 1;
+    g.C = S; g.c_rs = k;
+    g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
+    r = zgemm(c, g);
+    if (r != TNT_OK) break;
     k_ns_coef<<<gsz(k * k), 256, 0, st>>>(S, k);
     c->launches++;
     ZGemm h{};
     h.M = n; h.N = k; h.K = k;
-    h.A = U0; h.a_rs = k; h.a_cs = 1;
+    h.A = src; h.a_rs = lds; h.a_cs = 1;
     h.B = S; h.b_rs = k; h.b_cs = 1;
-    h.C = U; h.c_rs = ldu;
+    h.C = dst; h.c_rs = ldd;
     h.alpha = zmk(1, 0); h.beta = zmk(0, 0); h.batch = 1;
     r = zgemm(c, h);
+    src = dst;
+    lds = ldd;
+  }
+  if (r == TNT_OK) {
+    k_copy_cols<<<gsz(n * k), 256, 0, st>>>(U0, n, k, k, U, ldu);
+    c->launches++;
   }
   c->ws.top = top;
   return r;

@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(256) k_zgemm(ZGemm g) {
   __shared__ z Bs[GK][GN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.y * GM, n0 = (int64_t)blockIdx.x * GN;
+  if (g.lower_only && m0 + GM <= n0) return;  // strictly upper tile of a Hermitian result
   const int64_t bt = blockIdx.z;
   const z* A = g.A + bt * g.a_bs;
   const z* B = g.B + bt * g.b_bs;
@@ -102,8 +103,29 @@ int zgemm(Ctx* c, const ZGemm& g) {
                    (long long)g.M, (long long)g.N, (long long)g.batch);
   dim3 grid((unsigned)((g.N + GN - 1) / GN), (unsigned)((g.M + GM - 1) / GM),
             (unsigned)g.batch);
-  ProfScope ps(c, "zgemm_f64");
+  ProfScope ps(c, "zgemm_f64", (g.lower_only ? 4.0 : 8.0) * (double)g.M * (double)g.N *
+                                   (double)g.K * (double)g.batch);
   k_zgemm<<<grid, 256, 0, c->stream>>>(g);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+namespace {
+__global__ void k_herm_mirror(z* G, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    if (i < j) G[e] = zconj(G[j * n + i]);
+  }
+}
+}  // namespace
+
+int herm_mirror(Ctx* c, z* G, int64_t n) {
+  if (n <= 1) return TNT_OK;
+  int64_t b = (n * n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  k_herm_mirror<<<(unsigned)b, 256, 0, c->stream>>>(G, n);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;
@@ -208,7 +230,7 @@ int op_apply(Ctx* c, const OpApply& a) {
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   int nnz = a.nnz > 0 ? a.nnz : 1;
-  ProfScope ps(c, "op_apply");
+  ProfScope ps(c, "op_apply", 8.0 * (double)a.nnz * (double)total);
   k_op_apply<<<(unsigned)blocks, 256, 0, c->stream>>>(a, nnz);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
@@ -219,7 +241,7 @@ int op_apply(Ctx* c, const OpApply& a) {
 // Deterministic reductions: a fixed grid of RB blocks; block b always covers the same
 // elements in the same order; a single-block second pass sums the partials in order.
 namespace {
-constexpr int RB = 296;       // 2 x 148..152 SMs: enough blocks to saturate HBM
+constexpr int RB = 608;       // 4 blocks per SM (152 SMs): enough loads in flight for HBM
 constexpr int RT = 256;
 constexpr int KB = 8;         // vectors per multidot pass
 
@@ -244,41 +266,58 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// partial[v][blk] = sum over the block's range of conj(V_v[e]) w[e], v < kv
-__global__ void __launch_bounds__(RT) k_multidot(const z* __restrict__ V, int64_t ld, int kv,
+// partial[v][blk] = sum over the block's range of conj(V_v[e]) w[e], v < KV; the KV
+// loads of one element are independent and issued together
+template <int KV>
+__global__ void __launch_bounds__(RT) k_multidot(const z* __restrict__ V, int64_t ld,
                                                  const z* __restrict__ w, int64_t n,
-                                                 z* __restrict__ partial) {
+                                                 z* __restrict__ partial,
+                                                 const int* __restrict__ skip) {
+  if (skip && *skip) return;  // a pass the caller decided on the device not to need
   __shared__ double sh[32];
-  double ar[KB], ai[KB];
+  double ar[KV], ai[KV];
 #pragma unroll
-  for (int v = 0; v < KB; ++v) ar[v] = ai[v] = 0.0;
+  for (int v = 0; v < KV; ++v) ar[v] = ai[v] = 0.0;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = min(n, lo + chunk);
   for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-    z x = w[e];
+    const z x = w[e];
+    z u[KV];
 #pragma unroll
-    for (int v = 0; v < KB; ++v) {
-      if (v < kv) {
-        z u = V[(int64_t)v * ld + e];
-        ar[v] = fma(u.x, x.x, fma(u.y, x.y, ar[v]));
-        ai[v] = fma(u.x, x.y, fma(-u.y, x.x, ai[v]));
-      }
+    for (int v = 0; v < KV; ++v) u[v] = V[(int64_t)v * ld + e];
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {
+      ar[v] = fma(u[v].x, x.x, fma(u[v].y, x.y, ar[v]));
+      ai[v] = fma(u[v].x, x.y, fma(-u[v].y, x.x, ai[v]));
     }
   }
 #pragma unroll
-  for (int v = 0; v < KB; ++v) {
-    if (v < kv) {
-      double r = block_sum(ar[v], sh);
-      double i = block_sum(ai[v], sh);
-      if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = zmk(r, i);
-    }
+  for (int v = 0; v < KV; ++v) {
+    double r = block_sum(ar[v], sh);
+    double i = block_sum(ai[v], sh);
+    if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = zmk(r, i);
+  }
+}
+
+void launch_multidot(int kv, dim3 g, dim3 b, cudaStream_t st, const z* V, int64_t ld,
+                     const z* w, int64_t n, z* partial, const int* skip) {
+  switch (kv) {
+    case 1: k_multidot<1><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 2: k_multidot<2><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 3: k_multidot<3><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 4: k_multidot<4><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 5: k_multidot<5><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 6: k_multidot<6><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 7: k_multidot<7><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    default: k_multidot<8><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
   }
 }
 
 // out[v] = sum_b partial[v][b], fixed order; one block, kv outputs
 __global__ void k_reduce_partials(const z* __restrict__ partial, int nb, int kv,
-                                  z* __restrict__ out) {
+                                  z* __restrict__ out, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double sh[32];
   for (int v = 0; v < kv; ++v) {
     double r = 0, i = 0;
@@ -297,7 +336,9 @@ __global__ void k_reduce_partials(const z* __restrict__ partial, int nb, int kv,
 __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, int64_t ld,
                                                        int k, const z* __restrict__ coef,
                                                        z* __restrict__ w, int64_t n,
-                                                       double* __restrict__ partial) {
+                                                       double* __restrict__ partial,
+                                                       const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ z sc[64];
   __shared__ double sh[32];
   for (int t = threadIdx.x; t < k; t += blockDim.x) sc[t] = coef[t];
@@ -308,9 +349,21 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, 
   double acc = 0;
   for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     z x = w[e];
-    for (int v = 0; v < k; ++v) {
-      z u = V[(int64_t)v * ld + e];
-      z cv = sc[v];
+    int v = 0;
+    for (; v + 8 <= k; v += 8) {  // eight independent loads in flight per thread
+      z u[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u[q] = V[(int64_t)(v + q) * ld + e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const z cv = sc[v + q];
+        x.x -= cv.x * u[q].x - cv.y * u[q].y;
+        x.y -= cv.x * u[q].y + cv.y * u[q].x;
+      }
+    }
+    for (; v < k; ++v) {
+      const z u = V[(int64_t)v * ld + e];
+      const z cv = sc[v];
       x.x -= cv.x * u.x - cv.y * u.y;
       x.y -= cv.x * u.y + cv.y * u.x;
     }
@@ -322,7 +375,8 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, 
 }
 
 __global__ void k_reduce_real(const double* __restrict__ partial, int nb,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // out keeps its previous value
   __shared__ double sh[32];
   double r = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) r += partial[b];
@@ -353,7 +407,8 @@ __global__ void k_normalize(const z* __restrict__ x, z* __restrict__ y, int64_t 
 }
 }  // namespace
 
-int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots) {
+int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots,
+                 const int* d_skip) {
   if (k <= 0) return TNT_OK;
   // partial sums live in scratch only until the next launch on the same stream, so the
   // region is handed back immediately (stream order serialises its reuse)
@@ -363,9 +418,9 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
   for (int v0 = 0; v0 < k; v0 += KB) {
     int kv = (k - v0 < KB) ? (k - v0) : KB;
-    ProfScope ps(c, "multidot");
-    k_multidot<<<RB, RT, 0, c->stream>>>(V + (int64_t)v0 * ld, ld, kv, w, n, partial);
-    k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0);
+    ProfScope ps(c, "multidot", 16.0 * (double)(kv + 1) * (double)n);
+    launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip);
+    k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0, d_skip);
     c->launches += 2;
   }
   TNT_CHECK_LAUNCH(c);
@@ -373,17 +428,17 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
 }
 
 int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
-                       int64_t n, double* d_norm2) {
+                       int64_t n, double* d_norm2, const int* d_skip) {
   if (k > 64) return set_err(c, TNT_E_UNSUPPORTED, "multiaxpy with k=%d > 64", k);
   const size_t top = c->ws.top;
   double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * RB));
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy)");
   {
-    ProfScope ps(c, "multiaxpy");
-    k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial);
+    ProfScope ps(c, "multiaxpy", 16.0 * (double)(k + 2) * (double)n);
+    k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip);
   }
-  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2);
+  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2, d_skip);
   c->launches += 2;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;
@@ -395,7 +450,7 @@ int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2) {
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (norm2)");
   k_norm2_partial<<<RB, RT, 0, c->stream>>>(x, n, partial);
-  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2);
+  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2, nullptr);
   c->launches += 2;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;

@@ -497,7 +497,9 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
       g.A = Mp + B.moff; g.a_rs = 1; g.a_cs = B.nq; g.conj_a = 1;
       g.B = Mp + B.moff; g.b_rs = B.nq; g.b_cs = 1;
     }
+    g.lower_only = 1;  // G is Hermitian: form the lower tiles, mirror the rest
     TNT_TRY(zgemm(c, g));
+    TNT_TRY(herm_mirror(c, Gp + B.goff, B.g));
   }
   // ---- eigensolves: small blocks batched in one launch, large ones one by one
   {

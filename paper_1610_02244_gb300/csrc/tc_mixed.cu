@@ -444,7 +444,7 @@ int make_map(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int 
 }
 
 int launch_cgemm(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, int64_t M, int64_t N,
-                 int64_t Kp, int split, float* C, int64_t ldc) {
+                 int64_t Kp, int split, float* C, int64_t ldc, int64_t K_true) {
   static bool attr = false;
   if (!attr) {
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_cgemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -464,7 +464,7 @@ int launch_cgemm(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, int64_t M
   if ((int64_t)g.kb_per_split * (split - 1) >= g.kb_total)
     return set_err(c, TNT_E_INVALID, "split-K %d leaves an empty split", split);
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)split);
-  ProfScope ps(c, "cgemm_tf32x3");
+  ProfScope ps(c, "cgemm_tf32x3", 8.0 * (double)M * (double)N * (double)K_true);
   k_cgemm_tf32x3<<<grid, 192, SMEM_BYTES, c->stream>>>(tA, tB, g);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
@@ -552,21 +552,21 @@ int heff_run_mixed(Ctx* c, const HeffPlan& p, const z* theta, z* y) {
   // theta[a][(s1 s2 b)] -> planes [(s1 s2 b)][a]
   dim3 gt((unsigned)((m.Np1 + 31) / 32), (unsigned)((m.Kp1 + 31) / 32));
   {
-    ProfScope ps(c, "split_theta");
+    ProfScope ps(c, "split_theta", 32.0 * (double)m.K1 * (double)m.N1);
     k_split_transpose<<<gt, 256, 0, c->stream>>>(theta, m.K1, m.N1, m.Np1, m.Kp1, m.Thp);
   }
   c->launches++;
-  TNT_TRY(launch_cgemm(c, m.tmL, m.tmTh, m.M1, m.N1, m.Kp1, 1, m.T1, m.N1));
+  TNT_TRY(launch_cgemm(c, m.tmL, m.tmTh, m.M1, m.N1, m.Kp1, 1, m.T1, m.N1, m.K1));
   int64_t total = m.op.B0 * m.op.B2;
   int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
   {
-    ProfScope ps(c, "op_mixed");
+    ProfScope ps(c, "op_mixed", 8.0 * (double)m.M1 * (double)m.N1 + 16.0 * (double)m.M4 * (double)m.K4);
     k_op_mixed<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, c->stream>>>(
         m.op, m.T1, m.M1 * m.N1, m.T3p, m.Mp4 * m.Kp4);
   }
   c->launches++;
   TNT_CHECK_LAUNCH(c);
-  TNT_TRY(launch_cgemm(c, m.tmT3, m.tmR, m.M4, m.N4, m.Kp4, m.split4, m.Yp, m.N4));
+  TNT_TRY(launch_cgemm(c, m.tmT3, m.tmR, m.M4, m.N4, m.Kp4, m.split4, m.Yp, m.N4, m.K4));
   k_gather_y<<<grid1(m.M4 * m.N4), 256, 0, c->stream>>>(m.Yp, m.split4, m.M4, m.N4, y);
   c->launches++;
   TNT_CHECK_LAUNCH(c);

@@ -56,15 +56,20 @@ struct Ctx {
   std::string prof_cls;
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, end
   size_t prof_n = 0;
+  double prof_work = 0;  // algorithmic FLOPs or bytes of the timed launches
 };
 
-// Records CUDA events around the launches of one kernel class when that class is selected.
+// Records CUDA events around the launches of one kernel class when that class is
+// selected, and adds the launch's algorithmic work (FLOPs or bytes, per class).
 struct ProfScope {
   Ctx* c;
   bool on;
-  ProfScope(Ctx* cc, const char* cls)
+  ProfScope(Ctx* cc, const char* cls, double work = 0)
       : c(cc), on(!cc->prof_cls.empty() && cc->prof_cls == cls && 2 * cc->prof_n + 1 < cc->prof_ev.size()) {
-    if (on) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+    if (on) {
+      cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+      c->prof_work += work;
+    }
   }
   ~ProfScope() {
     if (on) {
@@ -112,8 +117,11 @@ struct ZGemm {
   int conj_a, conj_b;
   z alpha, beta;
   int64_t batch;
+  int lower_only;  // Hermitian result: skip 64x64 tiles strictly above the diagonal
 };
 int zgemm(Ctx* c, const ZGemm& g);
+// G[i][j] = conj(G[j][i]) for i < j (complete a Hermitian matrix from its lower part)
+int herm_mirror(Ctx* c, z* G, int64_t n);
 
 // Sparse small operator acting on a group of legs with strided batches:
 // out[b0*os0 + b1*os1 + b2*os2 + out_off[i]] (+)= sum_j op[i,j] in[b0*is0 + ... + in_off[j]]
@@ -139,11 +147,14 @@ int op_upload(Ctx* c, const std::vector<z>& dense, int nI, int nJ,
               OpApply* a);
 
 // Vector kernels (FP64, deterministic two-level reductions).
-// dots[i] = <V_i | w> for i < k   (V_i = V + i*ld)
-int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots);
-// w -= sum_i coef[i] V_i ; then d_norm2 = |w|^2   (coef on device)
+// dots[i] = <V_i | w> for i < k   (V_i = V + i*ld).  With d_skip set and *d_skip != 0 at
+// run time, the kernels return without work (a pass decided on the device to be unneeded).
+int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots,
+                 const int* d_skip = nullptr);
+// w -= sum_i coef[i] V_i ; then d_norm2 = |w|^2   (coef on device); skipped as above, in
+// which case w and d_norm2 keep their values
 int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
-                       int64_t n, double* d_norm2);
+                       int64_t n, double* d_norm2, const int* d_skip = nullptr);
 // y = x * (1 / sqrt(*d_norm2))  (d_norm2 on device); if x == y scales in place
 int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2);
 int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2);

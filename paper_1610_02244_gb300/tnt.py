@@ -103,10 +103,11 @@ class Context:
         self._chk(self.lib.tnt_profile_select(self.h, (kernel_class or "").encode()))
 
     def profile_read(self):
-        """(summed ms, launches) of the selected kernel class since the last read."""
-        ms, n = C.c_double(), C.c_int64()
-        self._chk(self.lib.tnt_profile_read(self.h, C.byref(ms), C.byref(n)))
-        return ms.value, n.value
+        """(summed ms, launches, summed algorithmic work) of the selected kernel class
+        since the last read; work is FLOPs or bytes depending on the class."""
+        ms, n, w = C.c_double(), C.c_int64(), C.c_double()
+        self._chk(self.lib.tnt_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(w)))
+        return ms.value, n.value, w.value
 
     # ---------------------------------------------------------------- kernels
     def theta_form(self, A, B, out=None):

@@ -148,6 +148,32 @@ def test_lanczos_mixed_energy_within_1e10(ctx):
     assert abs(res["E_rq"] - w[0]) <= 1e-10 * abs(w[0])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lanczos_cfg2_full_size(ctx, precision):
+    """The micro-benchmark shape (chi = 256, d = 4, D = 4; |theta| = 2^20) with 12 Krylov
+    steps.  Properties that hold at any size, checked with one oracle matvec: the
+    returned vector has unit norm, its Rayleigh quotient and residual |Hx - E x| agree
+    with the oracle's FP64 H_eff, and the Ritz value bounds the Rayleigh quotient."""
+    Le, W1, W2, Re, th = heff_inputs(11, 256, 4, 256)
+    ctx.set_params(precision=precision, krylov_cap=12, lanczos_maxit=12)
+    try:
+        t = dev(th)
+        res = ctx.lanczos_ground(dev(Le), dev(W1), dev(W2), dev(Re), t)
+    finally:
+        ctx.set_params(precision=0, krylov_cap=32, lanczos_maxit=300)
+    x = t.cpu().numpy()
+    assert abs(np.linalg.norm(x) - 1) < 1e-12
+    y = oc.heff_apply(Le, W1, W2, Re, x)
+    E = np.vdot(x, y).real
+    assert abs(res["E_rq"] - E) <= 1e-10 * abs(E)
+    r = np.linalg.norm(y - E * x)
+    assert abs(res["resid_fp64"] - r) <= 1e-8 * r
+    # the Ritz value of the last Krylov step is the Rayleigh quotient of the returned
+    # vector for the operator Lanczos saw (exact for FP64, within the split-TF32
+    # matvec error for the mixed path)
+    assert abs(res["E"] - E) <= (1e-10 if precision == 0 else 1e-5) * abs(E)
+
+
 def svd_case(seed, m, n, charged):
     g = synth.rng(seed)
     M = synth.complex_gaussian(g, (m, n))
