@@ -42,13 +42,19 @@ __device__ double block_sum_all(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------- persistent reduction
-// All columns in one cooperative launch.  Per column j (trailing size m = n - j - 1):
-//   barrier; p = tau A v (one warp per row, all blocks), per-block partial of p^H v;
-//   barrier; every block sums the partials (same order everywhere), updates the rows it
-//   owns (r = b, b + nb, ...); block 0 updates row 0 first and then forms the reflector
-//   of column j + 1 from that row.
-// The grid barrier spins on a generation counter with a %globaltimer limit; if any wait
-// expires, an abort flag makes every block leave at its next barrier.
+// All columns in one cooperative launch, one grid barrier per column.  Entering column j
+// every block holds the reflector (v_j, tau_j) in its workspace and p_j = tau_j T_j v_j is
+// complete in global memory (T_j: the trailing block after column j-1).  Then:
+//   every block: s_j = p_j^H v_j (from the per-block partials, same order everywhere),
+//     w_j = p_j - (tau_j s_j / 2) v_j, the updated row j+1 of A, and from it reflector
+//     j+1 (block 0 also stores it for the back-transformation);
+//   each warp: for the rows it owns, T <- T - v_j w_j^H - w_j v_j^H, and in the same pass
+//     the row's entry of p_{j+1} = tau_{j+1} T_{j+1} v_{j+1} and its share of s_{j+1};
+//   grid barrier.
+// Rows are owned by warps in a fixed round robin over the global row index.  p and the
+// partial sums are double-buffered by column parity.  The grid barrier spins on a
+// generation counter with a %globaltimer limit; if any wait expires, an abort flag makes
+// every block leave at its next barrier.
 struct TriArgs {
   z* G;
   int64_t n;
@@ -56,11 +62,12 @@ struct TriArgs {
   z* tau;
   double* d;
   double* e;
-  z* p;
-  z* part;             // nb partial sums of p^H v
+  z* p;                // 2 x n: p of even / odd columns
+  z* part;             // 2 x nb partial sums of p^H v
   unsigned* bar;       // [0] arrivals, [1] generation
   int* abort_flag;
   int* status;
+  z* gws;              // per-block workspace (4 n) when n exceeds the shared cache
 };
 
 __device__ __forceinline__ uint64_t gtime() {
@@ -103,21 +110,22 @@ __device__ bool grid_barrier(const TriArgs& a) {
   return s_ok != 0;
 }
 
-// reflector of column j from row j of the trailing matrix (one block)
-__device__ void tri_reflector(const TriArgs& a, int64_t j, double* sh) {
+// Reflector from x_r = conj(row[r]), r < m (row already in the workspace): v (length m,
+// v[0] = 1), tau, beta with H^H x = beta e_1.  Every thread of the block returns the same
+// tau and beta.
+__device__ void make_reflector(const z* row, int64_t m, z* v, z* tau_out, double* beta_out,
+                               double* sh) {
   __shared__ double s_xn2;
-  const int64_t n = a.n, m = n - j - 1;
-  const z* row = a.G + j * n + j + 1;  // x_r = conj(row[r])
   double acc = 0;
   for (int64_t r = 1 + threadIdx.x; r < m; r += blockDim.x) {
-    const z v = __ldcg(row + r);
-    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+    const z x = row[r];
+    acc = fma(x.x, x.x, fma(x.y, x.y, acc));
   }
   acc = block_sum_all(acc, sh);
   if (threadIdx.x == 0) s_xn2 = acc;
   __syncthreads();
   const double xn2 = s_xn2;
-  const z alpha = m > 0 ? zconj(__ldcg(row)) : zmk(0, 0);
+  const z alpha = m > 0 ? zconj(row[0]) : zmk(0, 0);
   double beta;
   z t, scale;
   if (m == 0 || (xn2 == 0.0 && alpha.y == 0.0)) {
@@ -128,136 +136,169 @@ __device__ void tri_reflector(const TriArgs& a, int64_t j, double* sh) {
     const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
     beta = alpha.x >= 0 ? -nrm : nrm;
     t = zmk((beta - alpha.x) / beta, -alpha.y / beta);
-    const z den = zmk(alpha.x - beta, alpha.y);
+    const z den = zmk(alpha.x - beta, alpha.y);  // scale = 1 / (alpha - beta)
     const double dd = den.x * den.x + den.y * den.y;
     scale = zmk(den.x / dd, -den.y / dd);
   }
-  z* v = a.Hv + j * n;
   for (int64_t r = threadIdx.x; r < m; r += blockDim.x)
-    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(__ldcg(row + r)), scale);
-  if (threadIdx.x == 0) {
-    a.tau[j] = t;
-    a.d[j] = __ldcg(a.G + j * n + j).x;
-    if (m > 0) a.e[j] = beta;
-  }
+    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(row[r]), scale);
+  *tau_out = t;
+  *beta_out = beta;
   __syncthreads();
 }
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
-constexpr int64_t TRI_CACHE = 4096;  // v and w of up to this many rows in shared memory
+constexpr int64_t TRI_CACHE = 2048;  // workspace in shared memory up to this n
 
 __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
-  extern __shared__ z sm_vw[];  // [TRI_CACHE] v, then [TRI_CACHE] w
-  z* sv = sm_vw;
-  z* sw = sm_vw + TRI_CACHE;
+  extern __shared__ z sm_tri[];
   __shared__ double sh[32];
   __shared__ double shr[TRI_WARPS], shi[TRI_WARPS];
   __shared__ z s_cf;
   const int64_t n = a.n;
   const int nb = gridDim.x, b = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (b == 0) tri_reflector(a, 0, sh);
-  for (int64_t j = 0; j + 1 < n; ++j) {
-    const int64_t m = n - j - 1;
-    const z* v = a.Hv + j * n;
-    if (!grid_barrier(a)) return;
-    const bool cached = (m <= TRI_CACHE);
-    if (cached) {
-      for (int64_t c = threadIdx.x; c < m; c += blockDim.x) sv[c] = __ldcg(v + c);
-      __syncthreads();
+  // row g belongs to block g mod nb, warp (g / nb) mod TRI_WARPS: consecutive rows land on
+  // different SMs, so every SM's FP64 units share each column's work
+  const int64_t nwarps = (int64_t)nb * TRI_WARPS, own0 = (int64_t)b + (int64_t)nb * warp;
+  z* ws = (n <= TRI_CACHE) ? sm_tri : a.gws + (int64_t)b * 4 * n;
+  z* sv = ws;           // v_j
+  z* sw = ws + n;       // w_j
+  z* srow = ws + 2 * n; // updated row j+1
+  z* sv2 = ws + 3 * n;  // v_{j+1}
+  // reflector 0 from row 0, and p_0 = tau_0 T_0 v_0 over the owned rows
+  z t;
+  double beta;
+  {
+    const int64_t m = n - 1;
+    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) srow[c] = __ldcg(a.G + 1 + c);
+    __syncthreads();
+    make_reflector(srow, m, sv, &t, &beta, sh);
+    if (b == 0) {
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x) a.Hv[c] = sv[c];
+      if (threadIdx.x == 0) {
+        a.tau[0] = t;
+        a.d[0] = __ldcg(a.G).x;
+        if (m > 0) a.e[0] = beta;
+      }
     }
-    const z t = __ldcg(a.tau + j);
-    // p = tau A v
     double pr = 0, pi = 0;
-    for (int64_t r = (int64_t)b * TRI_WARPS + warp; r < m; r += (int64_t)nb * TRI_WARPS) {
-      const z* row = a.G + (j + 1 + r) * n + j + 1;
+    for (int64_t g = own0; g < n; g += nwarps) {  // global row g = local row g - 1
+      if (g < 1) continue;
+      const z* row = a.G + g * n + 1;
       double sr = 0, si = 0;
-      if (cached) {
 #pragma unroll 4
-        for (int64_t c = lane; c < m; c += 32) {
-          const z x = __ldcg(row + c), y = sv[c];
-          sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
-          si = fma(x.x, y.y, fma(x.y, y.x, si));
-        }
-      } else {
-#pragma unroll 4
-        for (int64_t c = lane; c < m; c += 32) {
-          const z x = __ldcg(row + c), y = __ldcg(v + c);
-          sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
-          si = fma(x.x, y.y, fma(x.y, y.x, si));
-        }
+      for (int64_t c = lane; c < m; c += 32) {
+        const z x = __ldcg(row + c), y = sv[c];
+        sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+        si = fma(x.x, y.y, fma(x.y, y.x, si));
       }
       sr = warp_sum_d(sr);
       si = warp_sum_d(si);
       if (lane == 0) {
         const z pv = zmul(t, zmk(sr, si));
-        a.p[r] = pv;
-        const z vr = cached ? sv[r] : __ldcg(v + r);
+        a.p[g - 1] = pv;
+        const z vr = sv[g - 1];
         pr += pv.x * vr.x + pv.y * vr.y;
         pi += pv.x * vr.y - pv.y * vr.x;
       }
     }
-    if (lane == 0) {
-      shr[warp] = pr;
-      shi[warp] = pi;
-    }
+    if (lane == 0) { shr[warp] = pr; shi[warp] = pi; }
     __syncthreads();
     if (threadIdx.x == 0) {
       double sa = 0, sb = 0;
-      for (int q = 0; q < TRI_WARPS; ++q) {
-        sa += shr[q];
-        sb += shi[q];
-      }
+      for (int q = 0; q < TRI_WARPS; ++q) { sa += shr[q]; sb += shi[q]; }
       a.part[b] = zmk(sa, sb);
     }
+  }
+  for (int64_t j = 0; j + 1 < n; ++j) {
     if (!grid_barrier(a)) return;
-    if (threadIdx.x == 0) {
+    const int64_t m = n - j - 1;          // size of T_j (local rows/cols 0..m-1 = global j+1..)
+    const z* pj = a.p + (j & 1) * n;
+    z* pn = a.p + ((j + 1) & 1) * n;
+    const z* partj = a.part + (j & 1) * nb;
+    z* partn = a.part + ((j + 1) & 1) * nb;
+    if (warp == 0) {  // the nb partials, loaded by 32 lanes at once and summed by shuffles
       double sa = 0, sb = 0;
-      for (int q = 0; q < nb; ++q) {
-        const z pq = __ldcg(a.part + q);
+      for (int q = lane; q < nb; q += 32) {
+        const z pq = __ldcg(partj + q);
         sa += pq.x;
         sb += pq.y;
       }
-      const z ts = zmul(t, zmk(sa, sb));
-      s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+      sa = warp_sum_d(sa);
+      sb = warp_sum_d(sb);
+      if (lane == 0) {
+        const z ts = zmul(t, zmk(sa, sb));
+        s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+      }
     }
     __syncthreads();
     const z cf = s_cf;
-    if (cached) {  // w = p + cf v once per block, not once per element
-      for (int64_t c = threadIdx.x; c < m; c += blockDim.x)
-        sw[c] = zadd(__ldcg(a.p + c), zmul(cf, sv[c]));
-      __syncthreads();
-    }
-    // A <- A - v w^H - w v^H on the rows this block owns (w = p + cf v)
-    for (int64_t r = b; r < m; r += nb) {
-      const z vr = cached ? sv[r] : __ldcg(v + r);
-      const z wr = cached ? sw[r] : zadd(__ldcg(a.p + r), zmul(cf, vr));
-      z* row = a.G + (j + 1 + r) * n + j + 1;
-      if (cached) {
-#pragma unroll 2
-        for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
-          const z vc = sv[c], wc = sw[c];
-          z x = __ldcg(row + c);
-          x = zsub(x, zmul(vr, zconj(wc)));
-          x = zsub(x, zmul(wr, zconj(vc)));
-          row[c] = x;
-        }
-      } else {
-        for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
-          const z vc = __ldcg(v + c);
-          const z wc = zadd(__ldcg(a.p + c), zmul(cf, vc));
-          z x = __ldcg(row + c);
-          x = zsub(x, zmul(vr, zconj(wc)));
-          x = zsub(x, zmul(wr, zconj(vc)));
-          row[c] = x;
-        }
-      }
-      if (r == 0) {  // block 0: row j + 1 is final, form the next reflector from it
-        __syncthreads();
-        tri_reflector(a, j + 1, sh);
+    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) sw[c] = zadd(__ldcg(pj + c), zmul(cf, sv[c]));
+    __syncthreads();
+    // updated row j+1 (local row 0), then reflector j+1 from its entries 1..m-1
+    const z v0 = sv[0], w0 = sw[0];
+    {
+      const z* row = a.G + (j + 1) * n + j + 1;
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
+        z x = __ldcg(row + c);
+        x = zsub(x, zmul(v0, zconj(sw[c])));
+        x = zsub(x, zmul(w0, zconj(sv[c])));
+        srow[c] = x;
       }
     }
+    __syncthreads();
+    const int64_t m2 = m - 1;  // size of T_{j+1}
+    z t2;
+    make_reflector(srow + 1, m2, sv2, &t2, &beta, sh);
+    if (b == 0) {
+      for (int64_t c = threadIdx.x; c < m2; c += blockDim.x) a.Hv[(j + 1) * n + c] = sv2[c];
+      if (threadIdx.x == 0) {
+        a.tau[j + 1] = t2;
+        a.d[j + 1] = srow[0].x;
+        if (m2 > 0) a.e[j + 1] = beta;
+      }
+    }
+    // owned rows r >= 1 of T_j: update, and dot with v_{j+1} for p_{j+1}
+    double pr = 0, pi = 0;
+    for (int64_t g = own0 + ((j + 2 > own0) ? ((j + 2 - own0 + nwarps - 1) / nwarps) * nwarps : 0);
+         g < n; g += nwarps) {
+      const int64_t r = g - (j + 1);  // local row in T_j
+      z* row = a.G + g * n + j + 1;
+      const z vr = sv[r], wr = sw[r];
+      double sr = 0, si = 0;
+#pragma unroll 4
+      for (int64_t c = 1 + lane; c < m; c += 32) {
+        z x = __ldcg(row + c);
+        x = zsub(x, zmul(vr, zconj(sw[c])));
+        x = zsub(x, zmul(wr, zconj(sv[c])));
+        row[c] = x;
+        const z q = sv2[c - 1];
+        sr = fma(x.x, q.x, fma(-x.y, q.y, sr));
+        si = fma(x.x, q.y, fma(x.y, q.x, si));
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) {
+        const z pv = zmul(t2, zmk(sr, si));
+        pn[r - 1] = pv;
+        const z vv = sv2[r - 1];
+        pr += pv.x * vv.x + pv.y * vv.y;
+        pi += pv.x * vv.y - pv.y * vv.x;
+      }
+    }
+    if (lane == 0) { shr[warp] = pr; shi[warp] = pi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0, sb = 0;
+      for (int q = 0; q < TRI_WARPS; ++q) { sa += shr[q]; sb += shi[q]; }
+      partn[b] = zmk(sa, sb);
+    }
+    // v_{j+1} becomes the current reflector
+    for (int64_t c = threadIdx.x; c < m2; c += blockDim.x) sv[c] = sv2[c];
+    t = t2;
+    __syncthreads();
   }
 }
 
@@ -517,9 +558,13 @@ unsigned gsz(int64_t n) {
 }
 }  // namespace
 
+constexpr int TRI_MAX_BLOCKS = 1216;
+
 size_t heig_scratch_bound(int64_t n, int64_t k) {
-  return ws_round(sizeof(z) * n * n) + 2 * ws_round(sizeof(z) * n) + 3 * ws_round(sizeof(double) * n) +
-         ws_round(sizeof(z) * 1216) + ws_round(sizeof(double) * k) + ws_round(sizeof(double) * (6 * n * k + k)) +
+  const size_t gws = n > TRI_CACHE ? ws_round(sizeof(z) * 4 * n * TRI_MAX_BLOCKS) : 0;
+  return ws_round(sizeof(z) * n * n) + 3 * ws_round(sizeof(z) * n) + 3 * ws_round(sizeof(double) * n) +
+         gws + ws_round(sizeof(z) * 2 * TRI_MAX_BLOCKS) + ws_round(sizeof(double) * k) +
+         ws_round(sizeof(double) * (6 * n * k + k)) +
          ws_round(sizeof(double) * n * k) + 2 * ws_round(sizeof(z) * n * k) + 2 * ws_round(sizeof(z) * k * k) +
          (size_t)(1 << 20);
 }
@@ -532,11 +577,16 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   const size_t top = c->ws.top;
   z* Hv = (z*)ws_alloc(c, ws_round(sizeof(z) * n * n));
   z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
-  z* p = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  z* p = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * n));
   double* d = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
   double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
   double* tn = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
-  z* part = (z*)ws_alloc(c, ws_round(sizeof(z) * 1216));
+  z* part = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * TRI_MAX_BLOCKS));
+  z* gws = n > TRI_CACHE ? (z*)ws_alloc(c, ws_round(sizeof(z) * 4 * n * TRI_MAX_BLOCKS)) : nullptr;
+  if (n > TRI_CACHE && !gws) {
+    c->ws.top = top;
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (tridiagonal workspace n=%lld)", (long long)n);
+  }
   double* work = (double*)ws_alloc(c, ws_round(sizeof(double) * (6 * n * k + k)));
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * n * k));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * n * k));
@@ -550,7 +600,7 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   {
     const double nn = (double)n;
     ProfScope ps(c, "heig_tridiag", 24.0 * (nn - 1) * nn * (2 * nn - 1) / 6.0);
-    const size_t tri_smem = 2 * TRI_CACHE * sizeof(z);
+    const size_t tri_smem = 4 * TRI_CACHE * sizeof(z);
     static int nsm = 0, occ = 0;
     if (!nsm) {
       TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_persistent,
@@ -561,9 +611,10 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
     }
     if (occ < 1) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal kernel cannot be resident");
     TNT_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 256, st));
-    TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status};
+    TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status,
+               gws};
     void* args[] = {&ta};
-    const int nb = std::min(nsm, 1216);
+    const int nb = std::min(nsm, TRI_MAX_BLOCKS);
     TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
                                                 dim3(TRI_THREADS), args, tri_smem, st));
     c->launches += 1;

@@ -214,6 +214,22 @@ def test_svd_trunc_matches_oracle(ctx, m, n, charged, side):
     assert abs(info["disc"] - inf_r["disc"]) <= 1e-10 * max(inf_r["disc"], 1e-14)
 
 
+def test_svd_block_beyond_shared_workspace(ctx):
+    """A 2200-row Gram block: the tridiagonal reduction keeps its per-block workspace in
+    global memory above 2048 rows."""
+    M, _, _ = svd_case(21, 2200, 2100, False)
+    ctx.set_params(chi_max=40)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), None, None, side=0)
+    finally:
+        ctx.set_params(chi_max=1 << 40)
+    s_ref = np.linalg.svd(M, compute_uv=False)
+    assert info["chi"] == 40
+    assert np.abs(S - s_ref[:40]).max() < 1e-11 * s_ref[0]
+    U = U.cpu().numpy()
+    assert np.abs(U.conj().T @ U - np.eye(40)).max() < 1e-11
+
+
 def test_svd_large_block_cfg2_shape(ctx):
     """One dense 1024 x 1024 block (theta of chi = 256, d = 4) through the multi-launch
     Jacobi path, truncated to chi = 256."""
