@@ -371,6 +371,8 @@ CLASSES = {
     "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("hbm", "byte"),
     "multiaxpy": ("hbm", "byte"), "jacobi_small": ("alu", None), "heig_tridiag": ("alu", "flop"),
     "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
+    "cgemm_grouped": ("tensor", "flop"), "zgemm_grouped": ("alu", "flop"),
+    "u1_wop": ("hbm", "byte"), "u1_pack_theta": ("hbm", "byte"), "u1_gather": ("hbm", "byte"),
 }
 
 
@@ -400,6 +402,134 @@ def roofline(cls, ms, n, work, peaks, src):
                 peak_source=f"{src} bf16 burst x nominal fp64/bf16 ratio")
 
 
+# ---------------------------------------------------------------- grouped U(1) workloads
+def u1_problem_inputs(seed, chi_l, chi_r, q_l, q_r, n_sec_l, n_sec_r, d, U):
+    """Synthetic U(1) H_eff problem: Gaussian sector profiles on both bonds, Hermitian
+    masked environments, the Bose-Hubbard MPO at (J = 1, U), compact random theta."""
+    from paper_1610_02244_gb300 import synth, tnt
+    g = synth.rng(seed)
+    qa = synth.gaussian_sector_labels(chi_l, n_sec_l, 2.0, q_l)
+    qb = synth.gaussian_sector_labels(chi_r, n_sec_r, 2.0, q_r)
+    Le = synth.hermitian_env(g, chi_l) * synth.env_mask(qa, qa)
+    Re = synth.hermitian_env(g, chi_r) * synth.env_mask(qb, qb)
+    W = tnt.bh_mpo_site(d - 1, J, U, MU, 0.0, 2.0, 0.0)
+    return {"L": Le, "R": Re, "W": W, "qa": qa, "qb": qb, "g": g}
+
+
+def run_grouped(args, ws, rank, local):
+    """--workload u1: one U(1) two-site eigensolve at chi = 1024, d = 5 (sector sizes 1..~200,
+    15 sectors); --workload chains: 32 independent chains (chi = 256, d = 5, U/J = 1..8) whose
+    eigensolves run in lock step with one grouped matvec per Krylov step."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = tnt.Context(local)
+    prec = tnt.TNT_PREC_MIXED if args.precision == "mixed" else tnt.TNT_PREC_FP64
+    ctx.set_params(krylov_cap=KRYLOV, lanczos_maxit=KRYLOV, precision=prec, lanczos_tol=1e-12)
+    if args.workload == "u1":
+        specs = [(1024, 1024, 31, 33, 15, 15, 5, 3.4)]
+        desc = ("U(1) two-site eigensolve, Bose-Hubbard d=5 D=4 U=3.4, chi=1024 both bonds, "
+                "15 charge sectors of 1..~200 (Gaussian profile), 32 Krylov steps")
+    else:
+        specs = [(256, 256, 15, 17, 9, 9, 5, float(u)) for u in np.linspace(1.0, 8.0, 32)]
+        desc = ("32 independent U(1) chains, Bose-Hubbard d=5 D=4, U/J = 1..8, chi=256, "
+                "9 charge sectors each, lock-step eigensolves, 32 Krylov steps")
+    probs, keep, xs = [], [], []
+    for i, sp in enumerate(specs):
+        inp = u1_problem_inputs(2000 + 97 * rank + i, *sp)
+        tl = {k: torch.from_numpy(np.ascontiguousarray(inp[k])).to(dev) for k in ("L", "R", "W")}
+        p = tnt.U1Problem(tl["L"], tl["W"], tl["W"], tl["R"], inp["qa"], inp["qb"], synth.BH_WQ)
+        probs.append(p)
+        keep.append((tl, inp))
+        n = ctx.u1_size(p)
+        xs.append(torch.from_numpy(synth.complex_gaussian(inp["g"], (n,))).to(dev))
+    x0 = torch.cat(xs)
+    x = torch.empty_like(x0)
+    solve = (lambda: ctx.lanczos_ground_u1(probs[0], x)) if len(probs) == 1 else \
+        (lambda: ctx.lanczos_ground_u1_batched(probs, x))
+    _, flops_mv = ctx.heff_apply_u1(probs, x0, precision=prec)
+    st = torch.cuda.current_stream(dev)
+
+    def timed(pr, n):
+        ctx.set_params(precision=pr)
+        x.copy_(x0)
+        solve()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n):
+            x.copy_(x0)
+            solve()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    # the same eigensolves in the other precision, for the mixed-vs-FP64 comparison
+    other = tnt.TNT_PREC_FP64 if prec == tnt.TNT_PREC_MIXED else tnt.TNT_PREC_MIXED
+    solve_ms = {("fp64" if other == tnt.TNT_PREC_FP64 else "mixed"): timed(other, max(1, min(args.steps, 2)))}
+    ctx.set_params(precision=prec)
+    for _ in range(args.warmup):
+        x.copy_(x0)
+        solve()
+    torch.cuda.synchronize()
+    # kernel classes (plain launches so each is timed with events)
+    per_class = {}
+    for cls in ("cgemm_grouped", "zgemm_grouped", "u1_wop", "u1_pack_theta", "u1_gather",
+                "multidot", "multiaxpy"):
+        ctx.profile_select(cls)
+        x.copy_(x0)
+        solve()
+        per_class[cls] = ctx.profile_read()
+    ctx.profile_select(None)
+    dom = max(per_class, key=lambda k: per_class[k][0])
+    ctx.profile_select(dom)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nmv = 0
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            x.copy_(x0)
+            r = solve()
+            rs = r if isinstance(r, list) else [r]
+            nmv += max(q["n_matvec"] for q in rs)
+        e1.record(st)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms_step = dist_max(e0.elapsed_time(e1) / args.steps, ws)
+    solve_ms[args.precision] = ms_step
+    dom_ms, dom_n, dom_work = ctx.profile_read()
+    ctx.profile_select(None)
+    launches = ctx.launch_count() - launches0
+    flops_step = nmv / args.steps * flops_mv
+    value = ws * flops_step / (ms_step * 1e-3) / 1e12
+    if rank == 0:
+        peaks, src = load_peaks()
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == tnt.TNT_PREC_FP64 else "tf32x3+f64", "data": "synthetic",
+                "config": {"workload": desc, "problems": len(probs), "precision": args.precision,
+                           "compact_entries": int(x0.numel()), "block_flops_per_matvec": flops_mv,
+                           "l2": "inputs larger than L2 (Krylov basis per step)"},
+                "solve_ms": solve_ms, "fp64_over_mixed_time": solve_ms["fp64"] / solve_ms["mixed"],
+                "kernel_ms_per_step": {k: v[0] for k, v in per_class.items()},
+                "kernel_rooflines": {k: roofline(k, *v, peaks, src) for k, v in per_class.items() if v[1] > 0},
+                "roofline": roofline(dom, dom_ms, dom_n, dom_work, peaks, src),
+                "gpu_launches": launches, "clocks": clk.summary(),
+                "energies": [q["E_rq"] for q in rs][:4]}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,10 +538,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["update", "u1", "chains"], default="update")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != "update":
+        return run_grouped(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

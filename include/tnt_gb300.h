@@ -68,6 +68,7 @@ typedef struct tnt_ctx tnt_ctx;
 typedef struct tnt_mpo tnt_mpo;
 typedef struct tnt_mps tnt_mps;
 typedef struct tnt_dmrg tnt_dmrg;
+typedef struct tnt_tebd tnt_tebd;
 
 /*
  * Simulation parameters (the library's system settings, App. A.3 and App. B.5).
@@ -293,6 +294,89 @@ int tnt_mps_norm2(tnt_ctx* ctx, const tnt_mps* mps, double* norm2);
 int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* mps, const tnt_mpo* mpo, tnt_dmrg** out);
 int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
 int tnt_dmrg_destroy(tnt_dmrg* dmrg);
+
+/* ------------------------------------------------------------------ U(1) blocks, grouped */
+
+/* One two-site H_eff problem with U(1) boson-number labels (App. A.1.1: every leg carries
+ * quantum numbers; here a bond label counts the bosons to the left of the bond, and the
+ * physical index s is its own boson number).  theta[a,s1,s2,b] is non-zero only where
+ * q_b = q_a + s1 + s2, L[a',w,a] only where q_a' = q_a + wq[w], R[b',w,b] only where
+ * q_b' = q_b + wq[w]; wq are the charges of the MPO bond index (the hand-built
+ * Bose-Hubbard MPO of tnt_bh_mpo_site: wq = {0, +1, -1, 0}).  Environments and W are the
+ * dense device arrays of tnt_heff_apply (entries outside the blocks are never read);
+ * h_qa, h_qb, h_wq are host arrays, copied; labels must be non-decreasing.
+ *
+ * Compact theta (the vectors of the calls below): the blocks only, left sectors in
+ * ascending charge; within sector q the slab [a in q][(s1, s2) row-major][b in the right
+ * sector of charge q + s1 + s2] (pairs whose right sector is absent are skipped). */
+typedef struct {
+  const tnt_cplx* d_L;   /* chl x D x chl */
+  const tnt_cplx* d_W1;  /* D x D x d x d, site i   */
+  const tnt_cplx* d_W2;  /* D x D x d x d, site i+1 */
+  const tnt_cplx* d_R;   /* chr x D x chr */
+  int64_t chl, d, D, chr;
+  const int64_t* h_qa;   /* chl labels of the left bond  */
+  const int64_t* h_qb;   /* chr labels of the right bond */
+  const int* h_wq;       /* D charges of the MPO bond index */
+} tnt_u1_problem;
+
+/* Length of the compact theta of one problem (host only; TNT_E_INVALID on bad labels). */
+int tnt_u1_size(const tnt_u1_problem* prob, int64_t* n);
+/* Dense theta (chl x d x d x chr, device) -> compact (device), and back (the dense result
+ * is zero outside the blocks).  Integer index work only (App. B.1.2 reshape). */
+int tnt_u1_pack(tnt_ctx* ctx, const tnt_u1_problem* prob, const tnt_cplx* d_theta, tnt_cplx* d_x);
+int tnt_u1_unpack(tnt_ctx* ctx, const tnt_u1_problem* prob, const tnt_cplx* d_x, tnt_cplx* d_theta);
+/* a3 over U(1) blocks, several problems at once (independent chains, each with its own
+ * environments, MPO and labels): y_p = H_eff,p x_p (Sec. 4.2 Listing 1 order) where x and
+ * y hold the problems' compact vectors back to back.  All blocks of all problems go into
+ * one grouped launch per contraction stage; precision TNT_PREC_FP64 (FP64 grouped GEMM)
+ * or TNT_PREC_MIXED (split TF32 on tcgen05, FP32 accumulate, tile shape autotuned once
+ * per block structure and cached in the context).  h_flops (optional) receives the
+ * algorithmic FLOPs of the block-sparse matvec.  x and y must not alias.  Returns
+ * TNT_E_TIMEOUT if a tensor-core pipeline wait expired (the result is then invalid). */
+int tnt_heff_apply_u1(tnt_ctx* ctx, int nprob, const tnt_u1_problem* probs, const tnt_cplx* d_x,
+                      tnt_cplx* d_y, int precision, double* h_flops);
+/* a4 over U(1) blocks: the Lanczos ground state of tnt_lanczos_ground on a compact theta
+ * (in: start vector, out: ground state, unit norm), with the grouped matvec replayed as a
+ * CUDA graph and, in TNT_PREC_MIXED, the FP64 grouped matvec for the win-back. */
+int tnt_lanczos_ground_u1(tnt_ctx* ctx, const tnt_u1_problem* prob, tnt_cplx* d_x,
+                          tnt_lanczos_result* res);
+/* a4 for several independent problems at once (e.g. chains at different U/J): one
+ * Lanczos recurrence per problem, run in lock step so that every Krylov step is one
+ * grouped matvec over all problems; inner products, norms, the tridiagonal eigenpairs and
+ * the stop rule are per problem, and a converged problem is frozen while the others go
+ * on.  d_x holds the compact start vectors back to back (out: ground states, unit norm
+ * each); h_res receives nprob results.  TNT_E_NOCONV if any problem hit the cap. */
+int tnt_lanczos_ground_u1_batched(tnt_ctx* ctx, int nprob, const tnt_u1_problem* probs,
+                                  tnt_cplx* d_x, tnt_lanczos_result* h_res);
+/* Graph replay of the grouped matvec on (1, default) or off (plain launches; also off
+ * while a kernel class is being profiled). */
+int tnt_set_graphs(tnt_ctx* ctx, int on);
+/* The autotuner's choice for these problems' block structure: h_tiles[0] = N tile of the
+ * L.theta stage, [1] = N tile of the T3.R stage, [2] = its split-K.  TNT_E_INVALID if the
+ * structure has not been tuned yet by a call above. */
+int tnt_u1_tiles(tnt_ctx* ctx, int nprob, const tnt_u1_problem* probs, int* h_tiles);
+
+/* Second-order Trotter TEBD (Sec. 3, Trotterised update; Sec. 5, real-time evolution with
+ * the accumulated truncation error and 1 - <psi|psi> tracked).  The paper prints no scheme;
+ * one step is exp(-i H_odd dt/2) exp(-i H_even dt) exp(-i H_odd dt/2), odd bonds (1,2),
+ * (3,4), ... (1-based), hbar = 1, with the Bose-Hubbard bond term
+ *   h = -J (b+ (x) b + b (x) b+) + c1 h_site (x) I + c2 I (x) h_site,
+ *   h_site = U/2 n(n-1) - mu n,  c = 1 on the end sites, 1/2 elsewhere.
+ * Gates within a layer go in ascending bond order; before each the orthogonality centre
+ * moves to the bond by exact SVD moves, then theta = A_i A_{i+1} (a1), theta' = G theta
+ * (a2), truncated SVD by the context's parameters (a5, a6), A_i <- U, A_{i+1} <- S V^H
+ * (a7).  The state is NOT renormalised: the discarded weight leaves <psi|psi>.
+ * create: the MPS (borrowed; it must outlive the handle and is updated in place) gets its
+ *   centre at site 0 by exact moves; n_max + 1 must equal the MPS's d; the gates are built
+ *   on the host in FP64.  TNT_E_INVALID on bad arguments.
+ * step: one Trotter step; stats gets the sums of the step's truncation errors (Eq. 3) and
+ *   discarded weights, the largest bond and the step's device time.  Bond dimensions are
+ *   capped by the context's chi_max and by the MPS's storage (its chi_cap). */
+int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* mps, int n_max, double J, double U, double mu,
+                    double dt, tnt_tebd** out);
+int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* tebd, tnt_step_stats* stats);
+int tnt_tebd_destroy(tnt_tebd* tebd);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -56,6 +56,13 @@ class tnt_sweep_stats(C.Structure):
                 ("seconds", C.c_double)]
 
 
+class tnt_u1_problem(C.Structure):
+    _fields_ = [("d_L", C.c_void_p), ("d_W1", C.c_void_p), ("d_W2", C.c_void_p),
+                ("d_R", C.c_void_p), ("chl", C.c_int64), ("d", C.c_int64), ("D", C.c_int64),
+                ("chr", C.c_int64), ("h_qa", C.c_void_p), ("h_qb", C.c_void_p),
+                ("h_wq", C.c_void_p)]
+
+
 class tnt_step_stats(C.Structure):
     _fields_ = [("err_sum", C.c_double), ("disc_sum", C.c_double), ("max_chi", C.c_int64),
                 ("seconds", C.c_double)]
@@ -106,6 +113,18 @@ SIGNATURES = {
     "tnt_dmrg_create": [P, P, P, C.POINTER(P)],
     "tnt_dmrg_sweep": [P, P, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_destroy": [P],
+    "tnt_tebd_create": [P, P, I, D, D, D, D, C.POINTER(P)],
+    "tnt_u1_size": [C.POINTER(tnt_u1_problem), PI64],
+    "tnt_u1_pack": [P, C.POINTER(tnt_u1_problem), P, P],
+    "tnt_u1_unpack": [P, C.POINTER(tnt_u1_problem), P, P],
+    "tnt_heff_apply_u1": [P, I, C.POINTER(tnt_u1_problem), P, P, I, PD],
+    "tnt_lanczos_ground_u1": [P, C.POINTER(tnt_u1_problem), P, C.POINTER(tnt_lanczos_result)],
+    "tnt_lanczos_ground_u1_batched": [P, I, C.POINTER(tnt_u1_problem), P,
+                                      C.POINTER(tnt_lanczos_result)],
+    "tnt_set_graphs": [P, I],
+    "tnt_u1_tiles": [P, I, C.POINTER(tnt_u1_problem), C.POINTER(C.c_int)],
+    "tnt_tebd_step": [P, P, C.POINTER(tnt_step_stats)],
+    "tnt_tebd_destroy": [P],
 }
 _RESTYPE = {"tnt_last_error": C.c_char_p, "tnt_launch_count": C.c_int64}
 

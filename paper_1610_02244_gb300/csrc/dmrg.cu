@@ -6,33 +6,12 @@
 #include <vector>
 
 #include "heff_plan.cuh"
-
-struct tnt_mpo {
-  int L = 0, d = 0, D = 4;
-  std::vector<tnt::z*> W;  // per site, D x D x d x d (device)
-  tnt::z* left = nullptr;   // boundary environment L_0[0,w,0] (device, D)
-  tnt::z* right = nullptr;  // boundary R_{L}[0,w,0]
-};
-
-struct tnt_mps {
-  int L = 0, d = 0;
-  std::vector<int64_t> chi, cap;      // bonds 0..L
-  std::vector<tnt::z*> A;             // sites 0..L-1, capacity cap[j] x d x cap[j+1]
-  std::vector<std::vector<int64_t>> q;  // bond labels (empty vectors: no labels)
-  bool labelled = false;
-};
-
-struct tnt_dmrg {
-  tnt_ctx* ctx = nullptr;
-  tnt_mps* mps = nullptr;
-  const tnt_mpo* mpo = nullptr;
-  std::vector<tnt::z*> Lenv, Renv;  // Lenv[i]: sites 0..i-1 (i = 0..L); Renv[i]: sites i..L-1
-  size_t scratch = 0;
-};
+#include "mps.cuh"
+#include "u1.cuh"
 
 namespace tnt {
 
-static int64_t ipow_cap(int64_t d, int64_t k, int64_t cap) {
+int64_t ipow_cap(int64_t d, int64_t k, int64_t cap) {
   int64_t r = 1;
   for (int64_t i = 0; i < k; ++i) {
     r *= d;
@@ -41,26 +20,19 @@ static int64_t ipow_cap(int64_t d, int64_t k, int64_t cap) {
   return std::min(r, cap);
 }
 
-static std::vector<int64_t> labels_or_zero(const tnt_mps* m, int bond) {
+std::vector<int64_t> labels_or_zero(const tnt_mps* m, int bond) {
   if (m->labelled) return m->q[bond];
   return std::vector<int64_t>((size_t)m->chi[bond], 0);
 }
 
 // exact SVD parameters for gauge moves (no truncation beyond exact zeros)
-static tnt_params exact_params(const tnt_params& p) {
+tnt_params exact_params(const tnt_params& p) {
   tnt_params e = p;
   e.chi_max = (int64_t)1 << 40;
   e.trunc_abs = -1.0;
   e.trunc_err = 0.0;
   return e;
 }
-
-struct ParamsGuard {
-  Ctx* c;
-  tnt_params saved;
-  ParamsGuard(Ctx* cc, const tnt_params& p) : c(cc), saved(cc->params) { c->params = p; }
-  ~ParamsGuard() { c->params = saved; }
-};
 
 // grow Lenv over one site: Lout = env_left(Lin, W, A)
 static int dmrg_env_left(Ctx* c, tnt_dmrg* g, int i) {
@@ -89,11 +61,37 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
   const int64_t d = m->d, D = g->mpo->D;
   const int64_t chl = m->chi[i], chm = m->chi[i + 1], chr = m->chi[i + 2];
   const int64_t n = chl * d * d * chr;
+  // labelled bonds with sorted labels: the eigensolve runs on the U(1) blocks only
+  std::vector<U1Spec> spec;
+  U1Plan up;
+  if (m->labelled && (int64_t)g->mpo->wq.size() == D &&
+      std::is_sorted(m->q[i].begin(), m->q[i].end()) &&
+      std::is_sorted(m->q[i + 2].begin(), m->q[i + 2].end())) {
+    spec.resize(1);
+    U1Spec& s = spec[0];
+    s.L = g->Lenv[i]; s.R = g->Renv[i + 2]; s.W1 = g->mpo->W[i]; s.W2 = g->mpo->W[i + 1];
+    s.chl = chl; s.chr = chr; s.d = d; s.D = D;
+    s.qa = m->q[i]; s.qb = m->q[i + 2]; s.wq = g->mpo->wq;
+    TNT_TRY(u1_layout(c, spec, &up));
+    if (c->ws.top == 0)
+      TNT_TRY(ws_reserve(c, std::max(g->scratch, ws_round(sizeof(z) * n) + ws_round(sizeof(z) * up.n) + up.bytes +
+                                                     lanczos_scratch_bound(up.n, c->params.krylov_cap) + (4 << 20))));
+  }
   const size_t top = c->ws.top;
   z* theta = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
   if (!theta) return set_err(c, TNT_E_ALLOC, "scratch exhausted (theta)");
   TNT_TRY(theta_form_impl(c, m->A[i], m->A[i + 1], chl, d, chm, chr, theta));
-  {
+  if (!spec.empty()) {
+    size_t t2 = c->ws.top;
+    z* x = (z*)ws_alloc(c, ws_round(sizeof(z) * up.n));
+    if (!x) return set_err(c, TNT_E_ALLOC, "scratch exhausted (compact theta)");
+    TNT_TRY(u1_convert(c, spec[0], theta, x, 1));
+    TNT_TRY(u1_prepare(c, spec, &up));
+    int r = lanczos_run(c, U1MatVec(up), x, lz);
+    if (r != TNT_OK && r != TNT_E_NOCONV) return r;
+    TNT_TRY(u1_convert(c, spec[0], x, theta, 0));
+    c->ws.top = t2;
+  } else {
     HeffPlan p;
     size_t t2 = c->ws.top;
     TNT_TRY(heff_prepare(c, g->Lenv[i], g->mpo->W[i], g->mpo->W[i + 1], g->Renv[i + 2], chl, d, D,
@@ -114,9 +112,14 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
   std::vector<int64_t> bq((size_t)capk);
   // U -> A_i (chl x d x k), X -> A_{i+1} (k x d x chr): the kernels write densely with
   // leading dimension k, exactly the site layouts
-  TNT_TRY(svd_trunc_impl(c, theta, chl * d, d * chr, rq.data(), cq.data(),
-                         dir > 0 ? TNT_SVD_LEFT : TNT_SVD_RIGHT, 1, m->A[i], m->A[i + 1], S.data(),
-                         bq.data(), tr));
+  {
+    tnt_params pp = c->params;  // the site storage bounds the kept dimension
+    pp.chi_max = std::min(pp.chi_max, m->cap[i + 1]);
+    ParamsGuard pg(c, pp);
+    TNT_TRY(svd_trunc_impl(c, theta, chl * d, d * chr, rq.data(), cq.data(),
+                           dir > 0 ? TNT_SVD_LEFT : TNT_SVD_RIGHT, 1, m->A[i], m->A[i + 1],
+                           S.data(), bq.data(), tr));
+  }
   m->chi[i + 1] = tr->chi;
   if (m->labelled) m->q[i + 1].assign(bq.begin(), bq.begin() + tr->chi);
   c->ws.top = top;
@@ -152,6 +155,7 @@ int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, dou
   o->L = L;
   o->d = n_max + 1;
   o->D = 4;
+  o->wq = {0, 1, -1, 0};  // b+ placed to the left: bra has one boson more (w = 1)
   const size_t nW = (size_t)16 * o->d * o->d;
   std::vector<z> h(nW);
   for (int j = 0; j < L; ++j) {

@@ -42,6 +42,8 @@ int heff_run(Ctx* c, const HeffPlan& p, const z* theta, z* y, int precision);
 int heff_run_f64(Ctx* c, const HeffPlan& p, const z* theta, z* y);
 
 // split-TF32 tensor-core path
+// 3-D TMA map over planes[4][rows][K] (FP32, K % 4 == 0): box 16 x box_rows x 1, 64 B swizzle
+int tma_map_planes(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows);
 size_t heff_mixed_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr);
 int heff_mixed_prepare(Ctx* c, HeffPlan* p);
 int heff_run_mixed(Ctx* c, const HeffPlan& p, const z* theta, z* y);
@@ -56,8 +58,20 @@ int theta_form_impl(Ctx* c, const z* A, const z* B, int64_t chl, int64_t d, int6
 int gate_apply_impl(Ctx* c, const std::vector<z>& G, const z* theta, int64_t chl, int64_t d,
                     int64_t chr, z* out);
 
-// Lanczos (lanczos.cu)
+// Lanczos (lanczos.cu) on any Hermitian operator given as a matvec y = A x over n complex
+// entries; precision selects the matvec path (the win-back asks for TNT_PREC_FP64).
+struct MatVec {
+  int64_t n = 0;
+  virtual int apply(Ctx* c, const z* x, z* y, int precision) const = 0;
+  virtual ~MatVec() = default;
+};
 size_t lanczos_scratch_bound(int64_t n, int krylov_cap);
+int lanczos_run(Ctx* c, const MatVec& A, z* theta, tnt_lanczos_result* res);
 int lanczos_impl(Ctx* c, const HeffPlan& p, z* theta, tnt_lanczos_result* res);
+// independent problems in lock step: off[p] .. off[p+1] is problem p's part of the vectors
+// (A must be block diagonal over those parts); one result per problem
+size_t lanczos_batched_scratch_bound(int64_t n, int nprob, int krylov_cap);
+int lanczos_batched(Ctx* c, const MatVec& A, const std::vector<int64_t>& off, z* x,
+                    std::vector<tnt_lanczos_result>* out);
 
 }  // namespace tnt

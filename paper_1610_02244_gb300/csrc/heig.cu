@@ -51,7 +51,8 @@ __device__ double block_sum_all(double v, double* sh) {
 //   each warp: for the rows it owns, T <- T - v_j w_j^H - w_j v_j^H, and in the same pass
 //     the row's entry of p_{j+1} = tau_{j+1} T_{j+1} v_{j+1} and its share of s_{j+1};
 //   grid barrier.
-// Rows are owned by warps in a fixed round robin over the global row index.  p and the
+// Row g belongs to block g mod nb and, within it, to warp (g / nb) mod 16, so the rows
+// left at every column stay spread over all blocks.  p and the
 // partial sums are double-buffered by column parity.  The grid barrier spins on a
 // generation counter with a %globaltimer limit; if any wait expires, an abort flag makes
 // every block leave at its next barrier.

@@ -489,9 +489,18 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
+// one block per problem: problem p's alpha, beta, y at p * 64, out at p * 2 (skipped
+// where skip[p] is set)
 __global__ void k_tridiag_lowest(const double* __restrict__ alpha,
                                  const double* __restrict__ beta, int k,
-                                 double* __restrict__ out, double* __restrict__ y) {
+                                 double* __restrict__ out, double* __restrict__ y,
+                                 const int* __restrict__ skip) {
+  const int pb = blockIdx.x;
+  if (skip && skip[pb]) return;
+  alpha += 64 * pb;
+  beta += 64 * pb;
+  out += 2 * pb;
+  y += 64 * pb;
   __shared__ double a[64], b[64];
   __shared__ double lo_s, hi_s;
   const int l = threadIdx.x;
@@ -605,7 +614,16 @@ __global__ void k_tridiag_lowest(const double* __restrict__ alpha,
 int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, double* d_out,
                    double* d_y) {
   if (k < 1 || k > 64) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal size %d", k);
-  k_tridiag_lowest<<<1, 32, 0, c->stream>>>(d_alpha, d_beta, k, d_out, d_y);
+  k_tridiag_lowest<<<1, 32, 0, c->stream>>>(d_alpha, d_beta, k, d_out, d_y, nullptr);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int tridiag_lowest_batched(Ctx* c, const double* d_alpha, const double* d_beta, int k,
+                           double* d_out, double* d_y, int nprob, const int* d_skip) {
+  if (k < 1 || k > 64) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal size %d", k);
+  k_tridiag_lowest<<<nprob, 32, 0, c->stream>>>(d_alpha, d_beta, k, d_out, d_y, d_skip);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;

@@ -57,11 +57,11 @@ size_t lanczos_scratch_bound(int64_t n, int krylov_cap) {
          (size_t)(2 << 20);
 }
 
-static int lanczos_cycle_loop(Ctx* c, const HeffPlan& p, z* theta, int precision,
+static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
                               int max_matvec, tnt_lanczos_result* res, z* V, z* w,
                               double* dsc) {
   const tnt_params& P = c->params;
-  const int64_t n = p.chl * p.d * p.d * p.chr;
+  const int64_t n = A.n;
   const int cap = P.krylov_cap;
   z* dots = (z*)dsc;                  // 64 complex
   double* norm2 = dsc + 128;          // 1
@@ -88,7 +88,7 @@ static int lanczos_cycle_loop(Ctx* c, const HeffPlan& p, z* theta, int precision
     bool stop = false, conv = false;
     for (int k = 0; k < cap; ++k) {
       z* vk = V + (int64_t)k * n;
-      TNT_TRY(heff_run(c, p, vk, w, precision));
+      TNT_TRY(A.apply(c, vk, w, precision));
       ++total;
       TNT_TRY(vec_norm2(c, w, n, norm2_w));
       TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, dots));
@@ -139,9 +139,23 @@ static int lanczos_cycle_loop(Ctx* c, const HeffPlan& p, z* theta, int precision
   }
 }
 
+namespace {
+struct HeffMatVec : MatVec {
+  const HeffPlan& p;
+  explicit HeffMatVec(const HeffPlan& pp) : p(pp) { n = pp.chl * pp.d * pp.d * pp.chr; }
+  int apply(Ctx* c, const z* x, z* y, int precision) const override {
+    return heff_run(c, p, x, y, precision);
+  }
+};
+}  // namespace
+
 int lanczos_impl(Ctx* c, const HeffPlan& p, z* theta, tnt_lanczos_result* res) {
+  return lanczos_run(c, HeffMatVec(p), theta, res);
+}
+
+int lanczos_run(Ctx* c, const MatVec& A, z* theta, tnt_lanczos_result* res) {
   const tnt_params& P = c->params;
-  const int64_t n = p.chl * p.d * p.d * p.chr;
+  const int64_t n = A.n;
   const int cap = P.krylov_cap;
   if (cap < 2 || cap > 64) return set_err(c, TNT_E_INVALID, "krylov_cap %d outside [2, 64]", cap);
   TNT_TRY(pinned_reserve(c, 64 * sizeof(double)));
@@ -152,14 +166,14 @@ int lanczos_impl(Ctx* c, const HeffPlan& p, z* theta, tnt_lanczos_result* res) {
   if (!V || !w || !w2 || !dsc) return set_err(c, TNT_E_ALLOC, "scratch exhausted (Lanczos)");
   *res = tnt_lanczos_result{};
   const int prec = P.precision;
-  TNT_TRY(lanczos_cycle_loop(c, p, theta, prec, P.lanczos_maxit, res, V, w, dsc));
+  TNT_TRY(lanczos_cycle_loop(c, A, theta, prec, P.lanczos_maxit, res, V, w, dsc));
   if (prec == TNT_PREC_MIXED) {
     // accuracy win-back: one FP64 matvec for the Rayleigh quotient and the true residual
     double* hp = c->h_pinned;
     z* dot = (z*)dsc;
     double* norm2 = dsc + 128;
     double* Erq = dsc + 130;
-    TNT_TRY(heff_run_f64(c, p, theta, w));
+    TNT_TRY(A.apply(c, theta, w, TNT_PREC_FP64));
     res->n_matvec += 1;
     TNT_TRY(vec_dot(c, theta, w, n, dot));
     k_copy_re<<<1, 32, 0, c->stream>>>(dot, Erq);
@@ -174,7 +188,7 @@ int lanczos_impl(Ctx* c, const HeffPlan& p, z* theta, tnt_lanczos_result* res) {
     if (res->resid_fp64 > 1e-5 * std::fabs(res->E_rq) && res->n_matvec < P.lanczos_maxit) {
       // not accurate enough for the FP64 energy: continue in FP64 from this vector
       tnt_lanczos_result r2{};
-      TNT_TRY(lanczos_cycle_loop(c, p, theta, TNT_PREC_FP64, P.lanczos_maxit - res->n_matvec,
+      TNT_TRY(lanczos_cycle_loop(c, A, theta, TNT_PREC_FP64, P.lanczos_maxit - res->n_matvec,
                                  &r2, V, w, dsc));
       res->n_matvec += r2.n_matvec;
       res->E = r2.E;

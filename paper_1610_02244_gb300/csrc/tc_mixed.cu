@@ -20,10 +20,12 @@
 #include <cmath>
 
 #include "heff_plan.cuh"
+#include "tc_common.cuh"
 
 namespace tnt {
 
 namespace {
+using namespace tc;
 constexpr int BM = 128, BN = 128, BK = 16;  // BK in FP32 elements: 64-byte rows
 constexpr int STAGES = 3;
 constexpr int TILE_A = BM * BK * 4;          // 8 KB per plane tile
@@ -31,98 +33,6 @@ constexpr int TILE_B = BN * BK * 4;
 constexpr int STAGE_BYTES = 4 * TILE_A + 4 * TILE_B;   // 64 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 4 * BN;            // acc_re+ | acc_im | acc_re- | (unused): 512
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok;
-}
-// bounded wait; false (and the status bit set) if the phase never completed
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status) {
-  if (mbar_try(b, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (!mbar_try(b, parity)) {
-    if (gtimer() - t0 > WAIT_NS) {
-      atomicOr(status, 1);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0,
-                                          int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)),
-      "l"((uint64_t)tm), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-// K-major operand tile, 64-byte rows, 64-byte swizzle: 8-row atoms of 512 bytes
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
-  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;  // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                        // descriptor version
-  d |= (uint64_t)4 << 61;                        // swizzle: 64 B
-  return d;
-}
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = BN
-__host__ __device__ constexpr uint32_t idesc_tf32() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
-}
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(id), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 struct CG {
   int64_t M, N;         // valid output extent
@@ -195,7 +105,7 @@ __global__ void __launch_bounds__(192, 1) k_cgemm_tf32x3(const __grid_constant__
       mbar_wait(&full[i % STAGES], (i / STAGES) & 1, g.status);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_tf32();
+    const uint32_t id = idesc_tf32_n(BN);
     const uint32_t t_re = tmem, t_im = tmem + BN, t_rn = tmem + 2 * BN;
     bool ok = true;
     for (int i = 0; i < nkb; ++i) {
@@ -278,18 +188,6 @@ __global__ void __launch_bounds__(192, 1) k_cgemm_tf32x3(const __grid_constant__
   }
 }
 
-// ------------------------------------------------------------------ operand preparation
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-__device__ __forceinline__ void split_tf32(double x, float* hi, float* lo) {
-  const float h = tf32_rna((float)x);
-  *hi = h;
-  *lo = tf32_rna((float)(x - (double)h));
-}
-
 // planes[p][r][k] (rows Mp, K Kp) from src[r * ld + k] (r < M, k < K), zeros elsewhere
 __global__ void k_split_rows(const z* __restrict__ src, int64_t M, int64_t K, int64_t ld,
                              int64_t Mp, int64_t Kp, float* __restrict__ out) {
@@ -338,19 +236,21 @@ __global__ void k_split_transpose(const z* __restrict__ src, int64_t K, int64_t 
   }
 }
 
-// T3 planes = W12 (x) T1 (FP32 re/im planes in, split TF32 planes out)
+// T3 planes = W12 (x) T1 (FP32 re/im planes in, split TF32 planes out).  FP32 arithmetic:
+// T1 itself carries the split-TF32 products' ~2^-22 relative error and W12 has a handful of
+// O(1) entries per output, so FP64 here would buy nothing (and ran on the FP64 pipe).
 __global__ void __launch_bounds__(256) k_op_mixed(OpApply a, const float* __restrict__ t1,
                                                   int64_t t1_plane, float* __restrict__ t3,
                                                   int64_t t3_plane) {
   __shared__ int s_row[257];
   __shared__ int s_col[2048];
-  __shared__ z s_val[2048];
+  __shared__ float2 s_val[2048];
   __shared__ int64_t s_in[256];
   __shared__ int64_t s_out[256];
   for (int t = threadIdx.x; t <= a.nI; t += blockDim.x) s_row[t] = a.row_ptr[t];
   for (int t = threadIdx.x; t < a.nnz; t += blockDim.x) {
     s_col[t] = a.col[t];
-    s_val[t] = a.val[t];
+    s_val[t] = make_float2((float)a.val[t].x, (float)a.val[t].y);
   }
   for (int t = threadIdx.x; t < a.nJ; t += blockDim.x) s_in[t] = a.in_off[t];
   for (int t = threadIdx.x; t < a.nI; t += blockDim.x) s_out[t] = a.out_off[t];
@@ -363,13 +263,13 @@ __global__ void __launch_bounds__(256) k_op_mixed(OpApply a, const float* __rest
     const float* iim = ire + t1_plane;
     float* o = t3 + b0 * a.os0 + b2 * a.os2;
     for (int i = 0; i < a.nI; ++i) {
-      double xr = 0, xi = 0;
+      float xr = 0.f, xi = 0.f;
       for (int t = s_row[i]; t < s_row[i + 1]; ++t) {
-        const z w = s_val[t];
+        const float2 w = s_val[t];
         const int64_t off = s_in[s_col[t]];
-        const double vr = ire[off], vi = iim[off];
-        xr = fma(w.x, vr, fma(-w.y, vi, xr));
-        xi = fma(w.x, vi, fma(w.y, vr, xi));
+        const float vr = ire[off], vi = iim[off];
+        xr = fmaf(w.x, vr, fmaf(-w.y, vi, xr));
+        xi = fmaf(w.x, vi, fmaf(w.y, vr, xi));
       }
       float h, l;
       const int64_t off = s_out[i];
@@ -471,6 +371,10 @@ int launch_cgemm(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, int64_t M
   return TNT_OK;
 }
 }  // namespace
+
+int tma_map_planes(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows) {
+  return make_map(c, tm, base, rows, K, box_rows);
+}
 
 size_t heff_mixed_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr) {
   const int64_t Mp1 = rup(chl * D, BM), Kp1 = rup(chl, BK), Np1 = rup(d * d * chr, BN);

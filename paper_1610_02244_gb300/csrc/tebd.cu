@@ -1,0 +1,244 @@
+// Second-order Trotter TEBD on the device MPS handle (Sec. 3, Trotterised update; Sec. 5,
+// real-time evolution from a product state with the accumulated truncation error and
+// 1 - <psi|psi> tracked).  The paper names the update but prints no scheme; the step is the
+// symmetric split
+//   U(dt) = exp(-i H_odd dt/2) exp(-i H_even dt) exp(-i H_odd dt/2),
+// odd bonds (1,2), (3,4), ... and even bonds (2,3), ... (1-based), hbar = 1.  The bond term
+// carries the on-site energy with weight 1/2 in the interior and 1 on the two end sites.
+// Each gate: move the orthogonality centre to site i by exact SVD moves, theta = A_i A_{i+1}
+// (a1), theta' = G theta (a2), truncated SVD of theta'[(a s1),(s2 b)] (a5, a6), A_i <- U,
+// A_{i+1} <- S V^H (a7).  No renormalisation: the discarded weight leaves the norm.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "heff_plan.cuh"
+#include "mps.cuh"
+
+struct tnt_tebd {
+  tnt_ctx* ctx = nullptr;
+  tnt_mps* mps = nullptr;
+  int centre = 0;
+  std::vector<std::vector<tnt::z>> G_half, G_full;  // per bond, d^2 x d^2 (host)
+  size_t scratch = 0;
+};
+
+namespace tnt {
+
+static size_t tebd_scratch_bound(const tnt_mps* m) {
+  size_t best = 0;
+  const int64_t d = m->d;
+  for (int i = 0; i + 1 < m->L; ++i) {
+    const int64_t chl = m->cap[i], chr = m->cap[i + 2];
+    const int64_t n = chl * d * d * chr;
+    best = std::max(best, 2 * ws_round(sizeof(z) * n) + svd_scratch_bound(chl * d, d * chr));
+  }
+  // centre moves: the site copy, the factor and the product each fit in the largest site
+  int64_t site = 0;
+  for (int j = 0; j < m->L; ++j) site = std::max(site, m->cap[j] * d * m->cap[j + 1]);
+  for (int j = 0; j < m->L; ++j) {
+    const int64_t chl = m->cap[j], chr = m->cap[j + 1];
+    best = std::max(best, 3 * ws_round(sizeof(z) * site) +
+                              std::max(svd_scratch_bound(chl * d, chr), svd_scratch_bound(chl, d * chr)));
+  }
+  return best + (size_t)(8 << 20);
+}
+
+// centre j -> j+1:  A_j = U (left-orthonormal), A_{j+1} <- (S V^H) A_{j+1}
+static int tebd_move_right(Ctx* c, tnt_tebd* t) {
+  tnt_mps* m = t->mps;
+  const int j = t->centre;
+  const int64_t d = m->d, chl = m->chi[j], chr = m->chi[j + 1], chn = m->chi[j + 2];
+  const size_t top = c->ws.top;
+  std::vector<int64_t> ql = labels_or_zero(m, j), qr = labels_or_zero(m, j + 1);
+  std::vector<int64_t> rq((size_t)(chl * d));
+  for (int64_t a = 0; a < chl; ++a)
+    for (int64_t s = 0; s < d; ++s) rq[(size_t)(a * d + s)] = m->labelled ? ql[(size_t)a] + s : 0;
+  const int64_t capk = std::min(chl * d, chr);
+  z* M = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * d * chr)));
+  z* X = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(capk * chr)));
+  z* B = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(capk * d * chn)));
+  if (!M || !X || !B) return set_err(c, TNT_E_ALLOC, "scratch exhausted (centre move)");
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(M, m->A[j], sizeof(z) * (size_t)(chl * d * chr),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+  std::vector<double> S((size_t)capk);
+  std::vector<int64_t> bq((size_t)capk);
+  tnt_trunc_result tr{};
+  {
+    ParamsGuard pg(c, exact_params(c->params));
+    TNT_TRY(svd_trunc_impl(c, M, chl * d, chr, rq.data(), qr.data(), TNT_SVD_LEFT, 0, m->A[j], X,
+                           S.data(), bq.data(), &tr));
+  }
+  const int64_t k = tr.chi;
+  ZGemm g{};
+  g.M = k; g.N = d * chn; g.K = chr;
+  g.A = X; g.a_rs = chr; g.a_cs = 1;
+  g.B = m->A[j + 1]; g.b_rs = d * chn; g.b_cs = 1;
+  g.C = B; g.c_rs = d * chn;
+  g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
+  TNT_TRY(zgemm(c, g));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(m->A[j + 1], B, sizeof(z) * (size_t)(k * d * chn),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+  m->chi[j + 1] = k;
+  if (m->labelled) m->q[j + 1].assign(bq.begin(), bq.begin() + k);
+  t->centre = j + 1;
+  c->ws.top = top;
+  return TNT_OK;
+}
+
+// centre j -> j-1:  A_j = V^H (right-orthonormal), A_{j-1} <- A_{j-1} (U S)
+static int tebd_move_left(Ctx* c, tnt_tebd* t) {
+  tnt_mps* m = t->mps;
+  const int j = t->centre;
+  const int64_t d = m->d, chl = m->chi[j], chr = m->chi[j + 1], chp = m->chi[j - 1];
+  const size_t top = c->ws.top;
+  std::vector<int64_t> ql = labels_or_zero(m, j), qr = labels_or_zero(m, j + 1);
+  std::vector<int64_t> cq((size_t)(d * chr));
+  for (int64_t s = 0; s < d; ++s)
+    for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s * chr + b)] = m->labelled ? qr[(size_t)b] - s : 0;
+  const int64_t capk = std::min(chl, d * chr);
+  z* M = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * d * chr)));
+  z* US = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * capk)));
+  z* A = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chp * d * capk)));
+  if (!M || !US || !A) return set_err(c, TNT_E_ALLOC, "scratch exhausted (centre move)");
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(M, m->A[j], sizeof(z) * (size_t)(chl * d * chr),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+  std::vector<double> S((size_t)capk);
+  std::vector<int64_t> bq((size_t)capk);
+  tnt_trunc_result tr{};
+  {
+    ParamsGuard pg(c, exact_params(c->params));
+    TNT_TRY(svd_trunc_impl(c, M, chl, d * chr, ql.data(), cq.data(), TNT_SVD_RIGHT, 0, US,
+                           m->A[j], S.data(), bq.data(), &tr));
+  }
+  const int64_t k = tr.chi;
+  ZGemm g{};
+  g.M = chp * d; g.N = k; g.K = chl;
+  g.A = m->A[j - 1]; g.a_rs = chl; g.a_cs = 1;
+  g.B = US; g.b_rs = k; g.b_cs = 1;
+  g.C = A; g.c_rs = k;
+  g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
+  TNT_TRY(zgemm(c, g));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(m->A[j - 1], A, sizeof(z) * (size_t)(chp * d * k),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+  m->chi[j] = k;
+  if (m->labelled) m->q[j].assign(bq.begin(), bq.begin() + k);
+  t->centre = j - 1;
+  c->ws.top = top;
+  return TNT_OK;
+}
+
+// one gate on bond (i, i+1) with the centre at i; leaves the centre at i+1
+static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, tnt_step_stats* st) {
+  tnt_mps* m = t->mps;
+  while (t->centre < i) TNT_TRY(tebd_move_right(c, t));
+  while (t->centre > i) TNT_TRY(tebd_move_left(c, t));
+  const int64_t d = m->d, chl = m->chi[i], chm = m->chi[i + 1], chr = m->chi[i + 2];
+  const int64_t n = chl * d * d * chr;
+  const size_t top = c->ws.top;
+  z* theta = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  z* theta2 = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  if (!theta || !theta2) return set_err(c, TNT_E_ALLOC, "scratch exhausted (theta)");
+  TNT_TRY(theta_form_impl(c, m->A[i], m->A[i + 1], chl, d, chm, chr, theta));
+  TNT_TRY(gate_apply_impl(c, G, theta, chl, d, chr, theta2));
+  std::vector<int64_t> ql = labels_or_zero(m, i), qr = labels_or_zero(m, i + 2);
+  std::vector<int64_t> rq((size_t)(chl * d)), cq((size_t)(d * chr));
+  for (int64_t a = 0; a < chl; ++a)
+    for (int64_t s = 0; s < d; ++s) rq[(size_t)(a * d + s)] = m->labelled ? ql[(size_t)a] + s : 0;
+  for (int64_t s = 0; s < d; ++s)
+    for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s * chr + b)] = m->labelled ? qr[(size_t)b] - s : 0;
+  const int64_t capk = std::min<int64_t>(m->cap[i + 1], std::min(chl * d, d * chr));
+  std::vector<double> S((size_t)capk);
+  std::vector<int64_t> bq((size_t)capk);
+  tnt_trunc_result tr{};
+  {
+    tnt_params pp = c->params;  // the site storage bounds the kept dimension
+    pp.chi_max = std::min(pp.chi_max, m->cap[i + 1]);
+    ParamsGuard pg(c, pp);
+    TNT_TRY(svd_trunc_impl(c, theta2, chl * d, d * chr, rq.data(), cq.data(), TNT_SVD_LEFT, 0,
+                           m->A[i], m->A[i + 1], S.data(), bq.data(), &tr));
+  }
+  m->chi[i + 1] = tr.chi;
+  if (m->labelled) m->q[i + 1].assign(bq.begin(), bq.begin() + tr.chi);
+  t->centre = i + 1;
+  st->err_sum += tr.err;
+  st->disc_sum += tr.disc;
+  c->ws.top = top;
+  return TNT_OK;
+}
+
+}  // namespace tnt
+
+using namespace tnt;
+
+extern "C" {
+
+int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* m, int n_max, double J, double U, double mu,
+                    double dt, tnt_tebd** out) {
+  if (!ctx || !m || !out || n_max + 1 != m->d || !std::isfinite(dt)) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  if (m->d * m->d > 256) return set_err(c, TNT_E_INVALID, "d^2 = %d exceeds 256", m->d * m->d);
+  tnt_tebd* t = new tnt_tebd();
+  t->ctx = ctx;
+  t->mps = m;
+  const int L = m->L, d2 = m->d * m->d;
+  t->G_half.assign((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
+  t->G_full.assign((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
+  for (int i = 0; i + 1 < L; ++i) {
+    const double c1 = (i == 0) ? 1.0 : 0.5, c2 = (i + 2 == L) ? 1.0 : 0.5;
+    bh_bond_gate_host(n_max, J, U, mu, c1, c2, 0.5 * dt, t->G_half[(size_t)i].data());
+    bh_bond_gate_host(n_max, J, U, mu, c1, c2, dt, t->G_full[(size_t)i].data());
+  }
+  t->scratch = tebd_scratch_bound(m);
+  // orthogonality centre at site 0: exact right-to-left moves (a gauge change only)
+  ws_reset(c);
+  int r = ws_reserve(c, t->scratch);
+  t->centre = L - 1;
+  while (r == TNT_OK && t->centre > 0) r = tebd_move_left(c, t);
+  ws_reset(c);
+  if (r == TNT_OK) r = cudaStreamSynchronize(c->stream) == cudaSuccess ? TNT_OK : TNT_E_CUDA;
+  if (r != TNT_OK) {
+    delete t;
+    return r;
+  }
+  *out = t;
+  return TNT_OK;
+}
+
+int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* t, tnt_step_stats* st) {
+  if (!ctx || !t || !st || t->ctx != ctx) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mps* m = t->mps;
+  const int L = m->L;
+  *st = tnt_step_stats{};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  ws_reset(c);
+  int r = ws_reserve(c, t->scratch);
+  // odd bonds (0-based i even) at dt/2, even bonds at dt, odd bonds at dt/2
+  for (int layer = 0; layer < 3 && r == TNT_OK; ++layer) {
+    const int first = (layer == 1) ? 1 : 0;
+    const auto& G = (layer == 1) ? t->G_full : t->G_half;
+    for (int i = first; i + 1 < L && r == TNT_OK; i += 2) r = tebd_gate(c, t, i, G[(size_t)i], st);
+  }
+  ws_reset(c);
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st->seconds = ms * 1e-3;
+  st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
+  return r;
+}
+
+int tnt_tebd_destroy(tnt_tebd* t) {
+  if (!t) return TNT_E_INVALID;
+  delete t;
+  return TNT_OK;
+}
+
+}  // extern "C"

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -57,6 +58,10 @@ struct Ctx {
   std::vector<cudaEvent_t> prof_ev;  // pairs: start, end
   size_t prof_n = 0;
   double prof_work = 0;  // algorithmic FLOPs or bytes of the timed launches
+  // grouped U(1) matvec: replay as a CUDA graph (off while kernel classes are profiled),
+  // and the autotuner's tile choice per block-structure signature
+  bool use_graphs = true;
+  std::map<std::string, std::vector<int>> tune;
 };
 
 // Records CUDA events around the launches of one kernel class when that class is
@@ -164,6 +169,10 @@ int vec_dot(Ctx* c, const z* x, const z* y, int64_t n, z* d_dot);
 // writes out[0] = E, out[1] = |y_{k-1}|, and y[0..k-1].
 int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, double* d_out,
                    double* d_y);
+// the same for nprob problems at once: problem p's alpha, beta, y at p * 64, out at p * 2;
+// problems with d_skip[p] != 0 are left untouched
+int tridiag_lowest_batched(Ctx* c, const double* d_alpha, const double* d_beta, int k,
+                           double* d_out, double* d_y, int nprob, const int* d_skip);
 
 // Hermitian eigensolvers (FP64 cyclic Jacobi) used by the truncated SVD.
 // Small blocks: one CTA per block (n <= 64), in place on G (packed, each block n_b x n_b at

@@ -25,7 +25,15 @@ __all__ = [
     "random_charged_mps",
     "mott_occupations",
     "charge_mask",
+    "gaussian_sector_labels",
+    "env_mask",
+    "theta_mask",
+    "BH_WQ",
 ]
+
+# charges of the Bose-Hubbard MPO bond index w = 0..3 (left boundary 3, right boundary 0):
+# an environment channel w relates bra and ket bond labels by q' = q + BH_WQ[w]
+BH_WQ = (0, 1, -1, 0)
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -130,3 +138,35 @@ def random_charged_mps(g: np.random.Generator, L: int, d: int, N: int, chi_max: 
 
 def mott_occupations(L: int, filling: int = 1) -> np.ndarray:
     return np.full(L, filling, dtype=np.int32)
+
+
+def gaussian_sector_labels(chi: int, n_sectors: int, sigma: float, q_center: int) -> np.ndarray:
+    """Sorted labels of one bond with n_sectors consecutive charges around q_center whose
+    sizes follow exp(-(q - q_center)^2 / (2 sigma^2)), at least 1 each, summing to chi
+    (the uneven sector profile of a U(1) bond at large chi)."""
+    qs = np.arange(n_sectors) - n_sectors // 2 + q_center
+    w = np.exp(-((qs - q_center) ** 2) / (2.0 * sigma ** 2))
+    sizes = np.maximum(1, np.floor(w / w.sum() * chi).astype(np.int64))
+    i = 0
+    order = np.argsort(-w, kind="stable")
+    while sizes.sum() < chi:
+        sizes[order[i % n_sectors]] += 1
+        i += 1
+    while sizes.sum() > chi:
+        j = order[i % n_sectors]
+        if sizes[j] > 1:
+            sizes[j] -= 1
+        i += 1
+    return np.concatenate([np.full(int(n), int(q), dtype=np.int64) for q, n in zip(qs, sizes)])
+
+
+def env_mask(q_bra: np.ndarray, q_ket: np.ndarray, wq=BH_WQ) -> np.ndarray:
+    """Boolean mask of allowed E[a', w, a]: q_bra[a'] == q_ket[a] + wq[w]."""
+    wq = np.asarray(wq)
+    return q_bra[:, None, None] == (q_ket[None, None, :] + wq[None, :, None])
+
+
+def theta_mask(qa: np.ndarray, d: int, qb: np.ndarray) -> np.ndarray:
+    """Boolean mask of allowed theta[a, s1, s2, b]: qb[b] == qa[a] + s1 + s2."""
+    s = np.arange(d)
+    return (qa[:, None, None, None] + s[None, :, None, None] + s[None, None, :, None]) == qb[None, None, None, :]

@@ -190,6 +190,60 @@ class Context:
         return (U[: m * k].view(m, k), X[: k * n].view(k, n), S[:k].copy(), bq[:k].copy(),
                 _struct_dict(res))
 
+    # ---------------------------------------------------------------- U(1) blocks
+    def u1_size(self, prob: "U1Problem") -> int:
+        n = C.c_int64()
+        self._chk(self.lib.tnt_u1_size(C.byref(prob.s), C.byref(n)))
+        return n.value
+
+    def u1_pack(self, prob: "U1Problem", theta):
+        x = torch.empty(self.u1_size(prob), dtype=torch.complex128, device=theta.device)
+        self._chk(self.lib.tnt_u1_pack(self.h, C.byref(prob.s), _ptr(theta), _ptr(x)))
+        return x
+
+    def u1_unpack(self, prob: "U1Problem", x):
+        th = torch.empty((prob.chl, prob.d, prob.d, prob.chr), dtype=torch.complex128,
+                         device=x.device)
+        self._chk(self.lib.tnt_u1_unpack(self.h, C.byref(prob.s), _ptr(x), _ptr(th)))
+        return th
+
+    def heff_apply_u1(self, probs, x, precision=TNT_PREC_FP64, out=None):
+        """y = H_eff x for the problems' compact vectors back to back; returns (y, flops)."""
+        probs = list(probs)
+        arr = (L.tnt_u1_problem * len(probs))(*[p.s for p in probs])
+        y = torch.empty_like(x) if out is None else out
+        fl = C.c_double()
+        self._chk(self.lib.tnt_heff_apply_u1(self.h, len(probs), arr, _ptr(x), _ptr(y),
+                                             precision, C.byref(fl)))
+        return y, fl.value
+
+    def lanczos_ground_u1(self, prob: "U1Problem", x):
+        """x (compact, device) is overwritten by the eigenvector; returns the result dict."""
+        res = L.tnt_lanczos_result()
+        self._chk(self.lib.tnt_lanczos_ground_u1(self.h, C.byref(prob.s), _ptr(x), C.byref(res)),
+                  ok=(0, L.TNT_E_NOCONV))
+        return _struct_dict(res)
+
+    def lanczos_ground_u1_batched(self, probs, x):
+        """x: the problems' compact start vectors back to back (overwritten by the ground
+        states); returns one result dict per problem."""
+        probs = list(probs)
+        arr = (L.tnt_u1_problem * len(probs))(*[p.s for p in probs])
+        res = (L.tnt_lanczos_result * len(probs))()
+        self._chk(self.lib.tnt_lanczos_ground_u1_batched(self.h, len(probs), arr, _ptr(x), res),
+                  ok=(0, L.TNT_E_NOCONV))
+        return [_struct_dict(r) for r in res]
+
+    def set_graphs(self, on: bool):
+        self._chk(self.lib.tnt_set_graphs(self.h, 1 if on else 0))
+
+    def u1_tiles(self, probs):
+        probs = list(probs)
+        arr = (L.tnt_u1_problem * len(probs))(*[p.s for p in probs])
+        t = (C.c_int * 3)()
+        self._chk(self.lib.tnt_u1_tiles(self.h, len(probs), arr, t))
+        return tuple(t)
+
     # ---------------------------------------------------------------- objects
     def mpo_bose_hubbard(self, L_, n_max, J, U, mu=0.0, V=0.0, j_c=0.0) -> "Mpo":
         h = C.c_void_p()
@@ -222,6 +276,11 @@ class Context:
         h = C.c_void_p()
         self._chk(self.lib.tnt_dmrg_create(self.h, mps.h, mpo.h, C.byref(h)))
         return Dmrg(self, h, mps, mpo)
+
+    def tebd_create(self, mps: "Mps", n_max, J, U, dt, mu=0.0) -> "Tebd":
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_tebd_create(self.h, mps.h, n_max, J, U, mu, dt, C.byref(h)))
+        return Tebd(self, h, mps)
 
 
 class Mpo:
@@ -290,3 +349,35 @@ class Dmrg:
         if getattr(self, "h", None):
             self.ctx.lib.tnt_dmrg_destroy(self.h)
             self.h = None
+
+
+class Tebd:
+    def __init__(self, ctx: Context, h, mps: Mps):
+        self.ctx, self.h, self.mps = ctx, h, mps
+
+    def step(self) -> dict:
+        st = L.tnt_step_stats()
+        self.ctx._chk(self.ctx.lib.tnt_tebd_step(self.ctx.h, self.h, C.byref(st)))
+        return _struct_dict(st)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tnt_tebd_destroy(self.h)
+            self.h = None
+
+
+class U1Problem:
+    """One U(1) H_eff problem for the grouped calls: device L, W1, W2, R and host labels
+    (kept alive here while the C struct points at them)."""
+
+    def __init__(self, Lenv, W1, W2, Renv, qa, qb, wq=(0, 1, -1, 0)):
+        self.chl, D, _ = Lenv.shape
+        self.chr = Renv.shape[0]
+        self.d = W1.shape[2]
+        self.qa = np.ascontiguousarray(qa, dtype=np.int64)
+        self.qb = np.ascontiguousarray(qb, dtype=np.int64)
+        self.wq = np.ascontiguousarray(wq, dtype=np.int32)
+        self.tensors = (Lenv, W1, W2, Renv)
+        self.s = L.tnt_u1_problem(_ptr(Lenv), _ptr(W1), _ptr(W2), _ptr(Renv), self.chl, self.d,
+                                  D, self.chr, self.qa.ctypes.data, self.qb.ctypes.data,
+                                  self.wq.ctypes.data)

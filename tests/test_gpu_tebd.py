@@ -1,0 +1,121 @@
+"""Second-order Trotter TEBD on the GPU (C-ABI step driver) against the FP64 oracle
+(Sec. 3 Trotterised update, Sec. 5 quench from a product state; scheme: symmetric split,
+odd / even / odd layers, centre moved to each bond, no renormalisation).
+
+Gauge-invariant comparisons only: the full state (overlap and norm), <n_j>, the bond
+dimensions and the per-step truncation errors and discarded weights.  The 7-site chain is
+used where truncation bites so that no reflection symmetry makes Schmidt values meet at
+the cut (with 8 sites the Trotter step maps the middle bond's charge sectors q and N - q
+onto each other, and the order of equal values at the cut would be a rounding accident)."""
+import numpy as np
+import pytest
+
+from oracle import bose_hubbard as bh
+from oracle import contract as oc
+from oracle import svd as osvd
+from oracle import tebd as otebd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1610_02244_gb300 import build as b
+    b.build()
+    from paper_1610_02244_gb300 import tnt
+    return tnt.Context(0)
+
+
+def _run(ctx, occ, n_max, J, U, dt, chi_max, err_tol, steps):
+    A, q = otebd.product_state(occ, n_max)
+    ref = otebd.Tebd(A, q, n_max, J, U, dt, osvd.TruncParams(chi_max=chi_max, err_tol=err_tol))
+    ctx.set_params(chi_max=chi_max, trunc_err=err_tol, trunc_abs=-1.0, trunc_rel=1e-16,
+                   trunc_type=0)
+    mps = ctx.mps_product(occ, n_max + 1, chi_max)
+    gpu = ctx.tebd_create(mps, n_max, J, U, dt)
+    per_step = []
+    for _ in range(steps):
+        e0, w0 = ref.eps_sum, ref.disc_sum
+        st = gpu.step()
+        ref.step()
+        per_step.append((st["err_sum"], ref.eps_sum - e0, st["disc_sum"], ref.disc_sum - w0))
+    return mps, ref, per_step
+
+
+def _compare_states(mps, ref, n_max, tol_overlap=1e-8, tol_norm=1e-10):
+    T = mps.tensors()
+    psi, phi = oc.mps_to_state(T), oc.mps_to_state(ref.A)
+    n1, n2 = np.vdot(psi, psi).real, np.vdot(phi, phi).real
+    ov = abs(np.vdot(psi, phi)) / np.sqrt(n1 * n2)
+    assert abs(1 - ov) <= tol_overlap, (ov, n1, n2)
+    assert abs(n1 - n2) <= tol_norm, (n1, n2)
+    assert abs(mps.norm2() - n1) <= 1e-12
+    assert [mps.bond_dim(k) for k in range(mps.L + 1)] == [1] + [t.shape[2] for t in ref.A]
+    dn = np.abs(oc.density(T, n_max) - oc.density(ref.A, n_max)).max()
+    assert dn <= 1e-9, dn
+    for k in range(1, mps.L):
+        assert np.array_equal(np.sort(mps.charges(k)), np.sort(ref.q[k]))
+
+
+def test_tebd_exact_bonds(ctx):
+    """L = 6, d = 3, chi 27 holds every Schmidt value: the pure Trotter product."""
+    mps, ref, per = _run(ctx, [1] * 6, 2, 1.0, 2.0, 0.05, 27, 1e-14, 8)
+    _compare_states(mps, ref, 2)
+    for e_g, e_r, w_g, w_r in per:
+        assert w_g <= 1e-20 + 1e-10 and w_r <= 1e-20 + 1e-10
+
+
+def test_tebd_truncating_chi6(ctx):
+    mps, ref, per = _run(ctx, [1] * 7, 2, 1.0, 2.0, 0.05, 6, 1e-12, 12)
+    assert sum(p[3] for p in per) > 1e-8  # chi = 6 really truncates
+    for e_g, e_r, w_g, w_r in per:
+        assert abs(w_g - w_r) <= 1e-6 * w_r + 1e-14, (w_g, w_r)
+        assert abs(e_g - e_r) <= 1e-6 * e_r + 1e-12, (e_g, e_r)
+    _compare_states(mps, ref, 2)
+    # no renormalisation: 1 - <psi|psi> is the accumulated discarded weight
+    disc = sum(p[2] for p in per)
+    assert abs((1 - mps.norm2()) - disc) <= 1e-3 * disc + 1e-13
+
+
+def test_tebd_hard_core_free_fermions(ctx):
+    """n_max = 1 (hard-core bosons = free fermions on an open chain): from the CDW state
+    |1010...>, <n_j(t)> = sum_k |[exp(-i h t)]_{jk}|^2 n_k(0) with h the hopping matrix;
+    second-order Trotter at dt = 0.05 is within 3e-4 of it at t = 1 (the oracle's own
+    Trotter error there is 1.34e-4), and the GPU state matches the oracle's."""
+    Ls, J, dt, steps = 10, 1.0, 0.05, 20
+    occ = [1, 0] * (Ls // 2)
+    ctx.set_params(chi_max=32, trunc_err=1e-14, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    mps = ctx.mps_product(occ, 2, 32)
+    gpu = ctx.tebd_create(mps, 1, J, 4.0, dt)
+    for _ in range(steps):
+        gpu.step()
+    h = np.zeros((Ls, Ls))
+    for j in range(Ls - 1):
+        h[j, j + 1] = h[j + 1, j] = -J
+    lam, Q = np.linalg.eigh(h)
+    Ut = (Q * np.exp(-1j * lam * dt * steps)) @ Q.conj().T
+    exact = (np.abs(Ut) ** 2) @ np.array(occ, dtype=float)
+    dens = oc.density(mps.tensors(), 1)
+    assert np.abs(dens - exact).max() < 3e-4
+    assert abs(dens.sum() - Ls // 2) < 1e-12
+    A, q = otebd.product_state(occ, 1)
+    ref = otebd.Tebd(A, q, 1, J, 4.0, dt, osvd.TruncParams(chi_max=32, err_tol=1e-14))
+    for _ in range(steps):
+        ref.step()
+    assert np.abs(dens - oc.density(ref.A, 1)).max() < 1e-10
+
+
+def test_tebd_energy_conserved_untruncated(ctx):
+    """<H> is conserved by the Trotter evolution up to O(dt^2) (no truncation here)."""
+    n_max, J, U, dt = 2, 1.0, 2.0, 0.02
+    occ = [2, 0, 1, 1, 0, 2]
+    ctx.set_params(chi_max=27, trunc_err=1e-14, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    mps = ctx.mps_product(occ, n_max + 1, 27)
+    mpo = ctx.mpo_bose_hubbard(6, n_max, J, U)
+    E0 = mps.expect_mpo(mpo)
+    Ws, l, r = bh.bh_mpo(6, n_max, J, U)
+    assert abs(E0 - oc.mps_expect_mpo(mps.tensors(), Ws, l, r).real) < 1e-12
+    gpu = ctx.tebd_create(mps, n_max, J, U, dt)
+    for _ in range(25):
+        gpu.step()
+    assert abs(mps.expect_mpo(mpo) / mps.norm2() - E0) < 5e-3
