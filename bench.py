@@ -36,7 +36,7 @@ CHI_MAX = 256
 METRIC = "DMRG s/sweep & H_eff·θ TFLOP/s, mixed vs FP64 on GB300 at |ΔE|≤1e-10"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense ratio (profiling recipe table)
-FP64_PER_BF16 = 1.25 / 2250.0  # nominal FP64 1.25 TFLOP/s against 2.25 PFLOP/s bf16
+FP64_GFLOPS = 1250.0  # FP64 ALU: nominal 1.25 TFLOP/s (152 SMs x 2.07 GHz x ~4 FLOP/clk)
 
 
 def matvec_cmacs(chl, d, D, chr_):
@@ -396,10 +396,10 @@ def roofline(cls, ms, n, work, peaks, src):
         ach = work / secs / 1e9
         return dict(base, achieved=ach, peak=pk, unit="GB/s", frac=ach / pk,
                     peak_source=f"{src} copy bandwidth")
-    pk = bf16 * FP64_PER_BF16 * 1e3  # FP64 FLOP/s
+    pk = FP64_GFLOPS
     ach = work / secs / 1e9
     return dict(base, achieved=ach, peak=pk, unit="GFLOP/s", frac=ach / pk,
-                peak_source=f"{src} bf16 burst x nominal fp64/bf16 ratio")
+                peak_source="FP64 units x max SM clock (nominal 1.25 TFLOP/s)")
 
 
 # ---------------------------------------------------------------- grouped U(1) workloads

@@ -169,9 +169,10 @@ def test_lanczos_u1_batched_chains(ctx, precision):
     cases = [(LABELS["gauss96"], 3.4, 1.0), (LABELS["small"], 1.0, 1.0),
              (LABELS["gauss96"], 8.0, 0.7), (LABELS["gaps"], 2.0, 1.0)]
     ctx.set_params(precision=precision, lanczos_tol=1e-12, lanczos_maxit=300, krylov_cap=32)
-    probs, xs, refs = [], [], []
+    probs, xs, refs, cases_inputs = [], [], [], []
     for i, ((qa, qb, d), U, J) in enumerate(cases):
         Le, W1, W2, Re, th = u1_inputs(40 + i, qa, qb, d, U=U, J=J)
+        cases_inputs.append((Le, W1, W2, Re))
         p = problem(Le, W1, W2, Re, qa, qb)
         probs.append(p)
         xs.append(ctx.u1_pack(p, dev(th)))
@@ -180,10 +181,20 @@ def test_lanczos_u1_batched_chains(ctx, precision):
     res = ctx.lanczos_ground_u1_batched(probs, x)
     ctx.set_params(precision=0)
     off = 0
-    for p, xi, (E, v, *_), r in zip(probs, xs, refs, res):
+    for i, (p, xi, (E, v, *_), r) in enumerate(zip(probs, xs, refs, res)):
         assert r["converged"] == 1
         assert abs(r["E_rq"] - E) <= 1e-10 * abs(E), (r, E)
         got = ctx.u1_unpack(p, x[off: off + xi.numel()]).cpu().numpy()
         off += xi.numel()
         assert abs(np.linalg.norm(got) - 1) < 1e-12
-        assert abs(1 - abs(np.vdot(v.ravel() / np.linalg.norm(v), got.ravel()))) < 1e-8
+        ov = abs(np.vdot(v.ravel() / np.linalg.norm(v), got.ravel()))
+        if precision == 0:
+            assert abs(1 - ov) < 1e-8
+        else:
+            # the split-TF32 solve promises |dE| <= 1e-10 |E| through an FP64 residual
+            # check ||H x - E x|| <= 1e-5 |E|; the vector is as good as that residual allows
+            # (1 - overlap ~ (residual / gap)^2 / 2): check the promise with the oracle
+            Le_, W1_, W2_, Re_ = cases_inputs[i]
+            Hx = oc.heff_apply(Le_, W1_, W2_, Re_, got)
+            assert np.linalg.norm(Hx - r["E_rq"] * got) <= 1e-5 * abs(E)
+            assert abs(1 - ov) < 1e-6
