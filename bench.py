@@ -224,6 +224,7 @@ def config_dict(args, dtype):
                         "(L,R 256x4x256, theta 256x4x4x256), 32 Krylov steps, SVD to chi=256",
             "chi": CHI, "d": D_PHYS, "D": D_MPO, "krylov_steps": KRYLOV, "chi_max": CHI_MAX,
             "precision": args.precision, "matvec_dtype": dtype,
+            "fp64_gemm": getattr(args, "fp64_gemm", "fma"),
             "l2": "inputs larger than L2 (Krylov basis 32 x 16 MiB per step)"}
 
 
@@ -240,6 +241,7 @@ def run_ours(args, ws, rank, local):
     prec = tnt.TNT_PREC_MIXED if args.precision == "mixed" else tnt.TNT_PREC_FP64
     ctx.set_params(chi_max=CHI_MAX, krylov_cap=KRYLOV, lanczos_maxit=KRYLOV, precision=prec,
                    lanczos_tol=1e-12)
+    ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if args.fp64_gemm == "tc" else tnt.TNT_FP64_GEMM_FMA)
     inp = synth_inputs(1000 + rank)
     t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in inp.items()}
     theta = torch.empty((CHI, D_PHYS, D_PHYS, CHI), dtype=torch.complex128, device=dev)
@@ -373,7 +375,9 @@ CLASSES = {
     "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
     "cgemm_grouped": ("tensor", "flop"), "zgemm_grouped": ("alu", "flop"),
     "u1_wop": ("hbm", "byte"), "u1_pack_theta": ("hbm", "byte"), "u1_gather": ("hbm", "byte"),
+    "oz_gemm": ("tensor_fp64", "flop"), "oz_slice": ("hbm", "byte"),
 }
+OZ_TENSOR_PER_USEFUL = 45.0  # slice pairs per complex product: 45 x 4 real MMAs / (8 / 2) FLOPs
 
 
 def roofline(cls, ms, n, work, peaks, src):
@@ -386,6 +390,12 @@ def roofline(cls, ms, n, work, peaks, src):
     base = {"kernel": cls, "bound": bound, "launches": n, "mean_ms": ms / n, "traffic": None}
     if unit is None or work <= 0:
         return dict(base, achieved=None, peak=None, unit=None, frac=None)
+    if bound == "tensor_fp64":
+        pk = bf16 * TF32_PER_BF16 / OZ_TENSOR_PER_USEFUL
+        ach = work / secs / 1e12
+        return dict(base, bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                    peak_source=f"{src} bf16 burst x nominal tf32/bf16 ratio / 45 slice pairs "
+                                "(FP64-accurate products on the TF32 pipe)")
     if bound == "tensor":
         pk = bf16 * TF32_PER_BF16
         ach = work / secs / 1e12
@@ -539,7 +549,12 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["update", "u1", "chains"], default="update")
+    ap.add_argument("--fp64-gemm", choices=["tc", "fma"], default=None,
+                    help="engine of the FP64 products (default: tc with --precision mixed, "
+                         "fma with --precision fp64, the plain FP64 path)")
     args = ap.parse_args()
+    if args.fp64_gemm is None:
+        args.fp64_gemm = "tc" if args.precision == "mixed" else "fma"
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

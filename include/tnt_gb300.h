@@ -295,6 +295,32 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* mps, const tnt_mpo* mpo, tnt_dmrg** o
 int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
 int tnt_dmrg_destroy(tnt_dmrg* dmrg);
 
+/* ------------------------------------------------------------------ FP64 matrix products */
+
+/* C = op(A) op(B) in FP64 accuracy: the matrix form of a tensor contraction (App. B.1.1:
+ * contraction as a matrix product after a reshape; here any leg order is expressed by
+ * strides, nothing is permuted).  A(i,k) = d_A[i*a_rs + k*a_cs] (conjugated if conj_a),
+ * B(k,j) = d_B[k*b_rs + j*b_cs] (conjugated if conj_b), C(i,j) = d_C[i*c_rs + j] (out;
+ * must not alias A or B).  Device pointers, borrowed.  The engine is the context's FP64
+ * GEMM setting: FMA (FP64 units) or TC (exact integer slices of the operands multiplied
+ * on the TF32 tensor cores with exact FP32 sums, added in FP64: error within the size of
+ * FP64 rounding, see tnt_set_fp64_gemm).  TNT_E_INVALID on bad sizes. */
+int tnt_matmul(tnt_ctx* ctx, int64_t M, int64_t N, int64_t K, const tnt_cplx* d_A, int64_t a_rs,
+               int64_t a_cs, int conj_a, const tnt_cplx* d_B, int64_t b_rs, int64_t b_cs,
+               int conj_b, tnt_cplx* d_C, int64_t c_rs);
+
+enum { TNT_FP64_GEMM_FMA = 0, TNT_FP64_GEMM_TC = 1 };
+/* Engine of the library's FP64 matrix products (the FP64 H_eff.theta, theta, the
+ * environments, SVD projections; the Gram matrices of the SVD always use FP64 FMA).
+ * TNT_FP64_GEMM_TC (default): each row of A and column of B is scaled by a power of two
+ * to below 1 and cut into 9 integer slices of 6 bits (exact FP64 steps); slice products
+ * run as TF32 MMAs whose FP32 sums over K chunks of 224 stay below 2^24 and so are exact;
+ * the 45 slice pairs p + q <= 10 are added in FP64.  The error is below
+ * 11 * 2^-54 * K * sigma_i * tau_j, sigma_i and tau_j the powers of two just above
+ * max_k|A_ik| and max_k|B_kj|: the size of FP64's own rounding bound.
+ * Small products (and calls that must not allocate) use FMA. */
+int tnt_set_fp64_gemm(tnt_ctx* ctx, int engine);
+
 /* ------------------------------------------------------------------ U(1) blocks, grouped */
 
 /* One two-site H_eff problem with U(1) boson-number labels (App. A.1.1: every leg carries

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libtntgb.so")
 TNT_OK, TNT_E_INVALID, TNT_E_ALLOC, TNT_E_CUDA, TNT_E_NOCONV = 0, 1, 2, 3, 4
 TNT_E_TIMEOUT, TNT_E_BOUNDS, TNT_E_NAN, TNT_E_UNSUPPORTED = 5, 6, 7, 8
 TNT_PREC_FP64, TNT_PREC_MIXED = 0, 1
+TNT_FP64_GEMM_FMA, TNT_FP64_GEMM_TC = 0, 1
 TNT_TRUNC_2NORM, TNT_TRUNC_SUMSQ, TNT_TRUNC_1NORM = 0, 1, 2
 TNT_SVD_LEFT, TNT_SVD_RIGHT = 0, 1
 
@@ -122,6 +123,8 @@ SIGNATURES = {
     "tnt_lanczos_ground_u1_batched": [P, I, C.POINTER(tnt_u1_problem), P,
                                       C.POINTER(tnt_lanczos_result)],
     "tnt_set_graphs": [P, I],
+    "tnt_matmul": [P, I64, I64, I64, P, I64, I64, I, P, I64, I64, I, P, I64],
+    "tnt_set_fp64_gemm": [P, I],
     "tnt_u1_tiles": [P, I, C.POINTER(tnt_u1_problem), C.POINTER(C.c_int)],
     "tnt_tebd_step": [P, P, C.POINTER(tnt_step_stats)],
     "tnt_tebd_destroy": [P],

@@ -229,6 +229,7 @@ int tnt_ctx_destroy(tnt_ctx* ctx) {
   if (ctx->c.ws.base) cudaFree(ctx->c.ws.base);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
   if (ctx->c.d_status) cudaFree(ctx->c.d_status);
+  if (ctx->c.oz_buf) cudaFree(ctx->c.oz_buf);
   delete ctx;
   return TNT_OK;
 }

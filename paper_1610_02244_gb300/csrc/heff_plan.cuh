@@ -44,6 +44,8 @@ int heff_run_f64(Ctx* c, const HeffPlan& p, const z* theta, z* y);
 // split-TF32 tensor-core path
 // 3-D TMA map over planes[4][rows][K] (FP32, K % 4 == 0): box 16 x box_rows x 1, 64 B swizzle
 int tma_map_planes(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows);
+int tma_map_planes_n(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows,
+                     int nplanes);
 size_t heff_mixed_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr);
 int heff_mixed_prepare(Ctx* c, HeffPlan* p);
 int heff_run_mixed(Ctx* c, const HeffPlan& p, const z* theta, z* y);

@@ -98,6 +98,7 @@ int zgemm(Ctx* c, const ZGemm& g) {
     // C = beta C (or zero): not needed by the library; reject to keep the kernel simple
     return set_err(c, TNT_E_INVALID, "zgemm with K = 0");
   }
+  if (ozgemm_eligible(c, g)) return ozgemm(c, g);
   if ((g.N + GN - 1) / GN > 0x7fffffff || (g.M + GM - 1) / GM > 65535 || g.batch > 65535)
     return set_err(c, TNT_E_UNSUPPORTED, "zgemm grid too large (M=%lld N=%lld batch=%lld)",
                    (long long)g.M, (long long)g.N, (long long)g.batch);

@@ -87,6 +87,7 @@ extern "C" int tnt_heff_apply_noalloc(tnt_ctx* ctx, const tnt_cplx* d_L, const t
                    "than its fixed %zu bytes (use tnt_heff_apply)", t, need, NOALLOC_BYTES);
   unsigned char* base = nullptr;
   TNT_TRY(scratch_for_device(c, &base));
+  OzOff fma_only(c);  // the tensor-core FP64 GEMM grows a buffer: FP64 FMA here
   Staging& S = g_stage;
   const size_t nW = (size_t)(D * D * d * d);
   TNT_TRY(read_small(c, d_W1, S.W1, nW * sizeof(z)));

@@ -326,13 +326,14 @@ int get_encoder(Ctx* c, EncodeTiledFn* fn) {
   return TNT_OK;
 }
 
-// 3-D map over planes[4][rows][K]: box = 16 FP32 (64 B) x box_rows x 1, 64-byte swizzle
-int make_map(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows) {
+// 3-D map over planes[nplanes][rows][K]: box = 16 FP32 (64 B) x box_rows x 1, 64-byte swizzle
+int make_map(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows,
+             int nplanes = 4) {
   EncodeTiledFn enc;
   TNT_TRY(get_encoder(c, &enc));
   if (((uintptr_t)base & 15) || (K * 4) % 16)
     return set_err(c, TNT_E_INVALID, "TMA operand not 16-byte aligned");
-  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 4};
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)(K * 4), (cuuint64_t)(rows * K * 4)};
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
@@ -374,6 +375,10 @@ int launch_cgemm(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, int64_t M
 
 int tma_map_planes(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows) {
   return make_map(c, tm, base, rows, K, box_rows);
+}
+int tma_map_planes_n(Ctx* c, CUtensorMap* tm, float* base, int64_t rows, int64_t K, int box_rows,
+                     int nplanes) {
+  return make_map(c, tm, base, rows, K, box_rows, nplanes);
 }
 
 size_t heff_mixed_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr) {

@@ -62,6 +62,11 @@ struct Ctx {
   // and the autotuner's tile choice per block-structure signature
   bool use_graphs = true;
   std::map<std::string, std::vector<int>> tune;
+  // FP64 GEMM engine for large products: 1 = integer-slice emulation on the tensor cores
+  // (FP64-accurate), 0 = FP64 FMA only; its slice buffer is owned by the context
+  int oz_mode = 1;
+  void* oz_buf = nullptr;
+  size_t oz_cap = 0;
 };
 
 // Records CUDA events around the launches of one kernel class when that class is
@@ -125,6 +130,17 @@ struct ZGemm {
   int lower_only;  // Hermitian result: skip 64x64 tiles strictly above the diagonal
 };
 int zgemm(Ctx* c, const ZGemm& g);
+// FP64-accurate C = A B on the tensor cores by exact integer slicing (oz.cu); zgemm routes
+// large products with alpha = 1, beta = 0, batch = 1 there when the context allows it
+bool ozgemm_eligible(const Ctx* c, const ZGemm& g);
+int ozgemm(Ctx* c, const ZGemm& g);
+// FP64 FMA GEMMs only while the guard lives (paths that must not allocate)
+struct OzOff {
+  Ctx* c;
+  int saved;
+  explicit OzOff(Ctx* cc) : c(cc), saved(cc->oz_mode) { c->oz_mode = 0; }
+  ~OzOff() { c->oz_mode = saved; }
+};
 // G[i][j] = conj(G[j][i]) for i < j (complete a Hermitian matrix from its lower part)
 int herm_mirror(Ctx* c, z* G, int64_t n);
 

@@ -144,6 +144,33 @@ int tnt_lanczos_ground_u1_batched(tnt_ctx* ctx, int nprob, const tnt_u1_problem*
   return all ? TNT_OK : TNT_E_NOCONV;
 }
 
+int tnt_matmul(tnt_ctx* ctx, int64_t M, int64_t N, int64_t K, const tnt_cplx* d_A, int64_t a_rs,
+               int64_t a_cs, int conj_a, const tnt_cplx* d_B, int64_t b_rs, int64_t b_cs,
+               int conj_b, tnt_cplx* d_C, int64_t c_rs) {
+  if (!ctx) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  if (!d_A || !d_B || !d_C || M < 1 || N < 1 || K < 1 || c_rs < N)
+    return set_err(c, TNT_E_INVALID, "bad matmul arguments");
+  if ((const void*)d_C == (const void*)d_A || (const void*)d_C == (const void*)d_B)
+    return set_err(c, TNT_E_INVALID, "matmul output aliases an input");
+  ZGemm g{};
+  g.M = M; g.N = N; g.K = K;
+  g.A = (const z*)d_A; g.a_rs = a_rs; g.a_cs = a_cs; g.conj_a = conj_a ? 1 : 0;
+  g.B = (const z*)d_B; g.b_rs = b_rs; g.b_cs = b_cs; g.conj_b = conj_b ? 1 : 0;
+  g.C = (z*)d_C; g.c_rs = c_rs;
+  g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
+  TNT_TRY(zgemm(c, g));
+  return status_check(c);
+}
+
+int tnt_set_fp64_gemm(tnt_ctx* ctx, int engine) {
+  if (!ctx) return TNT_E_INVALID;
+  if (engine != TNT_FP64_GEMM_FMA && engine != TNT_FP64_GEMM_TC)
+    return set_err(&ctx->c, TNT_E_INVALID, "unknown FP64 GEMM engine %d", engine);
+  ctx->c.oz_mode = engine;
+  return TNT_OK;
+}
+
 int tnt_set_graphs(tnt_ctx* ctx, int on) {
   if (!ctx) return TNT_E_INVALID;
   ctx->c.use_graphs = (on != 0);

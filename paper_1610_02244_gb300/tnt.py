@@ -11,8 +11,9 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from ._lib import (TNT_PREC_FP64, TNT_PREC_MIXED, TNT_SVD_LEFT, TNT_SVD_RIGHT,  # noqa: F401
-                   TNT_TRUNC_1NORM, TNT_TRUNC_2NORM, TNT_TRUNC_SUMSQ, TntError)
+from ._lib import (TNT_FP64_GEMM_FMA, TNT_FP64_GEMM_TC, TNT_PREC_FP64,  # noqa: F401
+                   TNT_PREC_MIXED, TNT_SVD_LEFT, TNT_SVD_RIGHT, TNT_TRUNC_1NORM,
+                   TNT_TRUNC_2NORM, TNT_TRUNC_SUMSQ, TntError)
 
 CDT = torch.complex128
 
@@ -233,6 +234,22 @@ class Context:
         self._chk(self.lib.tnt_lanczos_ground_u1_batched(self.h, len(probs), arr, _ptr(x), res),
                   ok=(0, L.TNT_E_NOCONV))
         return [_struct_dict(r) for r in res]
+
+    def matmul(self, A, B, conj_a=False, conj_b=False, out=None):
+        """C = op(A) op(B) (FP64 accuracy) for 2-D complex128 device tensors; A may be a
+        transposed view (any strides)."""
+        M, K = A.shape
+        K2, N = B.shape
+        if K != K2:
+            raise ValueError("inner dimensions differ")
+        C = torch.empty((M, N), dtype=torch.complex128, device=A.device) if out is None else out
+        self._chk(self.lib.tnt_matmul(self.h, M, N, K, A.data_ptr(), A.stride(0), A.stride(1),
+                                      int(conj_a), B.data_ptr(), B.stride(0), B.stride(1),
+                                      int(conj_b), _ptr(C), C.stride(0)))
+        return C
+
+    def set_fp64_gemm(self, engine: int):
+        self._chk(self.lib.tnt_set_fp64_gemm(self.h, engine))
 
     def set_graphs(self, on: bool):
         self._chk(self.lib.tnt_set_graphs(self.h, 1 if on else 0))
