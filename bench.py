@@ -540,6 +540,127 @@ def run_grouped(args, ws, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------- DMRG and TEBD drivers
+DMRG_L, DMRG_N, DMRG_NMAX, DMRG_U, DMRG_CHI, DMRG_SWEEPS = 8, 8, 3, 2.0, 32, 4
+
+
+def run_dmrg(args, ws, rank, local):
+    """--workload dmrg: the 8-site Bose-Hubbard ground state (N = 8, n_max = 3, J = 1, U = 2,
+    chi_max = 32) by 4 two-site sweeps from the seeded random MPS; one step = the 4-sweep
+    run (each from a fresh copy of the start state), metric s/sweep, mixed and FP64."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    g = synth.rng(0)
+    A, q = synth.random_charged_mps(g, DMRG_L, DMRG_NMAX + 1, DMRG_N, DMRG_CHI)
+    mpo = ctx.mpo_bose_hubbard(DMRG_L, DMRG_NMAX, J, DMRG_U)
+    st = torch.cuda.current_stream()
+
+    def sweeps(prec, n):
+        ctx.set_params(chi_max=DMRG_CHI, precision=prec, lanczos_tol=1e-12, lanczos_maxit=300,
+                       krylov_cap=32)
+        ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if prec == tnt.TNT_PREC_MIXED else tnt.TNT_FP64_GEMM_FMA)
+        states = [ctx.mps_create(A, q, chi_cap=DMRG_CHI) for _ in range(n)]
+        runs = [ctx.dmrg_create(m, mpo) for m in states]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        last = None
+        for r in runs:
+            for _ in range(DMRG_SWEEPS):
+                last = r.sweep()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / (n * DMRG_SWEEPS), last
+
+    for _ in range(max(1, args.warmup)):
+        sweeps(tnt.TNT_PREC_MIXED, 1)
+    launches0 = ctx.launch_count()
+    with ClockSampler(local) as clk:
+        ms_mixed, st_mixed = sweeps(tnt.TNT_PREC_MIXED, args.steps)
+    launches = ctx.launch_count() - launches0
+    ms_fp64, st_fp64 = sweeps(tnt.TNT_PREC_FP64, max(1, min(args.steps, 3)))
+    ms_mixed = dist_max(ms_mixed, ws)
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            from oracle import bose_hubbard as bh
+            from oracle import dmrg as od
+            Ws, l, r = bh.bh_mpo(DMRG_L, DMRG_NMAX, J, DMRG_U)
+            t0 = time.perf_counter()
+            _, _, hist = od.dmrg(A, q, Ws, l, r, DMRG_CHI, DMRG_SWEEPS)
+            t_or = (time.perf_counter() - t0) / DMRG_SWEEPS
+            cpu = {"value": t_or, "unit": "s/sweep", "cores": threads_used(), "kind": "oracle",
+                   "sample": f"the same {DMRG_SWEEPS}-sweep run", "E": hist[-1]["E"],
+                   "dE_mixed_rel": abs(st_mixed["E"] - hist[-1]["E"]) / abs(hist[-1]["E"]),
+                   "dE_fp64_rel": abs(st_fp64["E"] - hist[-1]["E"]) / abs(hist[-1]["E"])}
+        line = {"metric": METRIC, "value": ms_mixed * 1e-3, "unit": "s/sweep", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed * DMRG_SWEEPS,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "tf32x3+f64", "data": "synthetic",
+                "config": {"workload": "two-site DMRG, Bose-Hubbard L=8 N=8 n_max=3 J=1 U=2 "
+                                       "chi_max=32, 4 sweeps from a seeded random MPS in the N=8 blocks",
+                           "sweeps_per_step": DMRG_SWEEPS},
+                "s_per_sweep": {"mixed": ms_mixed * 1e-3, "fp64": ms_fp64 * 1e-3},
+                "E": {"mixed": st_mixed["E"], "fp64": st_fp64["E"]},
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+TEBD_L, TEBD_NMAX, TEBD_U, TEBD_DT, TEBD_CHI, TEBD_ERR = 64, 4, 2.0, 0.01, 512, 1e-10
+
+
+def run_tebd(args, ws, rank, local):
+    """--workload tebd: quench from the Mott state |1...1> of the 64-site chain (d = 5,
+    J = 1, U = 2), second-order Trotter steps of dt = 0.01 at chi_max = 512 and truncation
+    error 1e-10; one step = one Trotter step (95 two-site gates), metric s/step."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    ctx.set_params(chi_max=TEBD_CHI, trunc_err=TEBD_ERR, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    mps = ctx.mps_product([1] * TEBD_L, TEBD_NMAX + 1, TEBD_CHI)
+    mpo = ctx.mpo_bose_hubbard(TEBD_L, TEBD_NMAX, J, TEBD_U)
+    E0 = mps.expect_mpo(mpo)
+    tb = ctx.tebd_create(mps, TEBD_NMAX, J, TEBD_U, TEBD_DT)
+    for _ in range(args.warmup):
+        tb.step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    t0 = time.perf_counter()
+    stats = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            stats.append(tb.step())
+        torch.cuda.synchronize()
+    dt = dist_max((time.perf_counter() - t0) / args.steps, ws)
+    launches = ctx.launch_count() - launches0
+    n2 = mps.norm2()
+    if rank == 0:
+        line = {"metric": METRIC, "value": dt, "unit": "s/step", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "TEBD quench from |1...1>, Bose-Hubbard L=64 d=5 J=1 U=2, "
+                                       "2nd-order Trotter dt=0.01, chi_max=512, eps=1e-10",
+                           "time_reached": TEBD_DT * (args.warmup + args.steps)},
+                "device_s_per_step": statistics.mean(s["seconds"] for s in stats),
+                "max_chi": stats[-1]["max_chi"], "err_sum_last_step": stats[-1]["err_sum"],
+                "norm_loss": 1 - n2, "energy_drift": mps.expect_mpo(mpo) / n2 - E0,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,7 +669,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["update", "u1", "chains"], default="update")
+    ap.add_argument("--workload", choices=["update", "u1", "chains", "dmrg", "tebd"],
+                    default="update")
     ap.add_argument("--fp64-gemm", choices=["tc", "fma"], default=None,
                     help="engine of the FP64 products (default: tc with --precision mixed, "
                          "fma with --precision fp64, the plain FP64 path)")
@@ -558,8 +680,12 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
-    if args.workload != "update":
+    if args.workload in ("u1", "chains"):
         return run_grouped(args, ws, rank, local)
+    if args.workload == "dmrg":
+        return run_dmrg(args, ws, rank, local)
+    if args.workload == "tebd":
+        return run_tebd(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

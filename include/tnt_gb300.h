@@ -286,6 +286,13 @@ int tnt_mps_get_charges(const tnt_mps* mps, int bond, int64_t* h_out, int64_t ca
 int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* mps, const tnt_mpo* mpo, double* E);
 int tnt_mps_norm2(tnt_ctx* ctx, const tnt_mps* mps, double* norm2);
 
+/* Observables of Sec. 5's examples, FP64, for any (not necessarily normalised) MPS:
+ * h_n[j] = <n_j> / <psi|psi> (L values), and the single-particle density matrix
+ * h_rho[i*L + j] = <b+_i b_j> / <psi|psi> (L x L, Hermitian), by transfer environments
+ * (O(L) environment growths for the density, O(L^2) for the matrix).  Host outputs. */
+int tnt_mps_density(tnt_ctx* ctx, const tnt_mps* mps, double* h_n);
+int tnt_mps_bdagb(tnt_ctx* ctx, const tnt_mps* mps, tnt_cplx* h_rho);
+
 /* Two-site DMRG (Sec. 4.3 Listing 2 in two-site form).  Create brings the MPS to
  * right-canonical unit-norm form by exact SVD moves and builds the right environments.
  * One sweep = bonds 0..L-2 left to right, then L-2..0 right to left; each update forms

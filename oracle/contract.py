@@ -131,3 +131,31 @@ def density(tensors, n_max: int) -> np.ndarray:
                 E = np.einsum("pa,psq,asb->qb", E, A.conj(), A)
         out[j] = E[0, 0].real / norm
     return out
+
+
+def bdagb(tensors, n_max: int) -> np.ndarray:
+    """Single-particle density matrix rho_ij = <b+_i b_j> / <psi|psi> (Sec. 5 examples):
+    b+ placed at site i and b at site j in one transfer-matrix sweep (b+ b at i = j)."""
+    d = n_max + 1
+    b = np.diag(np.sqrt(np.arange(1, d, dtype=np.float64)), k=1).astype(np.complex128)
+    bd = b.conj().T
+    L = len(tensors)
+    norm = mps_overlap(tensors, tensors).real
+    rho = np.zeros((L, L), dtype=np.complex128)
+    for i in range(L):
+        for j in range(L):
+            E = np.ones((1, 1), dtype=np.complex128)
+            for k, A in enumerate(tensors):
+                op = None
+                if k == i and k == j:
+                    op = bd @ b
+                elif k == i:
+                    op = bd
+                elif k == j:
+                    op = b
+                if op is None:
+                    E = np.einsum("pa,psq,asb->qb", E, A.conj(), A)
+                else:
+                    E = np.einsum("pa,psq,st,atb->qb", E, A.conj(), op, A)
+            rho[i, j] = E[0, 0] / norm
+    return rho

@@ -114,6 +114,8 @@ SIGNATURES = {
     "tnt_dmrg_create": [P, P, P, C.POINTER(P)],
     "tnt_dmrg_sweep": [P, P, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_destroy": [P],
+    "tnt_mps_density": [P, P, PD],
+    "tnt_mps_bdagb": [P, P, P],
     "tnt_tebd_create": [P, P, I, D, D, D, D, C.POINTER(P)],
     "tnt_u1_size": [C.POINTER(tnt_u1_problem), PI64],
     "tnt_u1_pack": [P, C.POINTER(tnt_u1_problem), P, P],

@@ -19,10 +19,11 @@
 // GEMM's own rounding bound.  Complex products take four real MMAs per k step
 // (re+ += Ar Br, re- += Ai Bi, im += Ar Bi + Ai Br; re = re+ - re- in FP64).
 //
-// Kernel: persistent, one CTA per SM, 128 x 128 output tiles; warp 0 issues TMA loads of
-// the slice planes (3-D maps [plane][row][k], 64-byte swizzle), warp 1 the MMAs into
-// three TMEM accumulators, warps 2..5 convert each (chunk, level) accumulator and add it
-// to the FP64 output tile, handing TMEM back through an mbarrier.  All waits bounded.
+// Kernel: persistent, one CTA per SM over (output tile, level group) items, 128 x 128 or
+// 128 x 64 tiles; warp 0 issues TMA loads of the slice planes (3-D maps [plane][row][k],
+// 64-byte swizzle), warp 1 the MMAs into three TMEM accumulators, warps 2..5 convert each
+// (chunk, level) accumulator and add it to the item's FP64 partial tile, handing TMEM back
+// through an mbarrier; a second kernel adds the two level groups.  All waits bounded.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -39,12 +40,19 @@ constexpr int OZ_S = 9;         // slices per operand
 constexpr int OZ_BETA = 6;      // bits per slice
 constexpr int OZ_KC = 224;      // K chunk: 2 * S * KC * (2^beta - 1)^2 < 2^24
 constexpr int OZ_PLANES = 2 * OZ_S;
-constexpr int OBN = 128;
-constexpr int O_TILE = 128 * 16 * 4;                 // one plane tile, 8 KB
-constexpr int O_STAGE = 4 * O_TILE;                  // A re, A im, B re, B im
-constexpr int O_STAGES = 6;
-constexpr int O_SMEM = O_STAGES * O_STAGE + 1024 + 256;
-constexpr int O_TMEM = 512;
+constexpr int O_TILE_A = 128 * 16 * 4;               // one A plane tile, 8 KB
+// the levels of a tile in two groups of nearly equal work (21 and 24 slice pairs), each
+// group an independent work item with its own FP64 partial output
+constexpr int OZ_GROUP_SPLIT = 7;                    // levels 2..7 | 8..S+1
+
+template <int BN>
+struct OzCfg {
+  static constexpr int TILE_B = BN * 16 * 4;
+  static constexpr int STAGE = 2 * O_TILE_A + 2 * TILE_B;  // A re, A im, B re, B im
+  static constexpr int STAGES = (BN == 128) ? 6 : 8;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr int TMEM = (BN == 128) ? 512 : 256;
+};
 static_assert(2LL * OZ_S * OZ_KC * ((1 << OZ_BETA) - 1) * ((1 << OZ_BETA) - 1) < (1LL << 24),
               "a level sum over one K chunk must stay exact in FP32");
 static_assert(OZ_KC % 16 == 0, "K chunk in whole k-blocks");
@@ -53,8 +61,7 @@ struct OzArgs {
   int64_t M, N, Kp;
   int ntm, ntn;       // tiles along M and N
   int nchunk;         // K chunks of OZ_KC
-  z* C;
-  int64_t ldc;
+  z* P;               // two FP64 partial outputs, [group][M][N]
   const double* sA;   // row scales (powers of two)
   const double* sB;   // column scales
   int* status;
@@ -66,9 +73,13 @@ __device__ __forceinline__ void level_pairs(int l, int* p0, int* p1) {
   *p1 = min(OZ_S, l - 1);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB,
                                                     OzArgs g) {
+  using Cf = OzCfg<BN>;
+  constexpr int O_STAGES = Cf::STAGES;
+  constexpr int O_STAGE = Cf::STAGE;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + O_STAGES * O_STAGE);
@@ -79,6 +90,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = g.ntm * g.ntn;
+  const int nitems = 2 * ntiles;  // (tile, level group)
   const int kb_total = (int)(g.Kp / 16);
   const int kb_chunk = OZ_KC / 16;
 
@@ -96,7 +108,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tmem_slot)),
-                 "r"(O_TMEM)
+                 "r"(Cf::TMEM)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -109,11 +121,13 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     // ------------------------------------------------ TMA producer
     uint32_t it = 0;
     bool stop = false;
-    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * OBN;
+    for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
+      const int t = w % ntiles, grp = w / ntiles;
+      const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * BN;
+      const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
       for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
         const int kb0 = ch * kb_chunk, kb1 = min(kb_total, kb0 + kb_chunk);
-        for (int l = 2; l <= OZ_S + 1 && !stop; ++l) {
+        for (int l = l0; l <= l1 && !stop; ++l) {
           int p0, p1;
           level_pairs(l, &p0, &p1);
           for (int p = p0; p <= p1 && !stop; ++p) {
@@ -132,10 +146,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
               uint8_t* st = smem + s * O_STAGE;
               mbar_expect_tx(&full[s], O_STAGE);
               const int k = kb * 16;
-              tma_load3(st + 0 * O_TILE, &tmA, &full[s], k, m0, 2 * (p - 1));
-              tma_load3(st + 1 * O_TILE, &tmA, &full[s], k, m0, 2 * (p - 1) + 1);
-              tma_load3(st + 2 * O_TILE, &tmB, &full[s], k, n0, 2 * (q - 1));
-              tma_load3(st + 3 * O_TILE, &tmB, &full[s], k, n0, 2 * (q - 1) + 1);
+              tma_load3(st, &tmA, &full[s], k, m0, 2 * (p - 1));
+              tma_load3(st + O_TILE_A, &tmA, &full[s], k, m0, 2 * (p - 1) + 1);
+              tma_load3(st + 2 * O_TILE_A, &tmB, &full[s], k, n0, 2 * (q - 1));
+              tma_load3(st + 2 * O_TILE_A + Cf::TILE_B, &tmB, &full[s], k, n0, 2 * (q - 1) + 1);
               ++it;
             }
           }
@@ -146,14 +160,16 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
       mbar_wait(&full[i % O_STAGES], (i / O_STAGES) & 1, g.status);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_tf32_n(OBN);
-    const uint32_t t_re = tmem, t_im = tmem + OBN, t_rn = tmem + 2 * OBN;
+    const uint32_t id = idesc_tf32_n(BN);
+    const uint32_t t_re = tmem, t_im = tmem + BN, t_rn = tmem + 2 * BN;
     uint32_t it = 0, sub = 0;
     bool stop = false;
-    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+    for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
+      const int grp = w / ntiles;
+      const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
       for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
         const int kb0 = ch * kb_chunk, kb1 = min(kb_total, kb0 + kb_chunk);
-        for (int l = 2; l <= OZ_S + 1 && !stop; ++l) {
+        for (int l = l0; l <= l1 && !stop; ++l) {
           int p0, p1;
           level_pairs(l, &p0, &p1);
           if (sub > 0 && (*abort_flag || !mbar_wait(acce, (sub - 1) & 1, g.status))) {
@@ -175,10 +191,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
               const uint32_t base = su32(smem + s * O_STAGE);
               for (int ks = 0; ks < 2; ++ks) {
                 const uint32_t off = ks * 32;
-                const uint64_t ar = desc_sw64(base + 0 * O_TILE + off);
-                const uint64_t ai = desc_sw64(base + 1 * O_TILE + off);
-                const uint64_t br = desc_sw64(base + 2 * O_TILE + off);
-                const uint64_t bi = desc_sw64(base + 3 * O_TILE + off);
+                const uint64_t ar = desc_sw64(base + off);
+                const uint64_t ai = desc_sw64(base + O_TILE_A + off);
+                const uint64_t br = desc_sw64(base + 2 * O_TILE_A + off);
+                const uint64_t bi = desc_sw64(base + 2 * O_TILE_A + Cf::TILE_B + off);
                 const uint32_t acc = first ? 0u : 1u;
                 mma_tf32(t_re, ar, br, id, acc);
                 mma_tf32(t_rn, ai, bi, id, acc);
@@ -203,12 +219,15 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     const uint32_t lane_addr = (uint32_t)(q4 * 32) << 16;
     uint32_t sub = 0;
     bool stop = false;
-    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * OBN;
+    for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
+      const int t = w % ntiles, grp = w / ntiles;
+      const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * BN;
+      const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
       const int64_t gm = (int64_t)m0 + row;
       const double sa = (gm < g.M) ? g.sA[gm] : 0.0;
+      z* Cg = g.P + (int64_t)grp * g.M * g.N;
       for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
-        for (int l = 2; l <= OZ_S + 1; ++l) {
+        for (int l = l0; l <= l1; ++l) {
           if (*abort_flag || !mbar_wait(accf, sub & 1, g.status)) {
             *abort_flag = 1;
             stop = true;
@@ -216,15 +235,15 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const double lv = ldexp(sa, -l * OZ_BETA);
-          const bool first = (ch == 0 && l == 2);
-          for (int c0 = 0; c0 < OBN; c0 += 32) {
+          const bool first = (ch == 0 && l == l0);
+          for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t r[32], s[32], u[32];
             tmem_ld32(tmem + lane_addr + c0, r);
-            tmem_ld32(tmem + lane_addr + OBN + c0, s);
-            tmem_ld32(tmem + lane_addr + 2 * OBN + c0, u);
+            tmem_ld32(tmem + lane_addr + BN + c0, s);
+            tmem_ld32(tmem + lane_addr + 2 * BN + c0, u);
             if (gm < g.M) {
-              z* pc = g.C + gm * g.ldc + n0 + c0;
-#pragma unroll 8
+              z* pc = Cg + gm * g.N + n0 + c0;
+#pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const int64_t gn = (int64_t)n0 + c0 + j;
                 if (gn < g.N) {
@@ -253,9 +272,18 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(O_TMEM)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cf::TMEM)
                  : "memory");
   }
+}
+
+// C = P[0] + P[1], the two level groups, in a fixed order
+__global__ void k_oz_finish(const z* __restrict__ P, int64_t M, int64_t N, z* __restrict__ C,
+                            int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    C[(e / N) * ldc + e % N] = zadd(P[e], P[total + e]);
 }
 
 // ---------------------------------------------------------------- scales and slices
@@ -321,17 +349,32 @@ int64_t rup16(int64_t x) { return (x + 15) / 16 * 16; }
 size_t ozgemm_scratch_bytes(int64_t M, int64_t N, int64_t K) {
   const int64_t Kp = rup16(K);
   return ws_round(sizeof(float) * OZ_PLANES * M * Kp) + ws_round(sizeof(float) * OZ_PLANES * N * Kp) +
-         ws_round(sizeof(double) * M) + ws_round(sizeof(double) * N) + 4096;
+         ws_round(sizeof(double) * M) + ws_round(sizeof(double) * N) + ws_round(sizeof(z) * 2 * M * N) + 4096;
 }
 
 bool ozgemm_eligible(const Ctx* c, const ZGemm& g) {
   return c->oz_mode != 0 && g.batch == 1 && !g.lower_only && g.alpha.x == 1.0 && g.alpha.y == 0.0 &&
-         g.beta.x == 0.0 && g.beta.y == 0.0 && g.M >= 128 && g.N >= 128 && g.K >= 64 &&
+         g.beta.x == 0.0 && g.beta.y == 0.0 && g.M >= 128 && g.N >= 64 && g.K >= 64 &&
          (double)g.M * (double)g.N * (double)g.K >= 3.0e7 && g.M < (1LL << 31) && g.N < (1LL << 31);
 }
 
-// C = A B (FP64-accurate) through the integer-slice tensor-core kernel; the slices live
-// in the context's own buffer (grown between calls, never inside a capture)
+namespace {
+template <int BN>
+int launch_oz(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, const OzArgs& a, int nitems, int sm) {
+  static bool attr = false;
+  if (!attr) {
+    TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_oz_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         OzCfg<BN>::SMEM));
+    attr = true;
+  }
+  k_oz_gemm<BN><<<(unsigned)std::min(nitems, sm), 192, OzCfg<BN>::SMEM, c->stream>>>(tA, tB, a);
+  return TNT_OK;
+}
+}  // namespace
+
+// C = A B (FP64-accurate) through the integer-slice tensor-core kernel; slices and the two
+// partial outputs live in the context's own buffer (grown between calls, never inside a
+// capture)
 int ozgemm(Ctx* c, const ZGemm& g) {
   const int64_t M = g.M, N = g.N, K = g.K, Kp = rup16(K);
   const size_t need = ozgemm_scratch_bytes(M, N, K);
@@ -351,6 +394,8 @@ int ozgemm(Ctx* c, const ZGemm& g) {
   double* sA = (double*)b;
   b += ws_round(sizeof(double) * M);
   double* sB = (double*)b;
+  b += ws_round(sizeof(double) * N);
+  z* P = (z*)b;
   // B enters as rows n with K along the row: B^T[n][k] = B[k * b_rs + n * b_cs]
   k_oz_row_scale<<<ogrid(32 * M), 256, 0, c->stream>>>(g.A, M, K, g.a_rs, g.a_cs, sA);
   k_oz_row_scale<<<ogrid(32 * N), 256, 0, c->stream>>>(g.B, N, K, g.b_cs, g.b_rs, sB);
@@ -361,38 +406,35 @@ int ozgemm(Ctx* c, const ZGemm& g) {
   }
   c->launches += 4;
   TNT_CHECK_LAUNCH(c);
-  CUtensorMap tA, tB;
-  TNT_TRY(tma_map_planes_n(c, &tA, Ap, M, Kp, 128, OZ_PLANES));
-  TNT_TRY(tma_map_planes_n(c, &tB, Bp, N, Kp, OBN, OZ_PLANES));
-  static bool attr = false;
-  if (!attr) {
-    TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, O_SMEM));
-    attr = true;
+  static int sm = 0;
+  if (!sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sm < 1) sm = 152;
   }
   OzArgs a;
   a.M = M;
   a.N = N;
   a.Kp = Kp;
-  a.ntm = (int)((M + 127) / 128);
-  a.ntn = (int)((N + OBN - 1) / OBN);
   a.nchunk = (int)((Kp + OZ_KC - 1) / OZ_KC);
-  a.C = g.C;
-  a.ldc = g.c_rs;
+  a.ntm = (int)((M + 127) / 128);
+  // N tile 64 when 128-wide tiles would leave SMs idle
+  const int bn = (2LL * a.ntm * ((N + 127) / 128) < 2LL * sm) ? 64 : 128;
+  a.ntn = (int)((N + bn - 1) / bn);
+  a.P = P;
   a.sA = sA;
   a.sB = sB;
   a.status = c->d_status;
-  int sm = 152;
-  {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int ntiles = a.ntm * a.ntn;
+  CUtensorMap tA, tB;
+  TNT_TRY(tma_map_planes_n(c, &tA, Ap, M, Kp, 128, OZ_PLANES));
+  TNT_TRY(tma_map_planes_n(c, &tB, Bp, N, Kp, bn, OZ_PLANES));
+  const int nitems = 2 * a.ntm * a.ntn;
   {
     ProfScope ps(c, "oz_gemm", 8.0 * (double)M * (double)N * (double)K);
-    k_oz_gemm<<<(unsigned)std::min(ntiles, sm), 192, O_SMEM, c->stream>>>(tA, tB, a);
+    TNT_TRY(bn == 64 ? launch_oz<64>(c, tA, tB, a, nitems, sm) : launch_oz<128>(c, tA, tB, a, nitems, sm));
+    k_oz_finish<<<ogrid(M * N), 256, 0, c->stream>>>(P, M, N, g.C, g.c_rs);
   }
-  c->launches++;
+  c->launches += 2;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;
 }

@@ -342,6 +342,17 @@ class Mps:
         self.ctx._chk(self.ctx.lib.tnt_mps_expect_mpo(self.ctx.h, self.h, mpo.h, C.byref(v)))
         return v.value
 
+    def density(self) -> np.ndarray:
+        out = np.zeros(self.L)
+        self.ctx._chk(self.ctx.lib.tnt_mps_density(self.ctx.h, self.h, out.ctypes.data_as(L.PD)))
+        return out
+
+    def bdagb(self) -> np.ndarray:
+        """<b+_i b_j> / <psi|psi> as an L x L complex matrix."""
+        out = np.zeros((self.L, self.L), dtype=np.complex128)
+        self.ctx._chk(self.ctx.lib.tnt_mps_bdagb(self.ctx.h, self.h, out.ctypes.data))
+        return out
+
     def norm2(self) -> float:
         v = C.c_double()
         self.ctx._chk(self.ctx.lib.tnt_mps_norm2(self.ctx.h, self.h, C.byref(v)))

@@ -93,3 +93,38 @@ def test_density_and_overlap():
         nj = ed.number_operator_full(L, n_max, j)
         assert abs(dens[j - 1] - np.vdot(psi, nj * psi).real / nrm) < 1e-12
     assert abs(dens.sum() - N) < 1e-12
+
+
+def _apply_site(psi, op, site, L, d):
+    """op acting on one site of a full state vector (sites most significant first)."""
+    t = psi.reshape((d,) * L)
+    t = np.moveaxis(np.tensordot(op, t, axes=([1], [site])), 0, site)
+    return t.reshape(-1)
+
+
+def test_bdagb_against_full_state_vector():
+    """rho_ij = <b+_i b_j> by transfer matrices equals the brute-force value on the full
+    d^L vector (operators applied by reshaping), is Hermitian, has the density on its
+    diagonal and trace N (the random MPS lives in the N = 4 sector)."""
+    L, n_max, N = 5, 2, 4
+    d = n_max + 1
+    g = synth.rng(9)
+    A, _ = synth.random_charged_mps(g, L, d, N, 8)
+    psi = C.mps_to_state(A)
+    b = np.diag(np.sqrt(np.arange(1, d, dtype=float)), k=1)
+    rho = C.bdagb(A, n_max)
+    nrm = np.vdot(psi, psi).real
+    for i in range(L):
+        for j in range(L):
+            phi = _apply_site(_apply_site(psi, b, j, L, d), b.T, i, L, d)
+            assert abs(rho[i, j] - np.vdot(psi, phi) / nrm) < 1e-12
+    assert np.allclose(rho, rho.conj().T, atol=1e-13)
+    assert np.allclose(np.diag(rho).real, C.density(A, n_max), atol=1e-13)
+    assert abs(np.trace(rho).real - N) < 1e-12
+
+
+def test_bdagb_fock_state_is_diagonal():
+    from oracle import tebd
+    occ = [2, 0, 1, 1, 0]
+    A, _ = tebd.product_state(occ, 2)
+    assert np.allclose(C.bdagb(A, 2), np.diag(occ), atol=1e-15)
