@@ -366,12 +366,13 @@ def run_ours(args, ws, rank, local):
 
 # kernel class -> (bound, what its work counts).  The library sums, per launch, the
 # algorithmic work: useful complex-product FLOPs (8 M N K; the split-TF32 repeats are not
-# counted) for the GEMM classes, FP64 FLOPs for the eigensolver, bytes read plus written
-# for the memory-bound vector and conversion kernels.
+# counted) for the GEMM classes, FP64 FLOPs for the eigensolver and for the Lanczos dot
+# products and updates (on GB300 their 4 FP64 FMAs per complex element outrun HBM), bytes
+# read plus written for the memory-bound conversion kernels.
 CLASSES = {
     "cgemm_tf32x3": ("tensor", "flop"), "zgemm_f64": ("alu", "flop"), "op_apply": ("alu", "flop"),
-    "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("hbm", "byte"),
-    "multiaxpy": ("hbm", "byte"), "jacobi_small": ("alu", None), "heig_tridiag": ("alu", "flop"),
+    "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("alu", "flop"),
+    "multiaxpy": ("alu", "flop"), "jacobi_small": ("alu", None), "heig_tridiag": ("alu", "flop"),
     "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
     "cgemm_grouped": ("tensor", "flop"), "zgemm_grouped": ("alu", "flop"),
     "u1_wop": ("hbm", "byte"), "u1_pack_theta": ("hbm", "byte"), "u1_gather": ("hbm", "byte"),

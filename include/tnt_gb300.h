@@ -318,7 +318,7 @@ int tnt_matmul(tnt_ctx* ctx, int64_t M, int64_t N, int64_t K, const tnt_cplx* d_
 
 enum { TNT_FP64_GEMM_FMA = 0, TNT_FP64_GEMM_TC = 1 };
 /* Engine of the library's FP64 matrix products (the FP64 H_eff.theta, theta, the
- * environments, SVD projections; the Gram matrices of the SVD always use FP64 FMA).
+ * environments, the SVD's Gram matrices and projections).
  * TNT_FP64_GEMM_TC (default): each row of A and column of B is scaled by a power of two
  * to below 1 and cut into 9 integer slices of 6 bits (exact FP64 steps); slice products
  * run as TF32 MMAs whose FP32 sums over K chunks of 224 stay below 2^24 and so are exact;

@@ -303,14 +303,41 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
   }
 }
 
+// Number of eigenvalues of T below x from the signs of the leading principal minors
+// p_i = det(T_i - x I), p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm sequence of the
+// characteristic polynomials, Givens' bisection): a sign change between p_{i-1} and p_i
+// marks an eigenvalue below x.  Each step is one subtraction and two products; rounding in
+// a step perturbs only d_i and e_{i-1} by O(eps) relative, so the count is that of a
+// matrix within O(eps |T|).  Division-free: a full-warp FP64 division costs several times
+// the FP64-pipe issue slots of these three operations.  The pair (p_{i-1}, p_i) is
+// rescaled by an exact power of two when its exponent leaves [-400, 400]; signs and
+// exponents are read as integers.  A zero minor is replaced by 2^-60 |p_{i-1}| with the
+// sign opposite to its predecessor (the tiny negative pivot of the ratio form).
+__device__ __forceinline__ int hi_exp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 __device__ int sturm_lt(const double* d, const double* e, int64_t n, double x, double pivmin) {
+  (void)pivmin;
+  double pm2 = 1.0, pm1 = d[0] - x;
+  int neg_prev = 0;  // sign of p_0 = 1
   int cnt = 0;
-  double q = d[0] - x;
-  if (q < 0) cnt++;
+  if (pm1 == 0.0) pm1 = -0x1p-60;
+  int neg = __double2hiint(pm1) < 0;
+  cnt += neg != neg_prev;
+  neg_prev = neg;
   for (int64_t i = 1; i < n; ++i) {
-    if (fabs(q) < pivmin) q = -pivmin;
-    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
-    if (q < 0) cnt++;
+    const double ei = e[i - 1];
+    double p = fma(d[i] - x, pm1, -(ei * ei) * pm2);
+    if (p == 0.0) p = neg_prev ? 0x1p-60 * fabs(pm1) : -0x1p-60 * fabs(pm1);
+    neg = __double2hiint(p) < 0;
+    cnt += neg != neg_prev;
+    neg_prev = neg;
+    pm2 = pm1;
+    pm1 = p;
+    const int ex = hi_exp(p);
+    if (ex > 1023 + 400 || ex < 1023 - 400) {  // keep the pair in range: exact scaling
+      const double f = ldexp(1.0, 1023 - ex);
+      pm1 *= f;
+      pm2 *= f;
+    }
   }
   return cnt;
 }

@@ -419,7 +419,7 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
   for (int v0 = 0; v0 < k; v0 += KB) {
     int kv = (k - v0 < KB) ? (k - v0) : KB;
-    ProfScope ps(c, "multidot", 16.0 * (double)(kv + 1) * (double)n);
+    ProfScope ps(c, "multidot", 8.0 * (double)kv * (double)n);  // FP64 FLOPs (complex MAC = 8)
     launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip);
     k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0, d_skip);
     c->launches += 2;
@@ -436,7 +436,7 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy)");
   {
-    ProfScope ps(c, "multiaxpy", 16.0 * (double)(k + 2) * (double)n);
+    ProfScope ps(c, "multiaxpy", (8.0 * (double)k + 4.0) * (double)n);  // FP64 FLOPs
     k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip);
   }
   k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2, d_skip);
@@ -476,16 +476,29 @@ int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2) {
 // one warp (33 sub-intervals per step), then inverse iteration with a pivoted tridiagonal
 // LU (thread 0).  out[0] = E, out[1] = |y_{k-1}|.
 namespace {
+// number of eigenvalues < x: sign changes of the leading principal minors
+// p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2} (division-free Sturm sequence; a zero minor
+// takes 2^-60 |p_{i-1}| with the sign opposite to its predecessor; the pair is rescaled
+// by an exact power of two when its exponent leaves [-400, 400])
 __device__ int sturm_count(const double* a, const double* b, int k, double x) {
-  // number of eigenvalues < x (LDL^T of T - x I)
-  int cnt = 0;
-  double dd = a[0] - x;
-  const double tiny = 1e-300;
-  if (dd < 0) cnt++;
+  double pm2 = 1.0, pm1 = a[0] - x;
+  if (pm1 == 0.0) pm1 = -0x1p-60;
+  int neg_prev = __double2hiint(pm1) < 0;
+  int cnt = neg_prev;
   for (int i = 1; i < k; ++i) {
-    if (fabs(dd) < tiny) dd = -tiny;
-    dd = (a[i] - x) - b[i - 1] * b[i - 1] / dd;
-    if (dd < 0) cnt++;
+    double p = fma(a[i] - x, pm1, -(b[i - 1] * b[i - 1]) * pm2);
+    if (p == 0.0) p = neg_prev ? 0x1p-60 * fabs(pm1) : -0x1p-60 * fabs(pm1);
+    const int neg = __double2hiint(p) < 0;
+    cnt += neg != neg_prev;
+    neg_prev = neg;
+    pm2 = pm1;
+    pm1 = p;
+    const int ex = (__double2hiint(p) >> 20) & 0x7ff;
+    if (ex > 1023 + 400 || ex < 1023 - 400) {
+      const double f = ldexp(1.0, 1023 - ex);
+      pm1 *= f;
+      pm2 *= f;
+    }
   }
   return cnt;
 }

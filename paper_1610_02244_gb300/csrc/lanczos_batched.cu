@@ -259,7 +259,7 @@ int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, c
   for (int v0 = 0; v0 < k; v0 += SKB) {
     const int kv = std::min(SKB, k - v0);
     {
-      ProfScope ps(c, "multidot", 16.0 * (double)(kv + 1) * (double)s.n);
+      ProfScope ps(c, "multidot", 8.0 * (double)kv * (double)s.n);  // FP64 FLOPs
       sdot_kv(kv, s.nch, c->stream, basis + (int64_t)v0 * s.n, s.n, w, s.ch, s.part, skip);
     }
     k_sreduce_dots<<<s.P, 256, 0, c->stream>>>(s.part, s.nch, s.first, kv, v0, dots_out, skip);
@@ -271,7 +271,7 @@ int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, c
 int saxpy(Ctx* c, BScratch& s, int k, const z* coef, z* w, double* norm2, const int* skip,
           const int* kper = nullptr) {
   {
-    ProfScope ps(c, "multiaxpy", 16.0 * (double)(k + 2) * (double)s.n);
+    ProfScope ps(c, "multiaxpy", (8.0 * (double)k + 4.0) * (double)s.n);  // FP64 FLOPs
     k_saxpy_norm<<<s.nch, ST, 0, c->stream>>>(s.V, s.n, k, coef, w, s.ch, s.rpart, skip, kper);
   }
   k_sreduce_real<<<s.P, 256, 0, c->stream>>>(s.rpart, s.first, norm2, skip);

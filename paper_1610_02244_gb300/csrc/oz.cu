@@ -353,7 +353,8 @@ size_t ozgemm_scratch_bytes(int64_t M, int64_t N, int64_t K) {
 }
 
 bool ozgemm_eligible(const Ctx* c, const ZGemm& g) {
-  return c->oz_mode != 0 && g.batch == 1 && !g.lower_only && g.alpha.x == 1.0 && g.alpha.y == 0.0 &&
+  // (a Hermitian product asked for its lower part only is formed whole: the caller mirrors it)
+  return c->oz_mode != 0 && g.batch == 1 && g.alpha.x == 1.0 && g.alpha.y == 0.0 &&
          g.beta.x == 0.0 && g.beta.y == 0.0 && g.M >= 128 && g.N >= 64 && g.K >= 64 &&
          (double)g.M * (double)g.N * (double)g.K >= 3.0e7 && g.M < (1LL << 31) && g.N < (1LL << 31);
 }
