@@ -29,6 +29,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// x -= a conj(b) as four FMAs (the FP64 pipe is the bottleneck of these kernels on GB300)
+__device__ __forceinline__ void zsub_mul_conj(z& x, z a, z b) {
+  x.x = fma(-a.x, b.x, fma(-a.y, b.y, x.x));
+  x.y = fma(-a.y, b.x, fma(a.x, b.y, x.y));
+}
+
 // block-wide sum; valid in every thread on return
 __device__ double block_sum_all(double v, double* sh) {
   v = warp_sum_d(v);
@@ -236,7 +242,10 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
     }
     __syncthreads();
     const z cf = s_cf;
-    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) sw[c] = zadd(__ldcg(pj + c), zmul(cf, sv[c]));
+    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
+      const z pv = __ldcg(pj + c), vv = sv[c];
+      sw[c] = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pv.x)), fma(cf.x, vv.y, fma(cf.y, vv.x, pv.y)));
+    }
     __syncthreads();
     // updated row j+1 (local row 0), then reflector j+1 from its entries 1..m-1
     const z v0 = sv[0], w0 = sw[0];
@@ -244,8 +253,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
       const z* row = a.G + (j + 1) * n + j + 1;
       for (int64_t c = threadIdx.x; c < m; c += blockDim.x) {
         z x = __ldcg(row + c);
-        x = zsub(x, zmul(v0, zconj(sw[c])));
-        x = zsub(x, zmul(w0, zconj(sv[c])));
+        zsub_mul_conj(x, v0, sw[c]);
+        zsub_mul_conj(x, w0, sv[c]);
         srow[c] = x;
       }
     }
@@ -272,8 +281,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
 #pragma unroll 4
       for (int64_t c = 1 + lane; c < m; c += 32) {
         z x = __ldcg(row + c);
-        x = zsub(x, zmul(vr, zconj(sw[c])));
-        x = zsub(x, zmul(wr, zconj(sv[c])));
+        zsub_mul_conj(x, vr, sw[c]);
+        zsub_mul_conj(x, wr, sv[c]);
         row[c] = x;
         const z q = sv2[c - 1];
         sr = fma(x.x, q.x, fma(-x.y, q.y, sr));
@@ -515,16 +524,25 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   }
 }
 
-// U[:, i] = H_0 ... H_{n-2} y_i; one CTA per eigenvector, the vector in shared memory
+// U[:, i] = H_0 ... H_{n-2} y_i; one CTA per BT_COLS eigenvectors, held in shared memory.
+// Each reflector is read once per CTA for all its columns, and the CTA's reduction of the
+// BT_COLS dot products is one pass: the FP64 pipe, not the reflector loads or the
+// synchronisation, sets the pace.
+constexpr int BT_COLS = 2;
 __global__ void __launch_bounds__(256) k_backtransform(const double* __restrict__ Y,
                                                        const z* __restrict__ Hv,
                                                        const z* __restrict__ tau, int64_t n,
-                                                       z* __restrict__ U, int64_t ldu) {
+                                                       int64_t k, int cols, z* __restrict__ U,
+                                                       int64_t ldu) {
   extern __shared__ double sm_bt[];
-  z* y = (z*)sm_bt;
-  __shared__ double shr[8], shi[8];
-  const int64_t i = blockIdx.x;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) y[r] = zmk(Y[i * n + r], 0);
+  z* y = (z*)sm_bt;  // cols x n (cols = BT_COLS, or 1 when two vectors do not fit)
+  __shared__ double shr[8][BT_COLS], shi[8][BT_COLS];
+  __shared__ z s_ts[BT_COLS];
+  const int64_t i0 = (int64_t)blockIdx.x * cols;
+  const int ncol = (k - i0 < cols) ? (int)(k - i0) : cols;
+  for (int q = 0; q < cols; ++q)
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x)
+      y[q * n + r] = zmk(q < ncol ? Y[(i0 + q) * n + r] : 0.0, 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t j = n - 2; j >= 0; --j) {
@@ -532,30 +550,55 @@ __global__ void __launch_bounds__(256) k_backtransform(const double* __restrict_
     if (t.x == 0.0 && t.y == 0.0) continue;
     const int64_t m = n - j - 1;
     const z* v = Hv + j * n;
-    double sr = 0, si = 0;  // s = v^H y[j+1:]
+    double sr[BT_COLS], si[BT_COLS];  // s = v^H y[j+1:] per column
+#pragma unroll
+    for (int q = 0; q < BT_COLS; ++q) sr[q] = si[q] = 0;
     for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
-      const z a = v[r], b = y[j + 1 + r];
-      sr = fma(a.x, b.x, fma(a.y, b.y, sr));
-      si = fma(a.x, b.y, fma(-a.y, b.x, si));
+      const z a = v[r];
+#pragma unroll
+      for (int q = 0; q < BT_COLS; ++q) {
+        if (q >= cols) break;
+        const z b = y[q * n + j + 1 + r];
+        sr[q] = fma(a.x, b.x, fma(a.y, b.y, sr[q]));
+        si[q] = fma(a.x, b.y, fma(-a.y, b.x, si[q]));
+      }
     }
-    sr = warp_sum_d(sr);
-    si = warp_sum_d(si);
-    if (lane == 0) {
-      shr[warp] = sr;
-      shi[warp] = si;
+#pragma unroll
+    for (int q = 0; q < BT_COLS; ++q) {
+      sr[q] = warp_sum_d(sr[q]);
+      si[q] = warp_sum_d(si[q]);
+      if (lane == 0) {
+        shr[warp][q] = sr[q];
+        shi[warp][q] = si[q];
+      }
     }
     __syncthreads();
-    double a = 0, b = 0;
-    for (int q = 0; q < 8; ++q) {
-      a += shr[q];
-      b += shi[q];
+    if (threadIdx.x < cols) {
+      double a = 0, b = 0;
+      for (int w = 0; w < 8; ++w) {
+        a += shr[w][threadIdx.x];
+        b += shi[w][threadIdx.x];
+      }
+      s_ts[threadIdx.x] = zmul(t, zmk(a, b));
     }
-    const z ts = zmul(t, zmk(a, b));
-    for (int64_t r = threadIdx.x; r < m; r += blockDim.x)
-      y[j + 1 + r] = zsub(y[j + 1 + r], zmul(ts, v[r]));
+    __syncthreads();
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+      const z a = v[r];
+#pragma unroll
+      for (int q = 0; q < BT_COLS; ++q) {
+        if (q >= cols) break;
+        z* p = y + q * n + j + 1 + r;
+        const z ts = s_ts[q];
+        z x = *p;
+        x.x = fma(-ts.x, a.x, fma(ts.y, a.y, x.x));
+        x.y = fma(-ts.x, a.y, fma(-ts.y, a.x, x.y));
+        *p = x;
+      }
+    }
     __syncthreads();
   }
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) U[r * ldu + i] = y[r];
+  for (int q = 0; q < ncol; ++q)
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) U[r * ldu + i0 + q] = y[q * n + r];
 }
 
 // S <- 1.5 I - 0.5 S  (k x k)
@@ -672,9 +715,10 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   }
   {
     ProfScope ps(c, "heig_backtransform", 8.0 * (double)n * (double)n * (double)k);
-    const size_t smem = sizeof(z) * n;
+    const int cols = (sizeof(z) * n * BT_COLS <= (size_t)200 * 1024) ? BT_COLS : 1;
+    const size_t smem = sizeof(z) * n * cols;
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_backtransform<<<(unsigned)k, 256, smem, st>>>(Y, Hv, tau, n, U0, k);
+    k_backtransform<<<(unsigned)((k + cols - 1) / cols), 256, smem, st>>>(Y, Hv, tau, n, k, cols, U0, k);
     c->launches++;
     TNT_CHECK_LAUNCH(c);
   }

@@ -356,17 +356,17 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, 
 #pragma unroll
       for (int q = 0; q < 8; ++q) u[q] = V[(int64_t)(v + q) * ld + e];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < 8; ++q) {  // x -= cv u as four FMAs
         const z cv = sc[v + q];
-        x.x -= cv.x * u[q].x - cv.y * u[q].y;
-        x.y -= cv.x * u[q].y + cv.y * u[q].x;
+        x.x = fma(-cv.x, u[q].x, fma(cv.y, u[q].y, x.x));
+        x.y = fma(-cv.x, u[q].y, fma(-cv.y, u[q].x, x.y));
       }
     }
     for (; v < k; ++v) {
       const z u = V[(int64_t)v * ld + e];
       const z cv = sc[v];
-      x.x -= cv.x * u.x - cv.y * u.y;
-      x.y -= cv.x * u.y + cv.y * u.x;
+      x.x = fma(-cv.x, u.x, fma(cv.y, u.y, x.x));
+      x.y = fma(-cv.x, u.y, fma(-cv.y, u.x, x.y));
     }
     w[e] = x;
     acc = fma(x.x, x.x, fma(x.y, x.y, acc));
@@ -419,7 +419,9 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
   for (int v0 = 0; v0 < k; v0 += KB) {
     int kv = (k - v0 < KB) ? (k - v0) : KB;
-    ProfScope ps(c, "multidot", 8.0 * (double)kv * (double)n);  // FP64 FLOPs (complex MAC = 8)
+    // FP64 FLOPs (complex MAC = 8); a pass the device may skip is profiled apart, with no
+    // work claimed (the host cannot know whether it ran)
+    ProfScope ps(c, d_skip ? "multidot_cond" : "multidot", d_skip ? 0.0 : 8.0 * (double)kv * (double)n);
     launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip);
     k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0, d_skip);
     c->launches += 2;
@@ -436,7 +438,8 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy)");
   {
-    ProfScope ps(c, "multiaxpy", (8.0 * (double)k + 4.0) * (double)n);  // FP64 FLOPs
+    ProfScope ps(c, d_skip ? "multiaxpy_cond" : "multiaxpy",
+                 d_skip ? 0.0 : (8.0 * (double)k + 4.0) * (double)n);  // FP64 FLOPs
     k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip);
   }
   k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2, d_skip);

@@ -115,17 +115,17 @@ __global__ void __launch_bounds__(ST) k_saxpy_norm(const z* __restrict__ V, int6
 #pragma unroll
       for (int q = 0; q < 8; ++q) u[q] = V[(int64_t)(v + q) * ld + e];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < 8; ++q) {  // x -= cv u as four FMAs
         const z cv = sc[v + q];
-        x.x -= cv.x * u[q].x - cv.y * u[q].y;
-        x.y -= cv.x * u[q].y + cv.y * u[q].x;
+        x.x = fma(-cv.x, u[q].x, fma(cv.y, u[q].y, x.x));
+        x.y = fma(-cv.x, u[q].y, fma(-cv.y, u[q].x, x.y));
       }
     }
     for (; v < k; ++v) {
       const z u = V[(int64_t)v * ld + e];
       const z cv = sc[v];
-      x.x -= cv.x * u.x - cv.y * u.y;
-      x.y -= cv.x * u.y + cv.y * u.x;
+      x.x = fma(-cv.x, u.x, fma(cv.y, u.y, x.x));
+      x.y = fma(-cv.x, u.y, fma(-cv.y, u.x, x.y));
     }
     w[e] = x;
     acc = fma(x.x, x.x, fma(x.y, x.y, acc));
@@ -259,7 +259,8 @@ int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, c
   for (int v0 = 0; v0 < k; v0 += SKB) {
     const int kv = std::min(SKB, k - v0);
     {
-      ProfScope ps(c, "multidot", 8.0 * (double)kv * (double)s.n);  // FP64 FLOPs
+      ProfScope ps(c, skip == s.frozen || skip == s.none ? "multidot" : "multidot_cond",
+                   skip == s.frozen || skip == s.none ? 8.0 * (double)kv * (double)s.n : 0.0);
       sdot_kv(kv, s.nch, c->stream, basis + (int64_t)v0 * s.n, s.n, w, s.ch, s.part, skip);
     }
     k_sreduce_dots<<<s.P, 256, 0, c->stream>>>(s.part, s.nch, s.first, kv, v0, dots_out, skip);
@@ -271,7 +272,8 @@ int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, c
 int saxpy(Ctx* c, BScratch& s, int k, const z* coef, z* w, double* norm2, const int* skip,
           const int* kper = nullptr) {
   {
-    ProfScope ps(c, "multiaxpy", (8.0 * (double)k + 4.0) * (double)s.n);  // FP64 FLOPs
+    ProfScope ps(c, skip == s.frozen || skip == s.none ? "multiaxpy" : "multiaxpy_cond",
+                 skip == s.frozen || skip == s.none ? (8.0 * (double)k + 4.0) * (double)s.n : 0.0);
     k_saxpy_norm<<<s.nch, ST, 0, c->stream>>>(s.V, s.n, k, coef, w, s.ch, s.rpart, skip, kper);
   }
   k_sreduce_real<<<s.P, 256, 0, c->stream>>>(s.rpart, s.first, norm2, skip);

@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
                 const int64_t gn = (int64_t)n0 + c0 + j;
                 if (gn < g.N) {
                   const double f = lv * g.sB[gn];
-                  const double vr = ((double)__uint_as_float(r[j]) - (double)__uint_as_float(u[j])) * f;
-                  const double vi = (double)__uint_as_float(s[j]) * f;
+                  const double dr = (double)__uint_as_float(r[j]) - (double)__uint_as_float(u[j]);
+                  const double di = (double)__uint_as_float(s[j]);
                   if (first) {
-                    pc[j] = zmk(vr, vi);
+                    pc[j] = zmk(dr * f, di * f);
                   } else {
                     const z o = pc[j];
-                    pc[j] = zmk(o.x + vr, o.y + vi);
+                    pc[j] = zmk(fma(dr, f, o.x), fma(di, f, o.y));
                   }
                 }
               }
