@@ -39,7 +39,7 @@ static int dmrg_env_left(Ctx* c, tnt_dmrg* g, int i) {
   tnt_mps* m = g->mps;
   size_t top = c->ws.top;
   int r = env_left_impl(c, g->Lenv[i], g->mpo->W[i], m->A[i], m->chi[i], m->d, g->mpo->D,
-                        m->chi[i + 1], g->Lenv[i + 1]);
+                        m->chi[i + 1], g->Lenv[i + 1], g->mpo->hW[(size_t)i].data());
   c->ws.top = top;
   return r;
 }
@@ -49,7 +49,7 @@ static int dmrg_env_right(Ctx* c, tnt_dmrg* g, int j) {
   tnt_mps* m = g->mps;
   size_t top = c->ws.top;
   int r = env_right_impl(c, g->Renv[j + 1], g->mpo->W[j], m->A[j], m->chi[j], m->d, g->mpo->D,
-                         m->chi[j + 1], g->Renv[j]);
+                         m->chi[j + 1], g->Renv[j], g->mpo->hW[(size_t)j].data());
   c->ws.top = top;
   return r;
 }
@@ -72,6 +72,7 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     s.L = g->Lenv[i]; s.R = g->Renv[i + 2]; s.W1 = g->mpo->W[i]; s.W2 = g->mpo->W[i + 1];
     s.chl = chl; s.chr = chr; s.d = d; s.D = D;
     s.qa = m->q[i]; s.qb = m->q[i + 2]; s.wq = g->mpo->wq;
+    s.hW1 = g->mpo->hW[(size_t)i].data(); s.hW2 = g->mpo->hW[(size_t)i + 1].data();
     TNT_TRY(u1_layout(c, spec, &up));
     if (c->ws.top == 0)
       TNT_TRY(ws_reserve(c, std::max(g->scratch, ws_round(sizeof(z) * n) + ws_round(sizeof(z) * up.n) + up.bytes +
@@ -95,7 +96,8 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     HeffPlan p;
     size_t t2 = c->ws.top;
     TNT_TRY(heff_prepare(c, g->Lenv[i], g->mpo->W[i], g->mpo->W[i + 1], g->Renv[i + 2], chl, d, D,
-                         chr, c->params.precision, &p));
+                         chr, c->params.precision, &p, g->mpo->hW[(size_t)i].data(),
+                         g->mpo->hW[(size_t)i + 1].data()));
     int r = lanczos_impl(c, p, theta, lz);
     if (r != TNT_OK && r != TNT_E_NOCONV) return r;
     c->ws.top = t2;
@@ -166,6 +168,7 @@ int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, dou
       return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO failed");
     }
     o->W.push_back(dW);
+    o->hW.push_back(h);
     cudaMemcpy(dW, h.data(), nW * sizeof(z), cudaMemcpyHostToDevice);
   }
   z lb[4] = {zmk(0, 0), zmk(0, 0), zmk(0, 0), zmk(1, 0)};
@@ -299,7 +302,8 @@ int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* m, const tnt_mpo* o, double*
   TNT_CUDA_TRY(c, cudaMemcpyAsync(Ea, o->left, sizeof(z) * o->D, cudaMemcpyDeviceToDevice, c->stream));
   for (int j = 0; j < m->L; ++j) {
     size_t top = c->ws.top;
-    int r = env_left_impl(c, Ea, o->W[j], m->A[j], m->chi[j], m->d, o->D, m->chi[j + 1], Eb);
+    int r = env_left_impl(c, Ea, o->W[j], m->A[j], m->chi[j], m->d, o->D, m->chi[j + 1], Eb,
+                          o->hW[(size_t)j].data());
     c->ws.top = top;
     if (r != TNT_OK) { ws_reset(c); return r; }
     std::swap(Ea, Eb);

@@ -283,6 +283,37 @@ __global__ void __launch_bounds__(256) k_zgemm_grouped(ZGArgs g) {
   }
 }
 
+// the same over 16 x 16 tiles, one output per thread: for block structures whose 64 x 64
+// tiles would leave most SMs without FP64 work
+__global__ void __launch_bounds__(256) k_zgemm_grouped16(ZGArgs g) {
+  __shared__ z As[16][17];
+  __shared__ z Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const int4 tl = g.tiles[t];
+    const ZTask tk = g.tasks[tl.x];
+    const z* A = g.A + tk.a_off;
+    const z* B = g.B + tk.b_off;
+    z acc = zmk(0, 0);
+    for (int64_t k0 = 0; k0 < tk.K; k0 += 16) {
+      {
+        const int64_t gi = tl.y + ty, gk = k0 + tx;
+        As[ty][tx] = (gi < tk.M && gk < tk.K) ? A[gi * tk.a_rs + gk * tk.a_cs] : zmk(0, 0);
+      }
+      {
+        const int64_t gk = k0 + ty, gj = tl.z + tx;
+        Bs[ty][tx] = (gj < tk.N && gk < tk.K) ? B[gk * tk.b_rs + gj * tk.b_cs] : zmk(0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) zfma(acc, As[ty][kk], Bs[kk][tx]);
+      __syncthreads();
+    }
+    const int64_t gi = tl.y + ty, gj = tl.z + tx;
+    if (gi < tk.M && gj < tk.N) g.C[tk.c_off + gi * tk.c_rs + gj] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- operand packing
 // constant operands (environments): one warp per segment
 template <bool MIXED>
@@ -520,11 +551,11 @@ void make_tiles(const std::vector<TaskDesc>& ts, int bn, int split, std::vector<
   }
 }
 
-void make_ztiles(const std::vector<ZTask>& ts, std::vector<int4>* tiles) {
+void make_ztiles(const std::vector<ZTask>& ts, int tile, std::vector<int4>* tiles) {
   tiles->clear();
   for (size_t i = 0; i < ts.size(); ++i)
-    for (int64_t m0 = 0; m0 < ts[i].M; m0 += ZM)
-      for (int64_t n0 = 0; n0 < ts[i].N; n0 += ZN) tiles->push_back(make_int4((int)i, (int)m0, (int)n0, 0));
+    for (int64_t m0 = 0; m0 < ts[i].M; m0 += tile)
+      for (int64_t n0 = 0; n0 < ts[i].N; n0 += tile) tiles->push_back(make_int4((int)i, (int)m0, (int)n0, 0));
 }
 
 template <typename T>
@@ -719,8 +750,10 @@ int u1_layout(Ctx* c, const std::vector<U1Spec>& probs, U1Plan* p) {
     const P4Info& i4 = info4[pi];
     // W12[(s1' s2' w2), (w s1 s2)] = sum_w1 W1[w,w1,s1',s1] W2[w1,w2,s2',s2]  (host, FP64)
     std::vector<z> W1((size_t)(D * D * d * d)), W2((size_t)(D * D * d * d));
-    TNT_TRY(read_small(c, s.W1, W1.data(), W1.size() * sizeof(z)));
-    TNT_TRY(read_small(c, s.W2, W2.data(), W2.size() * sizeof(z)));
+    if (s.hW1) std::copy(s.hW1, s.hW1 + W1.size(), W1.begin());
+    else TNT_TRY(read_small(c, s.W1, W1.data(), W1.size() * sizeof(z)));
+    if (s.hW2) std::copy(s.hW2, s.hW2 + W2.size(), W2.begin());
+    else TNT_TRY(read_small(c, s.W2, W2.data(), W2.size() * sizeof(z)));
     auto at = [&](const std::vector<z>& W, int64_t w, int64_t wp, int64_t so, int64_t si) {
       return W[(size_t)(((w * D + wp) * d + so) * d + si)];
     };
@@ -848,8 +881,9 @@ int u1_layout(Ctx* c, const std::vector<U1Spec>& probs, U1Plan* p) {
        ws_round(sizeof(int2) * p->wtiles.size()) + ws_round(sizeof(GRow) * p->rows.size());
   // tiles: worst case N tile 64 and split 4
   int64_t t1 = 0, t4 = 0, z1 = 0, z4 = 0;
-  for (const TaskDesc& t : p->s1) { t1 += ((t.M + 127) / 128) * ((t.N + 63) / 64); z1 += ((t.M + 63) / 64) * ((t.N + 63) / 64); }
-  for (const TaskDesc& t : p->s4) { t4 += 4 * ((t.M + 127) / 128) * ((t.N + 63) / 64); z4 += ((t.M + 63) / 64) * ((t.N + 63) / 64); }
+  // FP64 tiles counted at the smaller (16 x 16) size, the larger of the two lists
+  for (const TaskDesc& t : p->s1) { t1 += ((t.M + 127) / 128) * ((t.N + 63) / 64); z1 += ((t.M + 15) / 16) * ((t.N + 15) / 16); }
+  for (const TaskDesc& t : p->s4) { t4 += 4 * ((t.M + 127) / 128) * ((t.N + 63) / 64); z4 += ((t.M + 15) / 16) * ((t.N + 15) / 16); }
   p->cap_g1tiles = (int)t1;
   p->cap_g4tiles = (int)t4;
   b += ws_round(sizeof(int4) * (t1 + t4 + z1 + z4)) + ws_round(sizeof(GTask) * (p->s1.size() + p->s4.size())) +
@@ -1002,8 +1036,14 @@ int u1_prepare(Ctx* c, const std::vector<U1Spec>& probs, U1Plan* p) {
   for (const TaskDesc& t : p->s4)
     z4.push_back(ZTask{t.M, t.N, t.K, t.a_row0 * p->KA4, p->KA4, 1, t.b_row0 * p->KA4, 1, p->KA4, t.c_off, t.ldc});
   std::vector<int4> zt1, zt4;
-  make_ztiles(z1, &zt1);
-  make_ztiles(z4, &zt4);
+  make_ztiles(z1, ZM, &zt1);
+  make_ztiles(z4, ZM, &zt4);
+  // 16 x 16 tiles when the 64 x 64 ones would not give every SM FP64 work
+  p->ztile = ((int64_t)zt1.size() < sm_count() || (int64_t)zt4.size() < sm_count()) ? 16 : ZM;
+  if (p->ztile == 16) {
+    make_ztiles(z1, 16, &zt1);
+    make_ztiles(z4, 16, &zt4);
+  }
   TNT_TRY(upload(c, &p->d_z1, z1));
   TNT_TRY(upload(c, &p->d_z4, z4));
   TNT_TRY(upload(c, &p->d_z1tiles, zt1));
@@ -1038,6 +1078,15 @@ int u1_prepare(Ctx* c, const std::vector<U1Spec>& probs, U1Plan* p) {
 }
 
 namespace {
+void* zfn(const U1Plan& p) { return p.ztile == 16 ? (void*)k_zgemm_grouped16 : (void*)k_zgemm_grouped; }
+int64_t zcap(const U1Plan& p) { return p.ztile == 16 ? 152 * 8 : 152 * 2; }
+void zlaunch(Ctx* c, const U1Plan& p, const ZGArgs& a, int ntiles) {
+  if (p.ztile == 16)
+    k_zgemm_grouped16<<<cap_grid(ntiles, zcap(p)), 256, 0, c->stream>>>(a);
+  else
+    k_zgemm_grouped<<<cap_grid(ntiles, zcap(p)), 256, 0, c->stream>>>(a);
+}
+
 // kernel-node parameters for a graph; args points at the single struct argument
 cudaKernelNodeParams knp(void* fn, unsigned grid, unsigned block, unsigned smem, void** args) {
   cudaKernelNodeParams k{};
@@ -1089,13 +1138,13 @@ int build_graph(Ctx* c, U1Plan& p, int mixed) {
   } else {
     ZGArgs z1 = p.in_zg;
     void* a0[] = {&z1};
-    TNT_TRY(add(knp((void*)k_zgemm_grouped, cap_grid(p.n_z1tiles, 152 * 2), 256, 0, a0)));
+    TNT_TRY(add(knp(zfn(p), cap_grid(p.n_z1tiles, zcap(p)), 256, 0, a0)));
     p.in_node[0] = node;
     void* a1[] = {&wa};
     TNT_TRY(add(knp((void*)k_wop<false>, gw, 256, 0, a1)));
     ZGArgs z4{p.d_z4, p.d_z4tiles, p.n_z4tiles, p.A4z, p.B4z, p.Yz};
     void* a2[] = {&z4};
-    TNT_TRY(add(knp((void*)k_zgemm_grouped, cap_grid(p.n_z4tiles, 152 * 2), 256, 0, a2)));
+    TNT_TRY(add(knp(zfn(p), cap_grid(p.n_z4tiles, zcap(p)), 256, 0, a2)));
     GthArgs ga = p.out_g[0];
     void* a3[] = {&ga};
     TNT_TRY(add(knp((void*)k_gather_u1<false>, gg, 256, 0, a3)));
@@ -1153,7 +1202,7 @@ int run_direct(Ctx* c, U1Plan& p, const z* x, z* y, int mixed) {
     z1.B = x;
     {
       ProfScope ps(c, "zgemm_grouped", f1);
-      k_zgemm_grouped<<<cap_grid(p.n_z1tiles, 152 * 2), 256, 0, c->stream>>>(z1);
+      zlaunch(c, p, z1, p.n_z1tiles);
     }
     {
       ProfScope ps(c, "u1_wop_f64", 16.0 * (double)p.P1 + 16.0 * (double)(p.rowsA4 * p.KA4));
@@ -1162,7 +1211,7 @@ int run_direct(Ctx* c, U1Plan& p, const z* x, z* y, int mixed) {
     ZGArgs z4{p.d_z4, p.d_z4tiles, p.n_z4tiles, p.A4z, p.B4z, p.Yz};
     {
       ProfScope ps(c, "zgemm_grouped", f4);
-      k_zgemm_grouped<<<cap_grid(p.n_z4tiles, 152 * 2), 256, 0, c->stream>>>(z4);
+      zlaunch(c, p, z4, p.n_z4tiles);
     }
     GthArgs ga = p.out_g[0];
     ga.y = y;
@@ -1194,7 +1243,7 @@ int u1_run(Ctx* c, U1Plan& p, const z* x, z* y, int precision) {
     ZGArgs z1 = p.in_zg;
     z1.B = x;
     void* a[] = {&z1};
-    cudaKernelNodeParams k = knp((void*)k_zgemm_grouped, cap_grid(p.n_z1tiles, 152 * 2), 256, 0, a);
+    cudaKernelNodeParams k = knp(zfn(p), cap_grid(p.n_z1tiles, zcap(p)), 256, 0, a);
     TNT_CUDA_TRY(c, cudaGraphExecKernelNodeSetParams(p.exec[0], p.in_node[0], &k));
     GthArgs ga = p.out_g[0];
     ga.y = y;

@@ -48,7 +48,8 @@ static void build_w12(const std::vector<z>& W1, const std::vector<z>& W2, int64_
 }
 
 int heff_prepare(Ctx* c, const z* L, const z* W1, const z* W2, const z* R, int64_t chl,
-                 int64_t d, int64_t D, int64_t chr, int precision, HeffPlan* p) {
+                 int64_t d, int64_t D, int64_t chr, int precision, HeffPlan* p, const z* hW1,
+                 const z* hW2) {
   p->L = L;
   p->R = R;
   p->chl = chl;
@@ -58,8 +59,10 @@ int heff_prepare(Ctx* c, const z* L, const z* W1, const z* W2, const z* R, int64
   p->precision = precision;
   const size_t nW = (size_t)(D * D * d * d);
   std::vector<z> h1(nW), h2(nW), w12;
-  TNT_TRY(read_small(c, W1, h1.data(), nW * sizeof(z)));
-  TNT_TRY(read_small(c, W2, h2.data(), nW * sizeof(z)));
+  if (hW1) std::copy(hW1, hW1 + nW, h1.begin());
+  else TNT_TRY(read_small(c, W1, h1.data(), nW * sizeof(z)));
+  if (hW2) std::copy(hW2, hW2 + nW, h2.begin());
+  else TNT_TRY(read_small(c, W2, h2.data(), nW * sizeof(z)));
   build_w12(h1, h2, d, D, &w12);
   const int nI = (int)(d * d * D), nJ = (int)(D * d * d);
   std::vector<int64_t> in_off(nJ), out_off(nI);
@@ -134,7 +137,7 @@ size_t env_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr) {
 }
 
 int env_left_impl(Ctx* c, const z* Lenv, const z* W, const z* A, int64_t chl, int64_t d,
-                  int64_t D, int64_t chr, z* Lout) {
+                  int64_t D, int64_t chr, z* Lout, const z* hWin) {
   // X[a'][w][s][m] = sum_a L[(a' w)][a] A[a][(s m)]
   const size_t nx = (size_t)chl * D * d * chr;
   z* X = (z*)ws_alloc(c, ws_round(sizeof(z) * nx));
@@ -150,7 +153,8 @@ int env_left_impl(Ctx* c, const z* Lenv, const z* W, const z* A, int64_t chl, in
   // Y[a'][(s' w')][m] = sum_{w,s} W[w,w',s',s] X[a'][(w s)][m]
   const size_t nW = (size_t)(D * D * d * d);
   std::vector<z> hW(nW);
-  TNT_TRY(read_small(c, W, hW.data(), nW * sizeof(z)));
+  if (hWin) std::copy(hWin, hWin + nW, hW.begin());
+  else TNT_TRY(read_small(c, W, hW.data(), nW * sizeof(z)));
   const int nI = (int)(d * D), nJ = (int)(D * d);
   std::vector<z> op((size_t)nI * nJ);
   for (int64_t so = 0; so < d; ++so)
@@ -179,7 +183,7 @@ int env_left_impl(Ctx* c, const z* Lenv, const z* W, const z* A, int64_t chl, in
 }
 
 int env_right_impl(Ctx* c, const z* Renv, const z* W, const z* B, int64_t chl, int64_t d,
-                   int64_t D, int64_t chr, z* Rout) {
+                   int64_t D, int64_t chr, z* Rout, const z* hWin) {
   // X[a][s][b'][w'] = sum_b B[(a s)][b] R[(b' w')][b]
   const size_t nx = (size_t)chl * d * chr * D;
   z* X = (z*)ws_alloc(c, ws_round(sizeof(z) * nx));
@@ -195,7 +199,8 @@ int env_right_impl(Ctx* c, const z* Renv, const z* W, const z* B, int64_t chl, i
   // Y[w][a][s'][b'] = sum_{s,w'} W[w,w',s',s] X[a][s][b'][w']
   const size_t nW = (size_t)(D * D * d * d);
   std::vector<z> hW(nW);
-  TNT_TRY(read_small(c, W, hW.data(), nW * sizeof(z)));
+  if (hWin) std::copy(hWin, hWin + nW, hW.begin());
+  else TNT_TRY(read_small(c, W, hW.data(), nW * sizeof(z)));
   const int nI = (int)(D * d), nJ = (int)(d * D);
   std::vector<z> op((size_t)nI * nJ);
   for (int64_t w = 0; w < D; ++w)

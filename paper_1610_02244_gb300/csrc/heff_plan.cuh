@@ -37,7 +37,8 @@ struct HeffPlan {
 
 size_t heff_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr, int precision);
 int heff_prepare(Ctx* c, const z* L, const z* W1, const z* W2, const z* R, int64_t chl,
-                 int64_t d, int64_t D, int64_t chr, int precision, HeffPlan* p);
+                 int64_t d, int64_t D, int64_t chr, int precision, HeffPlan* p,
+                 const z* hW1 = nullptr, const z* hW2 = nullptr);
 int heff_run(Ctx* c, const HeffPlan& p, const z* theta, z* y, int precision);
 int heff_run_f64(Ctx* c, const HeffPlan& p, const z* theta, z* y);
 
@@ -51,10 +52,11 @@ int heff_mixed_prepare(Ctx* c, HeffPlan* p);
 int heff_run_mixed(Ctx* c, const HeffPlan& p, const z* theta, z* y);
 
 size_t env_scratch_bound(int64_t chl, int64_t d, int64_t D, int64_t chr);
+// hW (optional): a host copy of W, which spares the read-back of the device tensor
 int env_left_impl(Ctx* c, const z* Lenv, const z* W, const z* A, int64_t chl, int64_t d,
-                  int64_t D, int64_t chr, z* Lout);
+                  int64_t D, int64_t chr, z* Lout, const z* hW = nullptr);
 int env_right_impl(Ctx* c, const z* Renv, const z* W, const z* B, int64_t chl, int64_t d,
-                   int64_t D, int64_t chr, z* Rout);
+                   int64_t D, int64_t chr, z* Rout, const z* hW = nullptr);
 int theta_form_impl(Ctx* c, const z* A, const z* B, int64_t chl, int64_t d, int64_t chm,
                     int64_t chr, z* theta);
 int gate_apply_impl(Ctx* c, const std::vector<z>& G, const z* theta, int64_t chl, int64_t d,

@@ -92,6 +92,55 @@ __global__ void __launch_bounds__(256) k_zgemm(ZGemm g) {
 }
 }  // namespace
 
+namespace {
+// 16 x 16 output tiles, one element per thread: for products too small to give every SM
+// a 64 x 64 tile (GB300's FP64 units are ~2 FMA per clock per SM, so the FP64 work of a
+// small product must be spread thin)
+__global__ void __launch_bounds__(256) k_zgemm16(ZGemm g) {
+  __shared__ z As[16][17];
+  __shared__ z Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * 16, n0 = (int64_t)blockIdx.x * 16;
+  if (g.lower_only && m0 + 16 <= n0) return;
+  const int64_t bt = blockIdx.z;
+  const z* A = g.A + bt * g.a_bs;
+  const z* B = g.B + bt * g.b_bs;
+  z* C = g.C + bt * g.c_bs;
+  z acc = zmk(0, 0);
+  for (int64_t k0 = 0; k0 < g.K; k0 += 16) {
+    {
+      const int64_t gi = m0 + ty, gk = k0 + tx;
+      z v = zmk(0, 0);
+      if (gi < g.M && gk < g.K) {
+        v = A[gi * g.a_rs + gk * g.a_cs];
+        if (g.conj_a) v.y = -v.y;
+      }
+      As[ty][tx] = v;
+    }
+    {
+      const int64_t gk = k0 + ty, gj = n0 + tx;
+      z v = zmk(0, 0);
+      if (gj < g.N && gk < g.K) {
+        v = B[gk * g.b_rs + gj * g.b_cs];
+        if (g.conj_b) v.y = -v.y;
+      }
+      Bs[ty][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) zfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int64_t gi = m0 + ty, gj = n0 + tx;
+  if (gi < g.M && gj < g.N) {
+    z v = zmul(g.alpha, acc);
+    z* p = C + gi * g.c_rs + gj;
+    if (g.beta.x != 0.0 || g.beta.y != 0.0) v = zadd(v, zmul(g.beta, *p));
+    *p = v;
+  }
+}
+}  // namespace
+
 int zgemm(Ctx* c, const ZGemm& g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return TNT_OK;
   if (g.K <= 0) {
@@ -99,6 +148,21 @@ int zgemm(Ctx* c, const ZGemm& g) {
     return set_err(c, TNT_E_INVALID, "zgemm with K = 0");
   }
   if (ozgemm_eligible(c, g)) return ozgemm(c, g);
+  {
+    static int nsm = 0;
+    if (!nsm && (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || nsm < 1))
+      nsm = 152;
+    const int64_t tiles64 = ((g.M + GM - 1) / GM) * ((g.N + GN - 1) / GN) * g.batch;
+    if (tiles64 < nsm && (g.M + 15) / 16 <= 65535 && g.batch <= 65535) {
+      dim3 grid((unsigned)((g.N + 15) / 16), (unsigned)((g.M + 15) / 16), (unsigned)g.batch);
+      ProfScope ps(c, "zgemm_f64", (g.lower_only ? 4.0 : 8.0) * (double)g.M * (double)g.N *
+                                       (double)g.K * (double)g.batch);
+      k_zgemm16<<<grid, 256, 0, c->stream>>>(g);
+      c->launches++;
+      TNT_CHECK_LAUNCH(c);
+      return TNT_OK;
+    }
+  }
   if ((g.N + GN - 1) / GN > 0x7fffffff || (g.M + GM - 1) / GM > 65535 || g.batch > 65535)
     return set_err(c, TNT_E_UNSUPPORTED, "zgemm grid too large (M=%lld N=%lld batch=%lld)",
                    (long long)g.M, (long long)g.N, (long long)g.batch);
@@ -562,38 +626,41 @@ __global__ void k_tridiag_lowest(const double* __restrict__ alpha,
     double scale = 0;
     for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(a[i]) + (i < k - 1 ? fabs(b[i]) : 0));
     scale = fmax(scale, 1e-300);
-    for (int iter = 0; iter < 3; ++iter) {
-      for (int i = 0; i < k; ++i) {
-        dm[i] = a[i] - lam;
-        du[i] = (i < k - 1) ? b[i] : 0.0;
-        dl[i] = (i < k - 1) ? b[i] : 0.0;
+    // T - lam I = P L U once (the shift is the same for every sweep); pivots inverted once,
+    // so the three solves multiply instead of divide (a full-warp FP64 division costs
+    // several FP64-pipe issue slots per lane on GB300)
+    for (int i = 0; i < k; ++i) {
+      dm[i] = a[i] - lam;
+      du[i] = (i < k - 1) ? b[i] : 0.0;
+      dl[i] = (i < k - 1) ? b[i] : 0.0;
+      du2[i] = 0.0;
+      piv[i] = i;
+    }
+    for (int i = 0; i < k - 1; ++i) {  // LU with partial pivoting (tridiagonal, textbook gtsv)
+      if (fabs(dm[i]) >= fabs(dl[i])) {
+        if (fabs(dm[i]) < eps * scale) dm[i] = eps * scale;
+        double f = dl[i] / dm[i];
+        dl[i] = f;
+        dm[i + 1] -= f * du[i];
         du2[i] = 0.0;
         piv[i] = i;
-      }
-      // LU with partial pivoting (tridiagonal, as in a textbook gtsv)
-      for (int i = 0; i < k - 1; ++i) {
-        if (fabs(dm[i]) >= fabs(dl[i])) {
-          if (fabs(dm[i]) < eps * scale) dm[i] = eps * scale;
-          double f = dl[i] / dm[i];
-          dl[i] = f;
-          dm[i + 1] -= f * du[i];
-          du2[i] = 0.0;
-          piv[i] = i;
-        } else {
-          double f = dm[i] / dl[i];
-          dm[i] = dl[i];
-          dl[i] = f;
-          double t = du[i];
-          du[i] = dm[i + 1];
-          dm[i + 1] = t - f * du[i];
-          if (i < k - 2) {
-            du2[i] = du[i + 1];
-            du[i + 1] = -f * du[i + 1];
-          }
-          piv[i] = i + 1;
+      } else {
+        double f = dm[i] / dl[i];
+        dm[i] = dl[i];
+        dl[i] = f;
+        double t = du[i];
+        du[i] = dm[i + 1];
+        dm[i + 1] = t - f * du[i];
+        if (i < k - 2) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
         }
+        piv[i] = i + 1;
       }
-      if (fabs(dm[k - 1]) < eps * scale) dm[k - 1] = eps * scale;
+    }
+    if (fabs(dm[k - 1]) < eps * scale) dm[k - 1] = eps * scale;
+    for (int i = 0; i < k; ++i) dm[i] = 1.0 / dm[i];  // inverse pivots
+    for (int iter = 0; iter < 3; ++iter) {
       // forward: apply row swaps and L
       for (int i = 0; i < k - 1; ++i) {
         if (piv[i] == i) {
@@ -604,15 +671,15 @@ __global__ void k_tridiag_lowest(const double* __restrict__ alpha,
           v[i + 1] = t - dl[i] * v[i];
         }
       }
-      // backward: U has diagonals dm, du, du2
-      v[k - 1] /= dm[k - 1];
-      if (k > 1) v[k - 2] = (v[k - 2] - du[k - 2] * v[k - 1]) / dm[k - 2];
+      // backward: U has diagonals 1/dm, du, du2
+      v[k - 1] *= dm[k - 1];
+      if (k > 1) v[k - 2] = (v[k - 2] - du[k - 2] * v[k - 1]) * dm[k - 2];
       for (int i = k - 3; i >= 0; --i)
-        v[i] = (v[i] - du[i] * v[i + 1] - du2[i] * v[i + 2]) / dm[i];
+        v[i] = (v[i] - du[i] * v[i + 1] - du2[i] * v[i + 2]) * dm[i];
       double nrm = 0;
-      for (int i = 0; i < k; ++i) nrm += v[i] * v[i];
-      nrm = sqrt(nrm);
-      for (int i = 0; i < k; ++i) v[i] /= nrm;
+      for (int i = 0; i < k; ++i) nrm = fma(v[i], v[i], nrm);
+      const double rn = 1.0 / sqrt(nrm);
+      for (int i = 0; i < k; ++i) v[i] *= rn;
     }
     // fix the sign so that the first nonzero component is positive (deterministic)
     double sgn = 1.0;

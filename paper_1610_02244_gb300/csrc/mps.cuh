@@ -11,6 +11,7 @@ struct tnt_mpo {
   tnt::z* left = nullptr;   // boundary environment L_0[0,w,0] (device, D)
   tnt::z* right = nullptr;  // boundary R_{L}[0,w,0]
   std::vector<int> wq;      // U(1) charge of each MPO bond index (empty: none)
+  std::vector<std::vector<tnt::z>> hW;  // host copies of W (no read-back per update)
 };
 
 struct tnt_mps {

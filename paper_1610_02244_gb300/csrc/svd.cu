@@ -34,20 +34,27 @@ __device__ __forceinline__ void rr_pair(int t, int r, int np2, int* p, int* q) {
   *q = a < b ? b : a;
 }
 
+// Rotation that annihilates the (p, q) entry of a Hermitian 2 x 2 block [[app, apq],
+// [conj(apq), aqq]]: apq = |apq| e, tau = (aqq - app) / (2 |apq|), t the smaller root of
+// t^2 + 2 tau t - 1 = 0, cs = 1 / sqrt(1 + t^2), sn = t cs.  Written with reciprocal
+// square roots and one division: each FP64 division or square root is a long dependent
+// chain on GB300's FP64 units, and this sits on the critical path of every round.
 __device__ __forceinline__ void jacobi_rot(double app, double aqq, z apq, double* cs,
                                            double* sn, z* e) {
-  double ab = hypot(apq.x, apq.y);
-  if (ab <= 1e-300 || ab < 1e-18 * sqrt(fabs(app) * fabs(aqq))) {
+  const double ab2 = fma(apq.x, apq.x, apq.y * apq.y);
+  if (ab2 <= 1e-300 || ab2 < 1e-36 * fabs(app * aqq)) {
     *cs = 1.0;
     *sn = 0.0;
     *e = zmk(1.0, 0.0);
     return;
   }
-  *e = zmk(apq.x / ab, apq.y / ab);
-  double tau = (aqq - app) / (2.0 * ab);
-  double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  *cs = 1.0 / sqrt(1.0 + t * t);
-  *sn = t * (*cs);
+  const double inv_ab = rsqrt(ab2);
+  *e = zmk(apq.x * inv_ab, apq.y * inv_ab);
+  const double tau = (aqq - app) * (0.5 * inv_ab);
+  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+  const double c = rsqrt(fma(t, t, 1.0));
+  *cs = c;
+  *sn = t * c;
 }
 
 __global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t* off,
@@ -76,9 +83,9 @@ __global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t*
   for (; sweep < max_sweeps; ++sweep) {
     // convergence test before each sweep
     double mo = 0, md = 0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // squared magnitudes
       int i = e / n, j = e % n;
-      double a = hypot(sG[e].x, sG[e].y);
+      double a = fma(sG[e].x, sG[e].x, sG[e].y * sG[e].y);
       if (i == j) md = fmax(md, a); else mo = fmax(mo, a);
     }
     red_off[threadIdx.x] = mo;
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t*
         a = fmax(a, red_off[t]);
         b = fmax(b, red_dg[t]);
       }
-      s_done = (a <= tol * b) || (a <= 1e-300);
+      s_done = (a <= tol * tol * b) || (a <= 1e-300);
     }
     __syncthreads();
     if (s_done) break;

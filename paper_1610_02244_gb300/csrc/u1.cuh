@@ -31,6 +31,7 @@ struct Sector {
 // one problem as given by the caller (device pointers borrowed, host labels copied)
 struct U1Spec {
   const z *L = nullptr, *R = nullptr, *W1 = nullptr, *W2 = nullptr;
+  const z *hW1 = nullptr, *hW2 = nullptr;  // optional host copies of W1, W2
   int64_t chl = 0, chr = 0, d = 0, D = 0;
   std::vector<int64_t> qa, qb;
   std::vector<int> wq;
@@ -174,6 +175,7 @@ struct U1Plan {
   int cap_g1tiles = 0, cap_g4tiles = 0;
   // tile choice (autotuned): N tile of stage 1 and stage 4, split-K of stage 4
   int bn1 = 128, bn4 = 128, split4 = 1;
+  int ztile = 64;                   // FP64 grouped tiles: 64 x 64, or 16 x 16 for small structures
   CUtensorMap tmA1, tmB1, tmA4, tmB4;  // B maps are rebuilt for the chosen N tile
   // CUDA graphs of one matvec per precision (input / output pointers patched per replay)
   cudaGraph_t graph[2] = {nullptr, nullptr};
