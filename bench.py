@@ -16,6 +16,7 @@ metric: useful H_eff.theta FLOP/s of the update = (matvecs x 18.25 GFLOP) / upda
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -662,7 +663,224 @@ def run_tebd(args, ws, rank, local):
     return 0
 
 
+SPIN_L, SPIN_TWO_S = 101, 2
+SPIN_DMRG_CHI, SPIN_TEBD_CHI, SPIN_TEBD_DT, SPIN_TEBD_ERR = 200, 1000, 0.05, 1e-10
+# the paper's single-node times for these two workloads (Sec. 6, Tables 1 and 2, U(1)
+# blocking, fastest library stack): context from other hardware, not a target
+PAPER_SPIN1_DMRG_S_PER_SWEEP, PAPER_SPIN1_TEBD_S_PER_STEP = 135.0, 57.0
+
+
+def _spin_bond_terms(L_):
+    from oracle import bose_hubbard as bh  # noqa: F401  (weights only)
+    from oracle import spin as osp
+    return [osp.bond_hamiltonian(SPIN_TWO_S, 1.0, 1.0, 0.0, *bh.bond_weights(L_, j + 1))
+            for j in range(L_ - 1)]
+
+
+def run_spin1_dmrg(args, ws, rank, local):
+    """--workload spin1_dmrg: two-site DMRG sweeps of the isotropic spin-1 Heisenberg chain,
+    L = 101, chi = 200, U(1) in S^z (the workload of the paper's Table 1), from a seeded
+    random MPS in the S^z = 0 sector with a Gaussian sector profile (width 2) on every
+    bond; W warm-up sweeps, then K timed sweeps; metric s/sweep (2(L-1) updates)."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    prec = tnt.TNT_PREC_MIXED if args.precision == "mixed" else tnt.TNT_PREC_FP64
+    chi = args.chi or SPIN_DMRG_CHI
+    ctx.set_params(chi_max=chi, precision=prec, lanczos_tol=1e-12, lanczos_maxit=300,
+                   krylov_cap=32)
+    ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if args.fp64_gemm == "tc" else tnt.TNT_FP64_GEMM_FMA)
+    g = synth.rng(0)
+    N = SPIN_L * SPIN_TWO_S // 2
+    A, q = synth.random_charged_mps(g, SPIN_L, SPIN_TWO_S + 1, N, chi, "gauss", 2.0)
+    mps = ctx.mps_create(A, q, chi_cap=chi)
+    mpo = ctx.mpo_spin_heisenberg(SPIN_L, SPIN_TWO_S, 1.0)
+    dm = ctx.dmrg_create(mps, mpo)
+    hist = [dm.sweep() for _ in range(max(1, args.warmup))]
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            hist.append(dm.sweep())
+        e1.record(st)
+        torch.cuda.synchronize()
+    s_sweep = dist_max(e0.elapsed_time(e1) * 1e-3 / args.steps, ws)
+    launches = ctx.launch_count() - launches0
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = _oracle_spin_dmrg_sample(mps, chi)
+        E = hist[-1]["E"]
+        line = {"metric": METRIC, "value": s_sweep, "unit": "s/sweep", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_sweep * 1e3,
+                "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": s_sweep / PAPER_SPIN1_DMRG_S_PER_SWEEP if chi == SPIN_DMRG_CHI else None,
+                "dtype": "tf32x3+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": f"two-site DMRG sweep, spin-1 Heisenberg L=101 chi={chi}, "
+                                       "U(1) in S^z, S^z_total=0, seeded random MPS with a "
+                                       "Gaussian sector profile, sweeps after warm-up",
+                           "precision": args.precision, "fp64_gemm": args.fp64_gemm},
+                "E": E, "E_per_bond": E / (SPIN_L - 1),
+                "sweeps": [{k: h[k] for k in ("E", "max_err", "total_matvecs", "unconverged",
+                                              "seconds")} for h in hist],
+                "paper_s_per_sweep": PAPER_SPIN1_DMRG_S_PER_SWEEP,
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def _oracle_spin_dmrg_sample(mps, chi):
+    """The oracle's two-site update timed at the two central bonds of the GPU's state (centre
+    moved there by the oracle's exact SVD moves, environments grown by the oracle), scaled
+    to the 2(L-1) updates of a sweep (every bond but the outer four is at chi)."""
+    from oracle import contract as oc
+    from oracle import dmrg as od
+    from oracle import spin as osp
+    from oracle import tebd as ot
+    from oracle.svd import TruncParams
+    L_ = mps.L
+    A = mps.tensors()
+    q = [np.asarray(mps.charges(k), dtype=np.int64) for k in range(L_ + 1)]
+    Ws, l, r, _ = osp.heisenberg_mpo(L_, SPIN_TWO_S, 1.0, 1.0)
+    mover = ot.Tebd.from_bond_hamiltonians(A, q, _spin_bond_terms(L_), 0.0, od.EXACT)
+    c = L_ // 2 - 1
+    while mover.centre < c:
+        mover._move_right()
+    A, q = mover.A, mover.q
+    Lenv = [None] * (L_ + 1)
+    Lenv[0] = oc.boundary_left(l)
+    for j in range(c):
+        Lenv[j + 1] = oc.env_left(Lenv[j], Ws[j], A[j])
+    Renv = [None] * (L_ + 1)
+    Renv[L_] = oc.boundary_right(r)
+    for j in range(L_ - 1, c + 1, -1):  # Renv[j]: sites j..L-1, down to j = c + 2
+        Renv[j] = oc.env_right(Renv[j + 1], Ws[j], A[j])
+    lz = {"tol": 1e-12, "krylov_cap": 32, "max_matvec": 300}
+    tr = TruncParams(chi_max=chi)
+    t0 = time.perf_counter()
+    st1 = od.two_site_update(A, q, Ws, Lenv, Renv, c, +1, tr, lz)
+    Lenv[c + 1] = oc.env_left(Lenv[c], Ws[c], A[c])
+    st2 = od.two_site_update(A, q, Ws, Lenv, Renv, c + 1, +1, tr, lz)
+    t = (time.perf_counter() - t0) / 2
+    return {"value": t * 2 * (L_ - 1), "unit": "s/sweep", "cores": threads_used(),
+            "kind": "oracle", "sample": f"2 two-site updates at bonds {c},{c + 1} of the GPU "
+            f"state ({st1['matvecs']}+{st2['matvecs']} matvecs), x 2(L-1)",
+            "s_per_update": t}
+
+
+def _tebd_moves_per_step(L_):
+    """Centre moves of one steady-state Trotter step: layers on bonds 0,2,.. | 1,3,.. |
+    0,2,.. alternating direction; a gate needs the centre on i or i+1 and leaves it on
+    i+1 (ascending) or i (descending)."""
+    c, up, moves = 0, True, 0
+    for rep in range(2):
+        moves = 0
+        for first in (0, 1, 0):
+            bonds = list(range(first, L_ - 1, 2))
+            for i in (bonds if up else bonds[::-1]):
+                if c < i:
+                    moves, c = moves + i - c, i
+                elif c > i + 1:
+                    moves, c = moves + c - i - 1, i + 1
+                c = i + 1 if up else i
+            up = not up
+    return moves
+
+
+def run_spin1_tebd(args, ws, rank, local):
+    """--workload spin1_tebd: second-order Trotter steps of the isotropic spin-1 Heisenberg
+    chain, L = 101, chi_max = 1000, U(1) in S^z (the workload of the paper's Table 2),
+    dt = 0.05, truncation error 1e-10, on a seeded random MPS at chi = 1000 in the
+    S^z_total = +1 sector (one spin flip above S^z = 0) with a Gaussian sector profile:
+    every gate works at the full bond dimension.  W warm-up steps, K timed; s/step."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    chi = args.chi or SPIN_TEBD_CHI
+    ctx.set_params(chi_max=chi, trunc_err=SPIN_TEBD_ERR, trunc_abs=-1.0, trunc_rel=1e-16,
+                   trunc_type=0)
+    ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if args.fp64_gemm == "tc" else tnt.TNT_FP64_GEMM_FMA)
+    g = synth.rng(0)
+    N = SPIN_L * SPIN_TWO_S // 2 + 1
+    A, q = synth.random_charged_mps(g, SPIN_L, SPIN_TWO_S + 1, N, chi, "gauss", 2.0)
+    mps = ctx.mps_create(A, q, chi_cap=chi)
+    del A
+    tb = ctx.tebd_create_spin(mps, SPIN_TWO_S, 1.0, SPIN_TEBD_DT)
+    for _ in range(args.warmup):
+        tb.step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    stats = []
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            stats.append(tb.step())
+        torch.cuda.synchronize()
+    s_step = dist_max((time.perf_counter() - t0) / args.steps, ws)
+    launches = ctx.launch_count() - launches0
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = _oracle_spin_tebd_sample(mps, chi)
+        line = {"metric": METRIC, "value": s_step, "unit": "s/step", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_step * 1e3,
+                "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": s_step / PAPER_SPIN1_TEBD_S_PER_STEP if chi == SPIN_TEBD_CHI else None,
+                "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"TEBD step, spin-1 Heisenberg L=101 chi_max={chi}, U(1) in "
+                                       "S^z, S^z_total=+1, dt=0.05, eps=1e-10, seeded random MPS "
+                                       f"at chi={chi} with a Gaussian sector profile",
+                           "fp64_gemm": args.fp64_gemm},
+                "device_s_per_step": statistics.mean(s["seconds"] for s in stats),
+                "max_chi": stats[-1]["max_chi"], "err_sum_last_step": stats[-1]["err_sum"],
+                "paper_s_per_step": PAPER_SPIN1_TEBD_S_PER_STEP,
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def _oracle_spin_tebd_sample(mps, chi):
+    """The oracle's gate (theta, G theta, truncated SVD) and one exact centre move timed at
+    the central bond of the GPU's state, scaled to one step's gates and centre moves."""
+    from oracle import tebd as ot
+    from oracle.svd import TruncParams
+    L_ = mps.L
+    c = L_ // 2 - 1
+    A = mps.tensors()
+    q = [np.asarray(mps.charges(k), dtype=np.int64) for k in range(L_ + 1)]
+    ev = ot.Tebd.from_bond_hamiltonians(A, q, _spin_bond_terms(L_), SPIN_TEBD_DT,
+                                        TruncParams(chi_max=chi, err_tol=SPIN_TEBD_ERR))
+    ev.centre = c  # timing only: the cost of a gate does not depend on the gauge
+    t0 = time.perf_counter()
+    ev.apply_gate(c, ev.gates[("full", c)], True)
+    t_gate = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ev._move_right()
+    t_move = time.perf_counter() - t0
+    n_gates = 2 * len(range(0, L_ - 1, 2)) + len(range(1, L_ - 1, 2))
+    n_moves = _tebd_moves_per_step(L_)
+    return {"value": n_gates * t_gate + n_moves * t_move, "unit": "s/step",
+            "cores": threads_used(), "kind": "oracle",
+            "sample": f"1 gate and 1 centre move at bond {c} of the GPU state, x {n_gates} gates "
+                      f"and {n_moves} moves per step", "s_per_gate": t_gate, "s_per_move": t_move}
+
+
 def main():
+    faulthandler.enable()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -670,8 +888,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["update", "u1", "chains", "dmrg", "tebd"],
+    ap.add_argument("--workload", choices=["update", "u1", "chains", "dmrg", "tebd",
+                                           "spin1_dmrg", "spin1_tebd"],
                     default="update")
+    ap.add_argument("--chi", type=int, default=None,
+                    help="bond dimension of the spin1_dmrg / spin1_tebd workloads (default: "
+                         "the paper's 200 / 1000)")
     ap.add_argument("--fp64-gemm", choices=["tc", "fma"], default=None,
                     help="engine of the FP64 products (default: tc with --precision mixed, "
                          "fma with --precision fp64, the plain FP64 path)")
@@ -687,6 +909,10 @@ def main():
         return run_dmrg(args, ws, rank, local)
     if args.workload == "tebd":
         return run_tebd(args, ws, rank, local)
+    if args.workload == "spin1_dmrg":
+        return run_spin1_dmrg(args, ws, rank, local)
+    if args.workload == "spin1_tebd":
+        return run_spin1_tebd(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

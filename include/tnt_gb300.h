@@ -173,6 +173,27 @@ int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j
  * h_site = U/2 n(n-1) - mu n, as a d^2 x d^2 matrix G[(s1' s2'), (s1 s2)] (host). */
 int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2,
                      double tau, tnt_cplx* h_G);
+/* Spin-S Heisenberg chain (the performance model of Sec. 6, Tables 1 and 2, is the
+ * isotropic spin-1 case: two_s = 2, Jz = J, hz = 0):
+ *   H = sum_j [J/2 (S+_j S-_{j+1} + S-_j S+_{j+1}) + Jz S^z_j S^z_{j+1}] - hz sum_j S^z_j.
+ * Basis |s>, s = 0..two_s, magnetisation m = s - S, so that s counts quanta like a boson
+ * number: the U(1) label of a bond (the sum of s to its left) is S^z_left + S * sites,
+ * the sector S^z_total = 0 is N = L S, and every U(1) entry point of this library applies
+ * unchanged.  <s+1|S+|s> = sqrt(S(S+1) - m(m+1)).
+ * tnt_spin_mpo_site: W[5][5][d][d], d = two_s + 1, lower-triangular like the Bose-Hubbard
+ *   MPO: W[0][0] = I, W[1][0] = S-, W[2][0] = S+, W[3][0] = S^z, W[4][0] = -hz S^z,
+ *   W[4][1] = J/2 S+, W[4][2] = J/2 S-, W[4][3] = Jz S^z, W[4][4] = I; left boundary
+ *   e_4, right boundary e_0; MPO bond charges wq = {0, +1, -1, 0, 0}.
+ * tnt_spin_bond_h: the bond term with the field split c1 / c2 between the two sites,
+ *   h[(s1' s2'), (s1 s2)] (host, d^4 values).
+ * two_s in 1..15; TNT_E_INVALID otherwise. */
+int tnt_spin_mpo_site(int two_s, double J, double Jz, double hz, tnt_cplx* h_W);
+int tnt_spin_bond_h(int two_s, double J, double Jz, double hz, double c1, double c2,
+                    tnt_cplx* h_h);
+/* G = exp(-i tau h) of a Hermitian n x n host matrix h (row-major; its Hermitian part is
+ * used), by host cyclic Jacobi in FP64: the Trotter gate of any nearest-neighbour bond
+ * term (Sec. 3).  n in 1..256. */
+int tnt_bond_gate(int n, const tnt_cplx* h_h, double tau, tnt_cplx* h_G);
 
 /* ------------------------------------------------------------------ two-site kernels */
 
@@ -263,6 +284,18 @@ int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n,
 /* Bose-Hubbard MPO on L sites (Eq. 2 plus -mu N), device-resident. */
 int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, double mu,
                          double V, double j_c, tnt_mpo** out);
+/* Spin-S Heisenberg MPO of tnt_spin_mpo_site on L sites (device-resident, U(1) charges
+ * wq = {0, +1, -1, 0, 0}). */
+int tnt_mpo_spin_heisenberg(tnt_ctx* ctx, int L, int two_s, double J, double Jz, double hz,
+                            tnt_mpo** out);
+/* Any MPO from host tensors (Sec. 4.3: MPOs are built by hand): h_W[j] = W_j[D][D][d][d]
+ * (W[w][w'][s'][s], s' the bra index), h_left / h_right the D boundary vectors (the
+ * operator is left^T W_1 ... W_L right), h_wq (D values, or NULL) the U(1) charges of the
+ * MPO bond index (L[a',w,a] non-zero only where q_a' = q_a + wq[w]); with NULL the DMRG
+ * sweep runs the dense path.  Host arrays are copied.  d in 1..16, D in 1..64. */
+int tnt_mpo_create(tnt_ctx* ctx, int L, int d, int D, const tnt_cplx* const* h_W,
+                   const tnt_cplx* h_left, const tnt_cplx* h_right, const int* h_wq,
+                   tnt_mpo** out);
 int tnt_mpo_destroy(tnt_mpo* mpo);
 
 /* MPS from host data: h_chi[0..L] bond dimensions (h_chi[0] = h_chi[L] = 1), h_sites[j]
@@ -408,6 +441,16 @@ int tnt_u1_tiles(tnt_ctx* ctx, int nprob, const tnt_u1_problem* probs, int* h_ti
  *   capped by the context's chi_max and by the MPS's storage (its chi_cap). */
 int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* mps, int n_max, double J, double U, double mu,
                     double dt, tnt_tebd** out);
+/* The same Trotter step for the spin-S Heisenberg chain (the bond term of
+ * tnt_spin_bond_h with c1, c2 as above; two_s + 1 must equal the MPS's d). */
+int tnt_tebd_create_spin(tnt_ctx* ctx, tnt_mps* mps, int two_s, double J, double Jz,
+                         double hz, double dt, tnt_tebd** out);
+/* The same Trotter step for any nearest-neighbour Hamiltonian: h_bond[i] (host, d^2 x d^2,
+ * rows (s1' s2'), columns (s1 s2)) is the term of bond (i, i+1), i = 0..L-2, with the
+ * on-site parts already split between bonds.  Copied; TNT_E_NAN on a non-finite entry.
+ * With U(1)-labelled MPS bonds each term must conserve s1 + s2. */
+int tnt_tebd_create_bonds(tnt_ctx* ctx, tnt_mps* mps, const tnt_cplx* const* h_bond,
+                          double dt, tnt_tebd** out);
 int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* tebd, tnt_step_stats* stats);
 int tnt_tebd_destroy(tnt_tebd* tebd);
 

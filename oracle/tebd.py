@@ -8,10 +8,13 @@ the scheme used here is the symmetric second-order split
 
 with odd bonds (1,2), (3,4), ... and even bonds (2,3), (4,5), ... (1-based), hbar = 1.
 Each gate acts on one bond: theta = A_i A_{i+1}, theta' = G theta, truncated SVD
-(App. B.1.2), A_i <- U, A_{i+1} <- S V^H.  Before each gate the orthogonality centre is
-moved to site i by exact SVD moves, so every truncation happens at the centre.  The
-state is not renormalised after truncation, so 1 - <psi|psi> accumulates the discarded
-weight.  Gates within a layer are applied in ascending bond order.
+(App. B.1.2).  Before each gate the orthogonality centre is moved onto site i or i+1 by
+exact SVD moves, so every truncation happens at the centre.  The state is not
+renormalised after truncation, so 1 - <psi|psi> accumulates the discarded weight.
+The gates of a layer commute; the layers alternate direction (ascending, descending,
+ascending, then descending first in the next step): an ascending gate leaves
+A_i <- U, A_{i+1} <- S V^H (centre on i+1), a descending one A_i <- U S, A_{i+1} <- V^H
+(centre on i).
 """
 from __future__ import annotations
 
@@ -55,6 +58,18 @@ class Tebd:
                 self.gates[(tau_key, i)] = gate(h, tau)
         self.eps_sum = 0.0     # sum of per-gate truncation errors (Eq. 3)
         self.disc_sum = 0.0    # sum of discarded weights
+        self.up = True         # direction of the next layer
+
+    @classmethod
+    def from_bond_hamiltonians(cls, A, q, bond_hs, dt: float, trunc: TruncParams):
+        """The same scheme for any nearest-neighbour Hamiltonian: bond_hs[i] is the d^2 x
+        d^2 term of bond (i, i+1) (0-based), on-site parts already split between bonds."""
+        d = A[0].shape[1]
+        self = cls(A, q, d - 1, 0.0, 0.0, dt, trunc)
+        for i, h in enumerate(bond_hs):
+            self.gates[("half", i)] = gate(h, dt / 2)
+            self.gates[("full", i)] = gate(h, dt)
+        return self
 
     def _move_right(self):
         j, d = self.centre, self.d
@@ -78,10 +93,10 @@ class Tebd:
         self.q[j] = bq
         self.centre -= 1
 
-    def apply_gate(self, i: int, G: np.ndarray):
+    def apply_gate(self, i: int, G: np.ndarray, ascending: bool = True):
         while self.centre < i:
             self._move_right()
-        while self.centre > i:
+        while self.centre > i + 1:
             self._move_left()
         d = self.d
         theta = gate_apply(G, theta_form(self.A[i], self.A[i + 1]))
@@ -90,10 +105,15 @@ class Tebd:
         U, S, Vh, bq, info = svd_truncate(theta.reshape(chl * d, d * chr_), rows, cols,
                                           self.trunc)
         k = len(S)
-        self.A[i] = U.reshape(chl, d, k)
-        self.A[i + 1] = (S[:, None] * Vh).reshape(k, d, chr_)
+        if ascending:
+            self.A[i] = U.reshape(chl, d, k)
+            self.A[i + 1] = (S[:, None] * Vh).reshape(k, d, chr_)
+            self.centre = i + 1
+        else:
+            self.A[i] = (U * S[None, :]).reshape(chl, d, k)
+            self.A[i + 1] = Vh.reshape(k, d, chr_)
+            self.centre = i
         self.q[i + 1] = bq
-        self.centre = i + 1
         self.eps_sum += info["err"]
         self.disc_sum += info["disc"]
 
@@ -101,5 +121,7 @@ class Tebd:
         odd = range(0, self.L - 1, 2)
         even = range(1, self.L - 1, 2)
         for layer, key in ((odd, "half"), (even, "full"), (odd, "half")):
-            for i in layer:
-                self.apply_gate(i, self.gates[(key, i)])
+            order = layer if self.up else reversed(layer)
+            for i in order:
+                self.apply_gate(i, self.gates[(key, i)], self.up)
+            self.up = not self.up

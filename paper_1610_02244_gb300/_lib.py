@@ -91,6 +91,9 @@ SIGNATURES = {
     "tnt_sys_info": [P, C.c_char_p, C.c_size_t],
     "tnt_bh_mpo_site": [I, D, D, D, D, D, D, P],
     "tnt_bh_bond_gate": [I, D, D, D, D, D, D, P],
+    "tnt_spin_mpo_site": [I, D, D, D, P],
+    "tnt_spin_bond_h": [I, D, D, D, D, D, P],
+    "tnt_bond_gate": [I, P, D, P],
     "tnt_theta_form": [P, P, P, I64, I64, I64, I64, P],
     "tnt_gate_apply": [P, P, P, I64, I64, I64, P],
     "tnt_heff_apply": [P, P, P, P, P, P, I64, I64, I64, I64, I, P],
@@ -101,6 +104,8 @@ SIGNATURES = {
                            C.POINTER(tnt_lanczos_result)],
     "tnt_svd_trunc": [P, P, I64, I64, P, P, I, I, P, P, P, P, C.POINTER(tnt_trunc_result)],
     "tnt_mpo_bose_hubbard": [P, I, I, D, D, D, D, D, C.POINTER(P)],
+    "tnt_mpo_spin_heisenberg": [P, I, I, D, D, D, C.POINTER(P)],
+    "tnt_mpo_create": [P, I, I, I, C.POINTER(P), P, P, P, C.POINTER(P)],
     "tnt_mpo_destroy": [P],
     "tnt_mps_create": [P, I, I, I64, P, P, P, C.POINTER(P)],
     "tnt_mps_product": [P, I, I, I64, P, C.POINTER(P)],
@@ -117,6 +122,8 @@ SIGNATURES = {
     "tnt_mps_density": [P, P, PD],
     "tnt_mps_bdagb": [P, P, P],
     "tnt_tebd_create": [P, P, I, D, D, D, D, C.POINTER(P)],
+    "tnt_tebd_create_spin": [P, P, I, D, D, D, D, C.POINTER(P)],
+    "tnt_tebd_create_bonds": [P, P, C.POINTER(P), D, C.POINTER(P)],
     "tnt_u1_size": [C.POINTER(tnt_u1_problem), PI64],
     "tnt_u1_pack": [P, C.POINTER(tnt_u1_problem), P, P],
     "tnt_u1_unpack": [P, C.POINTER(tnt_u1_problem), P, P],

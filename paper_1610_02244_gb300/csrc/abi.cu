@@ -153,6 +153,19 @@ int bh_bond_gate_host(int n_max, double J, double U, double mu, double c1, doubl
           if (s1o == s1 && s2o == s2) v += c1 * hs(s1) + c2 * hs(s2);
           h[(size_t)(s1o * d + s2o) * n + (s1 * d + s2)] = zmk(v, 0);
         }
+  return bond_gate_host(n, h.data(), tau, G);
+}
+
+int bond_gate_host(int n, const z* h_in, double tau, z* G) {
+  if (n < 1) return TNT_E_INVALID;
+  std::vector<z> h(h_in, h_in + (size_t)n * n);
+  for (int i = 0; i < n; ++i)  // Hermitian part only (h is Hermitian up to rounding)
+    for (int j = 0; j <= i; ++j) {
+      const z a = h[(size_t)i * n + j], b = zconj(h[(size_t)j * n + i]);
+      const z m = zmk(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+      h[(size_t)i * n + j] = m;
+      h[(size_t)j * n + i] = zconj(m);
+    }
   std::vector<double> lam;
   std::vector<z> Q;
   herm_eig_host(n, h, &lam, &Q);
@@ -165,6 +178,73 @@ int bh_bond_gate_host(int n_max, double J, double U, double mu, double c1, doubl
       }
       G[(size_t)i * n + j] = acc;
     }
+  return TNT_OK;
+}
+
+// ---------------------------------------------------------------- spin-S Heisenberg (host)
+// Basis |s>, s = 0..2S, magnetisation m = s - S, so that s counts quanta like a boson
+// number and the U(1) label of a bond (the sum of s to its left) is S^z_left + S * sites.
+//   <s+1| S+ |s> = sqrt(S(S+1) - m(m+1)),  S- = (S+)^H,  S^z = diag(m).
+static void spin_ops(int two_s, std::vector<double>* sp, std::vector<double>* sz) {
+  const int d = two_s + 1;
+  sp->assign((size_t)d * d, 0.0);
+  sz->assign((size_t)d * d, 0.0);
+  for (int s = 0; s < d; ++s) {
+    const double m2 = 2.0 * s - two_s;  // 2m
+    (*sz)[(size_t)s * d + s] = 0.5 * m2;
+    if (s + 1 < d)  // S(S+1) - m(m+1) = (2S (2S + 2) - 2m (2m + 2)) / 4
+      (*sp)[(size_t)(s + 1) * d + s] = 0.5 * std::sqrt((double)two_s * (two_s + 2) - m2 * (m2 + 2));
+  }
+}
+
+// H = sum_j [J/2 (S+_j S-_{j+1} + S-_j S+_{j+1}) + Jz S^z_j S^z_{j+1}] - hz sum_j S^z_j,
+// MPO of bond dimension 5 in the lower-triangular form of the Bose-Hubbard MPO: rows
+//   0: I;  1: S-;  2: S+;  3: S^z;  4: -hz S^z, J/2 S+, J/2 S-, Jz S^z, I
+// (left boundary row 4, right boundary column 0).
+int spin_mpo_site_host(int two_s, double J, double Jz, double hz, z* W) {
+  const int d = two_s + 1, D = 5;
+  std::vector<double> sp, sz;
+  spin_ops(two_s, &sp, &sz);
+  for (int e = 0; e < D * D * d * d; ++e) W[e] = zmk(0, 0);
+  auto at = [&](int w, int v, int so, int si) -> z& { return W[((w * D + v) * d + so) * d + si]; };
+  for (int so = 0; so < d; ++so)
+    for (int si = 0; si < d; ++si) {
+      const double p = sp[(size_t)so * d + si];  // <so|S+|si>
+      const double m = sp[(size_t)si * d + so];  // <so|S-|si>
+      const double zz = sz[(size_t)so * d + si];
+      const double id = (so == si) ? 1.0 : 0.0;
+      at(0, 0, so, si) = zmk(id, 0);
+      at(1, 0, so, si) = zmk(m, 0);
+      at(2, 0, so, si) = zmk(p, 0);
+      at(3, 0, so, si) = zmk(zz, 0);
+      at(4, 0, so, si) = zmk(-hz * zz, 0);
+      at(4, 1, so, si) = zmk(0.5 * J * p, 0);
+      at(4, 2, so, si) = zmk(0.5 * J * m, 0);
+      at(4, 3, so, si) = zmk(Jz * zz, 0);
+      at(4, 4, so, si) = zmk(id, 0);
+    }
+  return TNT_OK;
+}
+
+// bond term with the field split c1 / c2 between the two sites (as the on-site energy of
+// the Bose-Hubbard bond term): rows (s1' s2'), columns (s1 s2)
+int spin_bond_h_host(int two_s, double J, double Jz, double hz, double c1, double c2, z* h) {
+  const int d = two_s + 1, n = d * d;
+  std::vector<double> sp, sz;
+  spin_ops(two_s, &sp, &sz);
+  for (int s1o = 0; s1o < d; ++s1o)
+    for (int s2o = 0; s2o < d; ++s2o)
+      for (int s1 = 0; s1 < d; ++s1)
+        for (int s2 = 0; s2 < d; ++s2) {
+          const double pm = sp[(size_t)s1o * d + s1] * sp[(size_t)s2 * d + s2o];  // S+ (x) S-
+          const double mp = sp[(size_t)s1 * d + s1o] * sp[(size_t)s2o * d + s2];  // S- (x) S+
+          double v = 0.5 * J * (pm + mp);
+          if (s1o == s1 && s2o == s2) {
+            const double m1 = sz[(size_t)s1 * d + s1], m2 = sz[(size_t)s2 * d + s2];
+            v += Jz * m1 * m2 - hz * (c1 * m1 + c2 * m2);
+          }
+          h[(size_t)(s1o * d + s2o) * n + (s1 * d + s2)] = zmk(v, 0);
+        }
   return TNT_OK;
 }
 
@@ -321,6 +401,22 @@ int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j
                     tnt_cplx* h_W) {
   if (n_max < 0 || !h_W) return TNT_E_INVALID;
   return bh_mpo_site_host(n_max, J, U, mu, V, j, j_c, (z*)h_W);
+}
+
+int tnt_spin_mpo_site(int two_s, double J, double Jz, double hz, tnt_cplx* h_W) {
+  if (two_s < 1 || two_s > 15 || !h_W) return TNT_E_INVALID;
+  return spin_mpo_site_host(two_s, J, Jz, hz, (z*)h_W);
+}
+
+int tnt_spin_bond_h(int two_s, double J, double Jz, double hz, double c1, double c2,
+                    tnt_cplx* h_h) {
+  if (two_s < 1 || two_s > 15 || !h_h) return TNT_E_INVALID;
+  return spin_bond_h_host(two_s, J, Jz, hz, c1, c2, (z*)h_h);
+}
+
+int tnt_bond_gate(int n, const tnt_cplx* h_h, double tau, tnt_cplx* h_G) {
+  if (n < 1 || n > 256 || !h_h || !h_G || !std::isfinite(tau)) return TNT_E_INVALID;
+  return bond_gate_host(n, (const z*)h_h, tau, (z*)h_G);
 }
 
 int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2, double tau,

@@ -149,39 +149,97 @@ using namespace tnt;
 
 extern "C" {
 
-int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, double mu, double V,
-                         double j_c, tnt_mpo** out) {
-  if (!ctx || !out || L < 2 || n_max < 0) return TNT_E_INVALID;
-  Ctx* c = &ctx->c;
+}  // extern "C"
+
+namespace tnt {
+// uploads host site tensors and boundary vectors into a new MPO handle
+static int mpo_upload(Ctx* c, int L, int d, int D, const std::vector<std::vector<z>>& sites,
+                      const std::vector<z>& lb, const std::vector<z>& rb, std::vector<int> wq,
+                      tnt_mpo** out) {
   tnt_mpo* o = new tnt_mpo();
   o->L = L;
-  o->d = n_max + 1;
-  o->D = 4;
-  o->wq = {0, 1, -1, 0};  // b+ placed to the left: bra has one boson more (w = 1)
-  const size_t nW = (size_t)16 * o->d * o->d;
-  std::vector<z> h(nW);
+  o->d = d;
+  o->D = D;
+  o->wq = std::move(wq);
+  o->hleft = lb;
+  o->hright = rb;
+  const size_t nW = (size_t)D * D * d * d;
   for (int j = 0; j < L; ++j) {
-    bh_mpo_site_host(n_max, J, U, mu, V, (double)(j + 1), j_c, h.data());
     z* dW = nullptr;
     if (cudaMalloc((void**)&dW, nW * sizeof(z)) != cudaSuccess) {
       tnt_mpo_destroy(o);
       return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO failed");
     }
     o->W.push_back(dW);
-    o->hW.push_back(h);
-    cudaMemcpy(dW, h.data(), nW * sizeof(z), cudaMemcpyHostToDevice);
+    o->hW.push_back(sites[(size_t)j]);
+    if (cudaMemcpy(dW, sites[(size_t)j].data(), nW * sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) {
+      tnt_mpo_destroy(o);
+      return set_err(c, TNT_E_CUDA, "MPO upload failed");
+    }
   }
-  z lb[4] = {zmk(0, 0), zmk(0, 0), zmk(0, 0), zmk(1, 0)};
-  z rb[4] = {zmk(1, 0), zmk(0, 0), zmk(0, 0), zmk(0, 0)};
-  if (cudaMalloc((void**)&o->left, sizeof(lb)) != cudaSuccess ||
-      cudaMalloc((void**)&o->right, sizeof(rb)) != cudaSuccess) {
+  if (cudaMalloc((void**)&o->left, sizeof(z) * D) != cudaSuccess ||
+      cudaMalloc((void**)&o->right, sizeof(z) * D) != cudaSuccess ||
+      cudaMemcpy(o->left, lb.data(), sizeof(z) * D, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(o->right, rb.data(), sizeof(z) * D, cudaMemcpyHostToDevice) != cudaSuccess) {
     tnt_mpo_destroy(o);
-    return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO boundaries failed");
+    return set_err(c, TNT_E_ALLOC, "MPO boundary upload failed");
   }
-  cudaMemcpy(o->left, lb, sizeof(lb), cudaMemcpyHostToDevice);
-  cudaMemcpy(o->right, rb, sizeof(rb), cudaMemcpyHostToDevice);
   *out = o;
   return TNT_OK;
+}
+
+// boundary vectors of the lower-triangular form: left e_{D-1}, right e_0
+static void triangular_boundaries(int D, std::vector<z>* lb, std::vector<z>* rb) {
+  lb->assign((size_t)D, zmk(0, 0));
+  rb->assign((size_t)D, zmk(0, 0));
+  (*lb)[(size_t)(D - 1)] = zmk(1, 0);
+  (*rb)[0] = zmk(1, 0);
+}
+}  // namespace tnt
+
+extern "C" {
+
+int tnt_mpo_bose_hubbard(tnt_ctx* ctx, int L, int n_max, double J, double U, double mu, double V,
+                         double j_c, tnt_mpo** out) {
+  if (!ctx || !out || L < 2 || n_max < 0) return TNT_E_INVALID;
+  const int d = n_max + 1, D = 4;
+  std::vector<std::vector<z>> sites((size_t)L, std::vector<z>((size_t)D * D * d * d));
+  for (int j = 0; j < L; ++j)
+    bh_mpo_site_host(n_max, J, U, mu, V, (double)(j + 1), j_c, sites[(size_t)j].data());
+  std::vector<z> lb, rb;
+  triangular_boundaries(D, &lb, &rb);
+  // b+ placed to the left: the bra has one boson more (w = 1)
+  return mpo_upload(&ctx->c, L, d, D, sites, lb, rb, {0, 1, -1, 0}, out);
+}
+
+int tnt_mpo_spin_heisenberg(tnt_ctx* ctx, int L, int two_s, double J, double Jz, double hz,
+                            tnt_mpo** out) {
+  if (!ctx || !out || L < 2 || two_s < 1 || two_s > 15) return TNT_E_INVALID;
+  const int d = two_s + 1, D = 5;
+  std::vector<std::vector<z>> sites((size_t)L, std::vector<z>((size_t)D * D * d * d));
+  for (int j = 0; j < L; ++j) spin_mpo_site_host(two_s, J, Jz, hz, sites[(size_t)j].data());
+  std::vector<z> lb, rb;
+  triangular_boundaries(D, &lb, &rb);
+  // channel 1 follows an S+ to the left (the bra carries one quantum more), channel 2 an S-
+  return mpo_upload(&ctx->c, L, d, D, sites, lb, rb, {0, 1, -1, 0, 0}, out);
+}
+
+int tnt_mpo_create(tnt_ctx* ctx, int L, int d, int D, const tnt_cplx* const* h_W,
+                   const tnt_cplx* h_left, const tnt_cplx* h_right, const int* h_wq,
+                   tnt_mpo** out) {
+  if (!ctx || !out || L < 2 || d < 1 || d > 16 || D < 1 || D > 64 || !h_W || !h_left || !h_right)
+    return TNT_E_INVALID;
+  const size_t nW = (size_t)D * D * d * d;
+  std::vector<std::vector<z>> sites((size_t)L);
+  for (int j = 0; j < L; ++j) {
+    if (!h_W[j]) return set_err(&ctx->c, TNT_E_INVALID, "MPO site %d is NULL", j);
+    const z* w = (const z*)h_W[j];
+    sites[(size_t)j].assign(w, w + nW);
+  }
+  std::vector<z> lb((const z*)h_left, (const z*)h_left + D), rb((const z*)h_right, (const z*)h_right + D);
+  std::vector<int> wq;
+  if (h_wq) wq.assign(h_wq, h_wq + D);
+  return mpo_upload(&ctx->c, L, d, D, sites, lb, rb, std::move(wq), out);
 }
 
 int tnt_mpo_destroy(tnt_mpo* mpo) {
@@ -308,11 +366,13 @@ int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* m, const tnt_mpo* o, double*
     if (r != TNT_OK) { ws_reset(c); return r; }
     std::swap(Ea, Eb);
   }
-  z h[4];
-  int r = read_small(c, Ea, h, sizeof(z) * o->D);
+  std::vector<z> h((size_t)o->D);
+  int r = read_small(c, Ea, h.data(), sizeof(z) * o->D);
   ws_reset(c);
   if (r != TNT_OK) return r;
-  *E = h[0].x;  // right boundary e_0
+  double e = 0;  // contract with the right boundary vector
+  for (int w = 0; w < o->D; ++w) e += h[(size_t)w].x * o->hright[(size_t)w].x - h[(size_t)w].y * o->hright[(size_t)w].y;
+  *E = e;
   return TNT_OK;
 }
 

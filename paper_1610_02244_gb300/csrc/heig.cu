@@ -47,6 +47,19 @@ __device__ double block_sum_all(double v, double* sh) {
   return r;
 }
 
+// block-wide maximum; valid in every thread on return
+__device__ double block_max_all(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
+  return r;
+}
+
 // ---------------------------------------------------------------- persistent reduction
 // All columns in one cooperative launch, one grid barrier per column.  Entering column j
 // every block holds the reflector (v_j, tau_j) in its workspace and p_j = tau_j T_j v_j is
@@ -415,7 +428,10 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   __shared__ double sdot[IV_CHUNK];
   __shared__ double sh[32];
   const int64_t i0 = blockIdx.x;
-  const double tn = fmax(tnorm[0], 1e-300);
+  // |T| floored well inside the normal range: a zero block (a charge sector of theta with
+  // no weight) has T = 0, and pivots of eps |T| would then be denormal and the solves
+  // would overflow; with the floor its eigenvectors come out as orthonormal start vectors
+  const double tn = fmax(tnorm[0], 1e-200);
   const double ortol = 1e3 * EPS * tn;
   if (i0 > 0 && ev[i0 - 1] - ev[i0] < ortol) return;  // not the head of its cluster
   int64_t i1 = i0 + 1;
@@ -487,10 +503,19 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
             y[r + 1] = t - dl[r] * y[r];
           }
         }
-        y[n - 1] /= dm[n - 1];
-        if (n > 1) y[n - 2] = (y[n - 2] - du[n - 2] * y[n - 1]) / dm[n - 2];
-        for (int64_t r = n - 3; r >= 0; --r)
-          y[r] = (y[r] - du[r] * y[r + 1] - du2[r] * y[r + 2]) / dm[r];
+        // back substitution; near-degenerate eigenvalues give several pivots of eps |T|
+        // whose quotients compound, so the whole vector (solved part and remaining right
+        // hand side alike: the solution of a scaled system is the scaled solution) is
+        // scaled down whenever an entry passes 2^500
+        for (int64_t r = n - 1; r >= 0; --r) {
+          double v = y[r];
+          if (r + 1 < n) v -= du[r] * y[r + 1];
+          if (r + 2 < n) v -= du2[r] * y[r + 2];
+          v /= dm[r];
+          y[r] = v;
+          if (fabs(v) > 0x1p500)
+            for (int64_t q = 0; q < n; ++q) y[q] *= 0x1p-500;
+        }
       }
       __syncthreads();
       for (int pass = 0; pass < 2 && i > i0; ++pass) {
@@ -512,10 +537,19 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
           __syncthreads();
         }
       }
+      // norm of y / max|y|: the solve can return entries near 1 / (eps |T|), whose squares
+      // would overflow
+      double mx = 0;
+      for (int64_t r = tid; r < n; r += IV_THREADS) mx = fmax(mx, fabs(y[r]));
+      mx = block_max_all(mx, sh);
+      const double sc = mx > 0 ? 1.0 / mx : 0.0;
       double acc = 0;
-      for (int64_t r = tid; r < n; r += IV_THREADS) acc = fma(y[r], y[r], acc);
+      for (int64_t r = tid; r < n; r += IV_THREADS) {
+        const double v = y[r] * sc;
+        acc = fma(v, v, acc);
+      }
       acc = block_sum_all(acc, sh);
-      const double inv = 1.0 / sqrt(acc);
+      const double inv = acc > 0 ? sc / sqrt(acc) : 0.0;
       for (int64_t r = tid; r < n; r += IV_THREADS) y[r] *= inv;
       __syncthreads();
     }

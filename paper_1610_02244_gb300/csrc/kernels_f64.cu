@@ -671,11 +671,17 @@ __global__ void k_tridiag_lowest(const double* __restrict__ alpha,
           v[i + 1] = t - dl[i] * v[i];
         }
       }
-      // backward: U has diagonals 1/dm, du, du2
-      v[k - 1] *= dm[k - 1];
-      if (k > 1) v[k - 2] = (v[k - 2] - du[k - 2] * v[k - 1]) * dm[k - 2];
-      for (int i = k - 3; i >= 0; --i)
-        v[i] = (v[i] - du[i] * v[i + 1] - du2[i] * v[i + 2]) * dm[i];
+      // backward: U has diagonals 1/dm, du, du2; the vector is scaled down whenever an
+      // entry passes 2^500 (compounding pivots of near-degenerate Ritz values)
+      for (int i = k - 1; i >= 0; --i) {
+        double t = v[i];
+        if (i + 1 < k) t -= du[i] * v[i + 1];
+        if (i + 2 < k) t -= du2[i] * v[i + 2];
+        t *= dm[i];
+        v[i] = t;
+        if (fabs(t) > 0x1p500)
+          for (int q = 0; q < k; ++q) v[q] *= 0x1p-500;
+      }
       double nrm = 0;
       for (int i = 0; i < k; ++i) nrm = fma(v[i], v[i], nrm);
       const double rn = 1.0 / sqrt(nrm);

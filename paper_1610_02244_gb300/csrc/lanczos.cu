@@ -2,9 +2,10 @@
 // calls with the contractor of Listing 1 as its matvec; Sec. 4.3, iteration cap 300 of
 // App. A.3).  Vectors, reductions and the tridiagonal eigenproblem stay in FP64 on the
 // GPU; only the matvec may run in split TF32.  Per Krylov step k:
-//   w = H v_k;  c = V^H w;  alpha_k = Re c_k;  w -= V c   (classical Gram-Schmidt), and a
-//   second pass c = V^H w; w -= V c when the first cancelled more than 99% of |w| (so the
-//   basis stays orthogonal to ~100 eps; the pass is skipped on the device otherwise)
+//   w = H v_k;  c = V^H w;  alpha_k = Re c_k;  w -= V c   (classical Gram-Schmidt), then
+//   the same pass once more ("twice is enough": one pass leaves w's components along
+//   converged Ritz directions at the size of the cancellation error, and a restarted
+//   Lanczos on a DMRG effective Hamiltonian then stalls short of its tolerance)
 //   beta_k = |w|;  (E_k, y) = lowest eigenpair of T_k;  resid = beta_k |y_k|
 //   stop if |E_k - E_{k-1}| <= tol |E_k| and resid <= max(tol, 10 u)|E_k|, u the matvec's
 //   unit roundoff (2^-52 FP64, 2^-22 split TF32), or if beta_k vanishes
@@ -44,12 +45,6 @@ __global__ void k_resid(const z* __restrict__ Hx, const z* __restrict__ x, const
 __global__ void k_copy_re(const z* src, double* dst) {
   if (threadIdx.x == 0) dst[0] = src[0].x;
 }
-// second Gram-Schmidt pass needed only if the first one cancelled more than 99% of |w|:
-// afterwards the coefficients' rounding leaves at most eps |w| / |w'| <= 100 eps of
-// non-orthogonality.  skip = 1 tells the pass-2 kernels to do nothing.
-__global__ void k_reorth_flag(const double* norm2_before, const double* norm2_after, int* skip) {
-  if (threadIdx.x == 0) skip[0] = (norm2_after[0] >= 1e-4 * norm2_before[0]) ? 1 : 0;
-}
 }  // namespace
 
 size_t lanczos_scratch_bound(int64_t n, int krylov_cap) {
@@ -70,8 +65,6 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
   double* tri = dsc + 264;            // 2
   double* y = dsc + 272;              // 64
   z* coef = (z*)(dsc + 336);          // 64 complex
-  double* norm2_w = dsc + 464;        // 1: |H v_k|^2 before Gram-Schmidt
-  int* skip2 = (int*)(dsc + 472);     // 1 int: second pass not needed
   const double u = (precision == TNT_PREC_MIXED) ? std::ldexp(1.0, -22) : std::ldexp(1.0, -52);
   const double tol = P.lanczos_tol;
   const double rtol = std::max(tol, 10.0 * u);
@@ -90,14 +83,12 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
       z* vk = V + (int64_t)k * n;
       TNT_TRY(A.apply(c, vk, w, precision));
       ++total;
-      TNT_TRY(vec_norm2(c, w, n, norm2_w));
       TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, dots));
       TNT_TRY(vec_multiaxpy_norm(c, V, n, k + 1, dots, w, n, norm2));
       k_lz_scalars<<<1, 32, 0, c->stream>>>(dots, k, norm2, alpha, beta);  // alpha_k from pass 1
-      k_reorth_flag<<<1, 32, 0, c->stream>>>(norm2_w, norm2, skip2);
-      c->launches += 2;
-      TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, coef, skip2));
-      TNT_TRY(vec_multiaxpy_norm(c, V, n, k + 1, coef, w, n, norm2, skip2));
+      c->launches += 1;
+      TNT_TRY(vec_multidot(c, V, n, k + 1, w, n, coef));
+      TNT_TRY(vec_multiaxpy_norm(c, V, n, k + 1, coef, w, n, norm2));
       // beta_k from pass 2 (overwrite), then the tridiagonal eigenpair of T_k
       k_lz_scalars<<<1, 32, 0, c->stream>>>(dots, k, norm2, alpha, beta);
       c->launches++;

@@ -1,8 +1,8 @@
 // Lanczos ground states of several independent problems in lock step (the eigensolver of
 // Sec. 4.3 run for many chains at once).  The problems' vectors lie back to back; each
 // Krylov step applies one grouped matvec to all of them and then runs the same FP64
-// recurrence as the single-problem solver (classical Gram-Schmidt with a device-decided
-// second pass, beta_k, lowest eigenpair of T_k, stop rule) with every inner product,
+// recurrence as the single-problem solver (classical Gram-Schmidt applied twice, beta_k,
+// lowest eigenpair of T_k, stop rule) with every inner product,
 // norm and scalar kept per problem: the vector kernels work on chunks that never cross a
 // problem boundary and reduce per problem in a fixed order.  A problem that has converged
 // is frozen (its chunks, scalars and tridiagonal solves are skipped) while the others go
@@ -201,12 +201,6 @@ __global__ void k_sscalars(const z* __restrict__ dots, int k, const double* __re
   bk[p] = beta[p * KMAX + k];
 }
 // second Gram-Schmidt pass only where the first cancelled more than 99% of |w|
-__global__ void k_sreorth(const double* __restrict__ nw, const double* __restrict__ n2,
-                          const int* __restrict__ frozen, int* __restrict__ skip2, int P) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  skip2[p] = (frozen[p] || n2[p] >= 1e-4 * nw[p]) ? 1 : 0;
-}
 // Ritz coefficients: coef[p][i] = -y[p][i] for i < kk[p], zero beyond
 __global__ void k_sritz(const double* __restrict__ y, const int* __restrict__ kk, z* __restrict__ coef,
                         int P) {
@@ -248,7 +242,7 @@ struct BScratch {
   z* dots = nullptr;      // P x KMAX
   z* coef = nullptr;      // P x KMAX
   double *alpha = nullptr, *beta = nullptr, *y = nullptr, *tri = nullptr;  // P x KMAX, tri 3 P
-  double *nw = nullptr, *n2 = nullptr;  // P
+  double *n2 = nullptr;  // P
   int *frozen = nullptr, *skip2 = nullptr, *kk = nullptr, *done = nullptr;  // P
   int* none = nullptr;    // P zeros
   double* h = nullptr;    // pinned: tri (2P) + beta_k (P)
@@ -324,14 +318,12 @@ int cycles(Ctx* c, const MatVec& A, BScratch& s, z* x, int precision, int max_ma
     for (; k < cap; ++k) {
       TNT_TRY(A.apply(c, s.V + (int64_t)k * s.n, s.w, precision));
       ++mv;
-      TNT_TRY(snorm2(c, s, s.w, s.nw, s.frozen));
       TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.dots, s.frozen));
       TNT_TRY(saxpy(c, s, k + 1, s.dots, s.w, s.n2, s.frozen));
       k_sscalars<<<(NP + 63) / 64, 64, 0, c->stream>>>(s.dots, k, s.n2, s.alpha, s.beta, s.tri + 2 * NP, NP, s.frozen);
-      k_sreorth<<<(NP + 63) / 64, 64, 0, c->stream>>>(s.nw, s.n2, s.frozen, s.skip2, NP);
-      c->launches += 2;
-      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.coef, s.skip2));
-      TNT_TRY(saxpy(c, s, k + 1, s.coef, s.w, s.n2, s.skip2));
+      c->launches += 1;
+      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.coef, s.frozen));  // second pass, always
+      TNT_TRY(saxpy(c, s, k + 1, s.coef, s.w, s.n2, s.frozen));
       k_sscalars<<<(NP + 63) / 64, 64, 0, c->stream>>>(s.dots, k, s.n2, s.alpha, s.beta, s.tri + 2 * NP, NP, s.frozen);
       c->launches++;
       TNT_TRY(tridiag_lowest_batched(c, s.alpha, s.beta, k + 1, s.tri, s.y, NP, s.frozen));
@@ -452,7 +444,6 @@ int lanczos_batched(Ctx* c, const MatVec& A, const std::vector<int64_t>& off, z*
   s.beta = (double*)al(sizeof(double) * KMAX * NP);
   s.y = (double*)al(sizeof(double) * KMAX * NP);
   s.tri = (double*)al(sizeof(double) * 3 * NP);  // (E, |y_k|) per problem, then beta_k
-  s.nw = (double*)al(sizeof(double) * NP);
   s.n2 = (double*)al(sizeof(double) * NP);
   s.frozen = (int*)al(sizeof(int) * NP);
   s.skip2 = (int*)al(sizeof(int) * NP);
@@ -460,7 +451,7 @@ int lanczos_batched(Ctx* c, const MatVec& A, const std::vector<int64_t>& off, z*
   s.done = (int*)al(sizeof(int) * NP);
   s.none = (int*)al(sizeof(int) * NP);
   if (!s.V || !s.w || !s.w2 || !s.ch || !s.first || !s.part || !s.rpart || !s.dots || !s.coef ||
-      !s.alpha || !s.beta || !s.y || !s.tri || !s.nw || !s.n2 || !s.frozen || !s.skip2 || !s.kk ||
+      !s.alpha || !s.beta || !s.y || !s.tri || !s.n2 || !s.frozen || !s.skip2 || !s.kk ||
       !s.done || !s.none)
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (batched Lanczos)");
   TNT_CUDA_TRY(c, cudaMemcpyAsync(s.ch, ch.data(), sizeof(int64_t) * ch.size(), cudaMemcpyHostToDevice, c->stream));

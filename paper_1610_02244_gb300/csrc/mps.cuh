@@ -12,6 +12,7 @@ struct tnt_mpo {
   tnt::z* right = nullptr;  // boundary R_{L}[0,w,0]
   std::vector<int> wq;      // U(1) charge of each MPO bond index (empty: none)
   std::vector<std::vector<tnt::z>> hW;  // host copies of W (no read-back per update)
+  std::vector<tnt::z> hleft, hright;    // host copies of the boundary vectors
 };
 
 struct tnt_mps {

@@ -574,6 +574,22 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   TNT_CUDA_TRY(c, cudaMemcpyAsync(hl.data(), d_loc_s, sizeof(int) * ntot_vals, cudaMemcpyDeviceToHost, st));
   TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
   const int64_t chi = sel.chi;
+  if (chi < 1 || chi > ntot_vals) return set_err(c, TNT_E_NAN, "SVD selection returned chi = %lld of %lld", (long long)chi, (long long)ntot_vals);
+  for (int64_t k = 0; k < ntot_vals; ++k)  // report the block of a non-finite value first
+    if (!std::isfinite(hs[k]) && hb[k] >= 0 && hb[k] < nb)
+      return set_err(c, TNT_E_NAN, "SVD of %lld x %lld (%d blocks): value %g in block %d (%lld x %lld, Gram %lld, candidate %d of %lld)",
+                     (long long)m, (long long)n, nb, hs[k], hb[k], (long long)bl[hb[k]].mq,
+                     (long long)bl[hb[k]].nq, (long long)bl[hb[k]].g, hl[k], (long long)bl[hb[k]].k);
+  for (int64_t k = 0; k < ntot_vals; ++k)  // a non-finite value sorts anywhere: never index with it
+    if (!std::isfinite(hs[k]) || hb[k] < 0 || hb[k] >= nb || hl[k] < 0 || hl[k] >= bl[hb[k]].k)
+      return set_err(c, TNT_E_NAN,
+                     "SVD of %lld x %lld (%d blocks): non-finite or misplaced value %g at sorted index "
+                     "%lld (block %d, %lld x %lld, Gram %lld, candidate %d of %lld)",
+                     (long long)m, (long long)n, nb, hs[k], (long long)k, hb[k],
+                     (hb[k] >= 0 && hb[k] < nb) ? (long long)bl[hb[k]].mq : -1LL,
+                     (hb[k] >= 0 && hb[k] < nb) ? (long long)bl[hb[k]].nq : -1LL,
+                     (hb[k] >= 0 && hb[k] < nb) ? (long long)bl[hb[k]].g : -1LL, hl[k],
+                     (hb[k] >= 0 && hb[k] < nb) ? (long long)bl[hb[k]].k : -1LL);
   // ---- bond order: charge ascending (block index), then sigma descending
   std::vector<int> order(chi);
   for (int64_t k = 0; k < chi; ++k) order[k] = (int)k;

@@ -19,6 +19,7 @@ struct tnt_tebd {
   tnt_ctx* ctx = nullptr;
   tnt_mps* mps = nullptr;
   int centre = 0;
+  bool up = true;  // direction of the next layer (alternates layer by layer, across steps)
   std::vector<std::vector<tnt::z>> G_half, G_full;  // per bond, d^2 x d^2 (host)
   size_t scratch = 0;
 };
@@ -128,11 +129,14 @@ static int tebd_move_left(Ctx* c, tnt_tebd* t) {
   return TNT_OK;
 }
 
-// one gate on bond (i, i+1) with the centre at i; leaves the centre at i+1
-static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, tnt_step_stats* st) {
+// one gate on bond (i, i+1): the centre is moved into {i, i+1} (theta = A_i A_{i+1} is
+// then the centre's two-site tensor); side TNT_SVD_LEFT leaves it at i+1 (A_i <- U,
+// A_{i+1} <- S V^H), TNT_SVD_RIGHT at i (A_i <- U S, A_{i+1} <- V^H)
+static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, int side,
+                     tnt_step_stats* st) {
   tnt_mps* m = t->mps;
   while (t->centre < i) TNT_TRY(tebd_move_right(c, t));
-  while (t->centre > i) TNT_TRY(tebd_move_left(c, t));
+  while (t->centre > i + 1) TNT_TRY(tebd_move_left(c, t));
   const int64_t d = m->d, chl = m->chi[i], chm = m->chi[i + 1], chr = m->chi[i + 2];
   const int64_t n = chl * d * d * chr;
   const size_t top = c->ws.top;
@@ -155,12 +159,12 @@ static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, tnt_st
     tnt_params pp = c->params;  // the site storage bounds the kept dimension
     pp.chi_max = std::min(pp.chi_max, m->cap[i + 1]);
     ParamsGuard pg(c, pp);
-    TNT_TRY(svd_trunc_impl(c, theta2, chl * d, d * chr, rq.data(), cq.data(), TNT_SVD_LEFT, 0,
+    TNT_TRY(svd_trunc_impl(c, theta2, chl * d, d * chr, rq.data(), cq.data(), side, 0,
                            m->A[i], m->A[i + 1], S.data(), bq.data(), &tr));
   }
   m->chi[i + 1] = tr.chi;
   if (m->labelled) m->q[i + 1].assign(bq.begin(), bq.begin() + tr.chi);
-  t->centre = i + 1;
+  t->centre = (side == TNT_SVD_LEFT) ? i + 1 : i;
   st->err_sum += tr.err;
   st->disc_sum += tr.disc;
   c->ws.top = top;
@@ -173,24 +177,25 @@ using namespace tnt;
 
 extern "C" {
 
-int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* m, int n_max, double J, double U, double mu,
-                    double dt, tnt_tebd** out) {
-  if (!ctx || !m || !out || n_max + 1 != m->d || !std::isfinite(dt)) return TNT_E_INVALID;
+}  // extern "C"
+
+namespace tnt {
+// gates from per-bond Hamiltonians (rows (s1' s2'), columns (s1 s2)), then the
+// orthogonality centre to site 0 by exact right-to-left moves (a gauge change only)
+static int tebd_from_bonds(tnt_ctx* ctx, tnt_mps* m, const std::vector<std::vector<z>>& h,
+                           double dt, tnt_tebd** out) {
   Ctx* c = &ctx->c;
-  if (m->d * m->d > 256) return set_err(c, TNT_E_INVALID, "d^2 = %d exceeds 256", m->d * m->d);
+  const int L = m->L, d2 = m->d * m->d;
   tnt_tebd* t = new tnt_tebd();
   t->ctx = ctx;
   t->mps = m;
-  const int L = m->L, d2 = m->d * m->d;
   t->G_half.assign((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
   t->G_full.assign((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
   for (int i = 0; i + 1 < L; ++i) {
-    const double c1 = (i == 0) ? 1.0 : 0.5, c2 = (i + 2 == L) ? 1.0 : 0.5;
-    bh_bond_gate_host(n_max, J, U, mu, c1, c2, 0.5 * dt, t->G_half[(size_t)i].data());
-    bh_bond_gate_host(n_max, J, U, mu, c1, c2, dt, t->G_full[(size_t)i].data());
+    bond_gate_host(d2, h[(size_t)i].data(), 0.5 * dt, t->G_half[(size_t)i].data());
+    bond_gate_host(d2, h[(size_t)i].data(), dt, t->G_full[(size_t)i].data());
   }
   t->scratch = tebd_scratch_bound(m);
-  // orthogonality centre at site 0: exact right-to-left moves (a gauge change only)
   ws_reset(c);
   int r = ws_reserve(c, t->scratch);
   t->centre = L - 1;
@@ -205,6 +210,74 @@ int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* m, int n_max, double J, double U, dou
   return TNT_OK;
 }
 
+// on-site weights of the bond terms: 1/2 in the interior, 1 on the two end sites
+static void bond_weights(int L, int i, double* c1, double* c2) {
+  *c1 = (i == 0) ? 1.0 : 0.5;
+  *c2 = (i + 2 == L) ? 1.0 : 0.5;
+}
+}  // namespace tnt
+
+extern "C" {
+
+int tnt_tebd_create(tnt_ctx* ctx, tnt_mps* m, int n_max, double J, double U, double mu,
+                    double dt, tnt_tebd** out) {
+  if (!ctx || !m || !out || n_max + 1 != m->d || !std::isfinite(dt)) return TNT_E_INVALID;
+  if (m->d * m->d > 256) return set_err(&ctx->c, TNT_E_INVALID, "d^2 = %d exceeds 256", m->d * m->d);
+  const int L = m->L, d = m->d, d2 = d * d;
+  std::vector<std::vector<z>> h((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
+  std::vector<double> b((size_t)d * d, 0.0);  // <s'|b|s>
+  for (int n = 1; n < d; ++n) b[(size_t)(n - 1) * d + n] = std::sqrt((double)n);
+  auto hs = [&](int s) { return 0.5 * U * s * (s - 1) - mu * s; };
+  for (int i = 0; i + 1 < L; ++i) {
+    double c1, c2;
+    bond_weights(L, i, &c1, &c2);
+    // -J (b+ (x) b + b (x) b+) + c1 h_site (x) 1 + c2 1 (x) h_site
+    for (int s1o = 0; s1o < d; ++s1o)
+      for (int s2o = 0; s2o < d; ++s2o)
+        for (int s1 = 0; s1 < d; ++s1)
+          for (int s2 = 0; s2 < d; ++s2) {
+            double v = -J * (b[(size_t)s1 * d + s1o] * b[(size_t)s2o * d + s2] +
+                             b[(size_t)s1o * d + s1] * b[(size_t)s2 * d + s2o]);
+            if (s1o == s1 && s2o == s2) v += c1 * hs(s1) + c2 * hs(s2);
+            h[(size_t)i][(size_t)(s1o * d + s2o) * d2 + (s1 * d + s2)] = zmk(v, 0);
+          }
+  }
+  return tebd_from_bonds(ctx, m, h, dt, out);
+}
+
+int tnt_tebd_create_spin(tnt_ctx* ctx, tnt_mps* m, int two_s, double J, double Jz, double hz,
+                         double dt, tnt_tebd** out) {
+  if (!ctx || !m || !out || two_s < 1 || two_s + 1 != m->d || !std::isfinite(dt))
+    return TNT_E_INVALID;
+  const int L = m->L, d2 = m->d * m->d;
+  std::vector<std::vector<z>> h((size_t)(L - 1), std::vector<z>((size_t)d2 * d2));
+  for (int i = 0; i + 1 < L; ++i) {
+    double c1, c2;
+    bond_weights(L, i, &c1, &c2);
+    spin_bond_h_host(two_s, J, Jz, hz, c1, c2, h[(size_t)i].data());
+  }
+  return tebd_from_bonds(ctx, m, h, dt, out);
+}
+
+int tnt_tebd_create_bonds(tnt_ctx* ctx, tnt_mps* m, const tnt_cplx* const* h_bond, double dt,
+                          tnt_tebd** out) {
+  if (!ctx || !m || !out || !h_bond || !std::isfinite(dt)) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  if (m->d * m->d > 256) return set_err(c, TNT_E_INVALID, "d^2 = %d exceeds 256", m->d * m->d);
+  const int L = m->L;
+  const size_t n2 = (size_t)m->d * m->d * m->d * m->d;
+  std::vector<std::vector<z>> h((size_t)(L - 1));
+  for (int i = 0; i + 1 < L; ++i) {
+    if (!h_bond[i]) return set_err(c, TNT_E_INVALID, "bond term %d is NULL", i);
+    const z* p = (const z*)h_bond[i];
+    for (size_t e = 0; e < n2; ++e)
+      if (!std::isfinite(p[e].x) || !std::isfinite(p[e].y))
+        return set_err(c, TNT_E_NAN, "bond term %d has a non-finite entry", i);
+    h[(size_t)i].assign(p, p + n2);
+  }
+  return tebd_from_bonds(ctx, m, h, dt, out);
+}
+
 int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* t, tnt_step_stats* st) {
   if (!ctx || !t || !st || t->ctx != ctx) return TNT_E_INVALID;
   Ctx* c = &ctx->c;
@@ -217,11 +290,25 @@ int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* t, tnt_step_stats* st) {
   cudaEventRecord(e0, c->stream);
   ws_reset(c);
   int r = ws_reserve(c, t->scratch);
-  // odd bonds (0-based i even) at dt/2, even bonds at dt, odd bonds at dt/2
+  // odd bonds (0-based i even) at dt/2, even bonds at dt, odd bonds at dt/2.  The gates of
+  // a layer commute; each layer runs opposite to the one before (ascending gates leave the
+  // centre on their right site, descending ones on their left), so consecutive gates are
+  // one centre move apart and no layer starts with a walk across the chain.
   for (int layer = 0; layer < 3 && r == TNT_OK; ++layer) {
     const int first = (layer == 1) ? 1 : 0;
     const auto& G = (layer == 1) ? t->G_full : t->G_half;
-    for (int i = first; i + 1 < L && r == TNT_OK; i += 2) r = tebd_gate(c, t, i, G[(size_t)i], st);
+    if (first + 1 < L) {
+      int last = first;
+      while (last + 2 + 1 < L) last += 2;
+      if (t->up) {
+        for (int i = first; i <= last && r == TNT_OK; i += 2)
+          r = tebd_gate(c, t, i, G[(size_t)i], TNT_SVD_LEFT, st);
+      } else {
+        for (int i = last; i >= first && r == TNT_OK; i -= 2)
+          r = tebd_gate(c, t, i, G[(size_t)i], TNT_SVD_RIGHT, st);
+      }
+    }
+    t->up = !t->up;
   }
   ws_reset(c);
   cudaEventRecord(e1, c->stream);

@@ -226,6 +226,11 @@ int bh_mpo_site_host(int n_max, double J, double U, double mu, double V, double 
                      z* W);
 int bh_bond_gate_host(int n_max, double J, double U, double mu, double c1, double c2,
                       double tau, z* G);
+// exp(-i tau h) of a Hermitian n x n host matrix (row-major), by host Jacobi
+int bond_gate_host(int n, const z* h, double tau, z* G);
+// spin-S Heisenberg pieces (two_s = 2S): MPO site tensor [5][5][d][d], bond term d^2 x d^2
+int spin_mpo_site_host(int two_s, double J, double Jz, double hz, z* W);
+int spin_bond_h_host(int two_s, double J, double Jz, double hz, double c1, double c2, z* h);
 
 // release the call's scratch on every return path
 struct Scope {

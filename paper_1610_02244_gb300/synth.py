@@ -68,25 +68,60 @@ def hermitian_env(g: np.random.Generator, chi: int, D: int = 4, pair=(1, 2)) -> 
     return np.ascontiguousarray(E)
 
 
+COUNT_CAP = 1 << 40  # sector counts saturate here (3^101 does not fit in int64)
+
+
 def sector_counts(k: int, n_max: int) -> np.ndarray:
-    """cnt[q] = number of occupation strings of k sites (0..n_max each) summing to q."""
+    """cnt[q] = number of occupation strings of k sites (0..n_max each) summing to q,
+    saturated at COUNT_CAP (only ever compared with bond dimensions)."""
     cnt = np.zeros(k * n_max + 1, dtype=np.int64)
     cnt[0] = 1
     for _ in range(k):
         new = np.zeros_like(cnt)
         for n in range(n_max + 1):
             new[n:] += cnt[: len(cnt) - n]
-        cnt = new
+        cnt = np.minimum(new, COUNT_CAP)
     return cnt
 
 
-def bond_charges(L: int, d: int, N: int, chi_max: int) -> list[np.ndarray]:
+def _gauss_sizes(qs, caps, total, centre, sigma):
+    """Sector sizes proportional to exp(-(q - centre)^2 / 2 sigma^2), each within its cap,
+    summing to total (largest remainders first, spilling to the next-heaviest sectors)."""
+    qs, caps = np.asarray(qs, dtype=np.float64), np.asarray(caps, dtype=np.int64)
+    w = np.exp(-0.5 * ((qs - centre) / sigma) ** 2)
+    sizes = np.zeros(len(qs), dtype=np.int64)
+    left = total
+    while left > 0:
+        free = sizes < caps
+        ww = np.where(free, w, 0.0)
+        if ww.sum() <= 0:  # far tails underflow: fill by distance from the centre
+            ww = np.where(free, 1.0 / (1.0 + np.abs(qs - centre)), 0.0)
+        target = left * ww / ww.sum()
+        add = np.minimum(np.floor(target).astype(np.int64), caps - sizes)
+        if add.sum() == 0:  # hand out single indices by remainder
+            order = np.argsort(-(target - np.floor(target)) - 1e-9 * np.arange(len(qs)))
+            for i in order:
+                if left == 0:
+                    break
+                if sizes[i] < caps[i]:
+                    sizes[i] += 1
+                    left -= 1
+            continue
+        sizes += add
+        left -= int(add.sum())
+    return sizes
+
+
+def bond_charges(L: int, d: int, N: int, chi_max: int, profile: str = "even",
+                 sigma: float = 2.0) -> list[np.ndarray]:
     """Charge label (bosons to the left of the bond) of every index of bonds 0..L.
 
     Bond k separates sites 1..k from k+1..L.  Every charge q reachable from both sides is
-    a sector; sector sizes are capped by the exact Schmidt bound min(#left, #right) and
-    filled one index at a time, round robin over sectors in ascending q, until the bond
-    holds min(chi_max, exact bound) indices.  Labels are returned sorted ascending.
+    a sector, its size capped by the exact Schmidt bound min(#left, #right); the bond holds
+    min(chi_max, exact bound) indices.  profile "even": filled one index at a time, round
+    robin over sectors in ascending q.  profile "gauss": sizes proportional to a Gaussian
+    of width sigma around the mean filling N k / L (the sector profile of a ground state or
+    of a state evolved from one).  Labels are returned sorted ascending.
     """
     n_max = d - 1
     out = []
@@ -100,15 +135,18 @@ def bond_charges(L: int, d: int, N: int, chi_max: int) -> list[np.ndarray]:
                 if c > 0:
                     qs.append(q)
                     caps.append(c)
-        total = min(chi_max, sum(caps))
-        sizes = [0] * len(qs)
-        filled = 0
-        while filled < total:
-            for i in range(len(qs)):
-                if filled < total and sizes[i] < caps[i]:
-                    sizes[i] += 1
-                    filled += 1
-        lab = np.concatenate([np.full(s, q, dtype=np.int64) for q, s in zip(qs, sizes)])
+        total = int(min(chi_max, sum(caps)))
+        if profile == "gauss":
+            sizes = [int(x) for x in _gauss_sizes(qs, caps, total, N * k / L, sigma)]
+        else:
+            sizes = [0] * len(qs)
+            filled = 0
+            while filled < total:
+                for i in range(len(qs)):
+                    if filled < total and sizes[i] < caps[i]:
+                        sizes[i] += 1
+                        filled += 1
+        lab = np.concatenate([np.full(s, q, dtype=np.int64) for q, s in zip(qs, sizes) if s > 0])
         out.append(lab)
     return out
 
@@ -119,19 +157,27 @@ def charge_mask(ql: np.ndarray, d: int, qr: np.ndarray) -> np.ndarray:
     return (ql[:, None, None] + s[None, :, None]) == qr[None, None, :]
 
 
-def random_charged_mps(g: np.random.Generator, L: int, d: int, N: int, chi_max: int):
-    """Random-normal MPS in the fixed-N sector: Gaussian entries inside allowed blocks.
+def random_charged_mps(g: np.random.Generator, L: int, d: int, N: int, chi_max: int,
+                       profile: str = "even", sigma: float = 2.0):
+    """Random-normal MPS in the fixed-N sector: Gaussian entries inside allowed blocks,
+    bond sectors as bond_charges(profile, sigma), each site scaled to |A_j|_F^2 = chi_{j+1}
+    (the left transfer map then keeps the identity at about unit size, so the norm of a
+    long chain stays near one instead of growing like prod_j |A_j|; the scale of a site
+    does not change the normalised state).
 
     Returns (tensors, charges): tensors[j] is A_j[a, s, b] (complex128) for sites
-    j = 0..L-1 and charges[k] the labels of bond k = 0..L.  No normalisation or gauge is
-    applied: both sides bring the state to canonical form themselves.
+    j = 0..L-1 and charges[k] the labels of bond k = 0..L.  No gauge is applied: both
+    sides bring the state to canonical form themselves.
     """
-    charges = bond_charges(L, d, N, chi_max)
+    charges = bond_charges(L, d, N, chi_max, profile, sigma)
     tensors = []
     for j in range(L):
         ql, qr = charges[j], charges[j + 1]
         A = complex_gaussian(g, (len(ql), d, len(qr)))
         A = np.where(charge_mask(ql, d, qr), A, 0.0)
+        nrm = np.linalg.norm(A)
+        if nrm > 0:
+            A = A * (np.sqrt(len(qr)) / nrm)
         tensors.append(np.ascontiguousarray(A.astype(np.complex128)))
     return tensors, charges
 

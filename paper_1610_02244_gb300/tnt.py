@@ -44,6 +44,30 @@ def bh_bond_gate(n_max, J, U, mu, c1, c2, tau) -> np.ndarray:
     return out
 
 
+def spin_mpo_site(two_s, J, Jz, hz=0.0) -> np.ndarray:
+    """Host builder of one spin-S Heisenberg MPO tensor W[5,5,d,d] (tnt_spin_mpo_site)."""
+    d = two_s + 1
+    out = np.zeros((5, 5, d, d), dtype=np.complex128)
+    L.check(None, L.load().tnt_spin_mpo_site(two_s, J, Jz, hz, out.ctypes.data))
+    return out
+
+
+def spin_bond_h(two_s, J, Jz, hz, c1, c2) -> np.ndarray:
+    """Host builder of the spin-S Heisenberg bond term, d^2 x d^2 (tnt_spin_bond_h)."""
+    d = two_s + 1
+    out = np.zeros((d * d, d * d), dtype=np.complex128)
+    L.check(None, L.load().tnt_spin_bond_h(two_s, J, Jz, hz, c1, c2, out.ctypes.data))
+    return out
+
+
+def bond_gate(h, tau) -> np.ndarray:
+    """exp(-i tau h) of a Hermitian host matrix (tnt_bond_gate)."""
+    h = np.ascontiguousarray(h, dtype=np.complex128)
+    out = np.zeros_like(h)
+    L.check(None, L.load().tnt_bond_gate(h.shape[0], h.ctypes.data, tau, out.ctypes.data))
+    return out
+
+
 def params_default() -> dict:
     p = L.tnt_params()
     L.check(None, L.load().tnt_params_default(C.byref(p)))
@@ -267,6 +291,27 @@ class Context:
         self._chk(self.lib.tnt_mpo_bose_hubbard(self.h, L_, n_max, J, U, mu, V, j_c, C.byref(h)))
         return Mpo(self, h)
 
+    def mpo_spin_heisenberg(self, L_, two_s, J=1.0, Jz=None, hz=0.0) -> "Mpo":
+        h = C.c_void_p()
+        Jz = J if Jz is None else Jz
+        self._chk(self.lib.tnt_mpo_spin_heisenberg(self.h, L_, two_s, J, Jz, hz, C.byref(h)))
+        return Mpo(self, h)
+
+    def mpo_create(self, Ws, left, right, wq=None) -> "Mpo":
+        Ws = [np.ascontiguousarray(W, dtype=np.complex128) for W in Ws]
+        D, d = Ws[0].shape[0], Ws[0].shape[2]
+        lb = np.ascontiguousarray(left, dtype=np.complex128)
+        rb = np.ascontiguousarray(right, dtype=np.complex128)
+        wp = None
+        if wq is not None:
+            wqa = np.ascontiguousarray(wq, dtype=np.int32)
+            wp = wqa.ctypes.data
+        sp = (C.c_void_p * len(Ws))(*[W.ctypes.data for W in Ws])
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_mpo_create(self.h, len(Ws), d, D, sp, lb.ctypes.data,
+                                          rb.ctypes.data, wp, C.byref(h)))
+        return Mpo(self, h)
+
     def mps_create(self, tensors, charges=None, chi_cap=None) -> "Mps":
         Ls = len(tensors)
         d = tensors[0].shape[1]
@@ -297,6 +342,19 @@ class Context:
     def tebd_create(self, mps: "Mps", n_max, J, U, dt, mu=0.0) -> "Tebd":
         h = C.c_void_p()
         self._chk(self.lib.tnt_tebd_create(self.h, mps.h, n_max, J, U, mu, dt, C.byref(h)))
+        return Tebd(self, h, mps)
+
+    def tebd_create_spin(self, mps: "Mps", two_s, J, dt, Jz=None, hz=0.0) -> "Tebd":
+        h = C.c_void_p()
+        Jz = J if Jz is None else Jz
+        self._chk(self.lib.tnt_tebd_create_spin(self.h, mps.h, two_s, J, Jz, hz, dt, C.byref(h)))
+        return Tebd(self, h, mps)
+
+    def tebd_create_bonds(self, mps: "Mps", bond_hs, dt) -> "Tebd":
+        hs = [np.ascontiguousarray(x, dtype=np.complex128) for x in bond_hs]
+        hp = (C.c_void_p * len(hs))(*[x.ctypes.data for x in hs])
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_tebd_create_bonds(self.h, mps.h, hp, dt, C.byref(h)))
         return Tebd(self, h, mps)
 
 

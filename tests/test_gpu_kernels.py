@@ -245,3 +245,27 @@ def test_svd_large_block_cfg2_shape(ctx):
     U = U.cpu().numpy()
     assert np.abs(U.conj().T @ U - np.eye(256)).max() < 1e-11
     assert abs(info["disc"] - np.sum(s_ref[256:] ** 2)) < 1e-10 * np.sum(s_ref ** 2)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_svd_zero_charge_blocks(ctx, side):
+    """Charge blocks with no weight (a sector of theta a gate has not reached): a 40 x 30
+    one (Jacobi path), a 200 x 210 one (tridiagonal path) and a zero 1 x 1 block.  Their
+    values are exact zeros and never kept; the weighted block comes out as the oracle's."""
+    g = np.random.default_rng(31)
+    rq = np.repeat([0, 1, 2, 3], [40, 200, 1, 120])
+    cq = np.repeat([0, 1, 2, 3], [30, 210, 1, 100])
+    M = np.zeros((len(rq), len(cq)), dtype=np.complex128)
+    blk = (rq[:, None] == 3) & (cq[None, :] == 3)
+    M[blk] = (g.normal(size=blk.sum()) + 1j * g.normal(size=blk.sum()))
+    ctx.set_params(chi_max=150, trunc_err=1e-8, trunc_rel=1e-16)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), rq, cq, side=side)
+    finally:
+        ctx.set_params(chi_max=1 << 40)
+    Ur, Sr, Vr, bqr, _ = osvd.svd_truncate(M, rq, cq, osvd.TruncParams(chi_max=150))
+    assert info["chi"] == len(Sr) == 100 and np.all(bq == 3)
+    assert np.abs(np.sort(S) - np.sort(Sr)).max() < 1e-12 * Sr.max()
+    U, X = U.cpu().numpy(), X.cpu().numpy()
+    assert np.isfinite(U).all() and np.isfinite(X).all()
+    assert np.abs(U @ X - M).max() < 1e-11 * Sr.max()

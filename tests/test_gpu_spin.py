@@ -1,0 +1,241 @@
+"""Spin-S Heisenberg chains on the GPU (the model of Sec. 6, Tables 1 and 2) against the FP64
+oracle and exact diagonalisation, through the C-ABI: the host model builders, the generic
+MPO entry point, two-site DMRG with a D = 5 MPO over U(1) magnetisation labels, and TEBD
+with spin and arbitrary bond terms (the central spin flip of Table 2 on a small chain).
+
+Targets as for the Bose-Hubbard chain: |dE| <= 1e-10 |E|, |1 - |<psi|psi_ref>|| <= 1e-8."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import bose_hubbard as bh
+from oracle import contract as oc
+from oracle import dmrg as odmrg
+from oracle import spin as ospin
+from oracle import tebd as otebd
+from oracle.svd import TruncParams
+from paper_1610_02244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+L, TWO_S = 8, 2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1610_02244_gb300 import build as b
+    b.build()
+    from paper_1610_02244_gb300 import tnt
+    return tnt.Context(0)
+
+
+def test_host_builders_match_oracle():
+    from paper_1610_02244_gb300 import tnt
+    for two_s, J, Jz, hz in ((2, 1.0, 1.0, 0.0), (1, 0.8, -0.3, 0.25), (3, 1.0, 0.5, 0.1)):
+        Ws, _, _, _ = ospin.heisenberg_mpo(2, two_s, J, Jz, hz)
+        assert np.abs(tnt.spin_mpo_site(two_s, J, Jz, hz) - Ws[0]).max() < 1e-15
+        for c1, c2 in ((1.0, 0.5), (0.5, 0.5), (0.5, 1.0)):
+            h = ospin.bond_hamiltonian(two_s, J, Jz, hz, c1, c2)
+            assert np.abs(tnt.spin_bond_h(two_s, J, Jz, hz, c1, c2) - h).max() < 1e-15
+            # the gate: host Jacobi against the oracle's eigh route
+            assert np.abs(tnt.bond_gate(h, 0.07) - bh.gate(h, 0.07)).max() < 1e-13
+
+
+# Where chi = 32 truncates, the comparison needs Schmidt values that do not meet at the cut:
+# the isotropic chain has SU(2) multiplets, and in the S^z = 0 sector the spin flip maps
+# sector k onto -k.  So the truncating comparison runs the XXZ chain (Jz = 0.7) with one
+# quantum above half filling (S^z_total = +1); the isotropic model runs untruncated below.
+JZ_T, N_T = 0.7, L + 1
+
+
+@pytest.fixture(scope="module")
+def oracle_spin1_chi32():
+    g = synth.rng(5)
+    A, q = synth.random_charged_mps(g, L, TWO_S + 1, N_T, 32)
+    Ws, l, r, _ = ospin.heisenberg_mpo(L, TWO_S, 1.0, JZ_T)
+    A2, q2, hist = odmrg.dmrg(A, q, Ws, l, r, 32, 4)
+    return (A, q), hist, oc.mps_to_state(A2)
+
+
+def _run_dmrg(ctx, A, q, chi, sweeps, precision, mpo):
+    from paper_1610_02244_gb300 import tnt
+    ctx.set_params(chi_max=chi, precision=precision)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=chi)
+        dm = ctx.dmrg_create(mps, mpo)
+        stats = [dm.sweep() for _ in range(sweeps)]
+        return stats, mps, oc.mps_to_state(mps.tensors())
+    finally:
+        ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dmrg_spin1_matches_oracle(ctx, oracle_spin1_chi32, precision):
+    (A, q), hist, psi_ref = oracle_spin1_chi32
+    mpo = ctx.mpo_spin_heisenberg(L, TWO_S, 1.0, JZ_T)
+    stats, mps, psi = _run_dmrg(ctx, A, q, 32, 4, precision, mpo)
+    E_ref = hist[-1]["E"]
+    assert abs(stats[-1]["E"] - E_ref) <= 1e-10 * abs(E_ref)
+    assert abs(1 - abs(np.vdot(psi_ref, psi))) <= 1e-8
+    # <H> through the D = 5 environment chain and the right boundary vector
+    assert abs(mps.expect_mpo(mpo) - E_ref) <= 1e-10 * abs(E_ref)
+    # every bond label is a quanta count: the state stays in its sector
+    assert abs(mps.density().sum() - N_T) < 1e-12
+    energies = [s["E"] for s in stats]
+    assert all(b <= a + 1e-10 for a, b in zip(energies, energies[1:]))
+
+
+@pytest.fixture(scope="module")
+def oracle_xxz_L24():
+    g = synth.rng(11)
+    A, q = synth.random_charged_mps(g, 24, 3, 25, 48, "gauss", 2.0)
+    Ws, l, r, _ = ospin.heisenberg_mpo(24, 2, 1.0, JZ_T)
+    A2, q2, hist = odmrg.dmrg(A, q, Ws, l, r, 48, 4)
+    return (A, q), hist, A2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dmrg_spin1_xxz_L24_many_sectors(ctx, oracle_xxz_L24, precision):
+    """24 sites at chi = 48 (truncation error ~2e-4 per bond; 10+ sectors per bond, some
+    of one state): sweep energies and the final state against the oracle's."""
+    (A, q), hist, A_ref = oracle_xxz_L24
+    mpo = ctx.mpo_spin_heisenberg(24, 2, 1.0, JZ_T)
+    from paper_1610_02244_gb300 import tnt
+    ctx.set_params(chi_max=48, precision=precision)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=48)
+        dm = ctx.dmrg_create(mps, mpo)
+        stats = [dm.sweep() for _ in range(4)]
+        T = mps.tensors()
+    finally:
+        ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
+    for s, h in zip(stats, hist):
+        assert abs(s["E"] - h["E"]) <= 1e-9 * abs(h["E"]), (s["E"], h["E"])
+        assert s["unconverged"] == 0
+    E_ref = hist[-1]["E"]
+    assert abs(stats[-1]["E"] - E_ref) <= 1e-10 * abs(E_ref)
+    ov = oc.mps_overlap(T, A_ref)
+    assert abs(1 - abs(ov)) <= 1e-8
+    # the split-TF32 solve promises its state through the overlap (1 - |<.|.>| <= 1e-8),
+    # which bounds the density error by ~3e-4; FP64 follows the oracle far closer
+    assert np.abs(oc.density(T, 2) - oc.density(A_ref, 2)).max() <= (1e-7 if precision == 0 else 1e-6)
+
+
+def test_dmrg_spin1_exact_bond_matches_ed(ctx):
+    E0, v0 = ospin.ground_state(L, TWO_S, 1.0, 1.0, 0.0, L)
+    g = synth.rng(6)
+    A, q = synth.random_charged_mps(g, L, TWO_S + 1, L, 81)
+    mpo = ctx.mpo_spin_heisenberg(L, TWO_S, 1.0)
+    stats, _, psi = _run_dmrg(ctx, A, q, 81, 3, 0, mpo)
+    assert abs(stats[-1]["E"] - E0) <= 1e-10 * abs(E0)
+    assert abs(1 - abs(np.vdot(v0, psi))) <= 1e-8
+
+
+def test_generic_mpo_entry_point(ctx):
+    """tnt_mpo_create with the oracle's own MPO tensors gives the same sweep as the built-in
+    Bose-Hubbard and spin MPOs (same W up to the last bit), and without charges runs the
+    dense path to the same energy."""
+    from paper_1610_02244_gb300 import synth as sy
+    g = sy.rng(2)
+    A, q = sy.random_charged_mps(g, 6, 4, 6, 16)
+    Ws, l, r = bh.bh_mpo(6, 3, 1.0, 2.0)
+    s1, _, _ = _run_dmrg(ctx, A, q, 16, 2, 0, ctx.mpo_bose_hubbard(6, 3, 1.0, 2.0))
+    s2, _, _ = _run_dmrg(ctx, A, q, 16, 2, 0, ctx.mpo_create(Ws, l, r, wq=[0, 1, -1, 0]))
+    assert abs(s1[-1]["E"] - s2[-1]["E"]) <= 1e-13 * abs(s1[-1]["E"])
+    s5, _, _ = _run_dmrg(ctx, A, q, 16, 2, 0, ctx.mpo_create(Ws, l, r))  # no charges: dense
+    assert abs(s1[-1]["E"] - s5[-1]["E"]) <= 1e-10 * abs(s1[-1]["E"])
+    g = sy.rng(3)
+    A, q = sy.random_charged_mps(g, 6, 3, 6, 27)
+    Wsp, lp, rp, wq = ospin.heisenberg_mpo(6, 2, 1.0, 0.5, 0.2)
+    s3, _, _ = _run_dmrg(ctx, A, q, 27, 3, 0, ctx.mpo_spin_heisenberg(6, 2, 1.0, 0.5, 0.2))
+    s4, _, _ = _run_dmrg(ctx, A, q, 27, 3, 0, ctx.mpo_create(Wsp, lp, rp, wq=wq))
+    assert abs(s3[-1]["E"] - s4[-1]["E"]) <= 1e-13 * abs(s3[-1]["E"])
+    E0, _ = ospin.ground_state(6, 2, 1.0, 0.5, 0.2, 6)
+    assert abs(s3[-1]["E"] - E0) <= 1e-10 * abs(E0)
+
+
+def _spin_flip_centre(A, q, j, two_s):
+    """S+ applied at site j (0-based) of a charged MPS: the central spin flip of Table 2 in
+    the raising direction (bond labels right of j move up by one)."""
+    sp_ = ospin.spin_ops(two_s)[0]
+    B = [t.copy() for t in A]
+    B[j] = np.einsum("ts,asb->atb", sp_, A[j])
+    q2 = [c.copy() for c in q]
+    for k in range(j + 1, len(q)):
+        q2[k] = q2[k] + 1
+    return B, q2
+
+
+def test_tebd_spin1_central_flip_matches_oracle_and_exact(ctx):
+    """Ground state of the L = 8 spin-1 chain (oracle DMRG at chi = 81, exact), S+ at the
+    centre, 10 Trotter steps of dt = 0.02 on both sides at chi = 81: same state to 1e-8
+    (gauge-invariant), and within the Trotter bound of exp(-iHt)|psi>."""
+    g = synth.rng(8)
+    A, q = synth.random_charged_mps(g, L, TWO_S + 1, L, 81)
+    Ws, l, r, _ = ospin.heisenberg_mpo(L, TWO_S, 1.0, 1.0)
+    A0, q0, _ = odmrg.dmrg(A, q, Ws, l, r, 81, 3)
+    B, qb = _spin_flip_centre(A0, q0, L // 2, TWO_S)
+    dt, steps = 0.02, 10
+    hs = [ospin.bond_hamiltonian(TWO_S, 1.0, 1.0, 0.0, *bh.bond_weights(L, j + 1))
+          for j in range(L - 1)]
+    ref = otebd.Tebd.from_bond_hamiltonians(B, qb, hs, dt, TruncParams(chi_max=81, err_tol=1e-14))
+    ctx.set_params(chi_max=81, trunc_err=1e-14, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    try:
+        mps = ctx.mps_create(B, qb, chi_cap=81)
+        ev = ctx.tebd_create_spin(mps, TWO_S, 1.0, dt)
+        for _ in range(steps):
+            ev.step()
+            ref.step()
+        psi, phi = oc.mps_to_state(mps.tensors()), oc.mps_to_state(ref.A)
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    n1, n2 = np.vdot(psi, psi).real, np.vdot(phi, phi).real
+    assert abs(1 - abs(np.vdot(psi, phi)) / np.sqrt(n1 * n2)) <= 1e-8
+    assert abs(n1 - n2) <= 1e-10
+    sz_gpu = mps.density() - 1.0
+    assert np.abs(sz_gpu - (oc.density(ref.A, TWO_S) - 1.0)).max() <= 1e-9
+    assert abs(sz_gpu.sum() - 1.0) < 1e-10  # one quantum added
+    psi0 = oc.mps_to_state(B)
+    H = ospin.full_hamiltonian(L, TWO_S, 1.0, 1.0, 0.0)
+    exact = spla.expm_multiply(-1j * dt * steps * H, psi0)
+    assert abs(1 - abs(np.vdot(exact, psi)) / np.sqrt(n1 * np.vdot(exact, exact).real)) < 1e-6
+
+
+def test_tebd_bond_terms_xx_chain_free_fermions(ctx):
+    """Arbitrary bond terms (tnt_tebd_create_bonds): the spin-1/2 XX chain from the Neel
+    state follows the free-fermion closed form to the Trotter error (3e-4 at t = 1,
+    dt = 0.05) and the oracle's Trotter state to 1e-10."""
+    Ls, dt, steps = 10, 0.05, 20
+    occ = [1, 0] * (Ls // 2)
+    hs = [ospin.bond_hamiltonian(1, 1.0, 0.0, 0.0, *bh.bond_weights(Ls, j + 1))
+          for j in range(Ls - 1)]
+    ctx.set_params(chi_max=32, trunc_err=1e-14, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    try:
+        mps = ctx.mps_product(occ, 2, 32)
+        ev = ctx.tebd_create_bonds(mps, hs, dt)
+        for _ in range(steps):
+            ev.step()
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    h1 = np.zeros((Ls, Ls))
+    for j in range(Ls - 1):
+        h1[j, j + 1] = h1[j + 1, j] = 0.5
+    lam, Q = np.linalg.eigh(h1)
+    Ut = (Q * np.exp(-1j * lam * dt * steps)) @ Q.conj().T
+    exact = (np.abs(Ut) ** 2) @ np.array(occ, dtype=float)
+    dens = mps.density()
+    assert np.abs(dens - exact).max() < 3e-4
+    A, q = otebd.product_state(occ, 1)
+    ref = otebd.Tebd.from_bond_hamiltonians(A, q, hs, dt, TruncParams(chi_max=32, err_tol=1e-14))
+    for _ in range(steps):
+        ref.step()
+    assert np.abs(dens - oc.density(ref.A, 1)).max() < 1e-10
+
+
+def test_tebd_bonds_rejects_nonfinite(ctx):
+    from paper_1610_02244_gb300 import tnt
+    mps = ctx.mps_product([1, 0, 1, 0], 2, 8)
+    hs = [np.zeros((4, 4), dtype=np.complex128) for _ in range(3)]
+    hs[1][0, 0] = np.nan
+    with pytest.raises(tnt.TntError):
+        ctx.tebd_create_bonds(mps, hs, 0.1)
