@@ -729,7 +729,8 @@ def run_spin1_dmrg(args, ws, rank, local):
                            "precision": args.precision, "fp64_gemm": args.fp64_gemm},
                 "E": E, "E_per_bond": E / (SPIN_L - 1),
                 "sweeps": [{k: h[k] for k in ("E", "max_err", "total_matvecs", "unconverged",
-                                              "seconds")} for h in hist],
+                                              "seconds", "t_plan", "t_eig", "t_svd", "t_env")}
+                           for h in hist],
                 "paper_s_per_sweep": PAPER_SPIN1_DMRG_S_PER_SWEEP,
                 "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -118,6 +118,10 @@ typedef struct {
   int total_matvecs;    /* matvecs of all eigensolves                                */
   int unconverged;      /* eigensolves that hit the cap                              */
   double seconds;       /* wall time of the sweep (CUDA events)                      */
+  double t_plan;        /* seconds per phase, summed over the sweep's updates (stream  */
+  double t_eig;         /*   time between events, host gaps included): eigensolve      */
+  double t_svd;         /*   planning (block tables, operator upload), the eigensolve, */
+  double t_env;         /*   theta formation + truncated SVD, environment growth        */
 } tnt_sweep_stats;
 
 /* Per-step TEBD statistics (second-order Trotter step). */

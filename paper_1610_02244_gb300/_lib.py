@@ -54,7 +54,8 @@ class tnt_trunc_result(C.Structure):
 class tnt_sweep_stats(C.Structure):
     _fields_ = [("E", C.c_double), ("max_err", C.c_double), ("max_disc", C.c_double),
                 ("max_chi", C.c_int64), ("total_matvecs", C.c_int), ("unconverged", C.c_int),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("t_plan", C.c_double), ("t_eig", C.c_double),
+                ("t_svd", C.c_double), ("t_env", C.c_double)]
 
 
 class tnt_u1_problem(C.Structure):

@@ -56,7 +56,7 @@ static int dmrg_env_right(Ctx* c, tnt_dmrg* g, int j) {
 
 // One two-site update on bond (i, i+1); dir > 0 left-to-right, dir < 0 right-to-left.
 static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* lz,
-                       tnt_trunc_result* tr) {
+                       tnt_trunc_result* tr, bool marks) {
   tnt_mps* m = g->mps;
   const int64_t d = m->d, D = g->mpo->D;
   const int64_t chl = m->chi[i], chm = m->chi[i + 1], chr = m->chi[i + 2];
@@ -88,6 +88,7 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     if (!x) return set_err(c, TNT_E_ALLOC, "scratch exhausted (compact theta)");
     TNT_TRY(u1_convert(c, spec[0], theta, x, 1));
     TNT_TRY(u1_prepare(c, spec, &up));
+    if (marks) cudaEventRecord(g->ev[1], c->stream);
     int r = lanczos_run(c, U1MatVec(up), x, lz);
     if (r != TNT_OK && r != TNT_E_NOCONV) return r;
     TNT_TRY(u1_convert(c, spec[0], x, theta, 0));
@@ -98,10 +99,12 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     TNT_TRY(heff_prepare(c, g->Lenv[i], g->mpo->W[i], g->mpo->W[i + 1], g->Renv[i + 2], chl, d, D,
                          chr, c->params.precision, &p, g->mpo->hW[(size_t)i].data(),
                          g->mpo->hW[(size_t)i + 1].data()));
+    if (marks) cudaEventRecord(g->ev[1], c->stream);
     int r = lanczos_impl(c, p, theta, lz);
     if (r != TNT_OK && r != TNT_E_NOCONV) return r;
     c->ws.top = t2;
   }
+  if (marks) cudaEventRecord(g->ev[2], c->stream);
   // SVD of M[(a s1), (s2 b)] with labels q_a + s1 and q_b - s2
   std::vector<int64_t> ql = labels_or_zero(m, i), qr = labels_or_zero(m, i + 2);
   std::vector<int64_t> rq((size_t)(chl * d)), cq((size_t)(d * chr));
@@ -419,6 +422,11 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) 
   const int L = m->L;
   g->Lenv.assign(L + 1, nullptr);
   g->Renv.assign(L + 1, nullptr);
+  for (cudaEvent_t& e : g->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      tnt_dmrg_destroy(g);
+      return set_err(c, TNT_E_CUDA, "event creation failed");
+    }
   for (int k = 0; k <= L; ++k) {
     const size_t ne = (size_t)(m->cap[k] * o->D * m->cap[k]);
     if (cudaMalloc((void**)&g->Lenv[k], ne * sizeof(z)) != cudaSuccess ||
@@ -510,19 +518,41 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
     st->max_disc = std::max(st->max_disc, tr.disc);
     E = lz.E_rq;
   };
+  // phase marks: ev[0] update start, ev[1] eigensolve start, ev[2] eigensolve end,
+  // ev[3] SVD end, ev[4] environment end (the update already synchronises on its SVD)
+  auto phases = [&]() {
+    float a = 0, b = 0, d = 0, e = 0;
+    cudaEventSynchronize(g->ev[4]);
+    cudaEventElapsedTime(&a, g->ev[0], g->ev[1]);
+    cudaEventElapsedTime(&b, g->ev[1], g->ev[2]);
+    cudaEventElapsedTime(&d, g->ev[2], g->ev[3]);
+    cudaEventElapsedTime(&e, g->ev[3], g->ev[4]);
+    st->t_plan += 1e-3 * a;
+    st->t_eig += 1e-3 * b;
+    st->t_svd += 1e-3 * d;
+    st->t_env += 1e-3 * e;
+  };
   int r = TNT_OK;
   for (int i = 0; i + 1 < L && r == TNT_OK; ++i) {
     tnt_lanczos_result lz{};
     tnt_trunc_result tr{};
-    r = dmrg_update(c, g, i, +1, &lz, &tr);
+    cudaEventRecord(g->ev[0], c->stream);
+    r = dmrg_update(c, g, i, +1, &lz, &tr, true);
+    cudaEventRecord(g->ev[3], c->stream);
     if (r == TNT_OK) r = dmrg_env_left(c, g, i);
+    cudaEventRecord(g->ev[4], c->stream);
+    if (r == TNT_OK) phases();
     account(lz, tr);
   }
   for (int i = L - 2; i >= 0 && r == TNT_OK; --i) {
     tnt_lanczos_result lz{};
     tnt_trunc_result tr{};
-    r = dmrg_update(c, g, i, -1, &lz, &tr);
+    cudaEventRecord(g->ev[0], c->stream);
+    r = dmrg_update(c, g, i, -1, &lz, &tr, true);
+    cudaEventRecord(g->ev[3], c->stream);
     if (r == TNT_OK) r = dmrg_env_right(c, g, i + 1);
+    cudaEventRecord(g->ev[4], c->stream);
+    if (r == TNT_OK) phases();
     account(lz, tr);
   }
   ws_reset(c);
@@ -540,6 +570,8 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
 
 int tnt_dmrg_destroy(tnt_dmrg* g) {
   if (!g) return TNT_E_INVALID;
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
   for (z* p : g->Lenv) if (p) cudaFree(p);
   for (z* p : g->Renv) if (p) cudaFree(p);
   delete g;

@@ -410,15 +410,43 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
   if (lane == 0) ev[i] = 0.5 * (lo + hi);
 }
 
-// inverse iteration on T - lambda I.  Eigenvalues closer than 1e3 eps |T| form a cluster,
-// handled by one block in order: thread 0 factors and solves (the recurrences are
-// serial), then the block re-orthogonalises the new iterate against the cluster's
-// earlier vectors (classical Gram-Schmidt, twice) after every solve, so coincident
-// eigenvalues still give independent vectors.  Wider gaps give iterates accurate to
-// eps |T| / gap, which the final Newton-Schulz steps absorb.  Work arrays live in shared
-// memory when they fit (smem_ok), else in the cluster head's slice of gwork.
+// Inverse iteration on T - lambda I, block form.  Eigenvalues closer than 1e3 eps |T|
+// form a cluster (in a truncated SVD's Gram block, typically the dozens of eigenvalues at
+// rounding level below the kept ones), handled by one block: thread 0 factors T - lambda I
+// once, lambda the cluster's largest eigenvalue; every sweep then solves for all members
+// at once (one thread per member, the recurrences are serial) and re-orthogonalises the
+// members in order (classical Gram-Schmidt, twice, then a max-scaled normalisation), so
+// coincident eigenvalues still give independent vectors.  Wider gaps give iterates
+// accurate to eps |T| / gap, which the final Newton-Schulz steps absorb.  The factors live
+// in shared memory when they fit (smem_ok), else in the cluster head's slice of gwork;
+// the iterates are the output columns Y[i * n ...] themselves.
 constexpr int IV_THREADS = 128;
 constexpr int IV_CHUNK = 1024;  // earlier cluster members handled per Gram-Schmidt chunk
+
+// solve (T - lambda I) y = y in place from the pivoted LU factors; the vector is scaled
+// down whenever an entry passes 2^500 (compounding pivots of near-degenerate eigenvalues:
+// the solution of a scaled system is the scaled solution)
+__device__ void iv_solve(double* y, int64_t n, const double* dl, const double* dm,
+                         const double* du, const double* du2, const int8_t* piv) {
+  for (int64_t r = 0; r < n - 1; ++r) {
+    if (piv[r] == 0) {
+      y[r + 1] -= dl[r] * y[r];
+    } else {
+      const double t = y[r];
+      y[r] = y[r + 1];
+      y[r + 1] = t - dl[r] * y[r];
+    }
+  }
+  for (int64_t r = n - 1; r >= 0; --r) {
+    double v = y[r];
+    if (r + 1 < n) v -= du[r] * y[r + 1];
+    if (r + 2 < n) v -= du2[r] * y[r + 2];
+    v /= dm[r];
+    y[r] = v;
+    if (fabs(v) > 0x1p500)
+      for (int64_t q = 0; q < n; ++q) y[q] *= 0x1p-500;
+  }
+}
 
 __global__ void __launch_bounds__(IV_THREADS) k_inviter(
     const double* __restrict__ d, const double* __restrict__ e, int64_t n,
@@ -441,83 +469,59 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   double* dm = work + n;
   double* du = work + 2 * n;
   double* du2 = work + 3 * n;
-  double* y = work + 4 * n;
   int8_t* piv = (int8_t*)(work + 5 * n);
   const double small = EPS * tn;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nwarps = IV_THREADS / 32;
-  double lam_prev = 0;
-  for (int64_t i = i0; i < i1; ++i) {
-    if (tid == 0) {
-      // shifts strictly decreasing inside a cluster, at least 10 eps |T| apart
-      double lam = ev[i];
-      if (i > i0) lam = fmin(lam, lam_prev - 10 * EPS * tn);
-      lam_prev = lam;
-      uint32_t h = 2166136261u ^ (uint32_t)(i * 2654435761u);
-      for (int64_t r = 0; r < n; ++r) {  // deterministic start vector, free of structure
-        h ^= (uint32_t)r;
-        h *= 16777619u;
-        y[r] = 0.5 + (double)(h & 0xffff) / 65536.0;
-      }
-      // LU with partial pivoting of T - lam I (tridiagonal, textbook)
-      for (int64_t r = 0; r < n; ++r) {
-        dm[r] = d[r] - lam;
-        du[r] = r < n - 1 ? e[r] : 0.0;
-        dl[r] = r < n - 1 ? e[r] : 0.0;
-        du2[r] = 0.0;
-      }
-      for (int64_t r = 0; r < n - 1; ++r) {
-        const double a = dm[r], b = dl[r];
-        if (fabs(a) >= fabs(b)) {
-          const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
-          dm[r] = aa;
-          const double f = b / aa;
-          dl[r] = f;
-          dm[r + 1] -= f * du[r];
-          piv[r] = 0;
-        } else {
-          const double f = a / b;
-          dm[r] = b;
-          dl[r] = f;
-          const double t = du[r];
-          du[r] = dm[r + 1];
-          dm[r + 1] = t - f * du[r];
-          if (r < n - 2) {
-            du2[r] = du[r + 1];
-            du[r + 1] = -f * du[r + 1];
-          }
-          piv[r] = 1;
-        }
-      }
-      if (fabs(dm[n - 1]) < small) dm[n - 1] = dm[n - 1] < 0 ? -small : small;
+  if (tid == 0) {
+    // LU with partial pivoting of T - lam I (tridiagonal, textbook), lam = ev[i0]
+    const double lam = ev[i0];
+    for (int64_t r = 0; r < n; ++r) {
+      dm[r] = d[r] - lam;
+      du[r] = r < n - 1 ? e[r] : 0.0;
+      dl[r] = r < n - 1 ? e[r] : 0.0;
+      du2[r] = 0.0;
     }
-    __syncthreads();
-    for (int sweep = 0; sweep < 3; ++sweep) {
-      if (tid == 0) {
-        for (int64_t r = 0; r < n - 1; ++r) {
-          if (piv[r] == 0) {
-            y[r + 1] -= dl[r] * y[r];
-          } else {
-            const double t = y[r];
-            y[r] = y[r + 1];
-            y[r + 1] = t - dl[r] * y[r];
-          }
+    for (int64_t r = 0; r < n - 1; ++r) {
+      const double a = dm[r], b = dl[r];
+      if (fabs(a) >= fabs(b)) {
+        const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
+        dm[r] = aa;
+        const double f = b / aa;
+        dl[r] = f;
+        dm[r + 1] -= f * du[r];
+        piv[r] = 0;
+      } else {
+        const double f = a / b;
+        dm[r] = b;
+        dl[r] = f;
+        const double t = du[r];
+        du[r] = dm[r + 1];
+        dm[r + 1] = t - f * du[r];
+        if (r < n - 2) {
+          du2[r] = du[r + 1];
+          du[r + 1] = -f * du[r + 1];
         }
-        // back substitution; near-degenerate eigenvalues give several pivots of eps |T|
-        // whose quotients compound, so the whole vector (solved part and remaining right
-        // hand side alike: the solution of a scaled system is the scaled solution) is
-        // scaled down whenever an entry passes 2^500
-        for (int64_t r = n - 1; r >= 0; --r) {
-          double v = y[r];
-          if (r + 1 < n) v -= du[r] * y[r + 1];
-          if (r + 2 < n) v -= du2[r] * y[r + 2];
-          v /= dm[r];
-          y[r] = v;
-          if (fabs(v) > 0x1p500)
-            for (int64_t q = 0; q < n; ++q) y[q] *= 0x1p-500;
-        }
+        piv[r] = 1;
       }
-      __syncthreads();
+    }
+    if (fabs(dm[n - 1]) < small) dm[n - 1] = dm[n - 1] < 0 ? -small : small;
+  }
+  // deterministic start vectors, free of structure, distinct per member
+  for (int64_t i = i0; i < i1; ++i)
+    for (int64_t r = tid; r < n; r += IV_THREADS) {
+      uint32_t h = 2166136261u ^ (uint32_t)(i * 2654435761u) ^ (uint32_t)(r * 2246822519u);
+      h *= 16777619u;
+      h ^= h >> 15;
+      h *= 2654435761u;
+      Y[i * n + r] = 0.5 + (double)(h & 0xffff) / 65536.0;
+    }
+  __syncthreads();
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_solve(Y + i * n, n, dl, dm, du, du2, piv);
+    __syncthreads();
+    for (int64_t i = i0; i < i1; ++i) {
+      double* y = Y + i * n;
       for (int pass = 0; pass < 2 && i > i0; ++pass) {
         for (int64_t q0 = i0; q0 < i; q0 += IV_CHUNK) {
           const int64_t q1 = min(i, q0 + IV_CHUNK);
@@ -553,8 +557,6 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
       for (int64_t r = tid; r < n; r += IV_THREADS) y[r] *= inv;
       __syncthreads();
     }
-    for (int64_t r = tid; r < n; r += IV_THREADS) Y[i * n + r] = y[r];
-    __syncthreads();
   }
 }
 

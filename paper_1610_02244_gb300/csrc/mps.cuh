@@ -29,6 +29,7 @@ struct tnt_dmrg {
   const tnt_mpo* mpo = nullptr;
   std::vector<tnt::z*> Lenv, Renv;  // Lenv[i]: sites 0..i-1 (i = 0..L); Renv[i]: sites i..L-1
   size_t scratch = 0;
+  cudaEvent_t ev[5] = {};  // phase marks of one update (sweep statistics)
 };
 
 namespace tnt {
