@@ -373,7 +373,7 @@ def run_ours(args, ws, rank, local):
 CLASSES = {
     "cgemm_tf32x3": ("tensor", "flop"), "zgemm_f64": ("alu", "flop"), "op_apply": ("alu", "flop"),
     "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("alu", "flop"),
-    "multiaxpy": ("alu", "flop"), "multidot_cond": ("alu", None), "multiaxpy_cond": ("alu", None), "jacobi_small": ("alu", None), "heig_tridiag": ("alu", "flop"),
+    "multiaxpy": ("alu", "flop"), "multidot_cond": ("alu", None), "multiaxpy_cond": ("alu", None), "heig_tridiag": ("alu", "flop"),
     "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
     "cgemm_grouped": ("tensor", "flop"), "zgemm_grouped": ("alu", "flop"),
     "u1_wop": ("hbm", "byte"), "u1_pack_theta": ("hbm", "byte"), "u1_gather": ("hbm", "byte"),

@@ -147,9 +147,10 @@ int64_t tnt_launch_count(const tnt_ctx* ctx);
 /* Diagnostics: time every launch of one kernel class with CUDA events recorded on the
  * context's stream, and sum its algorithmic work.  Classes and their work unit:
  *   "cgemm_tf32x3" (useful FLOPs 8 M N K of the complex product), "zgemm_f64" (8 M N K),
- *   "op_apply" (FLOPs), "op_mixed", "split_theta", "multidot", "multiaxpy" (bytes read
- *   plus written), "jacobi_small" (none), "heig_tridiag" (FLOPs), "heig_tridiag_eig"
- *   (none), "heig_backtransform" (FLOPs).
+ *   "op_apply" (FLOPs), "op_mixed", "split_theta" (bytes read plus written), "multidot",
+ *   "multiaxpy" (FP64 FLOPs), "heig_tridiag" (FLOPs), "heig_tridiag_eig" (none),
+ *   "heig_backtransform" (FLOPs), "cgemm_grouped", "zgemm_grouped", "oz_gemm" (useful
+ *   FLOPs), "u1_wop", "u1_pack_theta", "u1_gather", "oz_slice" (bytes).
  * NULL or "" switches timing off.  At most 16384 launches are recorded between reads. */
 int tnt_profile_select(tnt_ctx* ctx, const char* kernel_class);
 /* Synchronise the stream; return the summed duration (ms), the number of timed launches

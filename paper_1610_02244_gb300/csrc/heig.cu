@@ -325,6 +325,112 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- one block per CTA
+// The same Householder reduction for many small Hermitian blocks (the charge blocks of a
+// truncated SVD), one CTA per block and all blocks in one launch: no grid barrier, the
+// block (<= TRI_CTA_MAX rows) stays in L2 and the reflector and p live in shared memory.
+// On GB300 an SM retires two FP64 FMAs per clock, so a 115-row block takes about a
+// millisecond on its SM while the others reduce the other blocks.  Reflector j is kept in
+// row j of the block itself (columns 0..m-1), the layout the back-transformation reads:
+// after column j is eliminated, row j is read no more.
+constexpr int TRI_CTA_MAX = 256;
+constexpr int TRI_CTA_THREADS = 256;
+
+struct CtaBlk {
+  int64_t goff;  // block (row-major, n x n) offset in the Gram buffer
+  int64_t off;   // offset of its d, e, tau
+  int n;
+};
+
+__global__ void __launch_bounds__(TRI_CTA_THREADS) k_tridiag_cta(z* __restrict__ G,
+                                                                 const CtaBlk* __restrict__ blks,
+                                                                 double* __restrict__ dAll,
+                                                                 double* __restrict__ eAll,
+                                                                 z* __restrict__ tauAll) {
+  __shared__ z v[TRI_CTA_MAX], w[TRI_CTA_MAX];
+  __shared__ double sh[32];
+  __shared__ double shr[TRI_CTA_THREADS / 32], shi[TRI_CTA_THREADS / 32];
+  __shared__ z s_cf;
+  const CtaBlk B = blks[blockIdx.x];
+  const int64_t n = B.n;
+  z* A = G + B.goff;
+  double* d = dAll + B.off;
+  double* e = eAll + B.off;
+  z* tau = tauAll + B.off;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NW = TRI_CTA_THREADS / 32;
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    const int64_t m = n - j - 1;
+    z t;
+    double beta;
+    make_reflector(A + j * n + j + 1, m, v, &t, &beta, sh);
+    if (tid == 0) {
+      d[j] = A[j * n + j].x;
+      e[j] = beta;
+      tau[j] = t;
+    }
+    // p = t T v over the trailing rows (one warp per row), then s = p^H v
+    double pr = 0, pi = 0;
+    for (int64_t r = warp; r < m; r += NW) {
+      const z* row = A + (j + 1 + r) * n + j + 1;
+      double sr = 0, si = 0;
+      for (int64_t c = lane; c < m; c += 32) {
+        const z x = row[c], y = v[c];
+        sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+        si = fma(x.x, y.y, fma(x.y, y.x, si));
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) {
+        const z pv = zmul(t, zmk(sr, si));
+        w[r] = pv;
+        const z vr = v[r];
+        pr += pv.x * vr.x + pv.y * vr.y;
+        pi += pv.x * vr.y - pv.y * vr.x;
+      }
+    }
+    if (lane == 0) {
+      shr[warp] = pr;
+      shi[warp] = pi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double sa = 0, sb = 0;
+      for (int q = 0; q < NW; ++q) {
+        sa += shr[q];
+        sb += shi[q];
+      }
+      const z ts = zmul(t, zmk(sa, sb));
+      s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+    }
+    __syncthreads();
+    const z cf = s_cf;
+    for (int64_t r = tid; r < m; r += TRI_CTA_THREADS) {  // w = p - t/2 (p^H v) v
+      const z pv = w[r], vv = v[r];
+      w[r] = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pv.x)), fma(cf.x, vv.y, fma(cf.y, vv.x, pv.y)));
+    }
+    __syncthreads();
+    // T <- T - v w^H - w v^H
+    for (int64_t r = warp; r < m; r += NW) {
+      z* row = A + (j + 1 + r) * n + j + 1;
+      const z vr = v[r], wr = w[r];
+      for (int64_t c = lane; c < m; c += 32) {
+        z x = row[c];
+        zsub_mul_conj(x, vr, w[c]);
+        zsub_mul_conj(x, wr, v[c]);
+        row[c] = x;
+      }
+    }
+    __syncthreads();
+    for (int64_t c = tid; c < m; c += TRI_CTA_THREADS) A[j * n + c] = v[c];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d[n - 1] = A[(n - 1) * n + n - 1].x;
+    tau[n - 1] = zmk(0, 0);
+  }
+}
+
 // Number of eigenvalues of T below x from the signs of the leading principal minors
 // p_i = det(T_i - x I), p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm sequence of the
 // characteristic polynomials, Givens' bisection): a sign change between p_{i-1} and p_i
@@ -676,66 +782,22 @@ size_t heig_scratch_bound(int64_t n, int64_t k) {
          (size_t)(1 << 20);
 }
 
-// G (n x n, row-major, Hermitian, destroyed); U (n x k, leading dimension ldu): the
-// eigenvectors of the k largest eigenvalues, in descending order; ev (device, k).
-int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) {
-  if (k < 1 || k > n) return set_err(c, TNT_E_INVALID, "heig_top: k = %lld of n = %lld", (long long)k, (long long)n);
-  if (n > 8192) return set_err(c, TNT_E_UNSUPPORTED, "heig_top: n = %lld > 8192", (long long)n);
+// Second half of the eigensolve: from the tridiagonal form (d, e) and its reflectors
+// (Hv, row j = v_j, row stride ldh; tau) to the eigenvectors of the k largest eigenvalues
+// in U (n x k, leading dimension ldu), descending; ev (device, k).
+int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const double* d,
+                const double* e, z* U, int64_t ldu, double* ev) {
   const size_t top = c->ws.top;
-  z* Hv = (z*)ws_alloc(c, ws_round(sizeof(z) * n * n));
-  z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
-  z* p = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * n));
-  double* d = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
-  double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
-  double* tn = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
-  z* part = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * TRI_MAX_BLOCKS));
-  z* gws = n > TRI_CACHE ? (z*)ws_alloc(c, ws_round(sizeof(z) * 4 * n * TRI_MAX_BLOCKS)) : nullptr;
-  if (n > TRI_CACHE && !gws) {
-    c->ws.top = top;
-    return set_err(c, TNT_E_ALLOC, "scratch exhausted (tridiagonal workspace n=%lld)", (long long)n);
-  }
+  double* tn = (double*)ws_alloc(c, ws_round(sizeof(double)));
   double* work = (double*)ws_alloc(c, ws_round(sizeof(double) * (6 * n * k + k)));
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * n * k));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * n * k));
   z* S = (z*)ws_alloc(c, ws_round(sizeof(z) * k * k));
-  unsigned* bar = (unsigned*)ws_alloc(c, 256);
-  if (!Hv || !tau || !p || !d || !e || !tn || !part || !work || !Y || !U0 || !S || !bar) {
+  if (!tn || !work || !Y || !U0 || !S) {
     c->ws.top = top;
-    return set_err(c, TNT_E_ALLOC, "scratch exhausted (heig_top n=%lld k=%lld)", (long long)n, (long long)k);
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (eigenvectors n=%lld k=%lld)", (long long)n, (long long)k);
   }
   cudaStream_t st = c->stream;
-  {
-    const double nn = (double)n;
-    ProfScope ps(c, "heig_tridiag", 24.0 * (nn - 1) * nn * (2 * nn - 1) / 6.0);
-    const size_t tri_smem = 4 * TRI_CACHE * sizeof(z);
-    static int nsm = 0, occ = 0;
-    if (!nsm) {
-      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_persistent,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
-      TNT_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-      TNT_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_persistent,
-                                                                    TRI_THREADS, tri_smem));
-    }
-    if (occ < 1) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal kernel cannot be resident");
-    TNT_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 256, st));
-    TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status,
-               gws};
-    void* args[] = {&ta};
-    const int nb = std::min(nsm, TRI_MAX_BLOCKS);
-    TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
-                                                dim3(TRI_THREADS), args, tri_smem, st));
-    c->launches += 1;
-  }
-  {
-    int h_status = 0;
-    TNT_CUDA_TRY(c, cudaMemcpyAsync(&h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
-    if (h_status & 2) {
-      cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
-      c->ws.top = top;
-      return set_err(c, TNT_E_TIMEOUT, "tridiagonal reduction: a grid barrier wait expired");
-    }
-  }
   {
     ProfScope ps(c, "heig_tridiag_eig");
     k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, n, k, ev, tn);
@@ -789,6 +851,110 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
     k_copy_cols<<<gsz(n * k), 256, 0, st>>>(U0, n, k, k, U, ldu);
     c->launches++;
   }
+  c->ws.top = top;
+  return r;
+}
+
+// G (n x n, row-major, Hermitian, destroyed); U (n x k, leading dimension ldu): the
+// eigenvectors of the k largest eigenvalues, in descending order; ev (device, k).
+int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) {
+  if (k < 1 || k > n) return set_err(c, TNT_E_INVALID, "heig_top: k = %lld of n = %lld", (long long)k, (long long)n);
+  if (n > 8192) return set_err(c, TNT_E_UNSUPPORTED, "heig_top: n = %lld > 8192", (long long)n);
+  const size_t top = c->ws.top;
+  z* Hv = (z*)ws_alloc(c, ws_round(sizeof(z) * n * n));
+  z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  z* p = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * n));
+  double* d = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
+  double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * n));
+  z* part = (z*)ws_alloc(c, ws_round(sizeof(z) * 2 * TRI_MAX_BLOCKS));
+  z* gws = n > TRI_CACHE ? (z*)ws_alloc(c, ws_round(sizeof(z) * 4 * n * TRI_MAX_BLOCKS)) : nullptr;
+  unsigned* bar = (unsigned*)ws_alloc(c, 256);
+  if (!Hv || !tau || !p || !d || !e || !part || !bar || (n > TRI_CACHE && !gws)) {
+    c->ws.top = top;
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (heig_top n=%lld k=%lld)", (long long)n, (long long)k);
+  }
+  cudaStream_t st = c->stream;
+  {
+    const double nn = (double)n;
+    ProfScope ps(c, "heig_tridiag", 24.0 * (nn - 1) * nn * (2 * nn - 1) / 6.0);
+    const size_t tri_smem = 4 * TRI_CACHE * sizeof(z);
+    static int nsm = 0, occ = 0;
+    if (!nsm) {
+      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_persistent,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
+      TNT_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+      TNT_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_persistent,
+                                                                    TRI_THREADS, tri_smem));
+    }
+    if (occ < 1) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal kernel cannot be resident");
+    TNT_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 256, st));
+    TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status,
+               gws};
+    void* args[] = {&ta};
+    const int nb = std::min(nsm, TRI_MAX_BLOCKS);
+    TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
+                                                dim3(TRI_THREADS), args, tri_smem, st));
+    c->launches += 1;
+  }
+  {
+    int h_status = 0;
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(&h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (h_status & 2) {
+      cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
+      c->ws.top = top;
+      return set_err(c, TNT_E_TIMEOUT, "tridiagonal reduction: a grid barrier wait expired");
+    }
+  }
+  const int r = heig_finish(c, n, k, Hv, tau, d, e, U, ldu, ev);
+  c->ws.top = top;
+  return r;
+}
+
+// Many small blocks (n <= 256 each): one batched reduction launch, then each block's
+// eigenvectors.  blocks[i] = {offset of the n x n block in G (and of its eigenvector
+// columns in U, leading dimension n), n, k}.
+int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, double* ev) {
+  if (blocks.empty()) return TNT_OK;
+  int64_t tot = 0;
+  for (const SmallEig& b : blocks) {
+    if (b.n < 1 || b.n > TRI_CTA_MAX || b.k < 1 || b.k > b.n)
+      return set_err(c, TNT_E_INVALID, "small eigensolve block n=%lld k=%lld", (long long)b.n, (long long)b.k);
+    tot += b.n;
+  }
+  const size_t top = c->ws.top;
+  double* d = (double*)ws_alloc(c, ws_round(sizeof(double) * tot));
+  double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * tot));
+  z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * tot));
+  CtaBlk* dblk = (CtaBlk*)ws_alloc(c, ws_round(sizeof(CtaBlk) * blocks.size()));
+  if (!d || !e || !tau || !dblk) {
+    c->ws.top = top;
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (small eigensolves)");
+  }
+  std::vector<CtaBlk> hb(blocks.size());
+  int64_t off = 0;
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    hb[i] = CtaBlk{blocks[i].goff, off, (int)blocks[i].n};
+    off += blocks[i].n;
+  }
+  cudaStream_t st = c->stream;
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(dblk, hb.data(), sizeof(CtaBlk) * hb.size(), cudaMemcpyHostToDevice, st));
+  {
+    double fl = 0;
+    for (const SmallEig& b : blocks) fl += 24.0 * (double)(b.n - 1) * b.n * (2.0 * b.n - 1) / 6.0;
+    ProfScope ps(c, "heig_tridiag", fl);
+    k_tridiag_cta<<<(unsigned)blocks.size(), TRI_CTA_THREADS, 0, st>>>(G, dblk, d, e, tau);
+    c->launches++;
+    TNT_CHECK_LAUNCH(c);
+  }
+  int r = TNT_OK;
+  for (size_t i = 0; i < blocks.size() && r == TNT_OK; ++i) {
+    const SmallEig& b = blocks[i];
+    r = heig_finish(c, b.n, b.k, G + b.goff, tau + hb[i].off, d + hb[i].off, e + hb[i].off,
+                    U + b.goff, b.n, ev);
+  }
+  // the host table dies at return: the upload above must have completed
+  if (r == TNT_OK) TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
   c->ws.top = top;
   return r;
 }

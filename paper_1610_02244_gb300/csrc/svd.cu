@@ -1,7 +1,7 @@
 // Truncated SVD of the reshaped two-site tensor (App. B.1.2, Eq. 3), FP64, on the GPU.
 //
 // M is block diagonal under U(1) labels (App. A.1.1).  Per block q (rows R_q, columns C_q):
-//   LEFT  side: G = M_q M_q^H, Jacobi eigenvectors U_q (orthonormal), X_q = U_q^H M_q,
+//   LEFT  side: G = M_q M_q^H, eigenvectors U_q (orthonormal), X_q = U_q^H M_q,
 //               sigma_k = |row k of X_q|              (so X = S V^H without dividing by S)
 //   RIGHT side: G = M_q^H M_q, eigenvectors V_q,      Y_q = M_q V_q,
 //               sigma_k = |column k of Y_q|           (so Y = U S)
@@ -10,9 +10,9 @@
 // never formed is |M_q|_F^2 minus the candidates'.  Taking sigma as a projection norm
 // keeps its absolute error at ~eps |M| instead of the sqrt(eps) relative floor of
 // sqrt(lambda).  All candidates are then ordered globally (sigma desc, charge asc, index
-// asc) and cut by the four rules in one kernel.  Blocks up to 64 are diagonalised by
-// cyclic Jacobi (one CTA each, all in one launch); larger ones by Householder
-// tridiagonalisation, bisection and inverse iteration (heig.cu).
+// asc) and cut by the four rules in one kernel.  Every block is diagonalised by Householder
+// tridiagonalisation, bisection and inverse iteration (heig.cu): blocks up to 256 rows are
+// reduced together, one CTA each in one launch, larger ones across the whole GPU.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -22,152 +22,6 @@
 namespace tnt {
 
 namespace {
-constexpr double kEps = 2.220446049250313e-16;
-
-// -------------------------------------------------------------- Jacobi, small blocks
-// One CTA per block (n <= 64), G and V in shared memory, round-robin parallel ordering.
-__device__ __forceinline__ void rr_pair(int t, int r, int np2, int* p, int* q) {
-  // positions 0..np2-1 (np2 even); position 0 fixed, the others rotate by r
-  auto pos = [&](int i) { return i == 0 ? 0 : 1 + ((i - 1 + r) % (np2 - 1)); };
-  int a = pos(t), b = pos(np2 - 1 - t);
-  *p = a < b ? a : b;
-  *q = a < b ? b : a;
-}
-
-// Rotation that annihilates the (p, q) entry of a Hermitian 2 x 2 block [[app, apq],
-// [conj(apq), aqq]]: apq = |apq| e, tau = (aqq - app) / (2 |apq|), t the smaller root of
-// t^2 + 2 tau t - 1 = 0, cs = 1 / sqrt(1 + t^2), sn = t cs.  Written with reciprocal
-// square roots and one division: each FP64 division or square root is a long dependent
-// chain on GB300's FP64 units, and this sits on the critical path of every round.
-__device__ __forceinline__ void jacobi_rot(double app, double aqq, z apq, double* cs,
-                                           double* sn, z* e) {
-  const double ab2 = fma(apq.x, apq.x, apq.y * apq.y);
-  if (ab2 <= 1e-300 || ab2 < 1e-36 * fabs(app * aqq)) {
-    *cs = 1.0;
-    *sn = 0.0;
-    *e = zmk(1.0, 0.0);
-    return;
-  }
-  const double inv_ab = rsqrt(ab2);
-  *e = zmk(apq.x * inv_ab, apq.y * inv_ab);
-  const double tau = (aqq - app) * (0.5 * inv_ab);
-  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
-  const double c = rsqrt(fma(t, t, 1.0));
-  *cs = c;
-  *sn = t * c;
-}
-
-__global__ void __launch_bounds__(256) k_jacobi_small(z* G, z* V, const int64_t* off,
-                                                      const int* dims, int max_sweeps,
-                                                      double tol, int* sweeps_out) {
-  extern __shared__ double smem_d[];
-  const int n = dims[blockIdx.x];
-  if (n <= 0) return;
-  const int64_t o = off[blockIdx.x];
-  z* sG = (z*)smem_d;
-  z* sV = sG + n * n;
-  double* s_cs = (double*)(sV + n * n);
-  double* s_sn = s_cs + 32;
-  z* s_e = (z*)(s_sn + 32);
-  int* s_pq = (int*)(s_e + 32);
-  __shared__ double red_off[256], red_dg[256];
-  __shared__ int s_done;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    sG[e] = G[o + e];
-    sV[e] = (e / n == e % n) ? zmk(1, 0) : zmk(0, 0);
-  }
-  __syncthreads();
-  const int np2 = (n + 1) & ~1;
-  const int npairs = np2 / 2;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    // convergence test before each sweep
-    double mo = 0, md = 0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // squared magnitudes
-      int i = e / n, j = e % n;
-      double a = fma(sG[e].x, sG[e].x, sG[e].y * sG[e].y);
-      if (i == j) md = fmax(md, a); else mo = fmax(mo, a);
-    }
-    red_off[threadIdx.x] = mo;
-    red_dg[threadIdx.x] = md;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0, b = 0;
-      for (int t = 0; t < (int)blockDim.x; ++t) {
-        a = fmax(a, red_off[t]);
-        b = fmax(b, red_dg[t]);
-      }
-      s_done = (a <= tol * tol * b) || (a <= 1e-300);
-    }
-    __syncthreads();
-    if (s_done) break;
-    for (int r = 0; r < np2 - 1; ++r) {
-      if (threadIdx.x < npairs) {
-        int p, q;
-        rr_pair(threadIdx.x, r, np2, &p, &q);
-        double cs = 1, sn = 0;
-        z e = zmk(1, 0);
-        if (q < n) jacobi_rot(sG[p * n + p].x, sG[q * n + q].x, sG[p * n + q], &cs, &sn, &e);
-        s_cs[threadIdx.x] = cs;
-        s_sn[threadIdx.x] = sn;
-        s_e[threadIdx.x] = e;
-        s_pq[2 * threadIdx.x] = p;
-        s_pq[2 * threadIdx.x + 1] = q;
-      }
-      __syncthreads();
-      // rows: G <- J^H G
-      for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
-        int t = e / n, j = e % n;
-        int p = s_pq[2 * t], q = s_pq[2 * t + 1];
-        if (q >= n || s_sn[t] == 0.0) continue;
-        double cs = s_cs[t], sn = s_sn[t];
-        z ep = s_e[t];
-        z gp = sG[p * n + j], gq = sG[q * n + j];
-        z eq = zmul(ep, gq);
-        sG[p * n + j] = zsub(zscale(gp, cs), zscale(eq, sn));
-        sG[q * n + j] = zadd(zscale(gp, sn), zscale(eq, cs));
-      }
-      __syncthreads();
-      // columns: G <- G J, V <- V J
-      for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
-        int t = e / n, i = e % n;
-        int p = s_pq[2 * t], q = s_pq[2 * t + 1];
-        if (q >= n || s_sn[t] == 0.0) continue;
-        double cs = s_cs[t], sn = s_sn[t];
-        z ec = zconj(s_e[t]);
-        z gp = sG[i * n + p], gq = zmul(sG[i * n + q], ec);
-        sG[i * n + p] = zsub(zscale(gp, cs), zscale(gq, sn));
-        sG[i * n + q] = zadd(zscale(gp, sn), zscale(gq, cs));
-        z vp = sV[i * n + p], vq = zmul(sV[i * n + q], ec);
-        sV[i * n + p] = zsub(zscale(vp, cs), zscale(vq, sn));
-        sV[i * n + q] = zadd(zscale(vp, sn), zscale(vq, cs));
-      }
-      __syncthreads();
-    }
-  }
-  // sort eigenpairs by eigenvalue, descending (stable on index); write back
-  __shared__ int perm[64];
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    for (int i = 1; i < n; ++i) {
-      int v = perm[i];
-      double key = sG[v * n + v].x;
-      int j = i - 1;
-      while (j >= 0 && sG[perm[j] * n + perm[j]].x < key) {
-        perm[j + 1] = perm[j];
-        --j;
-      }
-      perm[j + 1] = v;
-    }
-    if (sweeps_out) sweeps_out[blockIdx.x] = sweep;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, k = e % n;
-    V[o + e] = sV[i * n + perm[k]];
-  }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) G[o + k] = zmk(sG[perm[k] * n + perm[k]].x, 0);
-}
 
 // sigma of each candidate: norm of row (LEFT: rows of X_q) or column (RIGHT: of Y_q)
 struct CandBlock {
@@ -353,22 +207,6 @@ unsigned gridn(int64_t n) {
 }
 }  // namespace
 
-// ==================================================================== Jacobi drivers
-int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_n,
-                         int nblocks, int max_n) {
-  if (nblocks <= 0) return TNT_OK;
-  if (max_n > 64) return set_err(c, TNT_E_INVALID, "small Jacobi block %d > 64", max_n);
-  size_t smem = (size_t)2 * max_n * max_n * sizeof(z) + 32 * (2 * sizeof(double) + sizeof(z) +
-                                                              2 * sizeof(int));
-  TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-  ProfScope ps(c, "jacobi_small");
-  k_jacobi_small<<<nblocks, 256, smem, c->stream>>>(G, V, d_off, d_n, 40, 1e-15, nullptr);
-  c->launches++;
-  TNT_CHECK_LAUNCH(c);
-  return TNT_OK;
-}
-
 // ==================================================================== truncated SVD
 size_t svd_scratch_bound(int64_t m, int64_t n) {
   const size_t mx = (size_t)std::max(m, n), mn = (size_t)std::min(m, n);
@@ -508,25 +346,15 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     TNT_TRY(zgemm(c, g));
     TNT_TRY(herm_mirror(c, Gp + B.goff, B.g));
   }
-  // ---- eigensolves: small blocks batched in one launch, large ones one by one
+  // ---- eigensolves: blocks up to 256 rows reduced together (one CTA each, one launch),
+  // larger ones one by one across the whole GPU
   {
-    int max_small = 0, n_small = 0;
+    std::vector<SmallEig> small;
     for (int b = 0; b < nb; ++b)
-      if (bl[b].g <= 64) { max_small = std::max<int>(max_small, (int)bl[b].g); n_small++; }
-    if (n_small > 0) {
-      // blocks > 64 get dim 0 in this launch (skipped)
-      std::vector<int> dims_small(nb);
-      for (int b = 0; b < nb; ++b) dims_small[b] = bl[b].g <= 64 ? (int)bl[b].g : 0;
-      int* d_dims_small = (int*)ws_alloc(c, ws_round(sizeof(int) * nb));
-      if (!d_dims_small) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd dims)");
-      TNT_CUDA_TRY(c, cudaMemcpyAsync(d_dims_small, dims_small.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-      TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // host vector lifetime
-      TNT_TRY(jacobi_small_batched(c, Gp, Vp, d_goff, d_dims_small, nb, max_small));
-    }
-    // larger blocks: Householder tridiagonalisation, bisection, inverse iteration (the k
-    // leading eigenvectors only, columns 0..k-1 of the block's V, leading dimension g)
+      if (bl[b].g <= 256) small.push_back(SmallEig{bl[b].goff, bl[b].g, bl[b].k});
+    TNT_TRY(heig_small_blocks(c, Gp, small, Vp, d_ev));
     for (int b = 0; b < nb; ++b) {
-      if (bl[b].g <= 64) continue;
+      if (bl[b].g <= 256) continue;
       const Blk& B = bl[b];
       if (B.g > 8192) return set_err(c, TNT_E_UNSUPPORTED, "SVD block of dim %lld > 8192", (long long)B.g);
       TNT_TRY(heig_top(c, Gp + B.goff, B.g, B.k, Vp + B.goff, B.g, d_ev));

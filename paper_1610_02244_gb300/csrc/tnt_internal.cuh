@@ -193,13 +193,18 @@ int tridiag_lowest_batched(Ctx* c, const double* d_alpha, const double* d_beta, 
 // Hermitian eigensolvers (FP64 cyclic Jacobi) used by the truncated SVD.
 // Small blocks: one CTA per block (n <= 64), in place on G (packed, each block n_b x n_b at
 // off_g[b]); eigenvectors to V at the same offsets.
-int jacobi_small_batched(Ctx* c, z* G, z* V, const int64_t* d_off, const int* d_n,
-                         int nblocks, int max_n);
+
 // One large block (any n), global-memory rounds.
 // Leading k eigenpairs of one large Hermitian block (Householder, bisection, inverse
 // iteration; heig.cu).  U: n x k with leading dimension ldu; ev: device, k values.
 size_t heig_scratch_bound(int64_t n, int64_t k);
 int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev);
+// a block of heig_small_blocks: offset of its n x n Gram block (and of its eigenvector
+// columns, leading dimension n), its size and the number of eigenvectors wanted
+struct SmallEig {
+  int64_t goff, n, k;
+};
+int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, double* ev);
 
 // Helpers: gather / scatter / conversion
 int gather2d(Ctx* c, const z* src, int64_t src_ld, const int64_t* d_rows, int64_t nr,
