@@ -279,6 +279,16 @@ int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
  * Kept indices are ordered by charge ascending, then lambda descending.
  * FP64 Gram matrix plus FP64 cyclic Jacobi per block: values below ~1e-8 lambda_0 are not
  * resolved to full relative accuracy. */
+/* Automatic blocking (Sec. 6, Fig. of the blocked array; the library's SVD zeroing
+ * tolerance, off (-1) by default as in its system listing, App. B): with tol >= 0, every
+ * truncated SVD of a matrix without charge labels (tnt_svd_trunc with NULL labels, and the
+ * SVDs of unlabelled MPS in DMRG and TEBD) first sets the entries with |M_ij| <= tol to
+ * zero, then groups rows and columns into the connected components of the remaining
+ * non-zero pattern (a row and a column are joined by a non-zero entry) and runs the block
+ * SVD on those blocks, exactly as for charge blocks; the bond labels returned are the
+ * component numbers (ascending in each component's first row).  tol < 0 switches it off.
+ * TNT_E_INVALID for a NaN tolerance. */
+int tnt_set_svd_zero_tol(tnt_ctx* ctx, double tol);
 int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n,
                   const int64_t* h_row_q, const int64_t* h_col_q, int side, int renorm,
                   tnt_cplx* d_U, tnt_cplx* d_X, double* h_S, int64_t* h_bond_q,

@@ -107,3 +107,29 @@ def svd_truncate(M: np.ndarray, row_q: np.ndarray, col_q: np.ndarray, p: TruncPa
         bond_q[k] = q
     info = {"err": err, "disc": float(np.sum(disc ** 2)), "spectrum": sig, "chi": chi}
     return U, S, Vh, bond_q, info
+
+
+def autoblock(M: np.ndarray, tol: float):
+    """Automatic blocking (Sec. 6, figure of the blocked array): entries with |M_ij| <= tol
+    are set to zero, and rows and columns are grouped into the connected components of the
+    remaining non-zero pattern (row i and column j are joined by a non-zero M_ij).  Returns
+    (the zeroed matrix, row labels, column labels); a component is numbered by the order of
+    its first row, components holding columns only come after, in column order."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    m, n = M.shape
+    Mz = np.where(np.abs(M) > tol, M, 0.0)
+    rows, cols = np.nonzero(Mz)
+    adj = sp.coo_matrix((np.ones(len(rows)), (rows, m + cols)), shape=(m + n, m + n))
+    _, comp = connected_components(adj, directed=False)
+    order = {}
+    for v in range(m + n):
+        order.setdefault(comp[v], len(order))
+    lab = np.array([order[comp[v]] for v in range(m + n)], dtype=np.int64)
+    return Mz, lab[:m], lab[m:]
+
+
+def svd_truncate_auto(M: np.ndarray, tol: float, p: TruncParams):
+    """Truncated SVD of M over its automatic blocks (autoblock, then svd_truncate)."""
+    Mz, rq, cq = autoblock(M, tol)
+    return svd_truncate(Mz, rq, cq, p)

@@ -386,13 +386,14 @@ int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n) {
            "Relative truncation tolerance is %g.\n"
            "Absolute truncation tolerance is %g.\n"
            "Truncation error tolerance is %g.\n"
+           "Tolerance for automatic blocking is %g.\n"
            "Current truncation type is %s.\n"
            "SVD type is FP64 Gram plus cyclic Jacobi (GPU).\n"
            "Maximum bond dimension is %lld.\n"
            "Maximum number of iterations for eigenvalue solver is %d.\n"
            "Krylov vectors before restart: %d; eigensolver tolerance %g.\n"
            "H_eff precision: %s.\n",
-           p.trunc_rel, p.trunc_abs, p.trunc_err, tt, (long long)p.chi_max, p.lanczos_maxit,
+           p.trunc_rel, p.trunc_abs, p.trunc_err, ctx->c.svd_zero_tol, tt, (long long)p.chi_max, p.lanczos_maxit,
            p.krylov_cap, p.lanczos_tol, p.precision == TNT_PREC_MIXED ? "split TF32 (tcgen05)" : "FP64");
   return TNT_OK;
 }
@@ -501,6 +502,13 @@ int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
   TNT_TRY(heff_prepare(c, (const z*)d_L, (const z*)d_W1, (const z*)d_W2, (const z*)d_R, chl, d, D,
                        chr, c->params.precision, &p));
   return lanczos_impl(c, p, (z*)d_theta, res);
+}
+
+int tnt_set_svd_zero_tol(tnt_ctx* ctx, double tol) {
+  CTX_CHECK(ctx);
+  ARG_CHECK(ctx, !std::isnan(tol), "tolerance is NaN");
+  ctx->c.svd_zero_tol = tol < 0 ? -1.0 : tol;
+  return TNT_OK;
 }
 
 int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n, const int64_t* h_row_q,

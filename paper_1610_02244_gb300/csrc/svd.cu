@@ -199,6 +199,27 @@ __global__ void k_scatter(const z* __restrict__ Vp, const z* __restrict__ Xp,
   }
 }
 
+// automatic blocking: Mz = M with |M_ij| <= tol set to zero, mask bit j of row i's word
+// j / 32 set where |M_ij| > tol; one thread per 32-column word
+__global__ void k_autoblock(const z* __restrict__ M, int64_t m, int64_t n, double tol,
+                            z* __restrict__ Mz, uint32_t* __restrict__ mask) {
+  const int64_t W = (n + 31) / 32;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m * W;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / W, w = t % W;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t j = w * 32 + b;
+      if (j >= n) break;
+      const z v = M[i * n + j];
+      const bool keep = sqrt(v.x * v.x + v.y * v.y) > tol;
+      Mz[i * n + j] = keep ? v : zmk(0, 0);
+      bits |= keep ? (1u << b) : 0u;
+    }
+    mask[t] = bits;
+  }
+}
+
 unsigned gridn(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 8) b = 152 * 8;
@@ -208,9 +229,13 @@ unsigned gridn(int64_t n) {
 }  // namespace
 
 // ==================================================================== truncated SVD
+static size_t autoblock_bytes(int64_t m, int64_t n) {
+  return ws_round(sizeof(z) * (size_t)m * n) + ws_round(sizeof(uint32_t) * (size_t)m * ((n + 31) / 32));
+}
+
 size_t svd_scratch_bound(int64_t m, int64_t n) {
   const size_t mx = (size_t)std::max(m, n), mn = (size_t)std::min(m, n);
-  return 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mn +
+  return autoblock_bytes(m, n) + 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mn +
          sizeof(KeptIdx) * mn + 12 * 8192 + heig_scratch_bound((int64_t)mx, (int64_t)mn) +
          (size_t)(4 << 20);
 }
@@ -219,6 +244,65 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
                    const int64_t* h_cq, int side, int renorm, z* U, z* X, double* h_S,
                    int64_t* h_bq, tnt_trunc_result* res) {
   const tnt_params& P = c->params;
+  TNT_TRY(ws_reserve(c, c->ws.top + svd_scratch_bound(m, n)));
+  // ---- automatic blocking of an unlabelled matrix (Sec. 6): zero |M_ij| <= tol, then the
+  // connected components of the non-zero pattern are the blocks (union-find on the host
+  // over the bit mask; a component is numbered by its first row, then columns alone)
+  std::vector<int64_t> arq, acq;
+  bool unlabelled = (h_rq == nullptr);
+  if (!unlabelled) {
+    unlabelled = true;
+    for (int64_t i = 1; i < m && unlabelled; ++i) unlabelled = (h_rq[i] == h_rq[0]);
+    for (int64_t j = 0; j < n && unlabelled; ++j) unlabelled = (h_cq[j] == h_rq[0]);
+  }
+  if (unlabelled && c->svd_zero_tol >= 0) {
+    const int64_t W = (n + 31) / 32;
+    z* Mz = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)m * n));
+    uint32_t* dmask = (uint32_t*)ws_alloc(c, ws_round(sizeof(uint32_t) * (size_t)m * W));
+    if (!Mz || !dmask) return set_err(c, TNT_E_ALLOC, "scratch exhausted (automatic blocking)");
+    k_autoblock<<<gridn(m * W), 256, 0, c->stream>>>(M, m, n, c->svd_zero_tol, Mz, dmask);
+    c->launches++;
+    TNT_CHECK_LAUNCH(c);
+    std::vector<uint32_t> hm((size_t)(m * W));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(hm.data(), dmask, sizeof(uint32_t) * hm.size(), cudaMemcpyDeviceToHost, c->stream));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> parent((size_t)(m + n));
+    for (int64_t v = 0; v < m + n; ++v) parent[(size_t)v] = v;
+    auto find = [&](int64_t v) {
+      while (parent[(size_t)v] != v) {
+        parent[(size_t)v] = parent[(size_t)parent[(size_t)v]];
+        v = parent[(size_t)v];
+      }
+      return v;
+    };
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t w = 0; w < W; ++w) {
+        uint32_t bits = hm[(size_t)(i * W + w)];
+        while (bits) {
+          const int b = __builtin_ctz(bits);
+          bits &= bits - 1;
+          const int64_t a = find(i), r = find(m + w * 32 + b);
+          if (a != r) parent[(size_t)std::max(a, r)] = std::min(a, r);
+        }
+      }
+    std::vector<int64_t> id((size_t)(m + n), -1);
+    int64_t next = 0;
+    arq.resize((size_t)m);
+    acq.resize((size_t)n);
+    for (int64_t i = 0; i < m; ++i) {
+      const int64_t r = find(i);
+      if (id[(size_t)r] < 0) id[(size_t)r] = next++;
+      arq[(size_t)i] = id[(size_t)r];
+    }
+    for (int64_t j = 0; j < n; ++j) {
+      const int64_t r = find(m + j);
+      if (id[(size_t)r] < 0) id[(size_t)r] = next++;
+      acq[(size_t)j] = id[(size_t)r];
+    }
+    M = Mz;
+    h_rq = arq.data();
+    h_cq = acq.data();
+  }
   // ---- block structure (host, integer only)
   std::map<int64_t, std::pair<std::vector<int64_t>, std::vector<int64_t>>> blocks;
   for (int64_t i = 0; i < m; ++i) blocks[h_rq ? h_rq[i] : 0].first.push_back(i);
@@ -270,7 +354,6 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   // ---- scratch
   int P2 = 1;
   while (P2 < ntot_vals) P2 <<= 1;
-  TNT_TRY(ws_reserve(c, c->ws.top + svd_scratch_bound(m, n)));
   int64_t* d_rows = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * rows_all.size()));
   int64_t* d_cols = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * cols_all.size()));
   z* Mp = (z*)ws_alloc(c, ws_round(sizeof(z) * mtot));

@@ -65,6 +65,7 @@ struct Ctx {
   // FP64 GEMM engine for large products: 1 = integer-slice emulation on the tensor cores
   // (FP64-accurate), 0 = FP64 FMA only; its slice buffer is owned by the context
   int oz_mode = 1;
+  double svd_zero_tol = -1.0;  // automatic blocking of unlabelled SVDs (< 0: off)
   void* oz_buf = nullptr;
   size_t oz_cap = 0;
 };

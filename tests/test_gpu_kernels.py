@@ -269,3 +269,41 @@ def test_svd_zero_charge_blocks(ctx, side):
     U, X = U.cpu().numpy(), X.cpu().numpy()
     assert np.isfinite(U).all() and np.isfinite(X).all()
     assert np.abs(U @ X - M).max() < 1e-11 * Sr.max()
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_svd_automatic_blocking(ctx, side):
+    """Automatic blocking (Sec. 6): a block-diagonal matrix with rows and columns shuffled
+    and 1e-12 noise everywhere; with the zeroing tolerance 1e-9 the GPU finds the four
+    planted blocks and truncates like the oracle's block-wise SVD of the zeroed matrix.
+    With the tolerance off, the same call is one dense block."""
+    from tests.test_oracle_autoblock import planted
+    M, rows, cols = planted(7, [40, 90, 7, 130], [35, 80, 9, 120])
+    chi_max = 150
+    p = osvd.TruncParams(chi_max=chi_max)
+    Ur, Sr, Vr, bqr, inf_r = osvd.svd_truncate_auto(M, 1e-9, p)
+    Mz, _, _ = osvd.autoblock(M, 1e-9)
+    ctx.set_params(chi_max=chi_max, trunc_err=1e-8, trunc_rel=1e-16)
+    ctx.set_svd_zero_tol(1e-9)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), None, None, side=side)
+    finally:
+        ctx.set_svd_zero_tol(-1)
+        ctx.set_params(chi_max=1 << 40)
+    assert info["n_blocks"] == 4
+    assert info["chi"] == len(Sr)
+    assert np.abs(np.sort(S) - np.sort(Sr)).max() < 1e-12 * Sr.max()
+    # bond labels: the oracle's component numbers (same numbering rule), values per block
+    for q in set(bqr.tolist()):
+        assert np.abs(np.sort(S[bq == q]) - np.sort(Sr[bqr == q])).max() < 1e-12 * Sr.max()
+    U, X = U.cpu().numpy(), X.cpu().numpy()
+    assert np.abs(U @ X - (Ur * Sr) @ Vr).max() < 1e-11 * Sr.max()
+    # off: one dense block of the unzeroed matrix
+    ctx.set_params(chi_max=chi_max, trunc_err=1e-8, trunc_rel=1e-16)
+    try:
+        _, _, S2, _, info2 = ctx.svd_trunc(dev(M), None, None, side=side)
+    finally:
+        ctx.set_params(chi_max=1 << 40)
+    assert info2["n_blocks"] == 1
+    _, Sd, _, _, _ = osvd.svd_truncate(M, np.zeros(M.shape[0], np.int64), np.zeros(M.shape[1], np.int64), p)
+    assert np.abs(np.sort(S2) - np.sort(Sd)).max() < 1e-12 * Sd.max()
