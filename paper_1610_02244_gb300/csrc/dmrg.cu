@@ -90,6 +90,10 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     TNT_TRY(u1_prepare(c, spec, &up));
     if (marks) cudaEventRecord(g->ev[1], c->stream);
     int r = lanczos_run(c, U1MatVec(up), x, lz);
+    if (r == TNT_E_NAN)  // name the update in the message
+      return set_err(c, r, "bond %d (%s, chi %lld|%lld|%lld, compact length %lld): %s", i,
+                     dir > 0 ? "left to right" : "right to left", (long long)chl, (long long)chm,
+                     (long long)chr, (long long)up.n, std::string(c->err).c_str());
     if (r != TNT_OK && r != TNT_E_NOCONV) return r;
     TNT_TRY(u1_convert(c, spec[0], x, theta, 0));
     c->ws.top = t2;

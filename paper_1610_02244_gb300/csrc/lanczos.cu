@@ -69,8 +69,12 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
   const double tol = P.lanczos_tol;
   const double rtol = std::max(tol, 10.0 * u);
   double* hp = c->h_pinned;
-  // v_0 = theta / |theta|
+  // v_0 = theta / |theta| (a zero or non-finite start vector is reported, not iterated)
   TNT_TRY(vec_norm2(c, theta, n, norm2));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(hp, norm2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (!(hp[0] > 0.0) || !std::isfinite(hp[0]))
+    return set_err(c, TNT_E_NAN, "Lanczos start vector has |x|^2 = %g (n = %lld)", hp[0], (long long)n);
   TNT_TRY(vec_normalize(c, theta, V, n, norm2));
   int total = 0;
   bool have_prev = false;
@@ -104,7 +108,8 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
         conv = true;
       if (bk <= rtol * std::fabs(E) * 1e-3 || bk == 0.0) conv = true;
       if (!std::isfinite(E) || !std::isfinite(bk))
-        return set_err(c, TNT_E_NAN, "Lanczos produced a non-finite value at step %d", total);
+        return set_err(c, TNT_E_NAN, "Lanczos produced a non-finite value at step %d (E = %g, beta = %g, %s matvec)",
+                       total, E, bk, precision == TNT_PREC_MIXED ? "split-TF32" : "FP64");
       have_prev = true;
       E_prev = E;
       if (conv || total >= max_matvec) {
