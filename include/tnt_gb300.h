@@ -348,6 +348,16 @@ int tnt_mps_bdagb(tnt_ctx* ctx, const tnt_mps* mps, tnt_cplx* h_rho);
  * with S renormalised (a7), and grows the environment (a8). */
 int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* mps, const tnt_mpo* mpo, tnt_dmrg** out);
 int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
+/* One single-site sweep with subspace expansion on the same handle (the sweep of Sec. 4.3
+ * on one site at a time; App. B's direct sums): sites 0..L-2 left to right, then L-1..1
+ * right to left.  At site i the FP64 eigensolve of L . W . R . M (the one-site H_eff) gives
+ * M; M is enlarged along the bond it hands over by a direct sum with the expansion term
+ * alpha L.W.M (left to right, new index (w', b) with U(1) label q_b + wq[w']) or
+ * alpha W.R.M (right to left, (w, a) with q_a + wq[w]), the neighbour by a zero block, and
+ * the truncated SVD of the enlarged tensor (context parameters, S renormalised) splits it
+ * back.  alpha = 0 is a plain one-site sweep, which cannot enlarge any bond.  Bonds are
+ * capped by the MPS storage (chi_cap).  TNT_E_INVALID for alpha < 0 or non-finite. */
+int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* dmrg, double alpha, tnt_sweep_stats* stats);
 int tnt_dmrg_destroy(tnt_dmrg* dmrg);
 
 /* ------------------------------------------------------------------ FP64 matrix products */

@@ -135,6 +135,259 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
   return TNT_OK;
 }
 
+// ---------------------------------------------------------------- one-site sweep
+// Single-site DMRG with subspace expansion by direct sums (Sec. 4.3 sweep on one site at a
+// time; App. B node algebra: the direct sum that expands one leg, and the one that pads a
+// leg with zeros).  One-site H_eff.M = L . W . R . M in FP64: T1 = L M (GEMM over a), T2 =
+// W T1 (sparse over (w, s)), y = T2 R^T (GEMM over (w', b)).  Left to right, T2 of the
+// optimised M scaled by alpha is the expansion term P[(a' s'), (w' b)]: M~ = [M | P], the
+// neighbour gets zero rows (so only its first chr rows meet the SVD's S V^H), and the new
+// index (w', b) carries the label q_b + wq[w'].  Right to left, the mirror stages give
+// P[(w a), (s' b')] with labels q_a + wq[w]: M~ = [M ; P], the left neighbour gets zero
+// columns.  The SVD of M~ then decides which of the offered directions to keep.
+namespace {
+struct OneSitePlan {
+  const z* R = nullptr;
+  int64_t chl = 0, d = 0, D = 0, chr = 0;
+  const z* L = nullptr;
+  z* X = nullptr;  // T1, chl D x d chr
+  z* Y = nullptr;  // T2, chl d x D chr
+  OpApply op{};
+};
+
+// T1 = scale L M, T2 = W T1 (the first two stages of the left environment growth)
+int onesite_left_stages(Ctx* c, const OneSitePlan& p, const z* M, z scale) {
+  ZGemm g{};
+  g.M = p.chl * p.D; g.N = p.d * p.chr; g.K = p.chl;
+  g.A = p.L; g.a_rs = p.chl; g.a_cs = 1;
+  g.B = M; g.b_rs = p.d * p.chr; g.b_cs = 1;
+  g.C = p.X; g.c_rs = p.d * p.chr;
+  g.alpha = scale; g.beta = zmk(0, 0); g.batch = 1;
+  TNT_TRY(zgemm(c, g));
+  OpApply a = p.op;
+  a.in = p.X;
+  a.out = p.Y;
+  return op_apply(c, a);
+}
+
+int onesite_prepare(Ctx* c, const z* Lenv, const z* Renv, const z* hW, int64_t chl, int64_t d,
+                    int64_t D, int64_t chr, OneSitePlan* p) {
+  p->L = Lenv;
+  p->R = Renv;
+  p->chl = chl;
+  p->d = d;
+  p->D = D;
+  p->chr = chr;
+  const size_t nx = (size_t)chl * D * d * chr;
+  p->X = (z*)ws_alloc(c, ws_round(sizeof(z) * nx));
+  p->Y = (z*)ws_alloc(c, ws_round(sizeof(z) * nx));
+  if (!p->X || !p->Y) return set_err(c, TNT_E_ALLOC, "scratch exhausted (one-site plan)");
+  // Y[a'][(s' w')][m] = sum_{w,s} W[w,w',s',s] X[a'][(w s)][m]
+  const int nI = (int)(d * D), nJ = (int)(D * d);
+  std::vector<z> op((size_t)nI * nJ);
+  for (int64_t so = 0; so < d; ++so)
+    for (int64_t wo = 0; wo < D; ++wo)
+      for (int64_t w = 0; w < D; ++w)
+        for (int64_t s = 0; s < d; ++s)
+          op[(size_t)((so * D + wo) * nJ + (w * d + s))] = hW[(size_t)(((w * D + wo) * d + so) * d + s)];
+  std::vector<int64_t> in_off(nJ), out_off(nI);
+  for (int j = 0; j < nJ; ++j) in_off[j] = (int64_t)j * chr;
+  for (int i = 0; i < nI; ++i) out_off[i] = (int64_t)i * chr;
+  TNT_TRY(op_upload(c, op, nI, nJ, in_off, out_off, &p->op));
+  p->op.B0 = chl; p->op.B1 = 1; p->op.B2 = chr;
+  p->op.is0 = D * d * chr; p->op.os0 = d * D * chr;
+  p->op.is2 = p->op.os2 = 1;
+  return TNT_OK;
+}
+
+struct OneSiteMatVec : MatVec {
+  const OneSitePlan& p;
+  explicit OneSiteMatVec(const OneSitePlan& pp) : p(pp) { n = pp.chl * pp.d * pp.chr; }
+  int apply(Ctx* c, const z* x, z* y, int) const override {
+    TNT_TRY(onesite_left_stages(c, p, x, zmk(1, 0)));
+    // y[(a' s')][b'] = sum_{(w' b)} T2[(a' s')][(w' b)] R[b'][(w' b)]
+    ZGemm g{};
+    g.M = p.chl * p.d; g.N = p.chr; g.K = p.D * p.chr;
+    g.A = p.Y; g.a_rs = p.D * p.chr; g.a_cs = 1;
+    g.B = p.R; g.b_rs = 1; g.b_cs = p.D * p.chr;
+    g.C = y; g.c_rs = p.chr;
+    g.alpha = zmk(1, 0); g.beta = zmk(0, 0); g.batch = 1;
+    return zgemm(c, g);
+  }
+};
+
+// P[(w a)][(s' b')] = scale sum W[w,w',s',s] R[b',w',b] M[a,s,b] (the first two stages of
+// the right environment growth), written to out
+int onesite_right_expansion(Ctx* c, const z* Renv, const z* hW, const z* M, int64_t chl,
+                            int64_t d, int64_t D, int64_t chr, z scale, z* out) {
+  const size_t nx = (size_t)chl * d * chr * D;
+  z* X = (z*)ws_alloc(c, ws_round(sizeof(z) * nx));
+  if (!X) return set_err(c, TNT_E_ALLOC, "scratch exhausted (one-site expansion)");
+  ZGemm g{};
+  g.M = chl * d; g.N = chr * D; g.K = chr;
+  g.A = M; g.a_rs = chr; g.a_cs = 1;
+  g.B = Renv; g.b_rs = 1; g.b_cs = chr;
+  g.C = X; g.c_rs = chr * D;
+  g.alpha = scale; g.beta = zmk(0, 0); g.batch = 1;
+  TNT_TRY(zgemm(c, g));
+  const int nI = (int)(D * d), nJ = (int)(d * D);
+  std::vector<z> op((size_t)nI * nJ);
+  for (int64_t w = 0; w < D; ++w)
+    for (int64_t so = 0; so < d; ++so)
+      for (int64_t s = 0; s < d; ++s)
+        for (int64_t wi = 0; wi < D; ++wi)
+          op[(size_t)((w * d + so) * nJ + (s * D + wi))] = hW[(size_t)(((w * D + wi) * d + so) * d + s)];
+  std::vector<int64_t> in_off(nJ), out_off(nI);
+  for (int64_t s = 0; s < d; ++s)
+    for (int64_t wi = 0; wi < D; ++wi) in_off[(size_t)(s * D + wi)] = s * chr * D + wi;
+  for (int64_t w = 0; w < D; ++w)
+    for (int64_t so = 0; so < d; ++so) out_off[(size_t)(w * d + so)] = w * chl * d * chr + so * chr;
+  OpApply a{};
+  TNT_TRY(op_upload(c, op, nI, nJ, in_off, out_off, &a));
+  a.in = X; a.out = out;
+  a.B0 = chl; a.B1 = 1; a.B2 = chr;
+  a.is0 = d * chr * D; a.is2 = D;
+  a.os0 = d * chr; a.os2 = 1;
+  return op_apply(c, a);
+}
+}  // namespace
+
+// one single-site update at site i; dir > 0 hands the centre to i + 1, dir < 0 to i - 1
+static int dmrg1_update(Ctx* c, tnt_dmrg* g, int i, int dir, double alpha,
+                        tnt_lanczos_result* lz, tnt_trunc_result* tr) {
+  tnt_mps* m = g->mps;
+  const tnt_mpo* o = g->mpo;
+  const int64_t d = m->d, D = o->D, chl = m->chi[i], chr = m->chi[i + 1];
+  const int64_t n = chl * d * chr;
+  const size_t top = c->ws.top;
+  OneSitePlan p;
+  TNT_TRY(onesite_prepare(c, g->Lenv[i], g->Renv[i + 1], o->hW[(size_t)i].data(), chl, d, D, chr, &p));
+  z* x = (z*)ws_alloc(c, ws_round(sizeof(z) * n));
+  if (!x) return set_err(c, TNT_E_ALLOC, "scratch exhausted (one-site tensor)");
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(x, m->A[i], sizeof(z) * n, cudaMemcpyDeviceToDevice, c->stream));
+  {
+    tnt_params pp = c->params;  // the one-site matvec is FP64
+    pp.precision = TNT_PREC_FP64;
+    ParamsGuard pg(c, pp);
+    const int r = lanczos_run(c, OneSiteMatVec(p), x, lz);
+    if (r != TNT_OK && r != TNT_E_NOCONV) return r;
+  }
+  std::vector<int> wq((size_t)D, 0);
+  if ((int64_t)o->wq.size() == D) wq = o->wq;
+  const z sc = zmk(alpha, 0);
+  if (dir > 0) {
+    const std::vector<int64_t> ql = labels_or_zero(m, i), qr = labels_or_zero(m, i + 1);
+    const int64_t ncol = chr + (alpha > 0 ? D * chr : 0);
+    z* Mt = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chl * d * ncol)));
+    if (!Mt) return set_err(c, TNT_E_ALLOC, "scratch exhausted (expanded tensor)");
+    TNT_CUDA_TRY(c, cudaMemcpy2DAsync(Mt, sizeof(z) * ncol, x, sizeof(z) * chr, sizeof(z) * chr,
+                                      (size_t)(chl * d), cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<int64_t> rq((size_t)(chl * d)), cq((size_t)ncol);
+    for (int64_t a = 0; a < chl; ++a)
+      for (int64_t s = 0; s < d; ++s) rq[(size_t)(a * d + s)] = m->labelled ? ql[(size_t)a] + s : 0;
+    for (int64_t b = 0; b < chr; ++b) cq[(size_t)b] = m->labelled ? qr[(size_t)b] : 0;
+    if (alpha > 0) {
+      TNT_TRY(onesite_left_stages(c, p, x, sc));
+      TNT_CUDA_TRY(c, cudaMemcpy2DAsync(Mt + chr, sizeof(z) * ncol, p.Y, sizeof(z) * D * chr,
+                                        sizeof(z) * D * chr, (size_t)(chl * d),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+      for (int64_t w = 0; w < D; ++w)
+        for (int64_t b = 0; b < chr; ++b)
+          cq[(size_t)(chr + w * chr + b)] = m->labelled ? qr[(size_t)b] + wq[(size_t)w] : 0;
+    }
+    const int64_t capk = std::min<int64_t>(m->cap[i + 1], std::min(chl * d, ncol));
+    z* Xs = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(capk * ncol)));
+    if (!Xs) return set_err(c, TNT_E_ALLOC, "scratch exhausted (expanded factor)");
+    std::vector<double> S((size_t)capk);
+    std::vector<int64_t> bq((size_t)capk);
+    {
+      tnt_params pp = c->params;
+      pp.chi_max = std::min(pp.chi_max, m->cap[i + 1]);
+      ParamsGuard pg(c, pp);
+      TNT_TRY(svd_trunc_impl(c, Mt, chl * d, ncol, rq.data(), cq.data(), TNT_SVD_LEFT, 1, m->A[i],
+                             Xs, S.data(), bq.data(), tr));
+    }
+    const int64_t k = tr->chi, chn = m->chi[i + 2];
+    // A_{i+1} <- (S V^H)[:, :chr] A_{i+1}: the zero rows of the padded neighbour drop out
+    z* Bn = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(k * d * chn)));
+    if (!Bn) return set_err(c, TNT_E_ALLOC, "scratch exhausted (one-site neighbour)");
+    ZGemm gm{};
+    gm.M = k; gm.N = d * chn; gm.K = chr;
+    gm.A = Xs; gm.a_rs = ncol; gm.a_cs = 1;
+    gm.B = m->A[i + 1]; gm.b_rs = d * chn; gm.b_cs = 1;
+    gm.C = Bn; gm.c_rs = d * chn;
+    gm.alpha = zmk(1, 0); gm.beta = zmk(0, 0); gm.batch = 1;
+    TNT_TRY(zgemm(c, gm));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(m->A[i + 1], Bn, sizeof(z) * (size_t)(k * d * chn),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    m->chi[i + 1] = k;
+    if (m->labelled) m->q[i + 1].assign(bq.begin(), bq.begin() + k);
+  } else {
+    const std::vector<int64_t> ql = labels_or_zero(m, i), qr = labels_or_zero(m, i + 1);
+    const int64_t nrow = chl + (alpha > 0 ? D * chl : 0);
+    z* Mt = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(nrow * d * chr)));
+    if (!Mt) return set_err(c, TNT_E_ALLOC, "scratch exhausted (expanded tensor)");
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(Mt, x, sizeof(z) * n, cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<int64_t> rq((size_t)nrow), cq((size_t)(d * chr));
+    for (int64_t a = 0; a < chl; ++a) rq[(size_t)a] = m->labelled ? ql[(size_t)a] : 0;
+    for (int64_t s = 0; s < d; ++s)
+      for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s * chr + b)] = m->labelled ? qr[(size_t)b] - s : 0;
+    if (alpha > 0) {
+      TNT_TRY(onesite_right_expansion(c, g->Renv[i + 1], o->hW[(size_t)i].data(), x, chl, d, D, chr,
+                                      sc, Mt + n));
+      for (int64_t w = 0; w < D; ++w)
+        for (int64_t a = 0; a < chl; ++a)
+          rq[(size_t)(chl + w * chl + a)] = m->labelled ? ql[(size_t)a] + wq[(size_t)w] : 0;
+    }
+    const int64_t capk = std::min<int64_t>(m->cap[i], std::min(nrow, d * chr));
+    z* US = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(nrow * capk)));
+    if (!US) return set_err(c, TNT_E_ALLOC, "scratch exhausted (expanded factor)");
+    std::vector<double> S((size_t)capk);
+    std::vector<int64_t> bq((size_t)capk);
+    {
+      tnt_params pp = c->params;
+      pp.chi_max = std::min(pp.chi_max, m->cap[i]);
+      ParamsGuard pg(c, pp);
+      TNT_TRY(svd_trunc_impl(c, Mt, nrow, d * chr, rq.data(), cq.data(), TNT_SVD_RIGHT, 1, US,
+                             m->A[i], S.data(), bq.data(), tr));
+    }
+    const int64_t k = tr->chi, chp = m->chi[i - 1];
+    // A_{i-1} <- A_{i-1} (U S)[:chl, :]: the zero columns of the padded neighbour drop out
+    z* An = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)(chp * d * k)));
+    if (!An) return set_err(c, TNT_E_ALLOC, "scratch exhausted (one-site neighbour)");
+    ZGemm gm{};
+    gm.M = chp * d; gm.N = k; gm.K = chl;
+    gm.A = m->A[i - 1]; gm.a_rs = chl; gm.a_cs = 1;
+    gm.B = US; gm.b_rs = k; gm.b_cs = 1;
+    gm.C = An; gm.c_rs = k;
+    gm.alpha = zmk(1, 0); gm.beta = zmk(0, 0); gm.batch = 1;
+    TNT_TRY(zgemm(c, gm));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(m->A[i - 1], An, sizeof(z) * (size_t)(chp * d * k),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    m->chi[i] = k;
+    if (m->labelled) m->q[i].assign(bq.begin(), bq.begin() + k);
+  }
+  c->ws.top = top;
+  return TNT_OK;
+}
+
+static size_t dmrg1_scratch_bound(const tnt_mps* m, int D, const tnt_params& p) {
+  size_t best = 0;
+  for (int i = 0; i < m->L; ++i) {
+    const int64_t chl = m->cap[i], chr = m->cap[i + 1], d = m->d;
+    const int64_t n = chl * d * chr;
+    const size_t plan = 2 * ws_round(sizeof(z) * (size_t)(chl * D * d * chr)) + (size_t)(1 << 20);
+    size_t b = plan + ws_round(sizeof(z) * n) + lanczos_scratch_bound(n, p.krylov_cap);
+    const int64_t wide = chr * (1 + D), tall = chl * (1 + D);
+    b = std::max(b, plan + ws_round(sizeof(z) * n) + 3 * ws_round(sizeof(z) * (size_t)(chl * d * wide)) +
+                        svd_scratch_bound(chl * d, wide) + ws_round(sizeof(z) * (size_t)(chl * d * chr)));
+    b = std::max(b, plan + ws_round(sizeof(z) * n) + 3 * ws_round(sizeof(z) * (size_t)(tall * d * chr)) +
+                        svd_scratch_bound(tall, d * chr) + ws_round(sizeof(z) * (size_t)(chl * d * chr * D)));
+    best = std::max(best, b);
+  }
+  return best + (size_t)(8 << 20);
+}
+
 static size_t dmrg_scratch_bound(const tnt_mps* m, int D, const tnt_params& p) {
   size_t best = 0;
   for (int i = 0; i + 1 < m->L; ++i) {
@@ -557,6 +810,54 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
     if (r == TNT_OK) r = dmrg_env_right(c, g, i + 1);
     cudaEventRecord(g->ev[4], c->stream);
     if (r == TNT_OK) phases();
+    account(lz, tr);
+  }
+  ws_reset(c);
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st->seconds = ms * 1e-3;
+  st->E = E;
+  st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
+  return r;
+}
+
+int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st) {
+  if (!ctx || !g || !st || g->ctx != ctx || !(alpha >= 0) || !std::isfinite(alpha)) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mps* m = g->mps;
+  const int L = m->L;
+  *st = tnt_sweep_stats{};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  ws_reset(c);
+  TNT_TRY(ws_reserve(c, std::max(g->scratch, dmrg1_scratch_bound(m, g->mpo->D, c->params))));
+  double E = 0;
+  auto account = [&](const tnt_lanczos_result& lz, const tnt_trunc_result& tr) {
+    st->total_matvecs += lz.n_matvec;
+    st->unconverged += lz.converged ? 0 : 1;
+    st->max_err = std::max(st->max_err, tr.err);
+    st->max_disc = std::max(st->max_disc, tr.disc);
+    E = lz.E_rq;
+  };
+  int r = TNT_OK;
+  for (int i = 0; i + 1 < L && r == TNT_OK; ++i) {
+    tnt_lanczos_result lz{};
+    tnt_trunc_result tr{};
+    r = dmrg1_update(c, g, i, +1, alpha, &lz, &tr);
+    if (r == TNT_OK) r = dmrg_env_left(c, g, i);
+    account(lz, tr);
+  }
+  for (int i = L - 1; i >= 1 && r == TNT_OK; --i) {
+    tnt_lanczos_result lz{};
+    tnt_trunc_result tr{};
+    r = dmrg1_update(c, g, i, -1, alpha, &lz, &tr);
+    if (r == TNT_OK) r = dmrg_env_right(c, g, i);
     account(lz, tr);
   }
   ws_reset(c);

@@ -435,6 +435,12 @@ class Dmrg:
         self.ctx._chk(self.ctx.lib.tnt_dmrg_sweep(self.ctx.h, self.h, C.byref(st)))
         return _struct_dict(st)
 
+    def sweep1(self, alpha: float) -> dict:
+        """One single-site sweep with subspace expansion (mixing factor alpha)."""
+        st = L.tnt_sweep_stats()
+        self.ctx._chk(self.ctx.lib.tnt_dmrg_sweep1(self.ctx.h, self.h, float(alpha), C.byref(st)))
+        return _struct_dict(st)
+
     def __del__(self):
         if getattr(self, "h", None):
             self.ctx.lib.tnt_dmrg_destroy(self.h)
