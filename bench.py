@@ -738,6 +738,55 @@ def run_spin1_dmrg(args, ws, rank, local):
     return 0
 
 
+def run_spin1_dmrg1(args, ws, rank, local):
+    """--workload spin1_dmrg1: single-site sweeps with subspace expansion of the spin-1
+    Heisenberg chain, L = 101, chi = 200, U(1) in S^z (the chain of the paper's Table 1);
+    W warm-up sweeps with alpha = 1e-3 10^-s, then K timed sweeps at alpha = 1e-6;
+    metric s/sweep (2(L-1) one-site updates, FP64 eigensolves)."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    chi = args.chi or SPIN_DMRG_CHI
+    ctx.set_params(chi_max=chi, precision=tnt.TNT_PREC_FP64, lanczos_tol=1e-12,
+                   lanczos_maxit=300, krylov_cap=32)
+    ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if args.fp64_gemm == "tc" else tnt.TNT_FP64_GEMM_FMA)
+    N = SPIN_L * SPIN_TWO_S // 2
+    A, q = synth.random_charged_mps(synth.rng(0), SPIN_L, SPIN_TWO_S + 1, N, chi, "gauss", 2.0)
+    mps = ctx.mps_create(A, q, chi_cap=chi)
+    dm = ctx.dmrg_create(mps, ctx.mpo_spin_heisenberg(SPIN_L, SPIN_TWO_S, 1.0))
+    hist = [dm.sweep1(1e-3 * 10.0 ** (-s)) for s in range(max(1, args.warmup))]
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            hist.append(dm.sweep1(1e-6))
+        e1.record(st)
+        torch.cuda.synchronize()
+    s_sweep = dist_max(e0.elapsed_time(e1) * 1e-3 / args.steps, ws)
+    if rank == 0:
+        line = {"metric": METRIC, "value": s_sweep, "unit": "s/sweep", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_sweep * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"single-site DMRG sweep with subspace expansion, spin-1 "
+                                       f"Heisenberg L=101 chi={chi}, U(1) in S^z, S^z_total=0",
+                           "fp64_gemm": args.fp64_gemm},
+                "sweeps": [{k: h[k] for k in ("E", "max_err", "total_matvecs", "unconverged",
+                                              "seconds", "max_chi")} for h in hist],
+                "cpu_baseline": None, "gpu_launches": ctx.launch_count() - launches0,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def _oracle_spin_dmrg_sample(mps, chi):
     """The oracle's two-site update timed at the two central bonds of the GPU's state (centre
     moved there by the oracle's exact SVD moves, environments grown by the oracle), scaled
@@ -890,7 +939,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["update", "u1", "chains", "dmrg", "tebd",
-                                           "spin1_dmrg", "spin1_tebd"],
+                                           "spin1_dmrg", "spin1_dmrg1", "spin1_tebd"],
                     default="update")
     ap.add_argument("--chi", type=int, default=None,
                     help="bond dimension of the spin1_dmrg / spin1_tebd workloads (default: "
@@ -912,6 +961,8 @@ def main():
         return run_tebd(args, ws, rank, local)
     if args.workload == "spin1_dmrg":
         return run_spin1_dmrg(args, ws, rank, local)
+    if args.workload == "spin1_dmrg1":
+        return run_spin1_dmrg1(args, ws, rank, local)
     if args.workload == "spin1_tebd":
         return run_spin1_tebd(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
