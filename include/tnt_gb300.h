@@ -289,6 +289,14 @@ int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
  * component numbers (ascending in each component's first row).  tol < 0 switches it off.
  * TNT_E_INVALID for a NaN tolerance. */
 int tnt_set_svd_zero_tol(tnt_ctx* ctx, double tol);
+/* The host half of automatic blocking (no GPU needed): the connected components of a
+ * bipartite non-zero pattern, rows 0..m-1 and columns 0..n-1, bit (j % 32) of
+ * h_mask[i * ceil(n/32) + j / 32] set where M_ij is non-zero.  h_row_q (m) and h_col_q (n)
+ * get component numbers: numbered by each component's first row, components of columns
+ * alone after them in column order; *h_count their number.  Host arrays, the caller's.
+ * TNT_E_INVALID on a null pointer or m, n < 1. */
+int tnt_autoblock_components(int64_t m, int64_t n, const uint32_t* h_mask, int64_t* h_row_q,
+                             int64_t* h_col_q, int64_t* h_count);
 int tnt_svd_trunc(tnt_ctx* ctx, const tnt_cplx* d_M, int64_t m, int64_t n,
                   const int64_t* h_row_q, const int64_t* h_col_q, int side, int renorm,
                   tnt_cplx* d_U, tnt_cplx* d_X, double* h_S, int64_t* h_bond_q,

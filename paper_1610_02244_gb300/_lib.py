@@ -135,6 +135,7 @@ SIGNATURES = {
                                       C.POINTER(tnt_lanczos_result)],
     "tnt_set_graphs": [P, I],
     "tnt_set_svd_zero_tol": [P, D],
+    "tnt_autoblock_components": [C.c_int64, C.c_int64, P, P, P, P],
     "tnt_matmul": [P, I64, I64, I64, P, I64, I64, I, P, I64, I64, I, P, I64],
     "tnt_set_fp64_gemm": [P, I],
     "tnt_u1_tiles": [P, I, C.POINTER(tnt_u1_problem), C.POINTER(C.c_int)],

@@ -229,6 +229,48 @@ unsigned gridn(int64_t n) {
 }  // namespace
 
 // ==================================================================== truncated SVD
+// connected components of the bipartite non-zero pattern (rows 0..m-1, columns m..m+n-1;
+// bit j % 32 of mask[i * W + j / 32] marks a non-zero M_ij, W = ceil(n / 32)), union-find
+// with path halving; a component is numbered by its first row, components of columns alone
+// follow in column order.  Returns the number of components.
+int64_t autoblock_components(int64_t m, int64_t n, const uint32_t* mask, int64_t* row_q,
+                             int64_t* col_q) {
+  const int64_t W = (n + 31) / 32;
+  std::vector<int64_t> parent((size_t)(m + n));
+  for (int64_t v = 0; v < m + n; ++v) parent[(size_t)v] = v;
+  auto find = [&](int64_t v) {
+    while (parent[(size_t)v] != v) {
+      parent[(size_t)v] = parent[(size_t)parent[(size_t)v]];
+      v = parent[(size_t)v];
+    }
+    return v;
+  };
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t w = 0; w < W; ++w) {
+      uint32_t bits = mask[(size_t)(i * W + w)];
+      while (bits) {
+        const int b = __builtin_ctz(bits);
+        bits &= bits - 1;
+        if (w * 32 + b >= n) break;
+        const int64_t a = find(i), r = find(m + w * 32 + b);
+        if (a != r) parent[(size_t)std::max(a, r)] = std::min(a, r);
+      }
+    }
+  std::vector<int64_t> id((size_t)(m + n), -1);
+  int64_t next = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t r = find(i);
+    if (id[(size_t)r] < 0) id[(size_t)r] = next++;
+    row_q[i] = id[(size_t)r];
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t r = find(m + j);
+    if (id[(size_t)r] < 0) id[(size_t)r] = next++;
+    col_q[j] = id[(size_t)r];
+  }
+  return next;
+}
+
 static size_t autoblock_bytes(int64_t m, int64_t n) {
   return ws_round(sizeof(z) * (size_t)m * n) + ws_round(sizeof(uint32_t) * (size_t)m * ((n + 31) / 32));
 }
@@ -266,39 +308,9 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     std::vector<uint32_t> hm((size_t)(m * W));
     TNT_CUDA_TRY(c, cudaMemcpyAsync(hm.data(), dmask, sizeof(uint32_t) * hm.size(), cudaMemcpyDeviceToHost, c->stream));
     TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    std::vector<int64_t> parent((size_t)(m + n));
-    for (int64_t v = 0; v < m + n; ++v) parent[(size_t)v] = v;
-    auto find = [&](int64_t v) {
-      while (parent[(size_t)v] != v) {
-        parent[(size_t)v] = parent[(size_t)parent[(size_t)v]];
-        v = parent[(size_t)v];
-      }
-      return v;
-    };
-    for (int64_t i = 0; i < m; ++i)
-      for (int64_t w = 0; w < W; ++w) {
-        uint32_t bits = hm[(size_t)(i * W + w)];
-        while (bits) {
-          const int b = __builtin_ctz(bits);
-          bits &= bits - 1;
-          const int64_t a = find(i), r = find(m + w * 32 + b);
-          if (a != r) parent[(size_t)std::max(a, r)] = std::min(a, r);
-        }
-      }
-    std::vector<int64_t> id((size_t)(m + n), -1);
-    int64_t next = 0;
     arq.resize((size_t)m);
     acq.resize((size_t)n);
-    for (int64_t i = 0; i < m; ++i) {
-      const int64_t r = find(i);
-      if (id[(size_t)r] < 0) id[(size_t)r] = next++;
-      arq[(size_t)i] = id[(size_t)r];
-    }
-    for (int64_t j = 0; j < n; ++j) {
-      const int64_t r = find(m + j);
-      if (id[(size_t)r] < 0) id[(size_t)r] = next++;
-      acq[(size_t)j] = id[(size_t)r];
-    }
+    autoblock_components(m, n, hm.data(), arq.data(), acq.data());
     M = Mz;
     h_rq = arq.data();
     h_cq = acq.data();
@@ -546,3 +558,10 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
 }
 
 }  // namespace tnt
+
+extern "C" int tnt_autoblock_components(int64_t m, int64_t n, const uint32_t* h_mask,
+                                        int64_t* h_row_q, int64_t* h_col_q, int64_t* h_count) {
+  if (m < 1 || n < 1 || !h_mask || !h_row_q || !h_col_q || !h_count) return TNT_E_INVALID;
+  *h_count = tnt::autoblock_components(m, n, h_mask, h_row_q, h_col_q);
+  return TNT_OK;
+}

@@ -68,6 +68,24 @@ def bond_gate(h, tau) -> np.ndarray:
     return out
 
 
+def autoblock_components(nonzero: np.ndarray):
+    """Component labels of a boolean non-zero pattern (tnt_autoblock_components, host only):
+    (row labels, column labels, count)."""
+    nz = np.asarray(nonzero, dtype=bool)
+    m, n = nz.shape
+    W = (n + 31) // 32
+    pad = np.zeros((m, W * 32), dtype=bool)
+    pad[:, :n] = nz
+    mask = np.packbits(pad.reshape(m, W, 4, 8)[..., ::-1], axis=-1).reshape(m, W, 4)
+    mask = np.ascontiguousarray(mask.view(np.uint32).reshape(m, W))  # little endian words
+    rq = np.zeros(m, dtype=np.int64)
+    cq = np.zeros(n, dtype=np.int64)
+    cnt = C.c_int64()
+    L.check(None, L.load().tnt_autoblock_components(m, n, mask.ctypes.data, rq.ctypes.data,
+                                                     cq.ctypes.data, C.byref(cnt)))
+    return rq, cq, cnt.value
+
+
 def params_default() -> dict:
     p = L.tnt_params()
     L.check(None, L.load().tnt_params_default(C.byref(p)))
