@@ -277,8 +277,10 @@ int tnt_lanczos_ground(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
  * Capacity: d_U holds m * cap, d_X holds cap * n, h_S and h_bond_q hold cap values, with
  * cap = min(m, n, chi_max); outputs are written densely with leading dimension chi.
  * Kept indices are ordered by charge ascending, then lambda descending.
- * FP64 Gram matrix plus FP64 cyclic Jacobi per block: values below ~1e-8 lambda_0 are not
- * resolved to full relative accuracy. */
+ * Per block an FP64 Gram matrix and its leading eigenvectors (Householder tridiagonal form,
+ * bisection, inverse iteration); each sigma is the norm of a projection (a row of U^H M or
+ * a column of M V), so its absolute error is ~eps |M|: values far below eps^(1/2) sigma_0
+ * keep their absolute, not their relative, accuracy. */
 /* Automatic blocking (Sec. 6, Fig. of the blocked array; the library's SVD zeroing
  * tolerance, off (-1) by default as in its system listing, App. B): with tol >= 0, every
  * truncated SVD of a matrix without charge labels (tnt_svd_trunc with NULL labels, and the

@@ -388,7 +388,7 @@ int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n) {
            "Truncation error tolerance is %g.\n"
            "Tolerance for automatic blocking is %g.\n"
            "Current truncation type is %s.\n"
-           "SVD type is FP64 Gram plus cyclic Jacobi (GPU).\n"
+           "SVD type is FP64 Gram plus tridiagonal eigensolver (GPU).\n"
            "Maximum bond dimension is %lld.\n"
            "Maximum number of iterations for eigenvalue solver is %d.\n"
            "Krylov vectors before restart: %d; eigensolver tolerance %g.\n"

@@ -7,13 +7,14 @@
 //      p = tau A v, w = p - (tau/2)(p^H v) v, A <- A - v w^H - w v^H.
 //   2. Multisection on Sturm counts of T for eigenvalues n-1, ..., n-k (one warp each),
 //      to full precision.
-//   3. Inverse iteration on T - lambda I (pivoted tridiagonal LU, three sweeps); inside a
-//      cluster of eigenvalues closer than 1e3 eps |T| the shifts are separated by 10 eps |T|
-//      and each iterate is re-orthogonalised against the cluster's earlier vectors.
+//   3. Inverse iteration on T - lambda I (pivoted tridiagonal LU, three sweeps); a cluster
+//      of eigenvalues closer than 1e3 eps |T| shares one factorisation, and each member's
+//      iterate is re-orthogonalised against the cluster's earlier vectors.
 //   4. Back-transformation U = H_0 H_1 ... H_{n-2} Y.
 //   5. Two Newton-Schulz steps U <- U (3 I - U^H U) / 2 in FP64 to restore orthonormality
 //      lost to close eigenvalues.
-// All arithmetic is FP64.  The cost is O(n^3) once, against O(sweeps n^3) for Jacobi.
+// All arithmetic is FP64.  The cost is O(n^3) once, against O(sweeps n^3) for a Jacobi
+// eigensolver.  Blocks of up to 256 rows are reduced together, one CTA each.
 #include <cmath>
 
 #include "heff_plan.cuh"

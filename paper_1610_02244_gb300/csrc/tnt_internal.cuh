@@ -191,17 +191,15 @@ int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, d
 int tridiag_lowest_batched(Ctx* c, const double* d_alpha, const double* d_beta, int k,
                            double* d_out, double* d_y, int nprob, const int* d_skip);
 
-// Hermitian eigensolvers (FP64 cyclic Jacobi) used by the truncated SVD.
-// Small blocks: one CTA per block (n <= 64), in place on G (packed, each block n_b x n_b at
-// off_g[b]); eigenvectors to V at the same offsets.
-
-// One large block (any n), global-memory rounds.
-// Leading k eigenpairs of one large Hermitian block (Householder, bisection, inverse
-// iteration; heig.cu).  U: n x k with leading dimension ldu; ev: device, k values.
+// Hermitian eigensolvers of the truncated SVD's Gram blocks (heig.cu, FP64: Householder
+// tridiagonalisation, bisection, inverse iteration, back-transformation).
+// One large block: leading k eigenpairs, the reduction spread over the whole GPU.
+// U: n x k with leading dimension ldu; ev: device, k values.
 size_t heig_scratch_bound(int64_t n, int64_t k);
 int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev);
-// a block of heig_small_blocks: offset of its n x n Gram block (and of its eigenvector
-// columns, leading dimension n), its size and the number of eigenvectors wanted
+// Many small blocks (n <= 256) at once, one CTA per block for the reduction.  A block of
+// heig_small_blocks: offset of its n x n Gram block (and of its eigenvector columns,
+// leading dimension n), its size and the number of eigenvectors wanted
 struct SmallEig {
   int64_t goff, n, k;
 };

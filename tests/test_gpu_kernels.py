@@ -231,8 +231,8 @@ def test_svd_block_beyond_shared_workspace(ctx):
 
 
 def test_svd_large_block_cfg2_shape(ctx):
-    """One dense 1024 x 1024 block (theta of chi = 256, d = 4) through the multi-launch
-    Jacobi path, truncated to chi = 256."""
+    """One dense 1024 x 1024 block (theta of chi = 256, d = 4) through the whole-GPU
+    tridiagonal reduction, truncated to chi = 256."""
     M, rq, cq = svd_case(9, 1024, 1024, False)
     ctx.set_params(chi_max=256)
     try:
@@ -250,7 +250,7 @@ def test_svd_large_block_cfg2_shape(ctx):
 @pytest.mark.parametrize("side", [0, 1])
 def test_svd_zero_charge_blocks(ctx, side):
     """Charge blocks with no weight (a sector of theta a gate has not reached): a 40 x 30
-    one (Jacobi path), a 200 x 210 one (tridiagonal path) and a zero 1 x 1 block.  Their
+    one and a 200 x 210 one (one CTA per block) and a zero 1 x 1 block.  Their
     values are exact zeros and never kept; the weighted block comes out as the oracle's."""
     g = np.random.default_rng(31)
     rq = np.repeat([0, 1, 2, 3], [40, 200, 1, 120])
