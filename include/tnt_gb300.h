@@ -170,12 +170,14 @@ int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n);
  * of Eq. 2 plus -mu n: lower-triangular hand construction (Sec. 4.3),
  *   W[0][0] = I, W[1][0] = b, W[2][0] = b+, W[3][0] = U/2 n(n-1) + (V (j-j_c)^2 - mu) n,
  *   W[3][1] = -J b+, W[3][2] = -J b, W[3][3] = I.
- * Left boundary vector e_3, right boundary e_0.  h_W: host, 16 d^2 elements. */
+ * Left boundary vector e_3, right boundary e_0.  h_W: host, 16 d^2 elements.
+ * TNT_E_INVALID for n_max < 0, a NULL output or a non-finite parameter. */
 int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j,
                     double j_c, tnt_cplx* h_W);
 /* Trotter gate exp(-i tau h) of the bond term
  *   h = -J (b+ (x) b + b (x) b+) + c1 h_site (x) I + c2 I (x) h_site,
- * h_site = U/2 n(n-1) - mu n, as a d^2 x d^2 matrix G[(s1' s2'), (s1 s2)] (host). */
+ * h_site = U/2 n(n-1) - mu n, as a d^2 x d^2 matrix G[(s1' s2'), (s1 s2)] (host).
+ * TNT_E_INVALID for n_max < 0, a NULL output or a non-finite parameter. */
 int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2,
                      double tau, tnt_cplx* h_G);
 /* Spin-S Heisenberg chain (the performance model of Sec. 6, Tables 1 and 2, is the
@@ -191,13 +193,14 @@ int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double
  *   e_4, right boundary e_0; MPO bond charges wq = {0, +1, -1, 0, 0}.
  * tnt_spin_bond_h: the bond term with the field split c1 / c2 between the two sites,
  *   h[(s1' s2'), (s1 s2)] (host, d^4 values).
- * two_s in 1..15; TNT_E_INVALID otherwise. */
+ * two_s in 1..15; TNT_E_INVALID otherwise, or for a non-finite parameter. */
 int tnt_spin_mpo_site(int two_s, double J, double Jz, double hz, tnt_cplx* h_W);
 int tnt_spin_bond_h(int two_s, double J, double Jz, double hz, double c1, double c2,
                     tnt_cplx* h_h);
 /* G = exp(-i tau h) of a Hermitian n x n host matrix h (row-major; its Hermitian part is
  * used), by host cyclic Jacobi in FP64: the Trotter gate of any nearest-neighbour bond
- * term (Sec. 3).  n in 1..256. */
+ * term (Sec. 3).  n in 1..256.  TNT_E_INVALID for n out of range, a NULL pointer, or a
+ * non-finite tau or entry of h. */
 int tnt_bond_gate(int n, const tnt_cplx* h_h, double tau, tnt_cplx* h_G);
 
 /* ------------------------------------------------------------------ two-site kernels */

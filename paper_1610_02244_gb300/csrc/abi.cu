@@ -2,6 +2,7 @@
 // two-site kernels.  Argument checking happens here; the work is in the other units.
 #include <cmath>
 #include <cstdarg>
+#include <initializer_list>
 #include <vector>
 
 #include "heff_plan.cuh"
@@ -252,6 +253,13 @@ int spin_bond_h_host(int two_s, double J, double Jz, double hz, double c1, doubl
 
 using namespace tnt;
 
+// every model parameter of a host builder must be a finite number
+static bool all_finite(std::initializer_list<double> v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
 #define CTX_CHECK(ctx)                   \
   do {                                   \
     if (!(ctx)) return TNT_E_INVALID;    \
@@ -400,29 +408,31 @@ int tnt_sys_info(const tnt_ctx* ctx, char* buf, size_t n) {
 
 int tnt_bh_mpo_site(int n_max, double J, double U, double mu, double V, double j, double j_c,
                     tnt_cplx* h_W) {
-  if (n_max < 0 || !h_W) return TNT_E_INVALID;
+  if (n_max < 0 || !h_W || !all_finite({J, U, mu, V, j, j_c})) return TNT_E_INVALID;
   return bh_mpo_site_host(n_max, J, U, mu, V, j, j_c, (z*)h_W);
 }
 
 int tnt_spin_mpo_site(int two_s, double J, double Jz, double hz, tnt_cplx* h_W) {
-  if (two_s < 1 || two_s > 15 || !h_W) return TNT_E_INVALID;
+  if (two_s < 1 || two_s > 15 || !h_W || !all_finite({J, Jz, hz})) return TNT_E_INVALID;
   return spin_mpo_site_host(two_s, J, Jz, hz, (z*)h_W);
 }
 
 int tnt_spin_bond_h(int two_s, double J, double Jz, double hz, double c1, double c2,
                     tnt_cplx* h_h) {
-  if (two_s < 1 || two_s > 15 || !h_h) return TNT_E_INVALID;
+  if (two_s < 1 || two_s > 15 || !h_h || !all_finite({J, Jz, hz, c1, c2})) return TNT_E_INVALID;
   return spin_bond_h_host(two_s, J, Jz, hz, c1, c2, (z*)h_h);
 }
 
 int tnt_bond_gate(int n, const tnt_cplx* h_h, double tau, tnt_cplx* h_G) {
   if (n < 1 || n > 256 || !h_h || !h_G || !std::isfinite(tau)) return TNT_E_INVALID;
+  for (int64_t i = 0; i < (int64_t)n * n; ++i)
+    if (!std::isfinite(h_h[i].re) || !std::isfinite(h_h[i].im)) return TNT_E_INVALID;
   return bond_gate_host(n, (const z*)h_h, tau, (z*)h_G);
 }
 
 int tnt_bh_bond_gate(int n_max, double J, double U, double mu, double c1, double c2, double tau,
                      tnt_cplx* h_G) {
-  if (n_max < 0 || !h_G) return TNT_E_INVALID;
+  if (n_max < 0 || !h_G || !all_finite({J, U, mu, c1, c2, tau})) return TNT_E_INVALID;
   return bh_bond_gate_host(n_max, J, U, mu, c1, c2, tau, (z*)h_G);
 }
 

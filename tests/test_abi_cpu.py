@@ -92,3 +92,80 @@ def test_argument_errors_are_reported(lib):
     assert lib.tnt_ctx_destroy(None) == 1
     assert lib.tnt_params_set(None, None) == 1
     assert lib.tnt_bh_mpo_site(-1, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, None) == 1
+
+
+@pytest.mark.parametrize("two_s,J,Jz,hz", [(2, 1.0, 1.0, 0.0), (1, 0.8, -0.3, 0.25),
+                                           (3, 1.0, 0.5, 0.1)])
+def test_spin_builders_match_oracle(lib, two_s, J, Jz, hz):
+    """The spin-S MPO tensor and bond term of Sec. 6 built by the library's host code equal
+    the oracle's, and the gate of each bond term equals the oracle's eigh-route gate."""
+    from oracle import spin as ospin
+    from paper_1610_02244_gb300 import tnt
+    Ws, _, _, _ = ospin.heisenberg_mpo(2, two_s, J, Jz, hz)
+    assert np.abs(tnt.spin_mpo_site(two_s, J, Jz, hz) - Ws[0]).max() < 1e-15
+    for c1, c2 in ((1.0, 0.5), (0.5, 0.5), (0.5, 1.0)):
+        h = ospin.bond_hamiltonian(two_s, J, Jz, hz, c1, c2)
+        assert np.abs(tnt.spin_bond_h(two_s, J, Jz, hz, c1, c2) - h).max() < 1e-15
+        assert np.abs(tnt.bond_gate(h, 0.07) - bh.gate(h, 0.07)).max() < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 4, 9, 25, 49])
+def test_bond_gate_is_the_matrix_exponential(lib, n):
+    """exp(-i tau h) of a random complex Hermitian h by the library's host eigensolver,
+    against scipy's Pade exponential (a route with no eigendecomposition): equal to rounding,
+    unitary, the identity at tau = 0, and blind to an anti-Hermitian part of its input."""
+    import scipy.linalg as sla
+    from paper_1610_02244_gb300 import tnt
+    tol = 10 * n * np.finfo(float).eps  # rotations accumulate O(n eps) in the eigenvectors
+    g = np.random.default_rng(n)
+    X = g.normal(size=(n, n)) + 1j * g.normal(size=(n, n))
+    h = 0.5 * (X + X.conj().T)
+    for tau in (0.01, 0.3):
+        G = tnt.bond_gate(h, tau)
+        Gr = sla.expm(-1j * tau * h)
+        assert np.abs(G - Gr).max() < tol
+        assert np.abs(G.conj().T @ G - np.eye(n)).max() < tol
+    assert np.abs(tnt.bond_gate(h, 0.0) - np.eye(n)).max() < tol
+    K = g.normal(size=(n, n)) + 1j * g.normal(size=(n, n))
+    assert np.abs(tnt.bond_gate(h + 0.5 * (K - K.conj().T), 0.3) - tnt.bond_gate(h, 0.3)).max() < tol
+
+
+def test_bond_gate_of_a_degenerate_term(lib):
+    """A bond term with a highly degenerate spectrum (the isotropic spin-1 exchange S.S has
+    only three distinct eigenvalues on nine states) still gives the exact gate."""
+    import scipy.linalg as sla
+    from oracle import spin as ospin
+    from paper_1610_02244_gb300 import tnt
+    h = ospin.bond_hamiltonian(2, 1.0, 1.0, 0.0, 0.0, 0.0)
+    assert len(np.unique(np.round(np.linalg.eigvalsh(h), 10))) == 3
+    assert np.abs(tnt.bond_gate(h, 0.2) - sla.expm(-0.2j * h)).max() < 1e-13
+
+
+def test_bond_gate_argument_errors(lib):
+    h = np.eye(4, dtype=np.complex128)
+    G = np.zeros_like(h)
+    assert lib.tnt_bond_gate(0, h.ctypes.data, 0.1, G.ctypes.data) == 1
+    assert lib.tnt_bond_gate(257, h.ctypes.data, 0.1, G.ctypes.data) == 1
+    assert lib.tnt_bond_gate(4, None, 0.1, G.ctypes.data) == 1
+    assert lib.tnt_bond_gate(4, h.ctypes.data, float("nan"), G.ctypes.data) == 1
+
+
+def test_host_builders_refuse_non_finite_input(lib):
+    """A NaN or infinite model parameter, or a non-finite entry of a bond term, is an
+    argument error, not a gate or MPO full of NaN."""
+    nan, inf = float("nan"), float("inf")
+    out = np.zeros(16 * 16 * 16, dtype=np.complex128)
+    p = out.ctypes.data
+    assert lib.tnt_bh_mpo_site(3, nan, 1.0, 0.0, 0.0, 1.0, 0.0, p) == 1
+    assert lib.tnt_bh_mpo_site(3, 1.0, 1.0, 0.0, inf, 1.0, 0.0, p) == 1
+    assert lib.tnt_bh_mpo_site(3, 1.0, 1.0, 0.0, 0.01, 1.0, 50.5, p) == 0
+    assert lib.tnt_bh_bond_gate(2, 1.0, nan, 0.0, 0.5, 0.5, 0.1, p) == 1
+    assert lib.tnt_bh_bond_gate(2, 1.0, 2.0, 0.0, 0.5, 0.5, inf, p) == 1
+    assert lib.tnt_spin_mpo_site(2, 1.0, nan, 0.0, p) == 1
+    assert lib.tnt_spin_bond_h(2, 1.0, 1.0, 0.0, 0.5, -inf, p) == 1
+    assert lib.tnt_spin_bond_h(2, 1.0, 1.0, 0.0, 0.5, 0.5, p) == 0
+    h = np.eye(9, dtype=np.complex128)
+    h[3, 4] = complex(0.0, nan)
+    assert lib.tnt_bond_gate(9, h.ctypes.data, 0.1, p) == 1
+    h[3, 4] = 0.0
+    assert lib.tnt_bond_gate(9, h.ctypes.data, 0.1, p) == 0
