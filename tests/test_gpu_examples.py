@@ -3,10 +3,13 @@ properties that hold at any size and, for the quench, by the free-fermion closed
 
 E1: ground state of L = 100 bosons, N = 100, n_max = 3, U/J = 5 in the harmonic trap
     V (j - j_c)^2 n_j with V/J = 0.01, j_c at the chain centre, chi = 100 (Fig. 4): density
-    profile and single-particle density matrix; and the same Hamiltonian on ten sites with a
-    stronger trap, against exact diagonalisation.
+    profile and single-particle density matrix; its first sweep against the FP64 oracle's
+    first sweep from the same start; and the same Hamiltonian on ten sites with a stronger
+    trap, against exact diagonalisation.
 E2: hard-core bosons (n_max = 1) on L = 51 sites from the CDW state |0101...0>, chi = 200
     (Fig. 5): <n_j(t)> against exp(-iht) of the free-fermion hopping matrix h."""
+import os
+
 import numpy as np
 import pytest
 
@@ -101,6 +104,44 @@ def test_e1_trap_reduced_to_ten_sites(ctx, precision):
     for B in mps.tensors()[1:]:
         Bm = B.reshape(B.shape[0], -1)
         assert np.abs(Bm @ Bm.conj().T - np.eye(B.shape[0])).max() < 1e-10
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                vals[k] = float(v)
+    return vals
+
+
+@pytest.mark.parametrize("precision", [
+    pytest.param(0, marks=pytest.mark.xfail(
+        strict=False, reason="the split-TF32 run of this chain leaves the oracle within the "
+                             "first sweep; whether the FP64 path does too is not known")),
+    pytest.param(1, marks=pytest.mark.xfail(
+        strict=False, reason="open defect: the split-TF32 run of this chain ends its first "
+                             "sweep at E = 1290.9 where the oracle has 530.16")),
+])
+def test_e1_first_sweep_matches_oracle(ctx, precision):
+    """The first sweep of E1 at the paper's size from the seeded start, against the FP64
+    oracle's first sweep from the same start (tests/golden/e1_trap_sweep0.txt, written by
+    tests/golden/make_e1_sweep0.py).  Same algorithm and truncation on both sides; only a
+    near-tie at a chi = 100 cut could separate them, by far less than the tolerance."""
+    from paper_1610_02244_gb300 import tnt
+    ref = _golden("e1_trap_sweep0.txt")["E_sweep0"]
+    Ls, N, n_max, J, U, V = 100, 100, 3, 1.0, 5.0, 0.01
+    A, q = synth.random_charged_mps(synth.rng(4), Ls, n_max + 1, N, 100, "gauss", 2.0)
+    ctx.set_params(chi_max=100, precision=precision)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=100)
+        mpo = ctx.mpo_bose_hubbard(Ls, n_max, J, U, 0.0, V, (Ls + 1) / 2.0)
+        dm = ctx.dmrg_create(mps, mpo)
+        E = dm.sweep()["E"]
+    finally:
+        ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
+    assert abs(E - ref) <= 1e-6 * abs(ref), (E, ref)
 
 
 @pytest.mark.xfail(run=False, strict=False,
