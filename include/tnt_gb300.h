@@ -371,6 +371,14 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
  * back.  alpha = 0 is a plain one-site sweep, which cannot enlarge any bond.  Bonds are
  * capped by the MPS storage (chi_cap).  TNT_E_INVALID for alpha < 0 or non-finite. */
 int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* dmrg, double alpha, tnt_sweep_stats* stats);
+/* The energy of every update of the last sweep on this handle (Sec. 4.3 Listing 2: the
+ * local eigensolve's ground-state energy, here the FP64 Rayleigh quotient of its
+ * eigenvector), in update order: 2(L-1) values after tnt_dmrg_sweep (bonds 0..L-2, then
+ * L-2..0) or tnt_dmrg_sweep1 (sites 0..L-2, then L-1..1), fewer after a sweep that stopped
+ * at an error, none before the first sweep.  *n receives the count; min(cap, *n) values
+ * are copied to h_E (host memory; NULL allowed with cap = 0).  Host only, no GPU work.
+ * TNT_E_INVALID for a NULL handle or n, cap < 0, or a NULL h_E with cap > 0. */
+int tnt_dmrg_update_energies(const tnt_dmrg* dmrg, double* h_E, int64_t cap, int64_t* n);
 int tnt_dmrg_destroy(tnt_dmrg* dmrg);
 
 /* ------------------------------------------------------------------ FP64 matrix products */

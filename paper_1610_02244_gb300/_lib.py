@@ -120,6 +120,7 @@ SIGNATURES = {
     "tnt_dmrg_create": [P, P, P, C.POINTER(P)],
     "tnt_dmrg_sweep": [P, P, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_sweep1": [P, P, D, C.POINTER(tnt_sweep_stats)],
+    "tnt_dmrg_update_energies": [P, C.POINTER(D), I64, C.POINTER(I64)],
     "tnt_dmrg_destroy": [P],
     "tnt_mps_density": [P, P, PD],
     "tnt_mps_bdagb": [P, P, P],

@@ -766,6 +766,7 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
   cudaEventCreate(&e1);
   cudaEventRecord(e0, c->stream);
   ws_reset(c);
+  g->last_E.clear();
   TNT_TRY(ws_reserve(c, g->scratch));
   double E = 0;
   auto account = [&](const tnt_lanczos_result& lz, const tnt_trunc_result& tr) {
@@ -800,6 +801,7 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
     cudaEventRecord(g->ev[4], c->stream);
     if (r == TNT_OK) phases();
     account(lz, tr);
+    if (r == TNT_OK) g->last_E.push_back(lz.E_rq);
   }
   for (int i = L - 2; i >= 0 && r == TNT_OK; --i) {
     tnt_lanczos_result lz{};
@@ -811,6 +813,7 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
     cudaEventRecord(g->ev[4], c->stream);
     if (r == TNT_OK) phases();
     account(lz, tr);
+    if (r == TNT_OK) g->last_E.push_back(lz.E_rq);
   }
   ws_reset(c);
   cudaEventRecord(e1, c->stream);
@@ -836,6 +839,7 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st
   cudaEventCreate(&e1);
   cudaEventRecord(e0, c->stream);
   ws_reset(c);
+  g->last_E.clear();
   TNT_TRY(ws_reserve(c, std::max(g->scratch, dmrg1_scratch_bound(m, g->mpo->D, c->params))));
   double E = 0;
   auto account = [&](const tnt_lanczos_result& lz, const tnt_trunc_result& tr) {
@@ -852,6 +856,7 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st
     r = dmrg1_update(c, g, i, +1, alpha, &lz, &tr);
     if (r == TNT_OK) r = dmrg_env_left(c, g, i);
     account(lz, tr);
+    if (r == TNT_OK) g->last_E.push_back(lz.E_rq);
   }
   for (int i = L - 1; i >= 1 && r == TNT_OK; --i) {
     tnt_lanczos_result lz{};
@@ -859,6 +864,7 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st
     r = dmrg1_update(c, g, i, -1, alpha, &lz, &tr);
     if (r == TNT_OK) r = dmrg_env_right(c, g, i);
     account(lz, tr);
+    if (r == TNT_OK) g->last_E.push_back(lz.E_rq);
   }
   ws_reset(c);
   cudaEventRecord(e1, c->stream);
@@ -871,6 +877,14 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st
   st->E = E;
   st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
   return r;
+}
+
+int tnt_dmrg_update_energies(const tnt_dmrg* g, double* h_E, int64_t cap, int64_t* n) {
+  if (!g || !n || cap < 0 || (cap > 0 && !h_E)) return TNT_E_INVALID;
+  *n = (int64_t)g->last_E.size();
+  const int64_t k = std::min(cap, *n);
+  for (int64_t i = 0; i < k; ++i) h_E[i] = g->last_E[(size_t)i];
+  return TNT_OK;
 }
 
 int tnt_dmrg_destroy(tnt_dmrg* g) {

@@ -30,6 +30,7 @@ struct tnt_dmrg {
   std::vector<tnt::z*> Lenv, Renv;  // Lenv[i]: sites 0..i-1 (i = 0..L); Renv[i]: sites i..L-1
   size_t scratch = 0;
   cudaEvent_t ev[5] = {};  // phase marks of one update (sweep statistics)
+  std::vector<double> last_E;  // energy of each update of the last sweep, in update order
 };
 
 namespace tnt {

@@ -459,6 +459,16 @@ class Dmrg:
         self.ctx._chk(self.ctx.lib.tnt_dmrg_sweep1(self.ctx.h, self.h, float(alpha), C.byref(st)))
         return _struct_dict(st)
 
+    def update_energies(self) -> np.ndarray:
+        """Energy of every update of the last sweep, in update order
+        (tnt_dmrg_update_energies)."""
+        n = C.c_int64()
+        self.ctx._chk(self.ctx.lib.tnt_dmrg_update_energies(self.h, None, 0, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.float64)
+        self.ctx._chk(self.ctx.lib.tnt_dmrg_update_energies(
+            self.h, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+        return out
+
     def __del__(self):
         if getattr(self, "h", None):
             self.ctx.lib.tnt_dmrg_destroy(self.h)

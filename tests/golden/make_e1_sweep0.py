@@ -1,8 +1,8 @@
-"""Writes e1_trap_sweep0.txt: the FP64 oracle's energy after the first two-site DMRG sweep
+"""Writes e1_trap_sweep0.txt: the FP64 oracle's energies in the first two-site DMRG sweep
 of the first example of Sec. 5 (Fig. 4: L = 100, N = 100, n_max = 3, U/J = 5, trap
 V/J = 0.01 about the chain centre, chi = 100), from the seeded random start with the
-Gaussian sector profile.  Calls only the oracle and the seeded input generator.  Takes
-about a quarter of an hour on eight cores.
+Gaussian sector profile: after the sweep and at each of its 198 updates.  Calls only the
+oracle and the seeded input generator.  Takes about a quarter of an hour on eight cores.
 
     python tests/golden/make_e1_sweep0.py
 """
@@ -33,6 +33,8 @@ def main():
         f.write(f"E_sweep0 {float(hist[0]['E'])!r}\n")
         f.write(f"unconverged {sum(not u['converged'] for u in ups)}\n")
         f.write(f"matvecs {sum(u['matvecs'] for u in ups)}\n")
+        for k, u in enumerate(ups):  # every update, in sweep order
+            f.write(f"E_u{k:03d} {float(u['E'])!r}\n")
 
 
 if __name__ == "__main__":

@@ -169,3 +169,11 @@ def test_host_builders_refuse_non_finite_input(lib):
     assert lib.tnt_bond_gate(9, h.ctypes.data, 0.1, p) == 1
     h[3, 4] = 0.0
     assert lib.tnt_bond_gate(9, h.ctypes.data, 0.1, p) == 0
+
+
+def test_update_energies_argument_errors(lib):
+    """The per-update energies call is host only; without a handle it is an argument
+    error (the values themselves are checked on the GPU after a sweep)."""
+    n = ctypes.c_int64(-1)
+    assert lib.tnt_dmrg_update_energies(None, None, 0, ctypes.byref(n)) == 1
+    assert lib.tnt_dmrg_update_energies(None, None, 0, None) == 1
