@@ -5,8 +5,10 @@
  * Library" (arXiv:1610.02244): the effective-Hamiltonian matvec L.W.W.R.theta that the
  * eigensolver applies in DMRG (Sec. 4.2 Listing 1, Sec. 4.3 Listing 2), the two-site
  * gate of TEBD (Sec. 3, Sec. 5), and the reshape plus truncated SVD of theta that follows
- * both (App. B.1.2, Eq. 3), on Bose-Hubbard chains (Sec. 5, Eq. 2) with optional U(1)
- * boson-number labels (App. A.1.1).
+ * both (App. B.1.2, Eq. 3), on Bose-Hubbard chains (Sec. 5, Eq. 2), spin-S Heisenberg
+ * chains (Sec. 6) or any hand-built MPO (Sec. 4.3), with optional U(1) labels (App. A.1.1);
+ * around it, the DMRG sweep (two-site, and single-site with subspace expansion), the TEBD
+ * step and the observables of the paper's examples.
  *
  * Conventions for every call
  *   - Every call returns an int status (TNT_OK = 0 or a TNT_E_* code); results go through
