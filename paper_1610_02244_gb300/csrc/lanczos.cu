@@ -116,7 +116,9 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
         stop = true;
         break;
       }
-      TNT_TRY(vec_normalize(c, w, V + (int64_t)(k + 1) * n, n, norm2));
+      // v_{k+1}, except after the last step of a cycle: the basis holds cap vectors, and
+      // the restart begins from the Ritz vector instead
+      if (k + 1 < cap) TNT_TRY(vec_normalize(c, w, V + (int64_t)(k + 1) * n, n, norm2));
     }
     // Ritz vector x = sum_i y_i v_i  (built in w, normalised)
     k_lz_ritz_coef<<<1, 64, 0, c->stream>>>(y, kk, coef);

@@ -200,7 +200,6 @@ __global__ void k_sscalars(const z* __restrict__ dots, int k, const double* __re
   beta[p * KMAX + k] = sqrt(norm2[p]);
   bk[p] = beta[p * KMAX + k];
 }
-// second Gram-Schmidt pass only where the first cancelled more than 99% of |w|
 // Ritz coefficients: coef[p][i] = -y[p][i] for i < kk[p], zero beyond
 __global__ void k_sritz(const double* __restrict__ y, const int* __restrict__ kk, z* __restrict__ coef,
                         int P) {
