@@ -124,3 +124,47 @@ def test_tebd_energy_conserved_untruncated(ctx):
     for _ in range(25):
         gpu.step()
     assert abs(mps.expect_mpo(mpo) / mps.norm2() - E0) < 5e-3
+
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_tebd_mott64_quench_matches_oracle(ctx):
+    """The 64-site quench from |1...1> at the size the TEBD benchmark runs (n_max = 4,
+    J = 1, U = 2, dt = 0.01, chi_max = 512, truncation error 1e-10), 50 Trotter steps
+    (t = 0.5, chi about 120), against the FP64 oracle's state after the same steps
+    (tests/golden/tebd_mott64_step50.txt, written by tests/golden/make_tebd_mott64.py):
+    every <n_j>, <H>, the norm and the summed discarded weight.  Both sides drop weight
+    below 1e-20 per gate, so they agree far inside these tolerances; the norm loss itself
+    (3e-12 in the oracle) is rounding accumulated over 4750 gates, not truncation (the
+    discarded weight sums to 3e-17), so it is compared at 1e-10."""
+    g = _golden("tebd_mott64_step50.txt")
+    L, n_max, J, U, dt = 64, 4, 1.0, 2.0, 0.01
+    ctx.set_params(chi_max=512, trunc_err=1e-10, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    try:
+        mps = ctx.mps_product([1] * L, n_max + 1, 512)
+        mpo = ctx.mpo_bose_hubbard(L, n_max, J, U)
+        tb = ctx.tebd_create(mps, n_max, J, U, dt)
+        disc = 0.0
+        for _ in range(50):
+            disc += tb.step()["disc_sum"]
+        n2 = mps.norm2()
+        E = mps.expect_mpo(mpo) / n2
+        n = mps.density()
+        chi = max(mps.bond_dim(k) for k in range(L + 1))
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    n_ref = np.array([g[f"n_{j:02d}"] for j in range(L)])
+    assert np.abs(n - n_ref).max() < 1e-8, np.abs(n - n_ref).max()
+    assert abs(E - g["E"]) < 1e-8, (E, g["E"])
+    assert abs(n2 - g["norm2"]) < 1e-10, (n2, g["norm2"])
+    assert abs(disc - g["disc_sum"]) <= 1e-18 + 0.05 * g["disc_sum"], (disc, g["disc_sum"])
+    assert abs(chi - g["max_chi"]) <= 0.05 * g["max_chi"], (chi, g["max_chi"])
