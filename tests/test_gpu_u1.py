@@ -198,3 +198,30 @@ def test_lanczos_u1_batched_chains(ctx, precision):
             Hx = oc.heff_apply(Le_, W1_, W2_, Re_, got)
             assert np.linalg.norm(Hx - r["E_rq"] * got) <= 1e-5 * abs(E)
             assert abs(1 - ov) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_heff_u1_chi1024_sampled_rows(ctx, precision):
+    """The U(1) matvec at the size the U(1) benchmark times (chi = 1024 on both bonds, d = 5,
+    15 Gaussian sectors of 1..~200 states, U/J = 3.4): the whole product on the GPU, and
+    rows a' of it recomputed one by one by the oracle (the contraction with L restricted to
+    one bra index a' is the same formula), in four different left sectors."""
+    d, chi = 5, 1024
+    qa = synth.gaussian_sector_labels(chi, 15, 2.0, 31)
+    qb = synth.gaussian_sector_labels(chi, 15, 2.0, 33)
+    g = synth.rng(2000)
+    Le = synth.hermitian_env(g, chi) * synth.env_mask(qa, qa)
+    Re = synth.hermitian_env(g, chi) * synth.env_mask(qb, qb)
+    Ws, _, _ = bh.bh_mpo(4, d - 1, 1.0, 3.4)
+    W = Ws[1]
+    mask = synth.theta_mask(qa, d, qb)
+    th = np.zeros(mask.shape, dtype=np.complex128)
+    th[mask] = synth.complex_gaussian(g, (int(mask.sum()),))
+    p = problem(Le, W, W, Re, qa, qb)
+    x = ctx.u1_pack(p, dev(th))
+    y, _ = ctx.heff_apply_u1([p], x, precision=precision)
+    rows = [0, 300, 511, 1023]
+    got = ctx.u1_unpack(p, y)[rows].cpu().numpy()
+    ref = np.concatenate([oc.heff_apply(Le[a:a + 1], W, W, Re, th) for a in rows])
+    assert rel(got, ref) < (FP64_TOL if precision == 0 else MIXED_TOL)
+    assert len(set(qa[rows])) == 4
