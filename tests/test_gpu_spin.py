@@ -227,3 +227,49 @@ def test_tebd_bonds_rejects_nonfinite(ctx):
     hs[1][0, 0] = np.nan
     with pytest.raises(tnt.TntError):
         ctx.tebd_create_bonds(mps, hs, 0.1)
+
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                k, v = ln.split()
+                vals[k] = float(v)
+    return vals
+
+
+@pytest.mark.parametrize("precision", [
+    0,
+    pytest.param(1, marks=pytest.mark.xfail(
+        strict=False, reason="split-TF32 first sweeps leave the oracle on the 100-site trapped "
+                             "chain (open defect); whether they do on this chain is not known")),
+])
+def test_spin1_table1_first_sweep_matches_oracle(ctx, precision):
+    """The DMRG benchmark's configuration (Table 1: L = 101, chi = 200, S^z_total = 0, the
+    seeded Gaussian-profile start): the GPU's first sweep against the FP64 oracle's first
+    sweep from the same start, update by update (tests/golden/spin1_sweep0.txt, written by
+    tests/golden/make_spin1_sweep0.py).  The sweep's energy to 1e-6 relative.  Single
+    updates are not held to that: from the random start, 9 of the oracle's 200 eigensolves
+    stop at the 300-matvec cap on vectors that depend on the iteration history, and the
+    rest of the sweep starts from them (the benchmark's split-TF32 sweep from this start
+    ended 2.3e-7 relative from the oracle's); the first update off by more than 1e-6 is
+    reported with a failure."""
+    from paper_1610_02244_gb300 import tnt
+    g = _golden("spin1_sweep0.txt")
+    Ls, two_s, chi = 101, 2, int(g["chi"])
+    A, q = synth.random_charged_mps(synth.rng(0), Ls, two_s + 1, Ls * two_s // 2, chi, "gauss", 2.0)
+    ctx.set_params(chi_max=chi, precision=precision)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=chi)
+        dm = ctx.dmrg_create(mps, ctx.mpo_spin_heisenberg(Ls, two_s, 1.0))
+        E = dm.sweep()["E"]
+        Eu = dm.update_energies()
+    finally:
+        ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
+    Eu_ref = np.array([g[f"E_u{k:03d}"] for k in range(2 * (Ls - 1))])
+    assert len(Eu) == len(Eu_ref) and Eu[-1] == E
+    off = np.abs(Eu - Eu_ref) > 1e-6 * np.abs(Eu_ref)
+    first = int(np.argmax(off)) if off.any() else -1
+    assert abs(E - g["E_sweep0"]) <= 1e-6 * abs(g["E_sweep0"]), (E, g["E_sweep0"], first)
