@@ -360,7 +360,10 @@ int tnt_mps_bdagb(tnt_ctx* ctx, const tnt_mps* mps, tnt_cplx* h_rho);
  * right-canonical unit-norm form by exact SVD moves and builds the right environments.
  * One sweep = bonds 0..L-2 left to right, then L-2..0 right to left; each update forms
  * theta (a1), runs the eigensolve (a3, a4), splits theta by the truncated SVD (a5, a6)
- * with S renormalised (a7), and grows the environment (a8). */
+ * with S renormalised (a7), and grows the environment (a8).  With TNT_PREC_MIXED each
+ * eigensolve runs its split-TF32 Lanczos and then an FP64 Lanczos from that vector on a
+ * budget of its own (lanczos_maxit matvecs), so the sweep's energies and states have the
+ * FP64 path's accuracy; the split-TF32 phase supplies the start. */
 int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* mps, const tnt_mpo* mpo, tnt_dmrg** out);
 int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* dmrg, tnt_sweep_stats* stats);
 /* One single-site sweep with subspace expansion on the same handle (the sweep of Sec. 4.3

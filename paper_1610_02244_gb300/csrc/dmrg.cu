@@ -89,7 +89,9 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
     TNT_TRY(u1_convert(c, spec[0], theta, x, 1));
     TNT_TRY(u1_prepare(c, spec, &up));
     if (marks) cudaEventRecord(g->ev[1], c->stream);
+    c->fp64_finish = true;  // the sweep's energies and states are FP64-accurate
     int r = lanczos_run(c, U1MatVec(up), x, lz);
+    c->fp64_finish = false;
     if (r == TNT_E_NAN)  // name the update in the message
       return set_err(c, r, "bond %d (%s, chi %lld|%lld|%lld, compact length %lld): %s", i,
                      dir > 0 ? "left to right" : "right to left", (long long)chl, (long long)chm,
@@ -104,7 +106,9 @@ static int dmrg_update(Ctx* c, tnt_dmrg* g, int i, int dir, tnt_lanczos_result* 
                          chr, c->params.precision, &p, g->mpo->hW[(size_t)i].data(),
                          g->mpo->hW[(size_t)i + 1].data()));
     if (marks) cudaEventRecord(g->ev[1], c->stream);
+    c->fp64_finish = true;
     int r = lanczos_impl(c, p, theta, lz);
+    c->fp64_finish = false;
     if (r != TNT_OK && r != TNT_E_NOCONV) return r;
     c->ws.top = t2;
   }

@@ -183,11 +183,15 @@ int lanczos_run(Ctx* c, const MatVec& A, z* theta, tnt_lanczos_result* res) {
     TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     res->E_rq = hp[0];
     res->resid_fp64 = std::sqrt(hp[1]);
-    if (res->resid_fp64 > 1e-5 * std::fabs(res->E_rq) && res->n_matvec < P.lanczos_maxit) {
-      // not accurate enough for the FP64 energy: continue in FP64 from this vector
+    // continue in FP64 from this vector when its residual is not accurate enough for the
+    // FP64 energy, within what is left of the budget; or always, on a budget of its own,
+    // when the caller asks for FP64 accuracy (a residual scaled by |E| says little where a
+    // constant offset inflates |E| over small gaps)
+    const bool finish = c->fp64_finish;
+    const int budget = finish ? P.lanczos_maxit : P.lanczos_maxit - res->n_matvec;
+    if ((finish || res->resid_fp64 > 1e-5 * std::fabs(res->E_rq)) && budget > 0) {
       tnt_lanczos_result r2{};
-      TNT_TRY(lanczos_cycle_loop(c, A, theta, TNT_PREC_FP64, P.lanczos_maxit - res->n_matvec,
-                                 &r2, V, w, dsc));
+      TNT_TRY(lanczos_cycle_loop(c, A, theta, TNT_PREC_FP64, budget, &r2, V, w, dsc));
       res->n_matvec += r2.n_matvec;
       res->E = r2.E;
       res->E_rq = r2.E;

@@ -66,6 +66,9 @@ struct Ctx {
   // (FP64-accurate), 0 = FP64 FMA only; its slice buffer is owned by the context
   int oz_mode = 1;
   double svd_zero_tol = -1.0;  // automatic blocking of unlabelled SVDs (< 0: off)
+  // split-TF32 eigensolves end with an FP64 Lanczos from their vector, on a budget of
+  // their own (set by the DMRG sweep around its eigensolves)
+  bool fp64_finish = false;
   void* oz_buf = nullptr;
   size_t oz_cap = 0;
 };
