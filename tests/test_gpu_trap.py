@@ -95,8 +95,9 @@ def _golden(name):
         strict=False, reason="the split-TF32 run of this chain leaves the oracle within the "
                              "first sweep; whether the FP64 path does too is not known")),
     pytest.param(1, marks=pytest.mark.xfail(
-        strict=False, reason="open defect: the split-TF32 run of this chain ends its first "
-                             "sweep at E = 1290.9 where the oracle has 530.16")),
+        strict=False, reason="open defect: the split-TF32 run of this chain ended its first "
+                             "sweep at E = 1290.9 where the oracle has 530.16, before its "
+                             "solves were finished in FP64; not yet run since")),
 ])
 def test_e1_first_sweep_matches_oracle(ctx, precision):
     """The first sweep of E1 at the paper's size from the seeded start, against the FP64
