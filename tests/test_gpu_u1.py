@@ -225,3 +225,51 @@ def test_heff_u1_chi1024_sampled_rows(ctx, precision):
     ref = np.concatenate([oc.heff_apply(Le[a:a + 1], W, W, Re, th) for a in rows])
     assert rel(got, ref) < (FP64_TOL if precision == 0 else MIXED_TOL)
     assert len(set(qa[rows])) == 4
+
+
+def _trapped_chain_bonds(bonds):
+    """Environments of the 100-site trapped chain of the first example (N = 100, n_max = 3,
+    U/J = 5, V/J = 0.01) for its seeded Gaussian-profile start at chi = 100: right-canonical
+    by the oracle's exact moves, then the centre moved right by exact SVDs; per bond i the
+    problem (L_i, W_i, W_{i+1}, R_{i+2}, theta = A_i A_{i+1}, labels)."""
+    from oracle import dmrg as odmrg
+    from oracle.svd import svd_truncate
+    Ls, N, n_max = 100, 100, 3
+    d = n_max + 1
+    A, q = synth.random_charged_mps(synth.rng(4), Ls, d, N, 100, "gauss", 2.0)
+    Ws, l, r = bh.bh_mpo(Ls, n_max, 1.0, 5.0, 0.0, 0.01, (Ls + 1) / 2.0)
+    odmrg.right_canonicalize(A, q)
+    Renv = odmrg.build_right_envs(A, Ws, r)
+    Lenv = [oc.boundary_left(l)]
+    out = {}
+    for j in range(max(bonds) + 1):
+        if j in bonds:
+            out[j] = (Lenv[j], Ws[j], Ws[j + 1], Renv[j + 2], oc.theta_form(A[j], A[j + 1]),
+                      q[j].copy(), q[j + 2].copy())
+        chl, _, chr_ = A[j].shape
+        rows = (q[j][:, None] + np.arange(d)[None, :]).reshape(-1)
+        U, S, Vh, bq, _ = svd_truncate(A[j].reshape(chl * d, chr_), rows, q[j + 1], odmrg.EXACT)
+        A[j] = U.reshape(chl, d, len(S))
+        A[j + 1] = np.einsum("km,msb->ksb", S[:, None] * Vh, A[j + 1])
+        q[j + 1] = bq
+        Lenv.append(oc.env_left(Lenv[j], Ws[j], A[j]))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_heff_u1_trapped_chain_bonds(ctx, precision):
+    """The U(1) matvec on bonds 12, 30 and 50 of the trapped chain of the first example, with
+    its site-dependent MPO tensors and environments whose entries reach several hundred
+    (the trap energy accumulated along the chain), against the oracle's dense contraction.
+    The split-TF32 tolerance is tight: the same contraction done in exact split-TF32
+    arithmetic (operands rounded to TF32 and split in two, three products, FP32
+    accumulation) errs by 1.0-1.8e-7 of max|y| on these bonds, so 2e-6 separates rounding
+    from a block handled wrongly."""
+    for i, (Le, W1, W2, Re, th, qa, qb) in _trapped_chain_bonds([12, 30, 50]).items():
+        from paper_1610_02244_gb300 import tnt
+        p = tnt.U1Problem(dev(Le), dev(W1), dev(W2), dev(Re), qa, qb, synth.BH_WQ)
+        x = ctx.u1_pack(p, dev(th))
+        y, _ = ctx.heff_apply_u1([p], x, precision=precision)
+        got = ctx.u1_unpack(p, y).cpu().numpy()
+        ref = oc.heff_apply(Le, W1, W2, Re, th)
+        assert rel(got, ref) < (FP64_TOL if precision == 0 else 2e-6), (i, rel(got, ref))
