@@ -127,8 +127,9 @@ def test_e1_first_sweep_matches_oracle(ctx, precision):
 
 @pytest.mark.xfail(run=False, strict=False,
                    reason="open defect: in split TF32 the eigensolves of this trapped chain "
-                          "stop at the 300-matvec cap, the sweep energies collapse and a start "
-                          "vector vanishes; the FP64 oracle converges on the same chain")
+                          "stopped at the 300-matvec cap, the sweep energies collapsed and a "
+                          "start vector vanished (before split-TF32 solves were finished in "
+                          "FP64; not run since); the FP64 oracle converges on the same chain")
 def test_e1_trapped_bosons_L100(ctx):
     from paper_1610_02244_gb300 import tnt
     Ls, N, n_max, J, U, V = 100, 100, 3, 1.0, 5.0, 0.01
