@@ -7,9 +7,9 @@
 //      p = tau A v, w = p - (tau/2)(p^H v) v, A <- A - v w^H - w v^H.
 //   2. Multisection on Sturm counts of T for eigenvalues n-1, ..., n-k (one warp each),
 //      to full precision.
-//   3. Inverse iteration on T - lambda I (pivoted tridiagonal LU, three sweeps); a cluster
-//      of eigenvalues closer than 1e3 eps |T| shares one factorisation, and each member's
-//      iterate is re-orthogonalised against the cluster's earlier vectors.
+//   3. Inverse iteration on T - lambda_i I (pivoted tridiagonal LU, three sweeps), each
+//      eigenvalue its own shift; the iterates of a cluster of eigenvalues closer than
+//      1e-11 |T| are re-orthogonalised against the cluster's earlier vectors.
 //   4. Back-transformation U = H_0 H_1 ... H_{n-2} Y.
 //   5. Two Newton-Schulz steps U <- U (3 I - U^H U) / 2 in FP64 to restore orthonormality
 //      lost to close eigenvalues.
@@ -517,24 +517,76 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
   if (lane == 0) ev[i] = 0.5 * (lo + hi);
 }
 
-// Inverse iteration on T - lambda I, block form.  Eigenvalues closer than 1e3 eps |T|
-// form a cluster (in a truncated SVD's Gram block, typically the dozens of eigenvalues at
-// rounding level below the kept ones), handled by one block: thread 0 factors T - lambda I
-// once, lambda the cluster's largest eigenvalue; every sweep then solves for all members
-// at once (one thread per member, the recurrences are serial) and re-orthogonalises the
-// members in order (classical Gram-Schmidt, twice, then a max-scaled normalisation), so
-// coincident eigenvalues still give independent vectors.  Wider gaps give iterates
-// accurate to eps |T| / gap, which the final Newton-Schulz steps absorb.  The factors live
-// in shared memory when they fit (smem_ok), else in the cluster head's slice of gwork;
-// the iterates are the output columns Y[i * n ...] themselves.
+// Inverse iteration on T - lambda_i I, one shift per eigenvalue.  Eigenvalues whose
+// consecutive gaps are below IV_ORTOL |T| form a cluster (in a truncated SVD's Gram block,
+// typically the tail of small Schmidt weights together with the rounding-level
+// eigenvalues), handled by one CTA: each member's thread factors T - lambda_i I with its
+// own eigenvalue as the shift (pivoted tridiagonal LU in the member's slice of gwork), every
+// sweep solves all members at once (one thread per member, the recurrences are serial) and
+// re-orthogonalises the members in order (classical Gram-Schmidt, twice, then a max-scaled
+// normalisation), so coincident eigenvalues still give independent vectors.  With its own
+// shift a member's iterate is dominated by its own eigenvector after each solve; a shared
+// shift (the cluster head's) left the members far from it dominated by the eigenvector
+// just outside the cluster, nearly parallel to that vector's own iterate, and Newton-Schulz
+// cannot restore a basis that far from orthonormal.  Outside a cluster an iterate is
+// accurate to about eps |T| / gap <= eps / IV_ORTOL, which the final Newton-Schulz steps
+// absorb.  The iterates are the output columns Y[i * n ...] themselves.
 constexpr int IV_THREADS = 128;
-constexpr int IV_CHUNK = 1024;  // earlier cluster members handled per Gram-Schmidt chunk
+constexpr int IV_CHUNK = 1024;   // earlier cluster members handled per Gram-Schmidt chunk
+constexpr double IV_ORTOL = 1e-11;
 
-// solve (T - lambda I) y = y in place from the pivoted LU factors; the vector is scaled
+// LU with partial pivoting of T - lam I (tridiagonal, textbook); factors in w[0 .. 5n):
+// dl, dm, du, du2 (n each), then n pivot bytes.  Pivots are floored at +-small in both
+// branches so that the solve never divides by less than eps |T|.
+__device__ void iv_factor(const double* d, const double* e, int64_t n, double lam, double small,
+                          double* w) {
+  double* dl = w;
+  double* dm = w + n;
+  double* du = w + 2 * n;
+  double* du2 = w + 3 * n;
+  int8_t* piv = (int8_t*)(w + 4 * n);
+  for (int64_t r = 0; r < n; ++r) {
+    dm[r] = d[r] - lam;
+    du[r] = r < n - 1 ? e[r] : 0.0;
+    dl[r] = r < n - 1 ? e[r] : 0.0;
+    du2[r] = 0.0;
+  }
+  for (int64_t r = 0; r < n - 1; ++r) {
+    const double a = dm[r], b = dl[r];
+    if (fabs(a) >= fabs(b)) {
+      const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
+      dm[r] = aa;
+      const double f = b / aa;
+      dl[r] = f;
+      dm[r + 1] -= f * du[r];
+      piv[r] = 0;
+    } else {
+      const double bb = fabs(b) < small ? (b < 0 ? -small : small) : b;
+      const double f = a / bb;
+      dm[r] = bb;
+      dl[r] = f;
+      const double t = du[r];
+      du[r] = dm[r + 1];
+      dm[r + 1] = t - f * du[r];
+      if (r < n - 2) {
+        du2[r] = du[r + 1];
+        du[r + 1] = -f * du[r + 1];
+      }
+      piv[r] = 1;
+    }
+  }
+  if (fabs(dm[n - 1]) < small) dm[n - 1] = dm[n - 1] < 0 ? -small : small;
+}
+
+// solve (T - lambda I) y = y in place from the factors of iv_factor; the vector is scaled
 // down whenever an entry passes 2^500 (compounding pivots of near-degenerate eigenvalues:
 // the solution of a scaled system is the scaled solution)
-__device__ void iv_solve(double* y, int64_t n, const double* dl, const double* dm,
-                         const double* du, const double* du2, const int8_t* piv) {
+__device__ void iv_solve(double* y, int64_t n, const double* w) {
+  const double* dl = w;
+  const double* dm = w + n;
+  const double* du = w + 2 * n;
+  const double* du2 = w + 3 * n;
+  const int8_t* piv = (const int8_t*)(w + 4 * n);
   for (int64_t r = 0; r < n - 1; ++r) {
     if (piv[r] == 0) {
       y[r + 1] -= dl[r] * y[r];
@@ -558,8 +610,7 @@ __device__ void iv_solve(double* y, int64_t n, const double* dl, const double* d
 __global__ void __launch_bounds__(IV_THREADS) k_inviter(
     const double* __restrict__ d, const double* __restrict__ e, int64_t n,
     const double* __restrict__ ev, int64_t k, const double* __restrict__ tnorm,
-    double* __restrict__ gwork, double* __restrict__ Y, int smem_ok) {
-  extern __shared__ double sm_iv[];
+    double* __restrict__ gwork, double* __restrict__ Y) {
   __shared__ double sdot[IV_CHUNK];
   __shared__ double sh[32];
   const int64_t i0 = blockIdx.x;
@@ -567,53 +618,15 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   // no weight) has T = 0, and pivots of eps |T| would then be denormal and the solves
   // would overflow; with the floor its eigenvectors come out as orthonormal start vectors
   const double tn = fmax(tnorm[0], 1e-200);
-  const double ortol = 1e3 * EPS * tn;
+  const double ortol = IV_ORTOL * tn;
   if (i0 > 0 && ev[i0 - 1] - ev[i0] < ortol) return;  // not the head of its cluster
   int64_t i1 = i0 + 1;
   while (i1 < k && ev[i1 - 1] - ev[i1] < ortol) ++i1;
-  double* work = smem_ok ? sm_iv : gwork + i0 * (6 * n);
-  double* dl = work;
-  double* dm = work + n;
-  double* du = work + 2 * n;
-  double* du2 = work + 3 * n;
-  int8_t* piv = (int8_t*)(work + 5 * n);
   const double small = EPS * tn;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nwarps = IV_THREADS / 32;
-  if (tid == 0) {
-    // LU with partial pivoting of T - lam I (tridiagonal, textbook), lam = ev[i0]
-    const double lam = ev[i0];
-    for (int64_t r = 0; r < n; ++r) {
-      dm[r] = d[r] - lam;
-      du[r] = r < n - 1 ? e[r] : 0.0;
-      dl[r] = r < n - 1 ? e[r] : 0.0;
-      du2[r] = 0.0;
-    }
-    for (int64_t r = 0; r < n - 1; ++r) {
-      const double a = dm[r], b = dl[r];
-      if (fabs(a) >= fabs(b)) {
-        const double aa = fabs(a) < small ? (a < 0 ? -small : small) : a;
-        dm[r] = aa;
-        const double f = b / aa;
-        dl[r] = f;
-        dm[r + 1] -= f * du[r];
-        piv[r] = 0;
-      } else {
-        const double f = a / b;
-        dm[r] = b;
-        dl[r] = f;
-        const double t = du[r];
-        du[r] = dm[r + 1];
-        dm[r + 1] = t - f * du[r];
-        if (r < n - 2) {
-          du2[r] = du[r + 1];
-          du[r + 1] = -f * du[r + 1];
-        }
-        piv[r] = 1;
-      }
-    }
-    if (fabs(dm[n - 1]) < small) dm[n - 1] = dm[n - 1] < 0 ? -small : small;
-  }
+  // each member's own factorisation, in its own 6n-double slice of gwork
+  for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_factor(d, e, n, ev[i], small, gwork + i * (6 * n));
   // deterministic start vectors, free of structure, distinct per member
   for (int64_t i = i0; i < i1; ++i)
     for (int64_t r = tid; r < n; r += IV_THREADS) {
@@ -625,7 +638,7 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
     }
   __syncthreads();
   for (int sweep = 0; sweep < 3; ++sweep) {
-    for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_solve(Y + i * n, n, dl, dm, du, du2, piv);
+    for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_solve(Y + i * n, n, gwork + i * (6 * n));
     __syncthreads();
     for (int64_t i = i0; i < i1; ++i) {
       double* y = Y + i * n;
@@ -802,13 +815,7 @@ int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const d
   {
     ProfScope ps(c, "heig_tridiag_eig");
     k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, n, k, ev, tn);
-    const size_t iv_smem = (size_t)n * (5 * sizeof(double) + 1);
-    const int smem_ok = iv_smem <= (size_t)180 * 1024;
-    if (smem_ok)
-      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)iv_smem));
-    k_inviter<<<(unsigned)k, IV_THREADS, smem_ok ? iv_smem : 0, st>>>(d, e, n, ev, k, tn, work, Y,
-                                                                     smem_ok);
+    k_inviter<<<(unsigned)k, IV_THREADS, 0, st>>>(d, e, n, ev, k, tn, work, Y);
     c->launches += 2;
     TNT_CHECK_LAUNCH(c);
   }
@@ -877,7 +884,9 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   cudaStream_t st = c->stream;
   {
     const double nn = (double)n;
-    ProfScope ps(c, "heig_tridiag", 24.0 * (nn - 1) * nn * (2 * nn - 1) / 6.0);
+    // Hermitian reduction to tridiagonal form: (16/3) n^3 real FLOPs (4 per complex
+    // multiply-add, two rank-2 updates of the trailing block and its matrix-vector product)
+    ProfScope ps(c, "heig_tridiag", 16.0 / 3.0 * nn * nn * nn);
     const size_t tri_smem = 4 * TRI_CACHE * sizeof(z);
     static int nsm = 0, occ = 0;
     if (!nsm) {
@@ -942,7 +951,7 @@ int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, d
   TNT_CUDA_TRY(c, cudaMemcpyAsync(dblk, hb.data(), sizeof(CtaBlk) * hb.size(), cudaMemcpyHostToDevice, st));
   {
     double fl = 0;
-    for (const SmallEig& b : blocks) fl += 24.0 * (double)(b.n - 1) * b.n * (2.0 * b.n - 1) / 6.0;
+    for (const SmallEig& b : blocks) fl += 16.0 / 3.0 * (double)b.n * b.n * b.n;
     ProfScope ps(c, "heig_tridiag", fl);
     k_tridiag_cta<<<(unsigned)blocks.size(), TRI_CTA_THREADS, 0, st>>>(G, dblk, d, e, tau);
     c->launches++;

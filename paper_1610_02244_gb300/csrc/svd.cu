@@ -33,8 +33,9 @@ struct CandBlock {
 };
 
 __global__ void k_cand_sigma(const z* __restrict__ X, const CandBlock* __restrict__ cb,
-                             double* __restrict__ sig) {
+                             const double* __restrict__ unscale, double* __restrict__ sig) {
   const CandBlock b = cb[blockIdx.x];
+  const double us = unscale[blockIdx.x];
   __shared__ double sh[256];
   for (int k = 0; k < b.r; ++k) {
     double acc = 0;
@@ -55,9 +56,37 @@ __global__ void k_cand_sigma(const z* __restrict__ X, const CandBlock* __restric
       if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) sig[b.vbase + k] = sqrt(sh[0]);
+    if (threadIdx.x == 0) sig[b.vbase + k] = sqrt(sh[0]) * us;
     __syncthreads();
   }
+}
+
+// Each gathered block M_q is scaled by the power of two 2^-e_q that brings max |Re|, |Im|
+// into [0.5, 1): exact, and it keeps the Gram matrix and its Householder reduction inside
+// the normal range whatever the sector's weight (a sector of theta far from the mean
+// filling can hold entries many orders below the rest, whose squares would underflow).
+// unscale[q] = 2^e_q multiplies every quantity read back from the scaled block.
+__global__ void k_block_scale(z* __restrict__ Mp, const int64_t* __restrict__ boff,
+                              const int64_t* __restrict__ bsize, double* __restrict__ unscale) {
+  __shared__ double sh[32];
+  const int64_t off = boff[blockIdx.x], cnt = bsize[blockIdx.x];
+  double mx = 0;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const z v = Mp[off + i];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
+  int ex = 0;
+  if (mx > 0 && isfinite(mx)) frexp(mx, &ex);
+  const double sc = ldexp(1.0, -ex);
+  if (threadIdx.x == 0) unscale[blockIdx.x] = ldexp(1.0, ex);
+  if (ex != 0)
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) Mp[off + i] = zscale(Mp[off + i], sc);
 }
 
 // -------------------------------------------------------------- global selection
@@ -175,14 +204,17 @@ struct KeptIdx {
   int64_t roff, nr;      // rows list slice
   int64_t coff, nc;      // cols list slice
   int loc;
+  int blk;               // block index (its unscale factor)
 };
 
 __global__ void k_scatter(const z* __restrict__ Vp, const z* __restrict__ Xp,
                           const KeptIdx* __restrict__ kept, const int64_t* __restrict__ rows,
-                          const int64_t* __restrict__ cols, int side, double scale, int64_t chi,
-                          int64_t n_total, z* __restrict__ U, z* __restrict__ X) {
+                          const int64_t* __restrict__ cols, const double* __restrict__ unscale,
+                          int side, double scale0, int64_t chi, int64_t n_total,
+                          z* __restrict__ U, z* __restrict__ X) {
   const int64_t k = blockIdx.y;
   const KeptIdx kd = kept[k];
+  const double scale = scale0 * unscale[kd.blk];
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < kd.nr;
        r += (int64_t)gridDim.x * blockDim.x) {
     z v;
@@ -384,6 +416,9 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   int* d_gdim = (int*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
   double* d_ev = (double*)ws_alloc(c, ws_round(sizeof(double) * 8192));
   double* d_tot = (double*)ws_alloc(c, ws_round(sizeof(double)));
+  double* d_unscale = (double*)ws_alloc(c, ws_round(sizeof(double) * nb));
+  int64_t* d_boff = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * 2 * nb));
+  if (!d_unscale || !d_boff) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
   if (!d_rows || !d_cols || !Mp || !Gp || !Vp || !Xp || !d_sig || !d_blk || !d_loc || !d_sig_s ||
       !d_blk_s || !d_loc_s || !d_sel || !d_cb || !d_goff || !d_gdim || !d_ev || !d_tot)
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
@@ -392,6 +427,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   std::vector<CandBlock> hcb(nb);
   std::vector<int64_t> hgoff(nb);
   std::vector<int> hgdim(nb), hblk(ntot_vals), hloc(ntot_vals);
+  std::vector<int64_t> hboff(2 * (size_t)nb);
   {
     int v = 0;
     for (int b = 0; b < nb; ++b) {
@@ -403,6 +439,8 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
       hcb[b].by_row = (side == TNT_SVD_LEFT);
       hgoff[b] = bl[b].goff;
       hgdim[b] = (int)bl[b].g;
+      hboff[b] = bl[b].moff;
+      hboff[nb + b] = bl[b].mq * bl[b].nq;
       for (int k = 0; k < bl[b].k; ++k, ++v) {
         hblk[v] = b;
         hloc[v] = k;
@@ -417,11 +455,19 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   TNT_CUDA_TRY(c, cudaMemcpyAsync(d_gdim, hgdim.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
   TNT_CUDA_TRY(c, cudaMemcpyAsync(d_blk, hblk.data(), sizeof(int) * ntot_vals, cudaMemcpyHostToDevice, st));
   TNT_CUDA_TRY(c, cudaMemcpyAsync(d_loc, hloc.data(), sizeof(int) * ntot_vals, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(d_boff, hboff.data(), sizeof(int64_t) * 2 * nb, cudaMemcpyHostToDevice, st));
 
-  // ---- gather blocks, Gram matrices
+  // ---- gather blocks, |M|_F^2 (unscaled), scale each block, Gram matrices
   for (int b = 0; b < nb; ++b) {
     const Blk& B = bl[b];
     TNT_TRY(gather2d(c, M, n, d_rows + B.roff, B.mq, d_cols + B.coff, B.nq, Mp + B.moff, B.nq, 0));
+  }
+  TNT_TRY(vec_norm2(c, Mp, mtot, d_tot));
+  k_block_scale<<<nb, 256, 0, st>>>(Mp, d_boff, d_boff + nb, d_unscale);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  for (int b = 0; b < nb; ++b) {
+    const Blk& B = bl[b];
     ZGemm g{};
     g.batch = 1;
     g.alpha = zmk(1, 0);
@@ -455,7 +501,6 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
       TNT_TRY(heig_top(c, Gp + B.goff, B.g, B.k, Vp + B.goff, B.g, d_ev));
     }
   }
-  TNT_TRY(vec_norm2(c, Mp, mtot, d_tot));
   // ---- candidate products and their norms
   for (int b = 0; b < nb; ++b) {
     const Blk& B = bl[b];
@@ -476,7 +521,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     }
     TNT_TRY(zgemm(c, g));
   }
-  k_cand_sigma<<<nb, 256, 0, st>>>(Xp, d_cb, d_sig);
+  k_cand_sigma<<<nb, 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
   c->launches++;
   // ---- global order and the four rules
   {
@@ -534,6 +579,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     K.coff = B.coff;
     K.nc = B.nq;
     K.loc = hl[e];
+    K.blk = hb[e];
     h_S[k] = hs[e] * scale;
     h_bq[k] = B.q;
   }
@@ -544,7 +590,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   TNT_TRY(zfill(c, X, chi * n, zmk(0, 0)));
   int64_t mx = std::max(m, n);
   dim3 gs((unsigned)std::min<int64_t>((mx + 255) / 256, 16), (unsigned)chi);
-  k_scatter<<<gs, 256, 0, st>>>(Vp, Xp, d_kept, d_rows, d_cols, side, scale, chi, n, U, X);
+  k_scatter<<<gs, 256, 0, st>>>(Vp, Xp, d_kept, d_rows, d_cols, d_unscale, side, scale, chi, n, U, X);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
   TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // host tables (hk) die at return

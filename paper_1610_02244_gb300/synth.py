@@ -20,6 +20,7 @@ __all__ = [
     "rng",
     "complex_gaussian",
     "hermitian_env",
+    "block_env",
     "sector_counts",
     "bond_charges",
     "random_charged_mps",
@@ -66,6 +67,35 @@ def hermitian_env(g: np.random.Generator, chi: int, D: int = 4, pair=(1, 2)) -> 
     E[:, p, :] = G[p]
     E[:, q, :] = G[p].conj().T
     return np.ascontiguousarray(E)
+
+
+def block_env(g: np.random.Generator, chi: int, side: str, gap: float = 1.0,
+              width: float = 10.0, coupling: float = 1.0, D: int = 4) -> np.ndarray:
+    """Environment E[a', w, a] with the channel structure a DMRG environment of the
+    lower-triangular Bose-Hubbard MPO has (left boundary channel 3, right boundary
+    channel 0), in the eigenbasis of its block Hamiltonian:
+
+      identity channel (3 on the left, 0 on the right): the unit matrix (a canonical block);
+      Hamiltonian channel (0 on the left, 3 on the right): diag(lam), lam_0 = 0 and the
+        other chi - 1 levels drawn uniformly in [gap, gap + width] (a gapped block spectrum);
+      channels 1 and 2: a boundary operator B with i.i.d. complex Gaussian entries of
+        variance coupling^2 / chi, and B^H (the Hermitian pairing of hermitian_env).
+
+    The two-site effective Hamiltonian built from a left and a right such environment is
+    Hermitian and has an isolated lowest level, as H_eff of a DMRG state does, so a
+    Lanczos solve converges (about 150 matvecs to 1e-12 at gap 1, width 10, chi 64..256)
+    where the i.i.d. Gaussian environments of hermitian_env give a dense low spectrum."""
+    if side not in ("left", "right"):
+        raise ValueError("side must be 'left' or 'right'")
+    ident, ham = (3, 0) if side == "left" else (0, 3)
+    E = np.zeros((chi, D, chi), dtype=np.complex128)
+    E[:, ident, :] = np.eye(chi)
+    lam = np.concatenate(([0.0], gap + width * np.sort(g.random(chi - 1))))
+    E[:, ham, :] = np.diag(lam)
+    B = complex_gaussian(g, (chi, chi)) * (coupling / np.sqrt(chi))
+    E[:, 1, :] = B
+    E[:, 2, :] = B.conj().T
+    return E
 
 
 COUNT_CAP = 1 << 40  # sector counts saturate here (3^101 does not fit in int64)

@@ -271,6 +271,69 @@ def test_svd_zero_charge_blocks(ctx, side):
     assert np.abs(U @ X - M).max() < 1e-11 * Sr.max()
 
 
+def low_rank_block(g, m, n, sigmas):
+    """m x n complex block U diag(sigmas) V^H with Haar-like orthonormal U, V."""
+    r = len(sigmas)
+    qu, _ = np.linalg.qr(g.normal(size=(m, r)) + 1j * g.normal(size=(m, r)))
+    qv, _ = np.linalg.qr(g.normal(size=(n, r)) + 1j * g.normal(size=(n, r)))
+    return (qu * np.asarray(sigmas)) @ qv.conj().T
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_svd_rank_deficient_blocks(ctx, side):
+    """Charge blocks whose rank is below their candidate count and whose spectra fall
+    geometrically to far below the Gram matrix's rounding level, the shape of theta early
+    in a quench from a product state (Sec. 5) and of any converged DMRG bond: 99 x 64 of
+    rank 40 (sigma 1 .. 1e-22), 120 x 110 of rank 30, 30 x 20 of rank 5, a 10 x 12 block
+    of weight 1e-170 (its Gram entries would underflow unscaled) and a 300 x 280 block of
+    rank 100 (the whole-GPU reduction).  With chi_max = 512 and the 1e-10 truncation error
+    of the 64-site quench, the kept factor must be orthonormal to rounding, every singular
+    value above 1e-8 must match the oracle's, and the truncated product must be within the
+    truncation error of M.  (Values below ~1e-8 |M| sit under the Gram matrix's resolution
+    and are compared through the product only.)"""
+    g = np.random.default_rng(1610 + side)
+    spec = [(99, 64, np.geomspace(1.0, 1e-22, 40)), (120, 110, np.geomspace(0.5, 1e-14, 30)),
+            (30, 20, np.geomspace(1e-3, 1e-9, 5)), (10, 12, 1e-170 * np.geomspace(1, 1e-3, 10)),
+            (300, 280, np.geomspace(0.8, 1e-20, 100))]
+    m = sum(s[0] for s in spec)
+    n = sum(s[1] for s in spec)
+    M = np.zeros((m, n), np.complex128)
+    rq = np.zeros(m, np.int64)
+    cq = np.zeros(n, np.int64)
+    r0 = c0 = 0
+    for q, (bm, bn, sig) in enumerate(spec):
+        M[r0:r0 + bm, c0:c0 + bn] = low_rank_block(g, bm, bn, sig)
+        rq[r0:r0 + bm] = q
+        cq[c0:c0 + bn] = q
+        r0 += bm
+        c0 += bn
+    pr, pc = g.permutation(m), g.permutation(n)
+    M, rq, cq = M[pr][:, pc], rq[pr], cq[pc]
+    ctx.set_params(chi_max=512, trunc_err=1e-10, trunc_rel=1e-16)
+    try:
+        U, X, S, bq, info = ctx.svd_trunc(dev(M), rq, cq, side=side)
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    Ur, Sr, Vr, bqr, inf_r = osvd.svd_truncate(M, rq, cq, osvd.TruncParams(chi_max=512,
+                                                                              err_tol=1e-10))
+    U, X = U.cpu().numpy(), X.cpu().numpy()
+    assert np.isfinite(S).all() and np.isfinite(U).all() and np.isfinite(X).all()
+    k = len(S)
+    if side == 0:
+        assert np.abs(U.conj().T @ U - np.eye(k)).max() < 1e-12
+    else:
+        assert np.abs(X @ X.conj().T - np.eye(k)).max() < 1e-12
+    big = np.sort(Sr[Sr > 1e-8])[::-1]
+    assert np.abs(np.sort(S)[::-1][:len(big)] - big).max() < 1e-12
+    assert info["err"] < 1e-10
+    assert np.linalg.norm(U @ X - M) < 3e-10 * np.linalg.norm(M)
+    # every kept value belongs to a block that holds it: labels agree where values are resolved
+    for q in range(len(spec)):
+        sq = np.sort(S[bq == q])[::-1]
+        rr = np.sort(Sr[(bqr == q) & (Sr > 1e-8)])[::-1]
+        assert np.abs(sq[:len(rr)] - rr).max(initial=0) < 1e-12
+
+
 @pytest.mark.parametrize("side", [0, 1])
 def test_svd_automatic_blocking(ctx, side):
     """Automatic blocking (Sec. 6): a block-diagonal matrix with rows and columns shuffled

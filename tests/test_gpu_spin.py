@@ -240,12 +240,7 @@ def _golden(name):
     return vals
 
 
-@pytest.mark.parametrize("precision", [
-    0,
-    pytest.param(1, marks=pytest.mark.xfail(
-        strict=False, reason="split-TF32 first sweeps leave the oracle on the 100-site trapped "
-                             "chain (open defect); whether they do on this chain is not known")),
-])
+@pytest.mark.parametrize("precision", [0, 1])
 def test_spin1_table1_first_sweep_matches_oracle(ctx, precision):
     """The DMRG benchmark's configuration (Table 1: L = 101, chi = 200, S^z_total = 0, the
     seeded Gaussian-profile start): the GPU's first sweep against the FP64 oracle's first

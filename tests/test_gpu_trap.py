@@ -125,7 +125,7 @@ def test_e1_first_sweep_matches_oracle(ctx, precision):
     assert abs(E - ref) <= 1e-6 * abs(ref), (E, ref, first, Eu[first], Eu_ref[first])
 
 
-@pytest.mark.xfail(run=False, strict=False,
+@pytest.mark.xfail(strict=False,
                    reason="open defect: in split TF32 the eigensolves of this trapped chain "
                           "stopped at the 300-matvec cap, the sweep energies collapsed and a "
                           "start vector vanished (before split-TF32 solves were finished in "
