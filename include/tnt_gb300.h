@@ -139,6 +139,27 @@ typedef struct {
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
  * NULL for the legacy default stream).  Fails with TNT_E_CUDA if no usable GPU exists. */
 int tnt_ctx_create(int device, void* stream, tnt_ctx** out);
+
+/* Device allocator supplied by the caller (the paper's tntSystem owns the library's
+ * resources, App. A.3; here an application that manages device memory itself, e.g. through
+ * PyTorch's caching allocator, hands the library its alloc/free pair).  alloc(bytes, user)
+ * returns device memory on the context's device, aligned to at least 256 bytes, or NULL
+ * (the call that needed it then fails with TNT_E_ALLOC); free(ptr, user) receives only
+ * pointers alloc returned.  Both are called on the thread that called into the library,
+ * never from a kernel; before memory goes back through free the library synchronises the
+ * device, so nothing of its own still uses it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} tnt_allocator;
+
+/* tnt_ctx_create with every device allocation of the context, and of the MPO, MPS, DMRG
+ * and TEBD handles made from it (scratch arena, status word, FP64 product slices, site
+ * tensors, environments), made through *alloc (copied; alloc->user must outlive them).
+ * TNT_E_INVALID if alloc or either callback is NULL. */
+int tnt_ctx_create_with_allocator(int device, void* stream, const tnt_allocator* alloc,
+                                  tnt_ctx** out);
 int tnt_ctx_destroy(tnt_ctx* ctx);
 /* Replace the stream used by later calls. */
 int tnt_set_stream(tnt_ctx* ctx, void* stream);
@@ -349,6 +370,32 @@ int tnt_mps_get_charges(const tnt_mps* mps, int bond, int64_t* h_out, int64_t ca
 int tnt_mps_expect_mpo(tnt_ctx* ctx, const tnt_mps* mps, const tnt_mpo* mpo, double* E);
 int tnt_mps_norm2(tnt_ctx* ctx, const tnt_mps* mps, double* norm2);
 
+/* <a|b> of two MPS of equal length and physical dimension (the <psi|O|psi> network of
+ * Sec. 4.3 with O = 1 and two different states), FP64, contracted site by site from the
+ * left (two GEMMs per site); labels are not used.  Host output; synchronises the stream.
+ * TNT_E_INVALID on mismatched L or d. */
+int tnt_mps_overlap(tnt_ctx* ctx, const tnt_mps* a, const tnt_mps* b, tnt_cplx* out);
+
+/* Replace the U(1) labels of bond `bond` (App. A.1.1: tntNodeSetQN sets the quantum numbers
+ * of a leg; here a bond label counts the bosons to the left of the bond).  h_q holds
+ * chi[bond] labels (host, copied).  Accepted only if every non-zero entry of the two sites
+ * next to the bond keeps q_left + s = q_right under the new labels (checked on the device);
+ * otherwise TNT_E_INVALID with the count of violating entries, and the labels are left as
+ * they were.  The MPS must carry labels; the boundary bonds' labels are fixed. */
+int tnt_mps_set_charges(tnt_ctx* ctx, tnt_mps* mps, int bond, const int64_t* h_q);
+
+/* File output and input of an MPS (App. B.5: the library writes its networks with their
+ * block labels and its system settings, and a file written by one calculation is the input
+ * of the next).  The file (native byte order) holds: the 8 bytes "TNTMPS01"; int32 L, d
+ * and a labels flag; the context's tnt_params; int64 chi[0..L]; with labels, chi[k] int64
+ * labels per bond; every site tensor (chi[j] x d x chi[j+1] tnt_cplx, row-major).
+ * tnt_mps_load creates a new MPS (storage cap chi_cap, as tnt_mps_create) and, if
+ * restore_params != 0, sets the context's parameters to the saved ones.  TNT_E_INVALID on
+ * an unreadable, truncated or foreign file, or a bond above chi_cap. */
+int tnt_mps_save(tnt_ctx* ctx, const tnt_mps* mps, const char* path);
+int tnt_mps_load(tnt_ctx* ctx, const char* path, int64_t chi_cap, int restore_params,
+                 tnt_mps** out);
+
 /* Observables of Sec. 5's examples, FP64, for any (not necessarily normalised) MPS:
  * h_n[j] = <n_j> / <psi|psi> (L values), and the single-particle density matrix
  * h_rho[i*L + j] = <b+_i b_j> / <psi|psi> (L x L, Hermitian), by transfer environments
@@ -384,6 +431,17 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* dmrg, double alpha, tnt_sweep_stats*
  * are copied to h_E (host memory; NULL allowed with cap = 0).  Host only, no GPU work.
  * TNT_E_INVALID for a NULL handle or n, cap < 0, or a NULL h_E with cap > 0. */
 int tnt_dmrg_update_energies(const tnt_dmrg* dmrg, double* h_E, int64_t cap, int64_t* n);
+/* One two-site update on bond (bond, bond + 1) of the handle's MPS (Sec. 4.3 Listing 2:
+ * one local optimisation, in two-site form): theta, the eigensolve, the truncated SVD with
+ * S renormalised and the environment growth, exactly as inside tnt_dmrg_sweep.  dir = +1
+ * leaves the orthogonality centre on site bond + 1 (A_bond <- U) and grows the left
+ * environment; dir = -1 leaves it on site bond (A_bond+1 <- V^H) and grows the right one.
+ * The centre must be on site bond or bond + 1 and the environments of the bond current
+ * (after tnt_dmrg_create the centre is on site 0, and a sweep ends there), else
+ * TNT_E_INVALID.  Results in *lz and *tr; TNT_E_NOCONV if the eigensolve hit its cap (the
+ * update is still applied).  A sweep requires the centre back on site 0. */
+int tnt_dmrg_update(tnt_ctx* ctx, tnt_dmrg* dmrg, int bond, int dir, tnt_lanczos_result* lz,
+                    tnt_trunc_result* tr);
 int tnt_dmrg_destroy(tnt_dmrg* dmrg);
 
 /* ------------------------------------------------------------------ FP64 matrix products */
@@ -503,6 +561,17 @@ int tnt_tebd_create_spin(tnt_ctx* ctx, tnt_mps* mps, int two_s, double J, double
 int tnt_tebd_create_bonds(tnt_ctx* ctx, tnt_mps* mps, const tnt_cplx* const* h_bond,
                           double dt, tnt_tebd** out);
 int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* tebd, tnt_step_stats* stats);
+/* One two-site gate on bond (bond, bond + 1) through the TEBD handle, which tracks the
+ * orthogonality centre (Sec. 3's Trotterised update is a sequence of these): the centre is
+ * moved to site bond or bond + 1 by exact SVD moves, theta' = G theta with h_gate the
+ * d^2 x d^2 matrix G[(s1' s2'), (s1 s2)] (host, row-major, copied; e.g. from tnt_bond_gate),
+ * then the truncated SVD with the context's parameters and no renormalisation; dir = +1
+ * leaves the centre on site bond + 1 (A_bond <- U), dir = -1 on site bond.  The SVD's
+ * result in *tr.  TNT_E_NAN for a non-finite gate entry. */
+int tnt_tebd_gate(tnt_ctx* ctx, tnt_tebd* tebd, int bond, const tnt_cplx* h_gate, int dir,
+                  tnt_trunc_result* tr);
+/* The site holding the orthogonality centre of the TEBD handle's MPS. */
+int tnt_tebd_centre(const tnt_tebd* tebd, int* centre);
 int tnt_tebd_destroy(tnt_tebd* tebd);
 
 #if defined(__GNUC__)

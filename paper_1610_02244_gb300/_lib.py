@@ -70,6 +70,14 @@ class tnt_step_stats(C.Structure):
                 ("seconds", C.c_double)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class tnt_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
 P = C.c_void_p
 I64 = C.c_int64
 I = C.c_int
@@ -80,6 +88,7 @@ PD = C.POINTER(C.c_double)
 # name -> argtypes (all return int unless listed in _RESTYPE)
 SIGNATURES = {
     "tnt_ctx_create": [I, P, C.POINTER(P)],
+    "tnt_ctx_create_with_allocator": [I, P, C.POINTER(tnt_allocator), C.POINTER(P)],
     "tnt_ctx_destroy": [P],
     "tnt_set_stream": [P, P],
     "tnt_last_error": [P],
@@ -117,10 +126,15 @@ SIGNATURES = {
     "tnt_mps_get_charges": [P, I, P, I64],
     "tnt_mps_expect_mpo": [P, P, P, PD],
     "tnt_mps_norm2": [P, P, PD],
+    "tnt_mps_overlap": [P, P, P, C.POINTER(tnt_cplx)],
+    "tnt_mps_set_charges": [P, P, I, P],
+    "tnt_mps_save": [P, P, C.c_char_p],
+    "tnt_mps_load": [P, C.c_char_p, I64, I, C.POINTER(P)],
     "tnt_dmrg_create": [P, P, P, C.POINTER(P)],
     "tnt_dmrg_sweep": [P, P, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_sweep1": [P, P, D, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_update_energies": [P, C.POINTER(D), I64, C.POINTER(I64)],
+    "tnt_dmrg_update": [P, P, I, I, C.POINTER(tnt_lanczos_result), C.POINTER(tnt_trunc_result)],
     "tnt_dmrg_destroy": [P],
     "tnt_mps_density": [P, P, PD],
     "tnt_mps_bdagb": [P, P, P],
@@ -141,6 +155,8 @@ SIGNATURES = {
     "tnt_set_fp64_gemm": [P, I],
     "tnt_u1_tiles": [P, I, C.POINTER(tnt_u1_problem), C.POINTER(C.c_int)],
     "tnt_tebd_step": [P, P, C.POINTER(tnt_step_stats)],
+    "tnt_tebd_gate": [P, P, I, P, I, C.POINTER(tnt_trunc_result)],
+    "tnt_tebd_centre": [P, C.POINTER(I)],
     "tnt_tebd_destroy": [P],
 }
 _RESTYPE = {"tnt_last_error": C.c_char_p, "tnt_launch_count": C.c_int64}

@@ -19,6 +19,29 @@ int set_err(Ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+int dev_alloc(const DevAlloc& a, void** p, size_t bytes) {
+  *p = nullptr;
+  if (a.alloc) {
+    *p = a.alloc(bytes, a.user);
+    return *p ? 0 : 1;
+  }
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    return 1;
+  }
+  return 0;
+}
+
+void dev_free(const DevAlloc& a, void* p) {
+  if (!p) return;
+  if (a.free) {
+    cudaDeviceSynchronize();  // no kernel of this library may still use the memory
+    a.free(p, a.user);
+  } else {
+    cudaFree(p);
+  }
+}
+
 int ws_reserve(Ctx* c, size_t bytes) {
   if (bytes <= c->ws.cap) return TNT_OK;
   if (c->ws.top != 0)
@@ -26,16 +49,14 @@ int ws_reserve(Ctx* c, size_t bytes) {
                    "scratch of %zu bytes needed while %zu bytes are in use (reserve first)", bytes,
                    c->ws.top);
   TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  if (c->ws.base) TNT_CUDA_TRY(c, cudaFree(c->ws.base));
+  dev_free(c->dalloc, c->ws.base);
   c->ws.base = nullptr;
   c->ws.cap = 0;
   size_t cap = ws_round(bytes + bytes / 8);
-  cudaError_t e = cudaMalloc((void**)&c->ws.base, cap);
-  if (e != cudaSuccess) {
-    c->ws.base = nullptr;
-    return set_err(c, TNT_E_ALLOC, "cudaMalloc of %zu bytes of scratch failed: %s", cap,
-                   cudaGetErrorString(e));
-  }
+  void* base = nullptr;
+  if (dev_alloc(c->dalloc, &base, cap) != 0)
+    return set_err(c, TNT_E_ALLOC, "device allocation of %zu bytes of scratch failed", cap);
+  c->ws.base = (char*)base;
   c->ws.cap = cap;
   return TNT_OK;
 }
@@ -286,7 +307,7 @@ int tnt_params_default(tnt_params* p) {
   return TNT_OK;
 }
 
-int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
+static int ctx_create(int device, void* stream, const DevAlloc& a, tnt_ctx** out) {
   if (!out) return TNT_E_INVALID;
   *out = nullptr;
   int n = 0;
@@ -295,14 +316,17 @@ int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
   tnt_ctx* t = new tnt_ctx();
   t->c.device = device;
   t->c.stream = (cudaStream_t)stream;
+  t->c.dalloc = a;
   tnt_params_default(&t->c.params);
-  if (cudaMalloc((void**)&t->c.d_status, 64) != cudaSuccess) {
+  void* st = nullptr;
+  if (dev_alloc(a, &st, 256) != 0) {
     delete t;
-    return TNT_E_CUDA;
+    return a.alloc ? TNT_E_ALLOC : TNT_E_CUDA;
   }
-  cudaMemset(t->c.d_status, 0, 64);
-  if (pinned_reserve(&t->c, 4096) != TNT_OK) {
-    cudaFree(t->c.d_status);
+  t->c.d_status = (int*)st;
+  cudaMemsetAsync(t->c.d_status, 0, 64, t->c.stream);
+  if (pinned_reserve(&t->c, 4096) != TNT_OK || cudaStreamSynchronize(t->c.stream) != cudaSuccess) {
+    dev_free(a, t->c.d_status);
     delete t;
     return TNT_E_ALLOC;
   }
@@ -310,14 +334,30 @@ int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
   return TNT_OK;
 }
 
+int tnt_ctx_create(int device, void* stream, tnt_ctx** out) {
+  return ctx_create(device, stream, DevAlloc{}, out);
+}
+
+int tnt_ctx_create_with_allocator(int device, void* stream, const tnt_allocator* alloc,
+                                  tnt_ctx** out) {
+  if (!out) return TNT_E_INVALID;
+  *out = nullptr;
+  if (!alloc || !alloc->alloc || !alloc->free) return TNT_E_INVALID;
+  DevAlloc a;
+  a.alloc = alloc->alloc;
+  a.free = alloc->free;
+  a.user = alloc->user;
+  return ctx_create(device, stream, a, out);
+}
+
 int tnt_ctx_destroy(tnt_ctx* ctx) {
   if (!ctx) return TNT_E_INVALID;
   cudaStreamSynchronize(ctx->c.stream);
   for (auto& e : ctx->c.prof_ev) cudaEventDestroy(e);
-  if (ctx->c.ws.base) cudaFree(ctx->c.ws.base);
+  dev_free(ctx->c.dalloc, ctx->c.ws.base);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
-  if (ctx->c.d_status) cudaFree(ctx->c.d_status);
-  if (ctx->c.oz_buf) cudaFree(ctx->c.oz_buf);
+  dev_free(ctx->c.dalloc, ctx->c.d_status);
+  dev_free(ctx->c.dalloc, ctx->c.oz_buf);
   delete ctx;
   return TNT_OK;
 }

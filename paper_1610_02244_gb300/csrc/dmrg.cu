@@ -421,6 +421,7 @@ static int mpo_upload(Ctx* c, int L, int d, int D, const std::vector<std::vector
                       const std::vector<z>& lb, const std::vector<z>& rb, std::vector<int> wq,
                       tnt_mpo** out) {
   tnt_mpo* o = new tnt_mpo();
+  o->dalloc = c->dalloc;
   o->L = L;
   o->d = d;
   o->D = D;
@@ -430,9 +431,9 @@ static int mpo_upload(Ctx* c, int L, int d, int D, const std::vector<std::vector
   const size_t nW = (size_t)D * D * d * d;
   for (int j = 0; j < L; ++j) {
     z* dW = nullptr;
-    if (cudaMalloc((void**)&dW, nW * sizeof(z)) != cudaSuccess) {
+    if (dev_alloc(c->dalloc, (void**)&dW, nW * sizeof(z)) != 0) {
       tnt_mpo_destroy(o);
-      return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPO failed");
+      return set_err(c, TNT_E_ALLOC, "device allocation for the MPO failed");
     }
     o->W.push_back(dW);
     o->hW.push_back(sites[(size_t)j]);
@@ -441,8 +442,8 @@ static int mpo_upload(Ctx* c, int L, int d, int D, const std::vector<std::vector
       return set_err(c, TNT_E_CUDA, "MPO upload failed");
     }
   }
-  if (cudaMalloc((void**)&o->left, sizeof(z) * D) != cudaSuccess ||
-      cudaMalloc((void**)&o->right, sizeof(z) * D) != cudaSuccess ||
+  if (dev_alloc(c->dalloc, (void**)&o->left, sizeof(z) * D) != 0 ||
+      dev_alloc(c->dalloc, (void**)&o->right, sizeof(z) * D) != 0 ||
       cudaMemcpy(o->left, lb.data(), sizeof(z) * D, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(o->right, rb.data(), sizeof(z) * D, cudaMemcpyHostToDevice) != cudaSuccess) {
     tnt_mpo_destroy(o);
@@ -508,9 +509,9 @@ int tnt_mpo_create(tnt_ctx* ctx, int L, int d, int D, const tnt_cplx* const* h_W
 
 int tnt_mpo_destroy(tnt_mpo* mpo) {
   if (!mpo) return TNT_E_INVALID;
-  for (z* w : mpo->W) cudaFree(w);
-  if (mpo->left) cudaFree(mpo->left);
-  if (mpo->right) cudaFree(mpo->right);
+  for (z* w : mpo->W) dev_free(mpo->dalloc, w);
+  dev_free(mpo->dalloc, mpo->left);
+  dev_free(mpo->dalloc, mpo->right);
   delete mpo;
   return TNT_OK;
 }
@@ -521,6 +522,7 @@ int tnt_mps_create(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int64_t* h
   Ctx* c = &ctx->c;
   if (h_chi[0] != 1 || h_chi[L] != 1) return set_err(c, TNT_E_INVALID, "boundary bonds must be 1");
   tnt_mps* m = new tnt_mps();
+  m->dalloc = c->dalloc;
   m->L = L;
   m->d = d;
   m->chi.assign(h_chi, h_chi + L + 1);
@@ -540,9 +542,9 @@ int tnt_mps_create(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int64_t* h
   for (int j = 0; j < L; ++j) {
     z* p = nullptr;
     const size_t capn = (size_t)(m->cap[j] * d * m->cap[j + 1]);
-    if (cudaMalloc((void**)&p, capn * sizeof(z)) != cudaSuccess) {
+    if (dev_alloc(c->dalloc, (void**)&p, capn * sizeof(z)) != 0) {
       tnt_mps_destroy(m);
-      return set_err(c, TNT_E_ALLOC, "cudaMalloc for MPS site %d failed", j);
+      return set_err(c, TNT_E_ALLOC, "device allocation for MPS site %d failed", j);
     }
     m->A.push_back(p);
     const size_t nn = (size_t)(m->chi[j] * d * m->chi[j + 1]);
@@ -576,7 +578,7 @@ int tnt_mps_product(tnt_ctx* ctx, int L, int d, int64_t chi_cap, const int* h_oc
 
 int tnt_mps_destroy(tnt_mps* m) {
   if (!m) return TNT_E_INVALID;
-  for (z* p : m->A) cudaFree(p);
+  for (z* p : m->A) dev_free(m->dalloc, p);
   delete m;
   return TNT_OK;
 }
@@ -678,6 +680,7 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) 
   Ctx* c = &ctx->c;
   tnt_dmrg* g = new tnt_dmrg();
   g->ctx = ctx;
+  g->dalloc = c->dalloc;
   g->mps = m;
   g->mpo = o;
   const int L = m->L;
@@ -690,10 +693,10 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) 
     }
   for (int k = 0; k <= L; ++k) {
     const size_t ne = (size_t)(m->cap[k] * o->D * m->cap[k]);
-    if (cudaMalloc((void**)&g->Lenv[k], ne * sizeof(z)) != cudaSuccess ||
-        cudaMalloc((void**)&g->Renv[k], ne * sizeof(z)) != cudaSuccess) {
+    if (dev_alloc(c->dalloc, (void**)&g->Lenv[k], ne * sizeof(z)) != 0 ||
+        dev_alloc(c->dalloc, (void**)&g->Renv[k], ne * sizeof(z)) != 0) {
       tnt_dmrg_destroy(g);
-      return set_err(c, TNT_E_ALLOC, "cudaMalloc for environments failed");
+      return set_err(c, TNT_E_ALLOC, "device allocation for environments failed");
     }
   }
   g->scratch = dmrg_scratch_bound(m, o->D, c->params);
@@ -755,13 +758,60 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) 
   }
   ws_reset(c);
   TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  g->centre = 0;
+  g->lvalid = 0;
+  g->rvalid = 1;
   *out = g;
   return TNT_OK;
+}
+
+// sweeps start and end with the centre on site 0 and every right environment current
+static int sweep_ready(Ctx* c, const tnt_dmrg* g) {
+  if (g->centre != 0 || g->rvalid > 1)
+    return set_err(c, TNT_E_INVALID,
+                   "a sweep starts with the centre on site 0 (it is on site %d; move it back "
+                   "with right-to-left updates)", g->centre);
+  return TNT_OK;
+}
+
+int tnt_dmrg_update(tnt_ctx* ctx, tnt_dmrg* g, int bond, int dir, tnt_lanczos_result* lz,
+                    tnt_trunc_result* tr) {
+  if (!ctx || !g || !lz || !tr || g->ctx != ctx) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mps* m = g->mps;
+  const int i = bond;
+  if (i < 0 || i + 1 >= m->L || (dir != 1 && dir != -1))
+    return set_err(c, TNT_E_INVALID, "bond %d / direction %d (bonds 0..%d, direction +1 or -1)",
+                   bond, dir, m->L - 2);
+  if ((g->centre != i && g->centre != i + 1) || g->lvalid < i || g->rvalid > i + 2)
+    return set_err(c, TNT_E_INVALID,
+                   "bond %d needs the centre on site %d or %d and its environments current "
+                   "(centre on site %d)", i, i, i + 1, g->centre);
+  *lz = tnt_lanczos_result{};
+  *tr = tnt_trunc_result{};
+  ws_reset(c);
+  TNT_TRY(ws_reserve(c, g->scratch));
+  int r = dmrg_update(c, g, i, dir, lz, tr, false);
+  if (r == TNT_OK) r = dir > 0 ? dmrg_env_left(c, g, i) : dmrg_env_right(c, g, i + 1);
+  ws_reset(c);
+  if (r != TNT_OK) return r;
+  if (dir > 0) {
+    g->centre = i + 1;
+    g->lvalid = i + 1;
+    g->rvalid = std::max(g->rvalid, i + 2);
+  } else {
+    g->centre = i;
+    g->rvalid = i + 1;
+    g->lvalid = std::min(g->lvalid, i);
+  }
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return lz->converged ? TNT_OK : TNT_E_NOCONV;
 }
 
 int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
   if (!ctx || !g || !st || g->ctx != ctx) return TNT_E_INVALID;
   Ctx* c = &ctx->c;
+  TNT_TRY(sweep_ready(c, g));
   tnt_mps* m = g->mps;
   const int L = m->L;
   *st = tnt_sweep_stats{};
@@ -829,12 +879,18 @@ int tnt_dmrg_sweep(tnt_ctx* ctx, tnt_dmrg* g, tnt_sweep_stats* st) {
   st->seconds = ms * 1e-3;
   st->E = E;
   st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
+  // a sweep that stopped at an error leaves the gauge unknown: no single update until the
+  // next full sweep is asked for, which then reports the state instead of running
+  g->centre = r == TNT_OK ? 0 : -1;
+  g->lvalid = 0;
+  g->rvalid = r == TNT_OK ? 1 : m->L + 1;
   return r;
 }
 
 int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st) {
   if (!ctx || !g || !st || g->ctx != ctx || !(alpha >= 0) || !std::isfinite(alpha)) return TNT_E_INVALID;
   Ctx* c = &ctx->c;
+  TNT_TRY(sweep_ready(c, g));
   tnt_mps* m = g->mps;
   const int L = m->L;
   *st = tnt_sweep_stats{};
@@ -880,6 +936,9 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* g, double alpha, tnt_sweep_stats* st
   st->seconds = ms * 1e-3;
   st->E = E;
   st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
+  g->centre = r == TNT_OK ? 0 : -1;
+  g->lvalid = 0;
+  g->rvalid = r == TNT_OK ? 1 : m->L + 1;
   return r;
 }
 
@@ -895,8 +954,8 @@ int tnt_dmrg_destroy(tnt_dmrg* g) {
   if (!g) return TNT_E_INVALID;
   for (cudaEvent_t e : g->ev)
     if (e) cudaEventDestroy(e);
-  for (z* p : g->Lenv) if (p) cudaFree(p);
-  for (z* p : g->Renv) if (p) cudaFree(p);
+  for (z* p : g->Lenv) dev_free(g->dalloc, p);
+  for (z* p : g->Renv) dev_free(g->dalloc, p);
   delete g;
   return TNT_OK;
 }

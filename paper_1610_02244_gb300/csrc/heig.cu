@@ -9,7 +9,7 @@
 //      to full precision.
 //   3. Inverse iteration on T - lambda_i I (pivoted tridiagonal LU, three sweeps), each
 //      eigenvalue its own shift; the iterates of a cluster of eigenvalues closer than
-//      1e-11 |T| are re-orthogonalised against the cluster's earlier vectors.
+//      1e3 eps |T| are re-orthogonalised against the cluster's earlier vectors.
 //   4. Back-transformation U = H_0 H_1 ... H_{n-2} Y.
 //   5. Two Newton-Schulz steps U <- U (3 I - U^H U) / 2 in FP64 to restore orthonormality
 //      lost to close eigenvalues.
@@ -471,15 +471,31 @@ __device__ int sturm_lt(const double* d, const double* e, int64_t n, double x, d
   return cnt;
 }
 
+// One eigenproblem of the eigen phase, several of which share each launch (the charge
+// blocks of one truncated SVD): the tridiagonal T (d, e, tau at off; n entries), its
+// reflectors (row j = v_j of Hv at hoff, row stride n), and the k wanted eigenpairs, whose
+// eigenvalues sit at ev[evo ..], iterates at Y[yo ..] (n k), first eigenvectors at
+// U0[yo ..] (n x k, leading dimension k), inverse-iteration factors at gwork[wo ..] (6 n k).
+struct EBlk {
+  int64_t n, k;
+  int64_t off, hoff, evo, yo, wo;
+};
+
 // eigenvalue of ascending index n-1-i for i < k; ev[i] descending.  One warp per
 // eigenvalue: the 32 lanes evaluate Sturm counts at 32 interior points, shrinking the
 // bracket 33-fold per step, to full precision (about 11 steps).  The values serve only as
 // shifts (singular values are taken later as FP64 projection norms), and each SM's few
-// FP64 units favour short dependent chains over many of them.
-__global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e, int64_t n,
-                         int64_t k, double* __restrict__ ev, double* __restrict__ tnorm_out) {
+// FP64 units favour short dependent chains over many of them.  Warp g works on eigenvalue
+// eig[g].y of problem eig[g].x; the warp of eigenvalue 0 also writes |T| of its problem.
+__global__ void k_bisect(const double* __restrict__ dAll, const double* __restrict__ eAll,
+                         const EBlk* __restrict__ blks, const int2* __restrict__ eig,
+                         double* __restrict__ evAll, double* __restrict__ tnorm_out) {
   const int lane = threadIdx.x & 31;
-  const int64_t i = blockIdx.x;
+  const int2 gi = eig[blockIdx.x];
+  const EBlk B = blks[gi.x];
+  const int64_t n = B.n, i = gi.y;
+  const double* d = dAll + B.off;
+  const double* e = eAll + B.off;
   double lo = INFINITY, hi = -INFINITY, tn = 0, emax2 = 0;
   for (int64_t r = lane; r < n; r += 32) {
     const double rad = (r > 0 ? fabs(e[r - 1]) : 0.0) + (r < n - 1 ? fabs(e[r]) : 0.0);
@@ -495,8 +511,7 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
     tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
     emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
   }
-  if (i == 0 && lane == 0 && tnorm_out) tnorm_out[0] = tn;
-  if (i >= k) return;
+  if (i == 0 && lane == 0) tnorm_out[gi.x] = tn;
   const double pivmin = fmax(1e-300, EPS * EPS * fmax(emax2, 1e-300)) + 1e-300;
   const int64_t idx = n - 1 - i;
   const double pad = 2 * EPS * tn + 1e-300;
@@ -514,13 +529,13 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) ev[i] = 0.5 * (lo + hi);
+  if (lane == 0) evAll[B.evo + i] = 0.5 * (lo + hi);
 }
 
 // Inverse iteration on T - lambda_i I, one shift per eigenvalue.  Eigenvalues whose
-// consecutive gaps are below IV_ORTOL |T| form a cluster (in a truncated SVD's Gram block,
-// typically the tail of small Schmidt weights together with the rounding-level
-// eigenvalues), handled by one CTA: each member's thread factors T - lambda_i I with its
+// consecutive gaps are below IV_ORTOL |T| = 1e3 eps |T| form a cluster (in a truncated
+// SVD's Gram block, typically the rounding-level eigenvalues of a rank-deficient block),
+// handled by one CTA: each member's thread factors T - lambda_i I with its
 // own eigenvalue as the shift (pivoted tridiagonal LU in the member's slice of gwork), every
 // sweep solves all members at once (one thread per member, the recurrences are serial) and
 // re-orthogonalises the members in order (classical Gram-Schmidt, twice, then a max-scaled
@@ -533,7 +548,7 @@ __global__ void k_bisect(const double* __restrict__ d, const double* __restrict_
 // absorb.  The iterates are the output columns Y[i * n ...] themselves.
 constexpr int IV_THREADS = 128;
 constexpr int IV_CHUNK = 1024;   // earlier cluster members handled per Gram-Schmidt chunk
-constexpr double IV_ORTOL = 1e-11;
+constexpr double IV_ORTOL = 1e3 * 2.220446049250313e-16;
 
 // LU with partial pivoting of T - lam I (tridiagonal, textbook); factors in w[0 .. 5n):
 // dl, dm, du, du2 (n each), then n pivot bytes.  Pivots are floored at +-small in both
@@ -608,16 +623,24 @@ __device__ void iv_solve(double* y, int64_t n, const double* w) {
 }
 
 __global__ void __launch_bounds__(IV_THREADS) k_inviter(
-    const double* __restrict__ d, const double* __restrict__ e, int64_t n,
-    const double* __restrict__ ev, int64_t k, const double* __restrict__ tnorm,
-    double* __restrict__ gwork, double* __restrict__ Y) {
+    const double* __restrict__ dAll, const double* __restrict__ eAll,
+    const EBlk* __restrict__ blks, const int2* __restrict__ eig,
+    const double* __restrict__ evAll, const double* __restrict__ tnorm,
+    double* __restrict__ gworkAll, double* __restrict__ YAll) {
   __shared__ double sdot[IV_CHUNK];
   __shared__ double sh[32];
-  const int64_t i0 = blockIdx.x;
+  const int2 gi = eig[blockIdx.x];
+  const EBlk B = blks[gi.x];
+  const int64_t n = B.n, k = B.k, i0 = gi.y;
+  const double* d = dAll + B.off;
+  const double* e = eAll + B.off;
+  const double* ev = evAll + B.evo;
+  double* gwork = gworkAll + B.wo;
+  double* Y = YAll + B.yo;
   // |T| floored well inside the normal range: a zero block (a charge sector of theta with
   // no weight) has T = 0, and pivots of eps |T| would then be denormal and the solves
   // would overflow; with the floor its eigenvectors come out as orthonormal start vectors
-  const double tn = fmax(tnorm[0], 1e-200);
+  const double tn = fmax(tnorm[gi.x], 1e-200);
   const double ortol = IV_ORTOL * tn;
   if (i0 > 0 && ev[i0 - 1] - ev[i0] < ortol) return;  // not the head of its cluster
   int64_t i1 = i0 + 1;
@@ -680,21 +703,28 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   }
 }
 
-// U[:, i] = H_0 ... H_{n-2} y_i; one CTA per BT_COLS eigenvectors, held in shared memory.
-// Each reflector is read once per CTA for all its columns, and the CTA's reduction of the
-// BT_COLS dot products is one pass: the FP64 pipe, not the reflector loads or the
-// synchronisation, sets the pace.
+// U[:, i] = H_0 ... H_{n-2} y_i; one CTA per BT_COLS eigenvectors of one problem
+// (bt[g] = (problem, first column)), held in shared memory.  Each reflector is read once
+// per CTA for all its columns, and the CTA's reduction of the BT_COLS dot products is one
+// pass: the FP64 pipe, not the reflector loads or the synchronisation, sets the pace.
 constexpr int BT_COLS = 2;
-__global__ void __launch_bounds__(256) k_backtransform(const double* __restrict__ Y,
-                                                       const z* __restrict__ Hv,
-                                                       const z* __restrict__ tau, int64_t n,
-                                                       int64_t k, int cols, z* __restrict__ U,
-                                                       int64_t ldu) {
+__global__ void __launch_bounds__(256) k_backtransform(const double* __restrict__ YAll,
+                                                       const z* __restrict__ HvAll,
+                                                       const z* __restrict__ tauAll,
+                                                       const EBlk* __restrict__ blks,
+                                                       const int2* __restrict__ bt, int cols,
+                                                       z* __restrict__ U0All) {
   extern __shared__ double sm_bt[];
   z* y = (z*)sm_bt;  // cols x n (cols = BT_COLS, or 1 when two vectors do not fit)
   __shared__ double shr[8][BT_COLS], shi[8][BT_COLS];
   __shared__ z s_ts[BT_COLS];
-  const int64_t i0 = (int64_t)blockIdx.x * cols;
+  const int2 gb = bt[blockIdx.x];
+  const EBlk B = blks[gb.x];
+  const int64_t n = B.n, k = B.k, i0 = gb.y;
+  const double* Y = YAll + B.yo;
+  const z* Hv = HvAll + B.hoff;
+  const z* tau = tauAll + B.off;
+  z* U = U0All + B.yo;  // n x k, leading dimension k
   const int ncol = (k - i0 < cols) ? (int)(k - i0) : cols;
   for (int q = 0; q < cols; ++q)
     for (int64_t r = threadIdx.x; r < n; r += blockDim.x)
@@ -754,7 +784,58 @@ __global__ void __launch_bounds__(256) k_backtransform(const double* __restrict_
     __syncthreads();
   }
   for (int q = 0; q < ncol; ++q)
-    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) U[r * ldu + i0 + q] = y[q * n + r];
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) U[r * k + i0 + q] = y[q * n + r];
+}
+
+// Small complex GEMMs of many problems in one launch (the Newton-Schulz steps of the
+// eigen phase): task t computes C = op(A) B, op(A)(i, l) = A[i a_rs + l a_cs] (conjugated
+// if conj_a), B(l, j) = B[l b_rs + j b_cs], C(i, j) = C[i c_rs + j]; one 16 x 16 output
+// tile per CTA iteration, tiles[g] = (task, m0, n0).  coef != 0 instead writes
+// C = 1.5 I - 0.5 op(A) B (the Newton-Schulz coefficient matrix).
+struct NsTask {
+  int64_t M, N, K;
+  const z* A;
+  int64_t a_rs, a_cs;
+  const z* B;
+  int64_t b_rs, b_cs;
+  z* C;
+  int64_t c_rs;
+  int conj_a, coef;
+};
+__global__ void __launch_bounds__(256) k_gemm_tasks(const NsTask* __restrict__ tasks,
+                                                    const int4* __restrict__ tiles, int ntiles) {
+  __shared__ z As[16][17];
+  __shared__ z Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 tl = tiles[t];
+    const NsTask tk = tasks[tl.x];
+    z acc = zmk(0, 0);
+    for (int64_t k0 = 0; k0 < tk.K; k0 += 16) {
+      {
+        const int64_t gi = tl.y + ty, gk = k0 + tx;
+        z v = (gi < tk.M && gk < tk.K) ? tk.A[gi * tk.a_rs + gk * tk.a_cs] : zmk(0, 0);
+        if (tk.conj_a) v.y = -v.y;
+        As[ty][tx] = v;
+      }
+      {
+        const int64_t gk = k0 + ty, gj = tl.z + tx;
+        Bs[ty][tx] = (gj < tk.N && gk < tk.K) ? tk.B[gk * tk.b_rs + gj * tk.b_cs] : zmk(0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) zfma(acc, As[ty][kk], Bs[kk][tx]);
+      __syncthreads();
+    }
+    const int64_t gi = tl.y + ty, gj = tl.z + tx;
+    if (gi < tk.M && gj < tk.N) {
+      if (tk.coef) {
+        acc = zscale(acc, -0.5);
+        if (gi == gj) acc.x += 1.5;
+      }
+      tk.C[gi * tk.c_rs + gj] = acc;
+    }
+  }
 }
 
 // S <- 1.5 I - 0.5 S  (k x k)
@@ -797,7 +878,7 @@ size_t heig_scratch_bound(int64_t n, int64_t k) {
 }
 
 // Second half of the eigensolve: from the tridiagonal form (d, e) and its reflectors
-// (Hv, row j = v_j, row stride ldh; tau) to the eigenvectors of the k largest eigenvalues
+// (Hv, row j = v_j, row stride n; tau) to the eigenvectors of the k largest eigenvalues
 // in U (n x k, leading dimension ldu), descending; ev (device, k).
 int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const double* d,
                 const double* e, z* U, int64_t ldu, double* ev) {
@@ -807,24 +888,36 @@ int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const d
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * n * k));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * n * k));
   z* S = (z*)ws_alloc(c, ws_round(sizeof(z) * k * k));
-  if (!tn || !work || !Y || !U0 || !S) {
+  EBlk* dblk = (EBlk*)ws_alloc(c, ws_round(sizeof(EBlk)));
+  int2* deig = (int2*)ws_alloc(c, ws_round(sizeof(int2) * (size_t)(2 * k + 2)));
+  if (!tn || !work || !Y || !U0 || !S || !dblk || !deig) {
     c->ws.top = top;
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (eigenvectors n=%lld k=%lld)", (long long)n, (long long)k);
   }
   cudaStream_t st = c->stream;
+  const int cols = (sizeof(z) * n * BT_COLS <= (size_t)200 * 1024) ? BT_COLS : 1;
+  const int64_t nbt = (k + cols - 1) / cols;
+  {  // one problem: the block table and the (eigenvalue, back-transformation) index tables
+    const EBlk hb{n, k, 0, 0, 0, 0, 0};
+    std::vector<int2> he((size_t)(k + nbt));
+    for (int64_t i = 0; i < k; ++i) he[(size_t)i] = make_int2(0, (int)i);
+    for (int64_t q = 0; q < nbt; ++q) he[(size_t)(k + q)] = make_int2(0, (int)(q * cols));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(dblk, &hb, sizeof(EBlk), cudaMemcpyHostToDevice, st));
+    TNT_CUDA_TRY(c, cudaMemcpyAsync(deig, he.data(), sizeof(int2) * he.size(), cudaMemcpyHostToDevice, st));
+    TNT_CUDA_TRY(c, cudaStreamSynchronize(st));  // the host tables die at the end of scope
+  }
   {
     ProfScope ps(c, "heig_tridiag_eig");
-    k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, n, k, ev, tn);
-    k_inviter<<<(unsigned)k, IV_THREADS, 0, st>>>(d, e, n, ev, k, tn, work, Y);
+    k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, dblk, deig, ev, tn);
+    k_inviter<<<(unsigned)k, IV_THREADS, 0, st>>>(d, e, dblk, deig, ev, tn, work, Y);
     c->launches += 2;
     TNT_CHECK_LAUNCH(c);
   }
   {
     ProfScope ps(c, "heig_backtransform", 8.0 * (double)n * (double)n * (double)k);
-    const int cols = (sizeof(z) * n * BT_COLS <= (size_t)200 * 1024) ? BT_COLS : 1;
     const size_t smem = sizeof(z) * n * cols;
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_backtransform<<<(unsigned)((k + cols - 1) / cols), 256, smem, st>>>(Y, Hv, tau, n, k, cols, U0, k);
+    k_backtransform<<<(unsigned)nbt, 256, smem, st>>>(Y, Hv, tau, dblk, deig + k, cols, U0);
     c->launches++;
     TNT_CHECK_LAUNCH(c);
   }
@@ -921,52 +1014,157 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
   return r;
 }
 
-// Many small blocks (n <= 256 each): one batched reduction launch, then each block's
-// eigenvectors.  blocks[i] = {offset of the n x n block in G (and of its eigenvector
-// columns in U, leading dimension n), n, k}.
+// Many small blocks (n <= 256 each): every stage of the eigensolve is one launch over all
+// blocks.  blocks[i] = {offset of the n x n block in G (and of its eigenvector columns in
+// U, leading dimension n), n, k}; the reduction keeps the reflectors in the blocks' rows.
+// ev (device) receives the eigenvalues of all blocks back to back.
 int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, double* ev) {
   if (blocks.empty()) return TNT_OK;
-  int64_t tot = 0;
+  int64_t tot = 0, kt = 0, nk = 0, k2 = 0, nmax = 0;
   for (const SmallEig& b : blocks) {
     if (b.n < 1 || b.n > TRI_CTA_MAX || b.k < 1 || b.k > b.n)
       return set_err(c, TNT_E_INVALID, "small eigensolve block n=%lld k=%lld", (long long)b.n, (long long)b.k);
     tot += b.n;
+    kt += b.k;
+    nk += b.n * b.k;
+    k2 += b.k * b.k;
+    nmax = std::max(nmax, b.n);
+  }
+  const int nb = (int)blocks.size();
+  const int cols = BT_COLS;  // sizeof(z) * 256 * 2 fits shared memory
+  // host tables: reduction blocks, eigen problems, eigenvalue and back-transformation
+  // indices, and the Newton-Schulz task lists with their 16 x 16 tiles
+  std::vector<CtaBlk> hc((size_t)nb);
+  std::vector<EBlk> he((size_t)nb);
+  std::vector<int2> heig, hbt;
+  int64_t off = 0, evo = 0, yo = 0, wo = 0, so = 0;
+  for (int i = 0; i < nb; ++i) {
+    const SmallEig& b = blocks[(size_t)i];
+    hc[(size_t)i] = CtaBlk{b.goff, off, (int)b.n};
+    he[(size_t)i] = EBlk{b.n, b.k, off, b.goff, evo, yo, wo};
+    for (int64_t q = 0; q < b.k; ++q) heig.push_back(make_int2(i, (int)q));
+    for (int64_t q = 0; q < b.k; q += cols) hbt.push_back(make_int2(i, (int)q));
+    off += b.n;
+    evo += b.k;
+    yo += b.n * b.k;
+    wo += 6 * b.n * b.k;
+    so += b.k * b.k;
   }
   const size_t top = c->ws.top;
   double* d = (double*)ws_alloc(c, ws_round(sizeof(double) * tot));
   double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * tot));
   z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * tot));
-  CtaBlk* dblk = (CtaBlk*)ws_alloc(c, ws_round(sizeof(CtaBlk) * blocks.size()));
-  if (!d || !e || !tau || !dblk) {
+  double* tn = (double*)ws_alloc(c, ws_round(sizeof(double) * nb));
+  double* work = (double*)ws_alloc(c, ws_round(sizeof(double) * 6 * nk));
+  double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * nk));
+  z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * nk));
+  z* U1 = (z*)ws_alloc(c, ws_round(sizeof(z) * nk));
+  z* S = (z*)ws_alloc(c, ws_round(sizeof(z) * k2));
+  CtaBlk* dc = (CtaBlk*)ws_alloc(c, ws_round(sizeof(CtaBlk) * nb));
+  EBlk* dbl = (EBlk*)ws_alloc(c, ws_round(sizeof(EBlk) * nb));
+  int2* deig = (int2*)ws_alloc(c, ws_round(sizeof(int2) * (heig.size() + hbt.size())));
+  NsTask* dtask = (NsTask*)ws_alloc(c, ws_round(sizeof(NsTask) * 4 * nb));
+  // tiles of the four task lists (S = X^H X and X S, twice)
+  std::vector<NsTask> ht;
+  std::vector<int4> htile[4];
+  for (int step = 0; step < 2; ++step) {
+    for (int i = 0; i < nb; ++i) {
+      const SmallEig& b = blocks[(size_t)i];
+      const EBlk& B = he[(size_t)i];
+      z* X = (step == 0 ? U0 : U1) + B.yo;                      // n x k, ld k
+      z* Xn = (step == 0) ? U1 + B.yo : U + b.goff;             // next X
+      const int64_t ldn = (step == 0) ? b.k : b.n;
+      z* Sb = S;  // offset filled below
+      (void)Sb;
+      NsTask ts{b.k, b.k, b.n, X, 1, b.k, X, b.k, 1, nullptr, b.k, 1, 1};
+      NsTask tx{b.n, b.k, b.k, X, b.k, 1, nullptr, b.k, 1, Xn, ldn, 0, 0};
+      ht.push_back(ts);
+      ht.push_back(tx);
+    }
+  }
+  {  // S offsets per block
+    int64_t o = 0;
+    for (int i = 0; i < nb; ++i) {
+      const int64_t kb = blocks[(size_t)i].k;
+      for (int step = 0; step < 2; ++step) {
+        ht[(size_t)(step * 2 * nb + 2 * i)].C = S + o;
+        ht[(size_t)(step * 2 * nb + 2 * i + 1)].B = S + o;
+      }
+      o += kb * kb;
+    }
+  }
+  for (int step = 0; step < 2; ++step)
+    for (int which = 0; which < 2; ++which) {
+      std::vector<int4>& tl = htile[2 * step + which];
+      for (int i = 0; i < nb; ++i) {
+        const int ti = step * 2 * nb + 2 * i + which;
+        const NsTask& t = ht[(size_t)ti];
+        for (int64_t m0 = 0; m0 < t.M; m0 += 16)
+          for (int64_t n0 = 0; n0 < t.N; n0 += 16) tl.push_back(make_int4(ti, (int)m0, (int)n0, 0));
+      }
+    }
+  size_t ntile_all = 0;
+  for (auto& v : htile) ntile_all += v.size();
+  int4* dtile = (int4*)ws_alloc(c, ws_round(sizeof(int4) * ntile_all));
+  if (!d || !e || !tau || !tn || !work || !Y || !U0 || !U1 || !S || !dc || !dbl || !deig || !dtask || !dtile) {
     c->ws.top = top;
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (small eigensolves)");
   }
-  std::vector<CtaBlk> hb(blocks.size());
-  int64_t off = 0;
-  for (size_t i = 0; i < blocks.size(); ++i) {
-    hb[i] = CtaBlk{blocks[i].goff, off, (int)blocks[i].n};
-    off += blocks[i].n;
-  }
   cudaStream_t st = c->stream;
-  TNT_CUDA_TRY(c, cudaMemcpyAsync(dblk, hb.data(), sizeof(CtaBlk) * hb.size(), cudaMemcpyHostToDevice, st));
+  heig.insert(heig.end(), hbt.begin(), hbt.end());
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(dc, hc.data(), sizeof(CtaBlk) * nb, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(dbl, he.data(), sizeof(EBlk) * nb, cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(deig, heig.data(), sizeof(int2) * heig.size(), cudaMemcpyHostToDevice, st));
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(dtask, ht.data(), sizeof(NsTask) * ht.size(), cudaMemcpyHostToDevice, st));
+  {
+    size_t o = 0;
+    for (auto& v : htile) {
+      if (!v.empty())
+        TNT_CUDA_TRY(c, cudaMemcpyAsync(dtile + o, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice, st));
+      o += v.size();
+    }
+  }
   {
     double fl = 0;
     for (const SmallEig& b : blocks) fl += 16.0 / 3.0 * (double)b.n * b.n * b.n;
     ProfScope ps(c, "heig_tridiag", fl);
-    k_tridiag_cta<<<(unsigned)blocks.size(), TRI_CTA_THREADS, 0, st>>>(G, dblk, d, e, tau);
+    k_tridiag_cta<<<(unsigned)nb, TRI_CTA_THREADS, 0, st>>>(G, dc, d, e, tau);
     c->launches++;
     TNT_CHECK_LAUNCH(c);
   }
-  int r = TNT_OK;
-  for (size_t i = 0; i < blocks.size() && r == TNT_OK; ++i) {
-    const SmallEig& b = blocks[i];
-    r = heig_finish(c, b.n, b.k, G + b.goff, tau + hb[i].off, d + hb[i].off, e + hb[i].off,
-                    U + b.goff, b.n, ev);
+  {
+    ProfScope ps(c, "heig_tridiag_eig");
+    k_bisect<<<(unsigned)kt, 32, 0, st>>>(d, e, dbl, deig, ev, tn);
+    k_inviter<<<(unsigned)kt, IV_THREADS, 0, st>>>(d, e, dbl, deig, ev, tn, work, Y);
+    c->launches += 2;
+    TNT_CHECK_LAUNCH(c);
   }
-  // the host table dies at return: the upload above must have completed
-  if (r == TNT_OK) TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
+  {
+    double fl = 0;
+    for (const SmallEig& b : blocks) fl += 8.0 * (double)b.n * b.n * b.k;
+    ProfScope ps(c, "heig_backtransform", fl);
+    const size_t smem = sizeof(z) * nmax * cols;
+    TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_backtransform<<<(unsigned)hbt.size(), 256, smem, st>>>(Y, G, tau, dbl, deig + kt, cols, U0);
+    c->launches++;
+    TNT_CHECK_LAUNCH(c);
+  }
+  {  // two Newton-Schulz steps over all blocks: U0 -> U1 -> U
+    size_t o = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int nt = (int)htile[q].size();
+      if (nt > 0) {
+        k_gemm_tasks<<<(unsigned)std::min(nt, 152 * 8), 256, 0, st>>>(dtask, dtile + o, nt);
+        c->launches++;
+        TNT_CHECK_LAUNCH(c);
+      }
+      o += htile[q].size();
+    }
+  }
+  // the host tables die at return: the uploads above must have completed
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
   c->ws.top = top;
-  return r;
+  return TNT_OK;
 }
 
 }  // namespace tnt

@@ -381,10 +381,11 @@ int ozgemm(Ctx* c, const ZGemm& g) {
   const size_t need = ozgemm_scratch_bytes(M, N, K);
   if (need > c->oz_cap) {
     TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (c->oz_buf) TNT_CUDA_TRY(c, cudaFree(c->oz_buf));
+    dev_free(c->dalloc, c->oz_buf);
     c->oz_buf = nullptr;
     c->oz_cap = 0;
-    TNT_CUDA_TRY(c, cudaMalloc(&c->oz_buf, need));
+    if (dev_alloc(c->dalloc, &c->oz_buf, need) != 0)
+      return set_err(c, TNT_E_ALLOC, "device allocation of %zu bytes (FP64 product slices) failed", need);
     c->oz_cap = need;
   }
   char* b = (char*)c->oz_buf;

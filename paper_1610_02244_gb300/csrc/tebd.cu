@@ -133,7 +133,7 @@ static int tebd_move_left(Ctx* c, tnt_tebd* t) {
 // then the centre's two-site tensor); side TNT_SVD_LEFT leaves it at i+1 (A_i <- U,
 // A_{i+1} <- S V^H), TNT_SVD_RIGHT at i (A_i <- U S, A_{i+1} <- V^H)
 static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, int side,
-                     tnt_step_stats* st) {
+                     tnt_step_stats* st, tnt_trunc_result* tr_out = nullptr) {
   tnt_mps* m = t->mps;
   while (t->centre < i) TNT_TRY(tebd_move_right(c, t));
   while (t->centre > i + 1) TNT_TRY(tebd_move_left(c, t));
@@ -167,6 +167,7 @@ static int tebd_gate(Ctx* c, tnt_tebd* t, int i, const std::vector<z>& G, int si
   t->centre = (side == TNT_SVD_LEFT) ? i + 1 : i;
   st->err_sum += tr.err;
   st->disc_sum += tr.disc;
+  if (tr_out) *tr_out = tr;
   c->ws.top = top;
   return TNT_OK;
 }
@@ -320,6 +321,36 @@ int tnt_tebd_step(tnt_ctx* ctx, tnt_tebd* t, tnt_step_stats* st) {
   st->seconds = ms * 1e-3;
   st->max_chi = *std::max_element(m->chi.begin(), m->chi.end());
   return r;
+}
+
+int tnt_tebd_gate(tnt_ctx* ctx, tnt_tebd* t, int bond, const tnt_cplx* h_gate, int dir,
+                  tnt_trunc_result* tr) {
+  if (!ctx || !t || !h_gate || !tr || t->ctx != ctx) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  tnt_mps* m = t->mps;
+  if (bond < 0 || bond + 1 >= m->L || (dir != 1 && dir != -1))
+    return set_err(c, TNT_E_INVALID, "bond %d / direction %d (bonds 0..%d, direction +1 or -1)",
+                   bond, dir, m->L - 2);
+  const size_t n2 = (size_t)m->d * m->d * m->d * m->d;
+  const z* p = (const z*)h_gate;
+  for (size_t e = 0; e < n2; ++e)
+    if (!std::isfinite(p[e].x) || !std::isfinite(p[e].y))
+      return set_err(c, TNT_E_NAN, "gate has a non-finite entry");
+  std::vector<z> G(p, p + n2);
+  tnt_step_stats st{};
+  *tr = tnt_trunc_result{};
+  ws_reset(c);
+  int r = ws_reserve(c, t->scratch);
+  if (r == TNT_OK) r = tebd_gate(c, t, bond, G, dir > 0 ? TNT_SVD_LEFT : TNT_SVD_RIGHT, &st, tr);
+  ws_reset(c);
+  if (r == TNT_OK) TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return r;
+}
+
+int tnt_tebd_centre(const tnt_tebd* t, int* centre) {
+  if (!t || !centre) return TNT_E_INVALID;
+  *centre = t->centre;
+  return TNT_OK;
 }
 
 int tnt_tebd_destroy(tnt_tebd* t) {

@@ -41,8 +41,21 @@ struct Arena {
   size_t top = 0;
 };
 
+// Device allocator of a context and of the handles made from it: cudaMalloc / cudaFree,
+// or the caller's callbacks (tnt_ctx_create_with_allocator).
+struct DevAlloc {
+  void* (*alloc)(size_t bytes, void* user) = nullptr;
+  void (*free)(void* ptr, void* user) = nullptr;
+  void* user = nullptr;
+};
+// 0 on success; *p = nullptr on failure
+int dev_alloc(const DevAlloc& a, void** p, size_t bytes);
+// synchronises the device first when the memory goes back to the caller's allocator
+void dev_free(const DevAlloc& a, void* p);
+
 struct Ctx {
   int device = 0;
+  DevAlloc dalloc;
   cudaStream_t stream = 0;
   tnt_params params;
   Arena ws;               // per-call scratch

@@ -92,17 +92,49 @@ def params_default() -> dict:
     return _struct_dict(p)
 
 
-class Context:
-    """A library context on one GPU, enqueueing on torch's current stream."""
+def torch_allocator(device: int, stream: torch.cuda.Stream):
+    """(alloc, free) callables that take the library's device memory from PyTorch's caching
+    allocator on `stream` (for Context(allocator=...))."""
+    def alloc(nbytes):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
 
-    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+    def free(ptr):
+        torch.cuda.caching_allocator_delete(ptr)
+    return alloc, free
+
+
+class Context:
+    """A library context on one GPU, enqueueing on torch's current stream.
+
+    allocator: optional (alloc(nbytes) -> device pointer as int, free(ptr)) pair through
+    which every device allocation of the context and its handles is made
+    (tnt_ctx_create_with_allocator); by default the library calls cudaMalloc."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None,
+                 allocator=None):
         self.lib = L.load()
         self.device = device
         torch.cuda.set_device(device)
         st = stream if stream is not None else torch.cuda.current_stream(device)
         self.stream = st
         h = C.c_void_p()
-        code = self.lib.tnt_ctx_create(device, C.c_void_p(st.cuda_stream), C.byref(h))
+        if allocator is None:
+            code = self.lib.tnt_ctx_create(device, C.c_void_p(st.cuda_stream), C.byref(h))
+        else:
+            alloc, free = allocator
+
+            def _alloc(nbytes, _user):
+                try:
+                    return int(alloc(nbytes)) or None
+                except Exception:
+                    return None
+
+            def _free(ptr, _user):
+                free(ptr)
+            # the callbacks must outlive the context (the library calls them until destroy)
+            self._cb = L.tnt_allocator(L.ALLOC_FN(_alloc), L.FREE_FN(_free), None)
+            code = self.lib.tnt_ctx_create_with_allocator(device, C.c_void_p(st.cuda_stream),
+                                                          C.byref(self._cb), C.byref(h))
         if code != 0:
             raise TntError(code, "tnt_ctx_create failed (no usable CUDA device?)")
         self.h = h
@@ -356,6 +388,13 @@ class Context:
                                            C.byref(h)))
         return Mps(self, h)
 
+    def mps_load(self, path: str, chi_cap: int, restore_params: bool = False) -> "Mps":
+        """MPS from a file written by Mps.save (tnt_mps_load)."""
+        h = C.c_void_p()
+        self._chk(self.lib.tnt_mps_load(self.h, str(path).encode(), int(chi_cap),
+                                        int(restore_params), C.byref(h)))
+        return Mps(self, h)
+
     def dmrg_create(self, mps: "Mps", mpo: "Mpo") -> "Dmrg":
         h = C.c_void_p()
         self._chk(self.lib.tnt_dmrg_create(self.h, mps.h, mpo.h, C.byref(h)))
@@ -438,6 +477,21 @@ class Mps:
         self.ctx._chk(self.ctx.lib.tnt_mps_norm2(self.ctx.h, self.h, C.byref(v)))
         return v.value
 
+    def overlap(self, other: "Mps") -> complex:
+        """<self|other> (tnt_mps_overlap)."""
+        v = L.tnt_cplx()
+        self.ctx._chk(self.ctx.lib.tnt_mps_overlap(self.ctx.h, self.h, other.h, C.byref(v)))
+        return complex(v.re, v.im)
+
+    def set_charges(self, bond: int, q):
+        """Replace the U(1) labels of one bond (tnt_mps_set_charges)."""
+        qa = np.ascontiguousarray(q, dtype=np.int64)
+        self.ctx._chk(self.ctx.lib.tnt_mps_set_charges(self.ctx.h, self.h, bond, qa.ctypes.data))
+
+    def save(self, path: str):
+        """Write the MPS and the context's parameters to a file (tnt_mps_save)."""
+        self.ctx._chk(self.ctx.lib.tnt_mps_save(self.ctx.h, self.h, str(path).encode()))
+
     def __del__(self):
         if getattr(self, "h", None):
             self.ctx.lib.tnt_mps_destroy(self.h)
@@ -458,6 +512,14 @@ class Dmrg:
         st = L.tnt_sweep_stats()
         self.ctx._chk(self.ctx.lib.tnt_dmrg_sweep1(self.ctx.h, self.h, float(alpha), C.byref(st)))
         return _struct_dict(st)
+
+    def update(self, bond: int, direction: int) -> tuple:
+        """One two-site update (tnt_dmrg_update): (Lanczos result, truncation result);
+        an eigensolve that hit its cap is returned, not raised."""
+        lz, tr = L.tnt_lanczos_result(), L.tnt_trunc_result()
+        self.ctx._chk(self.ctx.lib.tnt_dmrg_update(self.ctx.h, self.h, bond, direction,
+                                                   C.byref(lz), C.byref(tr)), ok=(0, 4))
+        return _struct_dict(lz), _struct_dict(tr)
 
     def update_energies(self) -> np.ndarray:
         """Energy of every update of the last sweep, in update order
@@ -483,6 +545,19 @@ class Tebd:
         st = L.tnt_step_stats()
         self.ctx._chk(self.ctx.lib.tnt_tebd_step(self.ctx.h, self.h, C.byref(st)))
         return _struct_dict(st)
+
+    def gate(self, bond: int, G, direction: int = 1) -> dict:
+        """One gate G[(s1' s2'), (s1 s2)] on bond (bond, bond+1) (tnt_tebd_gate)."""
+        g = np.ascontiguousarray(G, dtype=np.complex128)
+        tr = L.tnt_trunc_result()
+        self.ctx._chk(self.ctx.lib.tnt_tebd_gate(self.ctx.h, self.h, bond, g.ctypes.data,
+                                                 direction, C.byref(tr)))
+        return _struct_dict(tr)
+
+    def centre(self) -> int:
+        v = C.c_int()
+        self.ctx._chk(self.ctx.lib.tnt_tebd_centre(self.h, C.byref(v)))
+        return v.value
 
     def __del__(self):
         if getattr(self, "h", None):

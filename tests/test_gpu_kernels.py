@@ -288,9 +288,11 @@ def test_svd_rank_deficient_blocks(ctx, side):
     of weight 1e-170 (its Gram entries would underflow unscaled) and a 300 x 280 block of
     rank 100 (the whole-GPU reduction).  With chi_max = 512 and the 1e-10 truncation error
     of the 64-site quench, the kept factor must be orthonormal to rounding, every singular
-    value above 1e-8 must match the oracle's, and the truncated product must be within the
-    truncation error of M.  (Values below ~1e-8 |M| sit under the Gram matrix's resolution
-    and are compared through the product only.)"""
+    value above 1e-6 must match the oracle's to 1e-12, and the truncated product must be
+    within the truncation error of M.  (A value sigma reaches the Gram matrix as sigma^2: at
+    1e-6 that is 1e-12 |G|, resolved to about eps / 1e-12 in angle; near 1e-8 it meets the
+    rounding level of the Gram matrix, and such values are compared through the product
+    only.)"""
     g = np.random.default_rng(1610 + side)
     spec = [(99, 64, np.geomspace(1.0, 1e-22, 40)), (120, 110, np.geomspace(0.5, 1e-14, 30)),
             (30, 20, np.geomspace(1e-3, 1e-9, 5)), (10, 12, 1e-170 * np.geomspace(1, 1e-3, 10)),
@@ -323,14 +325,14 @@ def test_svd_rank_deficient_blocks(ctx, side):
         assert np.abs(U.conj().T @ U - np.eye(k)).max() < 1e-12
     else:
         assert np.abs(X @ X.conj().T - np.eye(k)).max() < 1e-12
-    big = np.sort(Sr[Sr > 1e-8])[::-1]
+    big = np.sort(Sr[Sr > 1e-6])[::-1]
     assert np.abs(np.sort(S)[::-1][:len(big)] - big).max() < 1e-12
     assert info["err"] < 1e-10
     assert np.linalg.norm(U @ X - M) < 3e-10 * np.linalg.norm(M)
     # every kept value belongs to a block that holds it: labels agree where values are resolved
     for q in range(len(spec)):
         sq = np.sort(S[bq == q])[::-1]
-        rr = np.sort(Sr[(bqr == q) & (Sr > 1e-8)])[::-1]
+        rr = np.sort(Sr[(bqr == q) & (Sr > 1e-6)])[::-1]
         assert np.abs(sq[:len(rr)] - rr).max(initial=0) < 1e-12
 
 

@@ -32,12 +32,7 @@ def _ed_density(vec, L, N, n_max):
     return (np.abs(vec)[:, None] ** 2 * occ).sum(axis=0)
 
 
-@pytest.mark.parametrize("precision", [
-    0,
-    pytest.param(1, marks=pytest.mark.xfail(
-        strict=False, reason="the 100-site trapped chain fails in split TF32 (open defect); "
-                             "whether ten trapped sites already show it is not known")),
-])
+@pytest.mark.parametrize("precision", [0, 1])
 def test_e1_trap_reduced_to_ten_sites(ctx, precision):
     """The first example's Hamiltonian on L = 10 (N = 10, n_max = 3, U/J = 5) with a trap
     strong enough to empty the edges (V/J = 0.5, every site its own MPO tensor), two-site
