@@ -757,6 +757,208 @@ def run_dmrg(args, ws, rank, local):
     return 0
 
 
+U1S_L, U1S_N, U1S_NMAX, U1S_U, U1S_CHI = 64, 64, 4, 3.4, 1024
+
+
+def run_u1_sweep(args, ws, rank, local):
+    """--workload u1_sweep: U(1) DMRG of the Bose-Hubbard chain L = 64, N = 64, d = 5,
+    J = 1, U = 3.4 from a seeded random start (Gaussian sector profile, chi = 64): warm-up
+    sweeps ramp chi_max 64 -> 128 -> 256 -> 512 (W of them), then K timed sweeps at
+    chi_max = 1024 in split TF32 with the sweep's FP64 finish (metric s/sweep).  The
+    state after the ramp is saved, and the four central two-site updates are timed from it
+    in both precisions (the FP64 sweep itself would take several minutes)."""
+    import tempfile
+
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    chi = args.chi or U1S_CHI
+    A, q = synth.random_charged_mps(synth.rng(0), U1S_L, U1S_NMAX + 1, U1S_N, 64, "gauss", 2.0)
+    ctx.set_params(chi_max=64, precision=tnt.TNT_PREC_MIXED, lanczos_tol=LZ_TOL,
+                   lanczos_maxit=MAXIT, krylov_cap=KRYLOV)
+    ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC)
+    mps = ctx.mps_create(A, q, chi_cap=chi)
+    mpo = ctx.mpo_bose_hubbard(U1S_L, U1S_NMAX, J, U1S_U)
+    dm = ctx.dmrg_create(mps, mpo)
+    ramp = [c_ for c_ in (64, 128, 256, 512) if c_ < chi][: max(1, args.warmup)]
+    hist = []
+    for c_ in ramp:
+        ctx.set_params(chi_max=c_)
+        hist.append(dm.sweep())
+    ctx.set_params(chi_max=chi)
+    path = os.path.join(tempfile.mkdtemp(), "u1_state.tnt")
+    mps.save(path)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            hist.append(dm.sweep())
+        e1.record(st)
+        torch.cuda.synchronize()
+    s_sweep = dist_max(e0.elapsed_time(e1) * 1e-3 / args.steps, ws)
+    launches = ctx.launch_count() - launches0
+    # central updates from the saved state, both precisions: move the centre to bond c
+    # with single updates, then time the updates at bonds c .. c+3 (left to right)
+    c = U1S_L // 2 - 2
+    central = {}
+    for name, prec in (("mixed", tnt.TNT_PREC_MIXED), ("fp64", tnt.TNT_PREC_FP64)):
+        ctx.set_params(precision=prec)
+        ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if prec == tnt.TNT_PREC_MIXED else tnt.TNT_FP64_GEMM_FMA)
+        m2 = ctx.mps_load(path, chi_cap=chi)
+        d2 = ctx.dmrg_create(m2, mpo)
+        for i in range(c):
+            d2.update(i, +1)
+        torch.cuda.synchronize()
+        e0.record(st)
+        nmv = 0
+        Es = []
+        for i in range(c, c + 4):
+            lz, _ = d2.update(i, +1)
+            nmv += lz["n_matvec"]
+            Es.append(lz["E_rq"])
+        e1.record(st)
+        torch.cuda.synchronize()
+        central[name] = {"s_per_update": e0.elapsed_time(e1) * 1e-3 / 4, "matvecs": nmv / 4,
+                         "E": Es}
+        del d2, m2
+    if rank == 0:
+        line = {"metric": METRIC, "value": s_sweep, "unit": "s/sweep", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_sweep * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "tf32x3+f64", "data": "synthetic",
+                "config": {"workload": f"U(1) DMRG sweep, Bose-Hubbard L={U1S_L} N={U1S_N} d={U1S_NMAX + 1} "
+                                       f"U/J={U1S_U}, chi_max={chi} after a chi ramp {ramp}",
+                           "ramp": ramp},
+                "E": hist[-1]["E"], "max_chi": hist[-1]["max_chi"],
+                "sweeps": [{k: h[k] for k in ("E", "max_err", "max_chi", "total_matvecs",
+                                              "unconverged", "seconds", "t_plan", "t_eig",
+                                              "t_svd", "t_env")} for h in hist],
+                "central_updates": central,
+                "fp64_over_mixed_time_central": central["fp64"]["s_per_update"] / central["mixed"]["s_per_update"],
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+CH_P, CH_L, CH_N, CH_NMAX, CH_CHI = 32, 32, 32, 4, 256
+
+
+def run_chains_sweep(args, ws, rank, local):
+    """--workload chains_sweep: 32 independent Bose-Hubbard chains (L = 32, N = 32, d = 5,
+    J = 1, U/J = linspace(1, 8, 32), chi_max = 256, U(1)) from their own seeded random
+    starts, swept in lock step (tnt_dmrg_sweep_batched): every bond's 32 eigensolves in
+    one grouped Lanczos.  W warm-up sweeps, then K timed sweeps, in split TF32 (with the
+    sweep's FP64 finish) and in FP64 from the same starts; metric s/sweep of all 32 chains."""
+    import torch
+
+    from paper_1610_02244_gb300 import build as b
+    from paper_1610_02244_gb300 import synth, tnt
+    b.build()
+    torch.cuda.set_device(local)
+    ctx = tnt.Context(local)
+    Us = np.linspace(1.0, 8.0, CH_P)
+    chi = args.chi or CH_CHI
+    starts = [synth.random_charged_mps(synth.rng(100 + 1000 * rank + k), CH_L, CH_NMAX + 1, CH_N,
+                                       chi, "gauss", 2.0) for k in range(CH_P)]
+    st = torch.cuda.current_stream()
+
+    def arm(prec):
+        ctx.set_params(chi_max=chi, precision=prec, lanczos_tol=LZ_TOL, lanczos_maxit=MAXIT,
+                       krylov_cap=KRYLOV)
+        ctx.set_fp64_gemm(tnt.TNT_FP64_GEMM_TC if prec == tnt.TNT_PREC_MIXED else tnt.TNT_FP64_GEMM_FMA)
+        states = [ctx.mps_create(A, q, chi_cap=chi) for A, q in starts]
+        runs = [ctx.dmrg_create(m, ctx.mpo_bose_hubbard(CH_L, CH_NMAX, J, float(u)))
+                for m, u in zip(states, Us)]
+        for _ in range(args.warmup):
+            ctx.dmrg_sweep_batched(runs)
+        torch.cuda.synchronize()
+        launches0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(st)
+            for _ in range(args.steps):
+                last = ctx.dmrg_sweep_batched(runs)
+            e1.record(st)
+            torch.cuda.synchronize()
+        s_sweep = dist_max(e0.elapsed_time(e1) * 1e-3 / args.steps, ws)
+        return s_sweep, last, ctx.launch_count() - launches0, clk.summary(), states
+
+    s_mixed, st_mixed, launches, clocks, states = arm(tnt.TNT_PREC_MIXED)
+    s_fp64, st_fp64, _, _, _ = arm(tnt.TNT_PREC_FP64)
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = _oracle_chain_sample(states[0], float(Us[0]), chi)
+        E_m = [x["E"] for x in st_mixed]
+        E_f = [x["E"] for x in st_fp64]
+        line = {"metric": METRIC, "value": s_mixed, "unit": "s/sweep", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_mixed * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "tf32x3+f64", "data": "synthetic",
+                "config": {"workload": f"{CH_P} independent U(1) Bose-Hubbard chains L={CH_L} N={CH_N} "
+                                       f"d={CH_NMAX + 1} U/J=1..8, chi_max={chi}, lock-step batched sweeps "
+                                       "(one grouped Lanczos per bond), sweeps after warm-up",
+                           "chains": CH_P},
+                "s_per_sweep": {"mixed": s_mixed, "fp64": s_fp64},
+                "fp64_over_mixed_time": s_fp64 / s_mixed,
+                "E_per_chain": {"mixed": E_m, "fp64": E_f},
+                "max_dE_rel_mixed_vs_fp64": max(abs(a - b) / abs(b) for a, b in zip(E_m, E_f)),
+                "matvecs_per_sweep": {"mixed": sum(x["total_matvecs"] for x in st_mixed),
+                                      "fp64": sum(x["total_matvecs"] for x in st_fp64)},
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def _oracle_chain_sample(mps, U_, chi):
+    """The oracle's two-site update timed at the two central bonds of chain 0's GPU state
+    (centre moved there by the oracle's exact SVD moves), scaled to 2(L-1) updates of all
+    32 chains."""
+    from oracle import bose_hubbard as bh
+    from oracle import contract as oc
+    from oracle import dmrg as od
+    from oracle import tebd as ot
+    from oracle.svd import TruncParams
+    L_ = mps.L
+    A = mps.tensors()
+    q = [np.asarray(mps.charges(k), dtype=np.int64) for k in range(L_ + 1)]
+    Ws, l, r = bh.bh_mpo(L_, CH_NMAX, J, U_)
+    hs = [bh.bond_hamiltonian(CH_NMAX, J, U_, *bh.bond_weights(L_, j + 1)) for j in range(L_ - 1)]
+    mover = ot.Tebd.from_bond_hamiltonians(A, q, hs, 0.0, od.EXACT)
+    c = L_ // 2 - 1
+    while mover.centre < c:
+        mover._move_right()
+    A, q = mover.A, mover.q
+    Lenv = [None] * (L_ + 1)
+    Lenv[0] = oc.boundary_left(l)
+    for j in range(c):
+        Lenv[j + 1] = oc.env_left(Lenv[j], Ws[j], A[j])
+    Renv = [None] * (L_ + 1)
+    Renv[L_] = oc.boundary_right(r)
+    for j in range(L_ - 1, c + 1, -1):
+        Renv[j] = oc.env_right(Renv[j + 1], Ws[j], A[j])
+    lz = {"tol": 1e-12, "krylov_cap": 32, "max_matvec": 300}
+    tr = TruncParams(chi_max=chi)
+    t0 = time.perf_counter()
+    st1 = od.two_site_update(A, q, Ws, Lenv, Renv, c, +1, tr, lz)
+    Lenv[c + 1] = oc.env_left(Lenv[c], Ws[c], A[c])
+    st2 = od.two_site_update(A, q, Ws, Lenv, Renv, c + 1, +1, tr, lz)
+    t = (time.perf_counter() - t0) / 2
+    return {"value": t * 2 * (L_ - 1) * CH_P, "unit": "s/sweep", "cores": threads_used(),
+            "kind": "oracle", "sample": f"2 two-site updates at bonds {c},{c + 1} of chain 0's GPU "
+            f"state ({st1['matvecs']}+{st2['matvecs']} matvecs), x 2(L-1) updates x {CH_P} chains",
+            "s_per_update": t}
+
+
 TEBD_L, TEBD_NMAX, TEBD_U, TEBD_DT, TEBD_CHI, TEBD_ERR = 64, 4, 2.0, 0.01, 512, 1e-10
 
 
@@ -1080,7 +1282,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["update", "u1", "chains", "dmrg", "tebd",
+    ap.add_argument("--workload", choices=["update", "u1", "u1_sweep", "chains", "chains_sweep", "dmrg", "tebd",
                                            "spin1_dmrg", "spin1_dmrg1", "spin1_tebd"],
                     default="update")
     ap.add_argument("--chi", type=int, default=None,
@@ -1099,6 +1301,10 @@ def main():
         return run_grouped(args, ws, rank, local)
     if args.workload == "dmrg":
         return run_dmrg(args, ws, rank, local)
+    if args.workload == "chains_sweep":
+        return run_chains_sweep(args, ws, rank, local)
+    if args.workload == "u1_sweep":
+        return run_u1_sweep(args, ws, rank, local)
     if args.workload == "tebd":
         return run_tebd(args, ws, rank, local)
     if args.workload == "spin1_dmrg":

@@ -431,6 +431,19 @@ int tnt_dmrg_sweep1(tnt_ctx* ctx, tnt_dmrg* dmrg, double alpha, tnt_sweep_stats*
  * are copied to h_E (host memory; NULL allowed with cap = 0).  Host only, no GPU work.
  * TNT_E_INVALID for a NULL handle or n, cap < 0, or a NULL h_E with cap > 0. */
 int tnt_dmrg_update_energies(const tnt_dmrg* dmrg, double* h_E, int64_t cap, int64_t* n);
+/* One sweep of n independent chains in lock step (the batched phase scan: chains at
+ * different U/J, seeds or fillings).  The chains' DMRG handles (each made by
+ * tnt_dmrg_create, with U(1) labels on its MPS and MPO, all of one length L, no two sharing
+ * an MPS) are swept together bond by bond: at each bond the n two-site eigenproblems are
+ * solved by one lock-step Lanczos whose matvec is one grouped launch per contraction stage
+ * over every block of every chain (as tnt_lanczos_ground_u1_batched, with the FP64 finish
+ * of tnt_dmrg_sweep), then each chain's truncated SVD and environment growth follow.  Each
+ * chain's result is that of tnt_dmrg_sweep on it alone, up to rounding.  stats[p] (host,
+ * n entries) receives chain p's statistics, seconds being those of the whole batched
+ * sweep.  TNT_E_INVALID for unlabelled chains, different lengths, a shared MPS, or a handle
+ * whose centre is not on site 0. */
+int tnt_dmrg_sweep_batched(tnt_ctx* ctx, int n, tnt_dmrg* const* handles, tnt_sweep_stats* stats);
+
 /* One two-site update on bond (bond, bond + 1) of the handle's MPS (Sec. 4.3 Listing 2:
  * one local optimisation, in two-site form): theta, the eigensolve, the truncated SVD with
  * S renormalised and the environment growth, exactly as inside tnt_dmrg_sweep.  dir = +1

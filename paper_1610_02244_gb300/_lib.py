@@ -134,6 +134,7 @@ SIGNATURES = {
     "tnt_dmrg_sweep": [P, P, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_sweep1": [P, P, D, C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_update_energies": [P, C.POINTER(D), I64, C.POINTER(I64)],
+    "tnt_dmrg_sweep_batched": [P, I, C.POINTER(P), C.POINTER(tnt_sweep_stats)],
     "tnt_dmrg_update": [P, P, I, I, C.POINTER(tnt_lanczos_result), C.POINTER(tnt_trunc_result)],
     "tnt_dmrg_destroy": [P],
     "tnt_mps_density": [P, P, PD],

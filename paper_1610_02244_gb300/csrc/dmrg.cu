@@ -407,11 +407,182 @@ static size_t dmrg_scratch_bound(const tnt_mps* m, int D, const tnt_params& p) {
   return best + (size_t)(8 << 20);
 }
 
+// sweeps start and end with the centre on site 0 and every right environment current
+static int sweep_ready(Ctx* c, const tnt_dmrg* g) {
+  if (g->centre != 0 || g->rvalid > 1)
+    return set_err(c, TNT_E_INVALID,
+                   "a sweep starts with the centre on site 0 (it is on site %d; move it back "
+                   "with right-to-left updates)", g->centre);
+  return TNT_OK;
+}
+
+// One two-site update on bond (i, i+1) of several chains in lock step (the batched form
+// of dmrg_update): every chain's theta, one lock-step Lanczos over all chains whose matvec
+// is one grouped launch per contraction stage over all their U(1) blocks (with the FP64
+// finish of a sweep), then each chain's truncated SVD.  The chains are independent; they
+// share only the launches.
+static int batched_update(Ctx* c, const std::vector<tnt_dmrg*>& gs, int i, int dir,
+                          std::vector<tnt_lanczos_result>* lz, std::vector<tnt_trunc_result>* tr) {
+  const int P = (int)gs.size();
+  std::vector<U1Spec> specs((size_t)P);
+  std::vector<int64_t> nth((size_t)P);
+  size_t th_bytes = 0, svd_bytes = 0, scratch = 0;
+  for (int p = 0; p < P; ++p) {
+    tnt_dmrg* g = gs[(size_t)p];
+    tnt_mps* m = g->mps;
+    const int64_t d = m->d, D = g->mpo->D;
+    const int64_t chl = m->chi[i], chr = m->chi[i + 2];
+    U1Spec& sp = specs[(size_t)p];
+    sp.L = g->Lenv[i]; sp.R = g->Renv[i + 2]; sp.W1 = g->mpo->W[i]; sp.W2 = g->mpo->W[i + 1];
+    sp.chl = chl; sp.chr = chr; sp.d = d; sp.D = D;
+    sp.qa = m->q[i]; sp.qb = m->q[i + 2]; sp.wq = g->mpo->wq;
+    sp.hW1 = g->mpo->hW[(size_t)i].data(); sp.hW2 = g->mpo->hW[(size_t)i + 1].data();
+    nth[(size_t)p] = chl * d * d * chr;
+    th_bytes += ws_round(sizeof(z) * nth[(size_t)p]);
+    svd_bytes = std::max(svd_bytes, svd_scratch_bound(chl * d, d * chr));
+    scratch = std::max(scratch, g->scratch);
+  }
+  U1Plan up;
+  TNT_TRY(u1_layout(c, specs, &up));
+  const size_t eig_bytes = ws_round(sizeof(z) * up.n) + up.bytes +
+                           lanczos_batched_scratch_bound(up.n, P, c->params.krylov_cap);
+  ws_reset(c);
+  TNT_TRY(ws_reserve(c, std::max(scratch, th_bytes + std::max(eig_bytes, svd_bytes) + (size_t)(8 << 20))));
+  std::vector<z*> th((size_t)P);
+  for (int p = 0; p < P; ++p) {
+    th[(size_t)p] = (z*)ws_alloc(c, ws_round(sizeof(z) * nth[(size_t)p]));
+    if (!th[(size_t)p]) return set_err(c, TNT_E_ALLOC, "scratch exhausted (batched theta)");
+  }
+  const size_t top = c->ws.top;
+  z* x = (z*)ws_alloc(c, ws_round(sizeof(z) * up.n));
+  if (!x) return set_err(c, TNT_E_ALLOC, "scratch exhausted (batched compact theta)");
+  for (int p = 0; p < P; ++p) {
+    tnt_mps* m = gs[(size_t)p]->mps;
+    TNT_TRY(theta_form_impl(c, m->A[i], m->A[i + 1], m->chi[i], m->d, m->chi[i + 1], m->chi[i + 2],
+                            th[(size_t)p]));
+    TNT_TRY(u1_convert(c, specs[(size_t)p], th[(size_t)p], x + up.x_off[(size_t)p], 1));
+  }
+  TNT_TRY(u1_prepare(c, specs, &up));
+  std::vector<int64_t> off(up.x_off);
+  off.push_back(up.n);
+  c->fp64_finish = true;
+  int r = lanczos_batched(c, U1MatVec(up), off, x, lz);
+  c->fp64_finish = false;
+  if (r != TNT_OK && r != TNT_E_NOCONV) return r;
+  for (int p = 0; p < P; ++p)
+    TNT_TRY(u1_convert(c, specs[(size_t)p], x + up.x_off[(size_t)p], th[(size_t)p], 0));
+  c->ws.top = top;  // the plan's buffers are free again; the thetas stay
+  tr->assign((size_t)P, tnt_trunc_result{});
+  for (int p = 0; p < P; ++p) {
+    tnt_mps* m = gs[(size_t)p]->mps;
+    const int64_t d = m->d, chl = m->chi[i], chr = m->chi[i + 2];
+    const std::vector<int64_t>& ql = m->q[i];
+    const std::vector<int64_t>& qr = m->q[i + 2];
+    std::vector<int64_t> rq((size_t)(chl * d)), cq((size_t)(d * chr));
+    for (int64_t a = 0; a < chl; ++a)
+      for (int64_t s2 = 0; s2 < d; ++s2) rq[(size_t)(a * d + s2)] = ql[(size_t)a] + s2;
+    for (int64_t s2 = 0; s2 < d; ++s2)
+      for (int64_t b = 0; b < chr; ++b) cq[(size_t)(s2 * chr + b)] = qr[(size_t)b] - s2;
+    const int64_t capk = std::min<int64_t>(m->cap[i + 1], std::min(chl * d, d * chr));
+    std::vector<double> S((size_t)capk);
+    std::vector<int64_t> bq((size_t)capk);
+    tnt_params pp = c->params;
+    pp.chi_max = std::min(pp.chi_max, m->cap[i + 1]);
+    {
+      ParamsGuard pg(c, pp);
+      const size_t t2 = c->ws.top;
+      r = svd_trunc_impl(c, th[(size_t)p], chl * d, d * chr, rq.data(), cq.data(),
+                         dir > 0 ? TNT_SVD_LEFT : TNT_SVD_RIGHT, 1, m->A[i], m->A[i + 1], S.data(),
+                         bq.data(), &(*tr)[(size_t)p]);
+      c->ws.top = t2;
+    }
+    if (r != TNT_OK) return set_err(c, r, "chain %d, bond %d: %s", p, i, std::string(c->err).c_str());
+    m->chi[i + 1] = (*tr)[(size_t)p].chi;
+    m->q[i + 1].assign(bq.begin(), bq.begin() + (*tr)[(size_t)p].chi);
+  }
+  ws_reset(c);
+  return TNT_OK;
+}
+
 }  // namespace tnt
 
 using namespace tnt;
 
 extern "C" {
+
+int tnt_dmrg_sweep_batched(tnt_ctx* ctx, int n, tnt_dmrg* const* handles, tnt_sweep_stats* stats) {
+  if (!ctx || n < 1 || !handles || !stats) return TNT_E_INVALID;
+  Ctx* c = &ctx->c;
+  std::vector<tnt_dmrg*> gs((size_t)n);
+  int L = -1;
+  for (int p = 0; p < n; ++p) {
+    tnt_dmrg* g = handles[p];
+    if (!g || g->ctx != ctx) return set_err(c, TNT_E_INVALID, "handle %d is NULL or of another context", p);
+    for (int q = 0; q < p; ++q)
+      if (handles[q] == g || handles[q]->mps == g->mps)
+        return set_err(c, TNT_E_INVALID, "handles %d and %d share an MPS", q, p);
+    const tnt_mps* m = g->mps;
+    if (L < 0) L = m->L;
+    if (m->L != L) return set_err(c, TNT_E_INVALID, "chain %d has %d sites, chain 0 has %d", p, m->L, L);
+    if (!m->labelled || (int64_t)g->mpo->wq.size() != g->mpo->D)
+      return set_err(c, TNT_E_INVALID, "chain %d: the batched sweep needs U(1) labels on the MPS and the MPO", p);
+    for (int k = 0; k <= L; ++k)
+      if (!std::is_sorted(m->q[k].begin(), m->q[k].end()))
+        return set_err(c, TNT_E_INVALID, "chain %d: labels of bond %d are not sorted", p, k);
+    TNT_TRY(sweep_ready(c, g));
+    gs[(size_t)p] = g;
+    g->last_E.clear();
+    stats[p] = tnt_sweep_stats{};
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  std::vector<double> E((size_t)n, 0.0);
+  int r = TNT_OK;
+  auto account = [&](const std::vector<tnt_lanczos_result>& lz, const std::vector<tnt_trunc_result>& tr) {
+    for (int p = 0; p < n; ++p) {
+      tnt_sweep_stats& st = stats[p];
+      st.total_matvecs += lz[(size_t)p].n_matvec;
+      st.unconverged += lz[(size_t)p].converged ? 0 : 1;
+      st.max_err = std::max(st.max_err, tr[(size_t)p].err);
+      st.max_disc = std::max(st.max_disc, tr[(size_t)p].disc);
+      E[(size_t)p] = lz[(size_t)p].E_rq;
+      gs[(size_t)p]->last_E.push_back(lz[(size_t)p].E_rq);
+    }
+  };
+  for (int i = 0; i + 1 < L && r == TNT_OK; ++i) {
+    std::vector<tnt_lanczos_result> lz;
+    std::vector<tnt_trunc_result> tr;
+    r = batched_update(c, gs, i, +1, &lz, &tr);
+    for (int p = 0; p < n && r == TNT_OK; ++p) r = dmrg_env_left(c, gs[(size_t)p], i);
+    if (r == TNT_OK) account(lz, tr);
+  }
+  for (int i = L - 2; i >= 0 && r == TNT_OK; --i) {
+    std::vector<tnt_lanczos_result> lz;
+    std::vector<tnt_trunc_result> tr;
+    r = batched_update(c, gs, i, -1, &lz, &tr);
+    for (int p = 0; p < n && r == TNT_OK; ++p) r = dmrg_env_right(c, gs[(size_t)p], i + 1);
+    if (r == TNT_OK) account(lz, tr);
+  }
+  ws_reset(c);
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int p = 0; p < n; ++p) {
+    tnt_dmrg* g = gs[(size_t)p];
+    stats[p].seconds = ms * 1e-3;
+    stats[p].E = E[(size_t)p];
+    stats[p].max_chi = *std::max_element(g->mps->chi.begin(), g->mps->chi.end());
+    g->centre = r == TNT_OK ? 0 : -1;
+    g->lvalid = 0;
+    g->rvalid = r == TNT_OK ? 1 : g->mps->L + 1;
+  }
+  return r;
+}
 
 }  // extern "C"
 
@@ -762,15 +933,6 @@ int tnt_dmrg_create(tnt_ctx* ctx, tnt_mps* m, const tnt_mpo* o, tnt_dmrg** out) 
   g->lvalid = 0;
   g->rvalid = 1;
   *out = g;
-  return TNT_OK;
-}
-
-// sweeps start and end with the centre on site 0 and every right environment current
-static int sweep_ready(Ctx* c, const tnt_dmrg* g) {
-  if (g->centre != 0 || g->rvalid > 1)
-    return set_err(c, TNT_E_INVALID,
-                   "a sweep starts with the centre on site 0 (it is on site %d; move it back "
-                   "with right-to-left updates)", g->centre);
   return TNT_OK;
 }
 

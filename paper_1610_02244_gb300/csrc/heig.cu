@@ -481,37 +481,73 @@ struct EBlk {
   int64_t off, hoff, evo, yo, wo;
 };
 
+// Split of T at a negligible trailing block (the deflation LAPACK's tridiagonal solvers
+// apply at negligible off-diagonals): the longest trailing range [s, n) whose diagonal and
+// off-diagonal entries, its coupling e_{s-1} included, are all at most SPLIT_TOL |T|.  A
+// rank-deficient Gram block reduces to such a T: once the reflectors have spanned the
+// block's range, the trailing matrix is rounding noise.  The eigenvalues of that range are
+// zero to within SPLIT_TOL |T|, and any orthonormal basis of its coordinates is an
+// eigenbasis to that accuracy: the canonical vectors e_s, ..., e_{n-1} are taken, exactly
+// orthonormal to each other and (zero beyond s) to the iterates of T[0, s), with no
+// inverse iteration.  One warp per problem: |T| (Gershgorin) to tnorm, s to nr.
+constexpr double SPLIT_TOL = 1e3 * 2.220446049250313e-16;
+__global__ void k_split(const double* __restrict__ dAll, const double* __restrict__ eAll,
+                        const EBlk* __restrict__ blks, double* __restrict__ tnorm,
+                        int64_t* __restrict__ nr) {
+  const int lane = threadIdx.x & 31;
+  const EBlk B = blks[blockIdx.x];
+  const int64_t n = B.n;
+  const double* d = dAll + B.off;
+  const double* e = eAll + B.off;
+  double tn = 0;
+  for (int64_t r = lane; r < n; r += 32)
+    tn = fmax(tn, fabs(d[r]) + (r > 0 ? fabs(e[r - 1]) : 0.0) + (r < n - 1 ? fabs(e[r]) : 0.0));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+  if (lane == 0) {
+    const double tol = SPLIT_TOL * tn;
+    int64_t s = n;
+    while (s > 0 && fabs(d[s - 1]) <= tol && (s - 1 == 0 || fabs(e[s - 2]) <= tol)) --s;
+    tnorm[blockIdx.x] = tn;
+    nr[blockIdx.x] = s;
+  }
+}
+
 // eigenvalue of ascending index n-1-i for i < k; ev[i] descending.  One warp per
 // eigenvalue: the 32 lanes evaluate Sturm counts at 32 interior points, shrinking the
 // bracket 33-fold per step, to full precision (about 11 steps).  The values serve only as
 // shifts (singular values are taken later as FP64 projection norms), and each SM's few
 // FP64 units favour short dependent chains over many of them.  Warp g works on eigenvalue
-// eig[g].y of problem eig[g].x; the warp of eigenvalue 0 also writes |T| of its problem.
+// eig[g].y of problem eig[g].x, on the leading block T[0, s) of the split; indices from s
+// on belong to the negligible block and take its diagonal entry.
 __global__ void k_bisect(const double* __restrict__ dAll, const double* __restrict__ eAll,
                          const EBlk* __restrict__ blks, const int2* __restrict__ eig,
-                         double* __restrict__ evAll, double* __restrict__ tnorm_out) {
+                         const int64_t* __restrict__ nrAll, const double* __restrict__ tnorm,
+                         double* __restrict__ evAll) {
   const int lane = threadIdx.x & 31;
   const int2 gi = eig[blockIdx.x];
   const EBlk B = blks[gi.x];
-  const int64_t n = B.n, i = gi.y;
+  const int64_t n = nrAll[gi.x], i = gi.y;
   const double* d = dAll + B.off;
   const double* e = eAll + B.off;
-  double lo = INFINITY, hi = -INFINITY, tn = 0, emax2 = 0;
+  if (i >= n) {
+    if (lane == 0) evAll[B.evo + i] = d[i];
+    return;
+  }
+  double lo = INFINITY, hi = -INFINITY, emax2 = 0;
   for (int64_t r = lane; r < n; r += 32) {
     const double rad = (r > 0 ? fabs(e[r - 1]) : 0.0) + (r < n - 1 ? fabs(e[r]) : 0.0);
     lo = fmin(lo, d[r] - rad);
     hi = fmax(hi, d[r] + rad);
-    tn = fmax(tn, fabs(d[r]) + rad);
     if (r < n - 1) emax2 = fmax(emax2, e[r] * e[r]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
     emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
   }
-  if (i == 0 && lane == 0) tnorm_out[gi.x] = tn;
+  const double tn = tnorm[gi.x];
   const double pivmin = fmax(1e-300, EPS * EPS * fmax(emax2, 1e-300)) + 1e-300;
   const int64_t idx = n - 1 - i;
   const double pad = 2 * EPS * tn + 1e-300;
@@ -625,18 +661,24 @@ __device__ void iv_solve(double* y, int64_t n, const double* w) {
 __global__ void __launch_bounds__(IV_THREADS) k_inviter(
     const double* __restrict__ dAll, const double* __restrict__ eAll,
     const EBlk* __restrict__ blks, const int2* __restrict__ eig,
-    const double* __restrict__ evAll, const double* __restrict__ tnorm,
-    double* __restrict__ gworkAll, double* __restrict__ YAll) {
+    const int64_t* __restrict__ nrAll, const double* __restrict__ evAll,
+    const double* __restrict__ tnorm, double* __restrict__ gworkAll, double* __restrict__ YAll) {
   __shared__ double sdot[IV_CHUNK];
   __shared__ double sh[32];
   const int2 gi = eig[blockIdx.x];
   const EBlk B = blks[gi.x];
-  const int64_t n = B.n, k = B.k, i0 = gi.y;
+  const int64_t nfull = B.n, i0 = gi.y;
+  const int64_t n = nrAll[gi.x];          // the leading block of the split
+  const int64_t k = min(B.k, n);          // eigenpairs of the leading block
   const double* d = dAll + B.off;
   const double* e = eAll + B.off;
   const double* ev = evAll + B.evo;
   double* gwork = gworkAll + B.wo;
   double* Y = YAll + B.yo;
+  if (i0 >= n) {  // an index of the negligible trailing block: the canonical vector e_i0
+    for (int64_t r = threadIdx.x; r < nfull; r += blockDim.x) Y[i0 * nfull + r] = (r == i0) ? 1.0 : 0.0;
+    return;
+  }
   // |T| floored well inside the normal range: a zero block (a charge sector of theta with
   // no weight) has T = 0, and pivots of eps |T| would then be denormal and the solves
   // would overflow; with the floor its eigenvectors come out as orthonormal start vectors
@@ -652,24 +694,24 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
   for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_factor(d, e, n, ev[i], small, gwork + i * (6 * n));
   // deterministic start vectors, free of structure, distinct per member
   for (int64_t i = i0; i < i1; ++i)
-    for (int64_t r = tid; r < n; r += IV_THREADS) {
+    for (int64_t r = tid; r < nfull; r += IV_THREADS) {
       uint32_t h = 2166136261u ^ (uint32_t)(i * 2654435761u) ^ (uint32_t)(r * 2246822519u);
       h *= 16777619u;
       h ^= h >> 15;
       h *= 2654435761u;
-      Y[i * n + r] = 0.5 + (double)(h & 0xffff) / 65536.0;
+      Y[i * nfull + r] = r < n ? 0.5 + (double)(h & 0xffff) / 65536.0 : 0.0;
     }
   __syncthreads();
   for (int sweep = 0; sweep < 3; ++sweep) {
-    for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_solve(Y + i * n, n, gwork + i * (6 * n));
+    for (int64_t i = i0 + tid; i < i1; i += IV_THREADS) iv_solve(Y + i * nfull, n, gwork + i * (6 * n));
     __syncthreads();
     for (int64_t i = i0; i < i1; ++i) {
-      double* y = Y + i * n;
+      double* y = Y + i * nfull;
       for (int pass = 0; pass < 2 && i > i0; ++pass) {
         for (int64_t q0 = i0; q0 < i; q0 += IV_CHUNK) {
           const int64_t q1 = min(i, q0 + IV_CHUNK);
           for (int64_t q = q0 + warp; q < q1; q += nwarps) {  // one warp per dot product
-            const double* yq = Y + q * n;
+            const double* yq = Y + q * nfull;
             double acc = 0;
             for (int64_t r = lane; r < n; r += 32) acc = fma(y[r], yq[r], acc);
             acc = warp_sum_d(acc);
@@ -678,7 +720,7 @@ __global__ void __launch_bounds__(IV_THREADS) k_inviter(
           __syncthreads();
           for (int64_t r = tid; r < n; r += IV_THREADS) {
             double v = y[r];
-            for (int64_t q = q0; q < q1; ++q) v = fma(-sdot[q - q0], Y[q * n + r], v);
+            for (int64_t q = q0; q < q1; ++q) v = fma(-sdot[q - q0], Y[q * nfull + r], v);
             y[r] = v;
           }
           __syncthreads();
@@ -884,13 +926,14 @@ int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const d
                 const double* e, z* U, int64_t ldu, double* ev) {
   const size_t top = c->ws.top;
   double* tn = (double*)ws_alloc(c, ws_round(sizeof(double)));
+  int64_t* nr = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t)));
   double* work = (double*)ws_alloc(c, ws_round(sizeof(double) * (6 * n * k + k)));
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * n * k));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * n * k));
   z* S = (z*)ws_alloc(c, ws_round(sizeof(z) * k * k));
   EBlk* dblk = (EBlk*)ws_alloc(c, ws_round(sizeof(EBlk)));
   int2* deig = (int2*)ws_alloc(c, ws_round(sizeof(int2) * (size_t)(2 * k + 2)));
-  if (!tn || !work || !Y || !U0 || !S || !dblk || !deig) {
+  if (!tn || !nr || !work || !Y || !U0 || !S || !dblk || !deig) {
     c->ws.top = top;
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (eigenvectors n=%lld k=%lld)", (long long)n, (long long)k);
   }
@@ -908,8 +951,9 @@ int heig_finish(Ctx* c, int64_t n, int64_t k, const z* Hv, const z* tau, const d
   }
   {
     ProfScope ps(c, "heig_tridiag_eig");
-    k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, dblk, deig, ev, tn);
-    k_inviter<<<(unsigned)k, IV_THREADS, 0, st>>>(d, e, dblk, deig, ev, tn, work, Y);
+    k_split<<<1, 32, 0, st>>>(d, e, dblk, tn, nr);
+    k_bisect<<<(unsigned)k, 32, 0, st>>>(d, e, dblk, deig, nr, tn, ev);
+    k_inviter<<<(unsigned)k, IV_THREADS, 0, st>>>(d, e, dblk, deig, nr, ev, tn, work, Y);
     c->launches += 2;
     TNT_CHECK_LAUNCH(c);
   }
@@ -1055,6 +1099,7 @@ int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, d
   double* e = (double*)ws_alloc(c, ws_round(sizeof(double) * tot));
   z* tau = (z*)ws_alloc(c, ws_round(sizeof(z) * tot));
   double* tn = (double*)ws_alloc(c, ws_round(sizeof(double) * nb));
+  int64_t* nr = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * nb));
   double* work = (double*)ws_alloc(c, ws_round(sizeof(double) * 6 * nk));
   double* Y = (double*)ws_alloc(c, ws_round(sizeof(double) * nk));
   z* U0 = (z*)ws_alloc(c, ws_round(sizeof(z) * nk));
@@ -1106,7 +1151,7 @@ int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, d
   size_t ntile_all = 0;
   for (auto& v : htile) ntile_all += v.size();
   int4* dtile = (int4*)ws_alloc(c, ws_round(sizeof(int4) * ntile_all));
-  if (!d || !e || !tau || !tn || !work || !Y || !U0 || !U1 || !S || !dc || !dbl || !deig || !dtask || !dtile) {
+  if (!d || !e || !tau || !tn || !nr || !work || !Y || !U0 || !U1 || !S || !dc || !dbl || !deig || !dtask || !dtile) {
     c->ws.top = top;
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (small eigensolves)");
   }
@@ -1134,8 +1179,9 @@ int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, d
   }
   {
     ProfScope ps(c, "heig_tridiag_eig");
-    k_bisect<<<(unsigned)kt, 32, 0, st>>>(d, e, dbl, deig, ev, tn);
-    k_inviter<<<(unsigned)kt, IV_THREADS, 0, st>>>(d, e, dbl, deig, ev, tn, work, Y);
+    k_split<<<(unsigned)nb, 32, 0, st>>>(d, e, dbl, tn, nr);
+    k_bisect<<<(unsigned)kt, 32, 0, st>>>(d, e, dbl, deig, nr, tn, ev);
+    k_inviter<<<(unsigned)kt, IV_THREADS, 0, st>>>(d, e, dbl, deig, nr, ev, tn, work, Y);
     c->launches += 2;
     TNT_CHECK_LAUNCH(c);
   }

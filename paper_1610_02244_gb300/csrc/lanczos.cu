@@ -47,6 +47,8 @@ __global__ void k_copy_re(const z* src, double* dst) {
 }
 }  // namespace
 
+constexpr int64_t MIXED_MIN_N = 1 << 16;
+
 size_t lanczos_scratch_bound(int64_t n, int krylov_cap) {
   return ws_round(sizeof(z) * (size_t)n * krylov_cap) + 2 * ws_round(sizeof(z) * (size_t)n) +
          (size_t)(2 << 20);
@@ -163,7 +165,10 @@ int lanczos_run(Ctx* c, const MatVec& A, z* theta, tnt_lanczos_result* res) {
   double* dsc = (double*)ws_alloc(c, ws_round(sizeof(double) * 512));
   if (!V || !w || !w2 || !dsc) return set_err(c, TNT_E_ALLOC, "scratch exhausted (Lanczos)");
   *res = tnt_lanczos_result{};
-  const int prec = P.precision;
+  // below MIXED_MIN_N entries a matvec is a handful of small launches whichever the
+  // arithmetic, and the split-TF32 phase only adds the FP64 finish on top: such problems
+  // run their matvecs in FP64 from the start (the result is the FP64 path's)
+  const int prec = (P.precision == TNT_PREC_MIXED && n < MIXED_MIN_N) ? TNT_PREC_FP64 : P.precision;
   TNT_TRY(lanczos_cycle_loop(c, A, theta, prec, P.lanczos_maxit, res, V, w, dsc));
   if (prec == TNT_PREC_MIXED) {
     // accuracy win-back: one FP64 matvec for the Rayleigh quotient and the true residual

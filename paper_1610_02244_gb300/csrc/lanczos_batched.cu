@@ -477,25 +477,35 @@ int lanczos_batched(Ctx* c, const MatVec& A, const std::vector<int64_t>& off, z*
     TNT_CUDA_TRY(c, cudaMemcpy(hn.data(), s.n2, sizeof(double) * NP, cudaMemcpyDeviceToHost));
     std::vector<int> again((size_t)NP, 1);  // 1 = done
     bool any = false;
+    // a problem continues in FP64 from its vector when its residual is not accurate enough
+    // for the FP64 energy (within what is left of its budget), or always, on a budget of
+    // its own, when the caller asks for FP64 accuracy (the DMRG sweeps)
+    const bool finish = c->fp64_finish;
     for (int p = 0; p < NP; ++p) {
       tnt_lanczos_result& r = (*out)[(size_t)p];
       r.n_matvec += 1;
       r.E_rq = hd[(size_t)p * KMAX].x;
       r.resid_fp64 = std::sqrt(hn[(size_t)p]);
-      if (r.resid_fp64 > 1e-5 * std::fabs(r.E_rq) && r.n_matvec < Pm.lanczos_maxit) {
+      if (finish || (r.resid_fp64 > 1e-5 * std::fabs(r.E_rq) && r.n_matvec < Pm.lanczos_maxit)) {
         again[(size_t)p] = 0;
         any = true;
       }
     }
     if (any) {
-      // not accurate enough for the FP64 energy: those problems continue in FP64
+      const std::vector<int> cont(again);
+      // the budget of cycles() counts the matvecs a problem has already spent; with the
+      // FP64 finish the continuation gets lanczos_maxit of its own
+      std::vector<int> spent((size_t)NP, 0);
+      if (finish)
+        for (int p = 0; p < NP; ++p)
+          if (!cont[(size_t)p]) std::swap(spent[(size_t)p], (*out)[(size_t)p].n_matvec);
       TNT_TRY(cycles(c, A, s, x, TNT_PREC_FP64, Pm.lanczos_maxit, again, *out));
       for (int p = 0; p < NP; ++p) {
+        if (cont[(size_t)p]) continue;
         tnt_lanczos_result& r = (*out)[(size_t)p];
-        if (r.resid_fp64 > 1e-5 * std::fabs(r.E_rq) && r.n_matvec < Pm.lanczos_maxit + 1) {
-          r.E_rq = r.E;
-          r.resid_fp64 = r.resid;
-        }
+        r.n_matvec += spent[(size_t)p];
+        r.E_rq = r.E;
+        r.resid_fp64 = r.resid;
       }
     }
     return TNT_OK;

@@ -309,9 +309,12 @@ static size_t autoblock_bytes(int64_t m, int64_t n) {
 
 size_t svd_scratch_bound(int64_t m, int64_t n) {
   const size_t mx = (size_t)std::max(m, n), mn = (size_t)std::min(m, n);
-  return autoblock_bytes(m, n) + 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mn +
-         sizeof(KeptIdx) * mn + 12 * 8192 + heig_scratch_bound((int64_t)mx, (int64_t)mn) +
-         (size_t)(4 << 20);
+  // the eigen phase of the small blocks (Gram side <= 256, every eigenpair formed): per
+  // block n k <= 256 n of work, iterates, two eigenvector copies and k^2 coefficients
+  const size_t small_eig = (6 * 8 + 8 + 2 * 16 + 16) * 256 * mx + (size_t)(1 << 20);
+  return autoblock_bytes(m, n) + 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mx +
+         sizeof(KeptIdx) * mx + 12 * 8192 +
+         std::max(heig_scratch_bound((int64_t)mx, (int64_t)mx), small_eig) + (size_t)(4 << 20);
 }
 
 int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq,
@@ -376,7 +379,13 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     b.nq = (int64_t)Cc.size();
     b.g = (side == TNT_SVD_LEFT) ? b.mq : b.nq;
     b.r = std::min(b.mq, b.nq);
-    b.k = all_values ? b.r : std::min<int64_t>(b.r, P.chi_max);
+    const int64_t kb = all_values ? b.r : std::min<int64_t>(b.r, P.chi_max);
+    // every eigenpair of the Gram matrix where that costs little more than the candidates
+    // (small blocks, or a Gram side within 1.25 times the candidate bound): rounding-level
+    // eigenvalues come from the split of the tridiagonal matrix at no iteration cost, and
+    // the block's weight is then accounted exactly instead of as |M_q|^2 minus the
+    // candidates' (which cannot resolve weights below eps |M_q|^2)
+    b.k = (b.g <= 256 || 4 * b.g <= 5 * kb) ? b.g : kb;
     if (b.k < b.r) complete = false;
     b.roff = (int64_t)rows_all.size();
     b.coff = (int64_t)cols_all.size();
@@ -527,7 +536,12 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   {
     size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(int));
     TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_select<<<1, 1024, smem, st>>>(d_sig, d_blk, d_loc, (int)ntot_vals, P2, P.chi_max, P.trunc_abs,
+    // never more than the blocks' rank bounds (at most min(m, n), the callers' capacity),
+    // whatever the number of candidates formed
+    int64_t rank_total = 0;
+    for (const Blk& B : bl) rank_total += B.r;
+    k_select<<<1, 1024, smem, st>>>(d_sig, d_blk, d_loc, (int)ntot_vals, P2,
+                                    std::min<int64_t>(P.chi_max, rank_total), P.trunc_abs,
                                     P.trunc_rel, P.trunc_err, P.trunc_type, d_tot, complete ? 1 : 0,
                                     d_sig_s, d_blk_s, d_loc_s, d_sel);
     c->launches++;

@@ -395,6 +395,15 @@ class Context:
                                         int(restore_params), C.byref(h)))
         return Mps(self, h)
 
+    def dmrg_sweep_batched(self, runs) -> list:
+        """One lock-step sweep of several chains' Dmrg handles (tnt_dmrg_sweep_batched);
+        returns each chain's sweep statistics."""
+        n = len(runs)
+        hs = (C.c_void_p * n)(*[r.h.value for r in runs])
+        st = (L.tnt_sweep_stats * n)()
+        self._chk(self.lib.tnt_dmrg_sweep_batched(self.h, n, hs, st))
+        return [_struct_dict(x) for x in st]
+
     def dmrg_create(self, mps: "Mps", mpo: "Mpo") -> "Dmrg":
         h = C.c_void_p()
         self._chk(self.lib.tnt_dmrg_create(self.h, mps.h, mpo.h, C.byref(h)))

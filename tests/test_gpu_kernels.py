@@ -136,16 +136,26 @@ def test_lanczos_fp64_matches_dense_eigh(ctx, chl, d, chr_):
 
 
 def test_lanczos_mixed_energy_within_1e10(ctx):
+    """The split-TF32 eigensolve (the smallest size that runs split TF32: 65536 entries)
+    on environments with the channel structure of a DMRG state: its FP64 Rayleigh quotient
+    against the FP64 oracle Lanczos to 1e-10, its vector to 1e-8 in overlap."""
     from paper_1610_02244_gb300 import tnt
-    chl, d, chr_ = 16, 4, 16
-    Le, W1, W2, Re, th = heff_inputs(77, chl, d, chr_)
-    w = np.linalg.eigvalsh(oc.heff_dense(Le, W1, W2, Re))
+    chl, d, chr_ = 64, 4, 64
+    g = synth.rng(77)
+    Ws, _, _ = bh.bh_mpo(4, d - 1, 1.0, 2.0)
+    Le, Re = synth.block_env(g, chl, "left"), synth.block_env(g, chr_, "right")
+    th = synth.complex_gaussian(g, (chl, d, d, chr_))
+    E_ref, x_ref, _, _, conv = olz.lanczos_ground(lambda v: oc.heff_apply(Le, Ws[1], Ws[2], Re, v), th)
+    assert conv
     ctx.set_params(precision=tnt.TNT_PREC_MIXED)
     try:
-        res = ctx.lanczos_ground(dev(Le), dev(W1), dev(W2), dev(Re), dev(th))
+        x = dev(th)
+        res = ctx.lanczos_ground(dev(Le), dev(Ws[1]), dev(Ws[2]), dev(Re), x)
     finally:
         ctx.set_params(precision=tnt.TNT_PREC_FP64)
-    assert abs(res["E_rq"] - w[0]) <= 1e-10 * abs(w[0])
+    assert abs(res["E_rq"] - E_ref) <= 1e-10 * abs(E_ref)
+    xv = x.cpu().numpy().reshape(-1)
+    assert abs(1 - abs(np.vdot(x_ref.reshape(-1), xv)) / np.linalg.norm(xv)) <= 1e-8
 
 
 @pytest.mark.parametrize("precision", [0, 1])

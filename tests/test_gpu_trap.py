@@ -85,20 +85,17 @@ def _golden(name):
     return vals
 
 
-@pytest.mark.parametrize("precision", [
-    pytest.param(0, marks=pytest.mark.xfail(
-        strict=False, reason="the split-TF32 run of this chain leaves the oracle within the "
-                             "first sweep; whether the FP64 path does too is not known")),
-    pytest.param(1, marks=pytest.mark.xfail(
-        strict=False, reason="open defect: the split-TF32 run of this chain ended its first "
-                             "sweep at E = 1290.9 where the oracle has 530.16, before its "
-                             "solves were finished in FP64; not yet run since")),
-])
+@pytest.mark.parametrize("precision", [0, 1])
 def test_e1_first_sweep_matches_oracle(ctx, precision):
     """The first sweep of E1 at the paper's size from the seeded start, against the FP64
     oracle's first sweep from the same start (tests/golden/e1_trap_sweep0.txt, written by
-    tests/golden/make_e1_sweep0.py).  Same algorithm and truncation on both sides; only a
-    near-tie at a chi = 100 cut could separate them, by far less than the tolerance."""
+    tests/golden/make_e1_sweep0.py), update by update.  Same algorithm and truncation on
+    both sides, but from a random start at chi = 100 every cut falls among near-equal
+    Schmidt values (a random state's spectrum is flat), so rounding decides part of the
+    kept subspace: the two runs agree to 1e-6 for the first hundred updates and drift to a
+    few 1e-6 by the end of the sweep.  Every update is compared at 1e-5 (a defective update,
+    like the former non-orthonormal eigenvectors, is off by far more); 1e-10 parity of the
+    trapped Hamiltonian at convergence is held by the ten-site test above."""
     from paper_1610_02244_gb300 import tnt
     ref = _golden("e1_trap_sweep0.txt")["E_sweep0"]
     Ls, N, n_max, J, U, V = 100, 100, 3, 1.0, 5.0, 0.01
@@ -115,34 +112,36 @@ def test_e1_first_sweep_matches_oracle(ctx, precision):
     g = _golden("e1_trap_sweep0.txt")
     Eu_ref = np.array([g[f"E_u{k:03d}"] for k in range(2 * (Ls - 1))])
     assert len(Eu) == len(Eu_ref) and Eu[-1] == E
-    off = np.abs(Eu - Eu_ref) > 1e-6 * np.abs(Eu_ref)
+    off = np.abs(Eu - Eu_ref) > 1e-5 * np.abs(Eu_ref)
     first = int(np.argmax(off)) if off.any() else -1  # first update off the oracle
-    assert abs(E - ref) <= 1e-6 * abs(ref), (E, ref, first, Eu[first], Eu_ref[first])
+    assert first == -1, (first, Eu[first], Eu_ref[first])
+    assert abs(E - ref) <= 1e-5 * abs(ref), (E, ref)
 
 
-@pytest.mark.xfail(strict=False,
-                   reason="open defect: in split TF32 the eigensolves of this trapped chain "
-                          "stopped at the 300-matvec cap, the sweep energies collapsed and a "
-                          "start vector vanished (before split-TF32 solves were finished in "
-                          "FP64; not run since); the FP64 oracle converges on the same chain")
-def test_e1_trapped_bosons_L100(ctx):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_e1_trapped_bosons_L100(ctx, precision):
+    """E1 at the paper's size (L = N = 100, n_max = 3, U/J = 5, V/J = 0.01, chi = 100) from
+    the seeded random start, swept until successive sweep energies differ by less than 1e-4
+    (the paper's default DMRG precision, Sec. 5), at most 24 sweeps: the energy falls
+    monotonically, the trap pulls the bosons to the centre (Fig. 4(b)), and the density
+    matrix is Hermitian with the density on its diagonal."""
     from paper_1610_02244_gb300 import tnt
     Ls, N, n_max, J, U, V = 100, 100, 3, 1.0, 5.0, 0.01
     j_c = (Ls + 1) / 2.0  # sites are numbered 1..L in the trap term of Eq. 2
     g = synth.rng(4)
     A, q = synth.random_charged_mps(g, Ls, n_max + 1, N, 100, "gauss", 2.0)
-    ctx.set_params(chi_max=100, precision=tnt.TNT_PREC_MIXED)
+    ctx.set_params(chi_max=100, precision=precision)
     try:
         mps = ctx.mps_create(A, q, chi_cap=100)
         mpo = ctx.mpo_bose_hubbard(Ls, n_max, J, U, 0.0, V, j_c)
         dm = ctx.dmrg_create(mps, mpo)
-        E = [dm.sweep()["E"] for _ in range(6)]
+        E = [dm.sweep()["E"], dm.sweep()["E"]]
+        while abs(E[-1] - E[-2]) > 1e-4 and len(E) < 24:
+            E.append(dm.sweep()["E"])
     finally:
         ctx.set_params(chi_max=1 << 40, precision=tnt.TNT_PREC_FP64)
-    # early sweeps truncate the random start hard (its energy may rise); converged sweeps
-    # do not
-    assert all(b <= a + 1e-8 * abs(a) for a, b in zip(E[3:], E[4:])), E
-    assert abs(E[-1] - E[-2]) <= 1e-6 * abs(E[-1]), E
+    assert all(b <= a + 1e-8 * abs(a) for a, b in zip(E, E[1:])), E
+    assert abs(E[-1] - E[-2]) <= 1e-4, E
     assert abs(mps.expect_mpo(mpo) - E[-1]) <= 1e-8 * abs(E[-1])
     n = mps.density()
     rho = mps.bdagb()
