@@ -252,19 +252,21 @@ int tnt_heff_apply(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
                    tnt_cplx* d_y);
 
 /* The FP64 path of tnt_heff_apply for callers that cannot allocate device memory (the
- * paper has no counterpart: this is an interface for embedding).  Code running during a
- * stream capture, plug-ins confined to a host application's allocator, and processes
- * with a fixed device-memory budget cannot call cudaMalloc; this call makes none (nor
- * cudaFree, nor any allocating library routine).  Its intermediates live in one
+ * paper has no counterpart: this is an interface for embedding).  A plug-in inside a host
+ * application that owns all device memory (its own pool, or a budget fixed at start-up),
+ * or a process sharing its GPU with a framework that reserved the rest, cannot call
+ * cudaMalloc; this call makes none (nor cudaFree, nor any allocating library routine).
+ * Its intermediates (the dense operator W1.W2, L.theta and W1.W2.L.theta) live in one
  * file-scope device array of 16 MiB that every GPU loading the library holds until the
- * process exits, so it accepts only chl * D * d * d * chr <= 522,240 (e.g. chi = 64,
- * d = 5, D = 4); larger shapes return TNT_E_UNSUPPORTED with the limit in the message.
- * The first call on a device looks the array's device address up (once, with that device
- * current); make that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (other streams or host threads) race on it.  Arguments,
- * layouts and results are those of tnt_heff_apply with TNT_PREC_FP64; the call returns
- * after the operator tables are uploaded (one stream synchronisation), with the matvec
- * enqueued on the context's stream. */
+ * process exits, so it accepts only d^2 D <= 256 and chl * D * d * d * chr <= 491,520
+ * (e.g. chi = 64, d = 5, D = 4); larger shapes return TNT_E_UNSUPPORTED with the limit in
+ * the message.  The first call on a device looks the array's device address up (once,
+ * with that device current, which may initialise the module); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, or other host threads on the same device)
+ * race on it.  Arguments, layouts and results are those of tnt_heff_apply with
+ * TNT_PREC_FP64; the call enqueues its four kernels on the context's stream and returns
+ * without synchronising. */
 int tnt_heff_apply_noalloc(tnt_ctx* ctx, const tnt_cplx* d_L, const tnt_cplx* d_W1,
                            const tnt_cplx* d_W2, const tnt_cplx* d_R, const tnt_cplx* d_theta,
                            int64_t chl, int64_t d, int64_t D, int64_t chr, tnt_cplx* d_y);
