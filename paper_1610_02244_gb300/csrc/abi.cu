@@ -324,9 +324,18 @@ static int ctx_create(int device, void* stream, const DevAlloc& a, tnt_ctx** out
     return a.alloc ? TNT_E_ALLOC : TNT_E_CUDA;
   }
   t->c.d_status = (int*)st;
-  cudaMemsetAsync(t->c.d_status, 0, 64, t->c.stream);
+  void* cnt = nullptr;
+  if (dev_alloc(a, &cnt, 256) != 0) {
+    dev_free(a, st);
+    delete t;
+    return a.alloc ? TNT_E_ALLOC : TNT_E_CUDA;
+  }
+  t->c.d_count = (unsigned*)cnt;
+  cudaMemsetAsync(t->c.d_status, 0, 256, t->c.stream);
+  cudaMemsetAsync(t->c.d_count, 0, 256, t->c.stream);
   if (pinned_reserve(&t->c, 4096) != TNT_OK || cudaStreamSynchronize(t->c.stream) != cudaSuccess) {
     dev_free(a, t->c.d_status);
+    dev_free(a, t->c.d_count);
     delete t;
     return TNT_E_ALLOC;
   }
@@ -357,6 +366,7 @@ int tnt_ctx_destroy(tnt_ctx* ctx) {
   dev_free(ctx->c.dalloc, ctx->c.ws.base);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);
   dev_free(ctx->c.dalloc, ctx->c.d_status);
+  dev_free(ctx->c.dalloc, ctx->c.d_count);
   dev_free(ctx->c.dalloc, ctx->c.oz_buf);
   delete ctx;
   return TNT_OK;

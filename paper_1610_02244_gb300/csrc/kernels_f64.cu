@@ -332,12 +332,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // partial[v][blk] = sum over the block's range of conj(V_v[e]) w[e], v < KV; the KV
-// loads of one element are independent and issued together
+// loads of one element are independent and issued together.  The last CTA to finish (an
+// arrival counter, reset by that CTA) sums the partials in block order into out[v]: the
+// reduction stays deterministic and needs no second launch.
 template <int KV>
 __global__ void __launch_bounds__(RT) k_multidot(const z* __restrict__ V, int64_t ld,
                                                  const z* __restrict__ w, int64_t n,
                                                  z* __restrict__ partial,
-                                                 const int* __restrict__ skip) {
+                                                 const int* __restrict__ skip,
+                                                 unsigned* __restrict__ counter,
+                                                 z* __restrict__ out) {
   if (skip && *skip) return;  // a pass the caller decided on the device not to need
   __shared__ double sh[32];
   double ar[KV], ai[KV];
@@ -357,52 +361,94 @@ __global__ void __launch_bounds__(RT) k_multidot(const z* __restrict__ V, int64_
       ai[v] = fma(u[v].x, x.y, fma(-u[v].y, x.x, ai[v]));
     }
   }
+  // all 2 KV sums in one pass: shuffles within each warp, then one barrier and a fixed-order
+  // sum over the warps (the per-value block reductions cost two barriers each, and with a
+  // few elements per thread they outweighed the loop)
+  __shared__ double shp[RT / 32][2 * KV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int v = 0; v < KV; ++v) {
-    double r = block_sum(ar[v], sh);
-    double i = block_sum(ai[v], sh);
-    if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = zmk(r, i);
+    ar[v] = warp_sum(ar[v]);
+    ai[v] = warp_sum(ai[v]);
   }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {
+      shp[wid][2 * v] = ar[v];
+      shp[wid][2 * v + 1] = ai[v];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * KV) {
+    double t = 0;
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) t += shp[q][threadIdx.x];
+    double* po = (double*)(partial + (int64_t)(threadIdx.x >> 1) * gridDim.x + blockIdx.x);
+    po[threadIdx.x & 1] = t;
+    __threadfence();
+  }
+  // the last CTA to arrive sums every CTA's partials, in block order
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double* pp = (const double*)partial;
+  double acc[2 * KV];
+#pragma unroll
+  for (int v = 0; v < 2 * KV; ++v) acc[v] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) {
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {
+      const z pv = __ldcg(partial + (int64_t)v * gridDim.x + b);
+      acc[2 * v] += pv.x;
+      acc[2 * v + 1] += pv.y;
+    }
+  }
+  (void)pp;
+#pragma unroll
+  for (int v = 0; v < 2 * KV; ++v) acc[v] = warp_sum(acc[v]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < 2 * KV; ++v) shp[wid][v] = acc[v];
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * KV) {
+    double t = 0;
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) t += shp[q][threadIdx.x];
+    ((double*)(out + (threadIdx.x >> 1)))[threadIdx.x & 1] = t;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  (void)sh;
 }
 
 void launch_multidot(int kv, dim3 g, dim3 b, cudaStream_t st, const z* V, int64_t ld,
-                     const z* w, int64_t n, z* partial, const int* skip) {
+                     const z* w, int64_t n, z* partial, const int* skip, unsigned* cnt,
+                     z* out) {
   switch (kv) {
-    case 1: k_multidot<1><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 2: k_multidot<2><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 3: k_multidot<3><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 4: k_multidot<4><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 5: k_multidot<5><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 6: k_multidot<6><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    case 7: k_multidot<7><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
-    default: k_multidot<8><<<g, b, 0, st>>>(V, ld, w, n, partial, skip); break;
+    case 1: k_multidot<1><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 2: k_multidot<2><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 3: k_multidot<3><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 4: k_multidot<4><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 5: k_multidot<5><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 6: k_multidot<6><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    case 7: k_multidot<7><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
+    default: k_multidot<8><<<g, b, 0, st>>>(V, ld, w, n, partial, skip, cnt, out); break;
   }
 }
 
-// out[v] = sum_b partial[v][b], fixed order; one block, kv outputs
-__global__ void k_reduce_partials(const z* __restrict__ partial, int nb, int kv,
-                                  z* __restrict__ out, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double sh[32];
-  for (int v = 0; v < kv; ++v) {
-    double r = 0, i = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      z p = partial[(int64_t)v * nb + b];
-      r += p.x;
-      i += p.y;
-    }
-    r = block_sum(r, sh);
-    i = block_sum(i, sh);
-    if (threadIdx.x == 0) out[v] = zmk(r, i);
-  }
-}
-
-// w[e] -= sum_v coef[v] V_v[e]; partial[blk] = sum |w[e]|^2
+// w[e] -= sum_v coef[v] V_v[e]; partial[blk] = sum |w[e]|^2, and the last CTA to finish
+// writes the total |w|^2
 __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, int64_t ld,
                                                        int k, const z* __restrict__ coef,
                                                        z* __restrict__ w, int64_t n,
                                                        double* __restrict__ partial,
-                                                       const int* __restrict__ skip) {
+                                                       const int* __restrict__ skip,
+                                                       unsigned* __restrict__ counter,
+                                                       double* __restrict__ norm2_out) {
   if (skip && *skip) return;
   __shared__ z sc[64];
   __shared__ double sh[32];
@@ -436,7 +482,23 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, 
     acc = fma(x.x, x.x, fma(x.y, x.y, acc));
   }
   double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+  }
+  // the last CTA to arrive sums every CTA's partial, in block order
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double r = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) r += __ldcg(partial + b);
+  r = block_sum(r, sh);
+  if (threadIdx.x == 0) {
+    *norm2_out = r;
+    *counter = 0u;
+  }
 }
 
 __global__ void k_reduce_real(const double* __restrict__ partial, int nb,
@@ -486,9 +548,9 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
     // FP64 FLOPs (complex MAC = 8); a pass the device may skip is profiled apart, with no
     // work claimed (the host cannot know whether it ran)
     ProfScope ps(c, d_skip ? "multidot_cond" : "multidot", d_skip ? 0.0 : 8.0 * (double)kv * (double)n);
-    launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip);
-    k_reduce_partials<<<1, 256, 0, c->stream>>>(partial, RB, kv, d_dots + v0, d_skip);
-    c->launches += 2;
+    launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip,
+                    c->d_count, d_dots + v0);
+    c->launches += 1;
   }
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;
@@ -504,10 +566,10 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
   {
     ProfScope ps(c, d_skip ? "multiaxpy_cond" : "multiaxpy",
                  d_skip ? 0.0 : (8.0 * (double)k + 4.0) * (double)n);  // FP64 FLOPs
-    k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip);
+    k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip,
+                                               c->d_count + 1, d_norm2);
   }
-  k_reduce_real<<<1, 256, 0, c->stream>>>(partial, RB, d_norm2, d_skip);
-  c->launches += 2;
+  c->launches += 1;
   TNT_CHECK_LAUNCH(c);
   return TNT_OK;
 }

@@ -64,6 +64,9 @@ struct Ctx {
   size_t h_pinned_cap = 0;
   // device status word written by kernels (bounds / NaN / timeout flags)
   int* d_status = nullptr;
+  // arrival counters of the kernels that finish their reduction in the last CTA to arrive
+  // (zero between launches: that CTA resets its counter)
+  unsigned* d_count = nullptr;
   // counters (diagnostics, not hot-path state)
   int64_t launches = 0;
   // optional CUDA-event timing of one kernel class (tnt_profile_select)
