@@ -485,14 +485,16 @@ struct EBlk {
 // apply at negligible off-diagonals): the longest trailing range [s, n) whose diagonal and
 // off-diagonal entries, its coupling e_{s-1} included, are all at most SPLIT_TOL |T|.  A
 // rank-deficient Gram block reduces to such a T: once the reflectors have spanned the
-// block's range, the trailing matrix is rounding noise (below 1 eps |T| in emulations of
-// rank-deficient blocks of up to 256 rows); 8 eps |T| catches it while absorbing only
-// eigenvalues below the Gram matrix's own resolution (sigma under ~4e-8 sigma_max).  The eigenvalues of that range are
+// block's range, the trailing matrix is rounding noise (a few eps |T| and more where the
+// Gram matrix itself carries the rounding of a long sum); 1e3 eps |T| catches it.  The
+// split also absorbs real eigenvalues below that level (singular values under ~5e-7
+// sigma_max): the canonical vectors span their subspace exactly, and the truncated SVD
+// resolves its singular values in a second pass over that subspace.  The eigenvalues of that range are
 // zero to within SPLIT_TOL |T|, and any orthonormal basis of its coordinates is an
 // eigenbasis to that accuracy: the canonical vectors e_s, ..., e_{n-1} are taken, exactly
 // orthonormal to each other and (zero beyond s) to the iterates of T[0, s), with no
 // inverse iteration.  One warp per problem: |T| (Gershgorin) to tnorm, s to nr.
-constexpr double SPLIT_TOL = 8 * 2.220446049250313e-16;
+constexpr double SPLIT_TOL = 1e3 * 2.220446049250313e-16;
 __global__ void k_split(const double* __restrict__ dAll, const double* __restrict__ eAll,
                         const EBlk* __restrict__ blks, double* __restrict__ tnorm,
                         int64_t* __restrict__ nr) {

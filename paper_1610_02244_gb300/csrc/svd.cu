@@ -89,6 +89,16 @@ __global__ void k_block_scale(z* __restrict__ Mp, const int64_t* __restrict__ bo
     for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) Mp[off + i] = zscale(Mp[off + i], sc);
 }
 
+// dst[r * ldd + c] = src[r * lds + c], r < rows, c < cols
+__global__ void k_copy_strided(const z* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                               z* __restrict__ dst, int64_t ldd) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, cc = e % cols;
+    dst[r * ldd + cc] = src[r * lds + cc];
+  }
+}
+
 // -------------------------------------------------------------- global selection
 struct SelOut {
   int64_t chi;
@@ -312,10 +322,148 @@ size_t svd_scratch_bound(int64_t m, int64_t n) {
   // the eigen phase of the small blocks (Gram side <= 256, every eigenpair formed): per
   // block n k <= 256 n of work, iterates, two eigenvector copies and k^2 coefficients
   const size_t small_eig = (6 * 8 + 8 + 2 * 16 + 16) * 256 * mx + (size_t)(1 << 20);
+  // the tail pass: its Gram matrices and eigenvectors (sum t^2 <= mx mn each), one rotation
+  // buffer (<= mx mn), eigenvalues
+  const size_t tail = 3 * 16 * mx * mn + 8 * std::max<size_t>(mx * mn, 8192);
   return autoblock_bytes(m, n) + 8 * (size_t)(m + n) + 2 * 16 * (size_t)m * n + 2 * 16 * mx * mx + 6 * 8 * mx +
-         sizeof(KeptIdx) * mx + 12 * 8192 +
+         sizeof(KeptIdx) * mx + 12 * 8192 + tail +
          std::max(heig_scratch_bound((int64_t)mx, (int64_t)mx), small_eig) + (size_t)(4 << 20);
 }
+
+namespace {
+// one charge block of the truncated SVD (host tables)
+struct Blk {
+  int64_t q, mq, nq, g, r, k;
+  int64_t roff, coff, moff, goff, xoff;
+};
+// Second pass over each block's tail.  An eigenvector of the Gram matrix whose eigenvalue
+// lies at the Gram matrix's rounding level (or below the split of its tridiagonal form) is
+// only known to lie in the right subspace: its projection norm mixes the tiny singular
+// values of that subspace with the Gram matrix's rounding, which is ~sqrt(eps) |M| rather
+// than eps |M|.  So the candidates of a block whose sigma is below TAIL_REL times the
+// block's largest (a suffix of the candidate list, which runs in eigenvalue order) are
+// diagonalised once more, from their own projections: LEFT, H = X_t X_t^H of the tail rows
+// X_t = U_t^H M_q; RIGHT, H = Y_t^H Y_t of the tail columns Y_t = M_q V_t.  H carries the
+// tail's own scale, so its eigenvectors W resolve the tail's singular values down to about
+// eps |M|; U_t <- U_t W (V_t <- V_t W) and X_t <- W^H X_t (Y_t <- Y_t W) rotate the
+// candidates within the tail subspace, keeping them orthonormal, and the projection norms
+// are taken again.
+constexpr double TAIL_REL = 1e-4;
+
+struct TailBlk {
+  int b;
+  int64_t t0, t, toff;
+};
+
+int refine_tails(Ctx* c, int side, const std::vector<Blk>& bl, z* Vp, z* Xp,
+                 const CandBlock* d_cb, const double* d_unscale, double* d_sig, int64_t ntot) {
+  cudaStream_t st = c->stream;
+  std::vector<double> hs((size_t)ntot);
+  TNT_CUDA_TRY(c, cudaMemcpyAsync(hs.data(), d_sig, sizeof(double) * ntot, cudaMemcpyDeviceToHost, st));
+  TNT_CUDA_TRY(c, cudaStreamSynchronize(st));
+  std::vector<TailBlk> tb;
+  int64_t gt = 0, vbase = 0, tmpmax = 0;
+  for (int b = 0; b < (int)bl.size(); ++b) {
+    const Blk& B = bl[(size_t)b];
+    double mx = 0;
+    for (int64_t i = 0; i < B.k; ++i) mx = std::max(mx, hs[(size_t)(vbase + i)]);
+    int64_t t0 = B.k;
+    while (t0 > 0 && !(hs[(size_t)(vbase + t0 - 1)] >= TAIL_REL * mx)) --t0;
+    const int64_t t = B.k - t0;
+    if (t >= 2 && mx > 0) {
+      tb.push_back(TailBlk{b, t0, t, gt});
+      gt += t * t;
+      const int64_t rows_x = (side == TNT_SVD_LEFT) ? t : B.mq;
+      const int64_t cols_x = (side == TNT_SVD_LEFT) ? B.nq : t;
+      tmpmax = std::max(tmpmax, std::max(B.g * t, rows_x * cols_x));
+    }
+    vbase += B.k;
+  }
+  if (tb.empty()) return TNT_OK;
+  const size_t top = c->ws.top;
+  z* H = (z*)ws_alloc(c, ws_round(sizeof(z) * gt));
+  z* W = (z*)ws_alloc(c, ws_round(sizeof(z) * gt));
+  z* tmp = (z*)ws_alloc(c, ws_round(sizeof(z) * tmpmax));
+  double* ev = (double*)ws_alloc(c, ws_round(sizeof(double) * (gt > 8192 ? gt : 8192)));
+  if (!H || !W || !tmp || !ev) {
+    c->ws.top = top;
+    return set_err(c, TNT_E_ALLOC, "scratch exhausted (SVD tail pass)");
+  }
+  // tail Gram matrices
+  for (const TailBlk& T : tb) {
+    const Blk& B = bl[(size_t)T.b];
+    ZGemm g{};
+    g.batch = 1;
+    g.alpha = zmk(1, 0);
+    g.beta = zmk(0, 0);
+    g.M = T.t; g.N = T.t;
+    g.C = H + T.toff; g.c_rs = T.t;
+    if (side == TNT_SVD_LEFT) {  // H = X_t X_t^H, X_t rows t0.. of X_q (ld n_q)
+      const z* Xt = Xp + B.xoff + T.t0 * B.nq;
+      g.K = B.nq;
+      g.A = Xt; g.a_rs = B.nq; g.a_cs = 1;
+      g.B = Xt; g.b_rs = 1; g.b_cs = B.nq; g.conj_b = 1;
+    } else {  // H = Y_t^H Y_t, Y_t columns t0.. of Y_q (ld k)
+      const z* Yt = Xp + B.xoff + T.t0;
+      g.K = B.mq;
+      g.A = Yt; g.a_rs = 1; g.a_cs = B.k; g.conj_a = 1;
+      g.B = Yt; g.b_rs = B.k; g.b_cs = 1;
+    }
+    TNT_TRY(zgemm(c, g));
+  }
+  // eigenvectors of every tail Gram matrix (all of them, descending)
+  {
+    std::vector<SmallEig> small;
+    for (const TailBlk& T : tb)
+      if (T.t <= 256) small.push_back(SmallEig{T.toff, T.t, T.t});
+    TNT_TRY(heig_small_blocks(c, H, small, W, ev));
+    for (const TailBlk& T : tb)
+      if (T.t > 256) TNT_TRY(heig_top(c, H + T.toff, T.t, T.t, W + T.toff, T.t, ev));
+  }
+  // rotate the tail candidates within their subspace
+  for (const TailBlk& T : tb) {
+    const Blk& B = bl[(size_t)T.b];
+    z* Wt = W + T.toff;
+    {  // eigenvectors: U_t (or V_t), g x t at column t0 of the block (ld g) <- U_t W
+      ZGemm g{};
+      g.batch = 1; g.alpha = zmk(1, 0); g.beta = zmk(0, 0);
+      g.M = B.g; g.N = T.t; g.K = T.t;
+      g.A = Vp + B.goff + T.t0; g.a_rs = B.g; g.a_cs = 1;
+      g.B = Wt; g.b_rs = T.t; g.b_cs = 1;
+      g.C = tmp; g.c_rs = T.t;
+      TNT_TRY(zgemm(c, g));
+      k_copy_strided<<<gridn(B.g * T.t), 256, 0, st>>>(tmp, B.g, T.t, T.t, Vp + B.goff + T.t0, B.g);
+      c->launches++;
+    }
+    ZGemm g{};
+    g.batch = 1; g.alpha = zmk(1, 0); g.beta = zmk(0, 0);
+    if (side == TNT_SVD_LEFT) {  // X_t <- W^H X_t  (t x n_q, contiguous rows)
+      z* Xt = Xp + B.xoff + T.t0 * B.nq;
+      g.M = T.t; g.N = B.nq; g.K = T.t;
+      g.A = Wt; g.a_rs = 1; g.a_cs = T.t; g.conj_a = 1;
+      g.B = Xt; g.b_rs = B.nq; g.b_cs = 1;
+      g.C = tmp; g.c_rs = B.nq;
+      TNT_TRY(zgemm(c, g));
+      TNT_CUDA_TRY(c, cudaMemcpyAsync(Xt, tmp, sizeof(z) * T.t * B.nq, cudaMemcpyDeviceToDevice, st));
+    } else {  // Y_t <- Y_t W  (m_q x t at column t0, ld k)
+      z* Yt = Xp + B.xoff + T.t0;
+      g.M = B.mq; g.N = T.t; g.K = T.t;
+      g.A = Yt; g.a_rs = B.k; g.a_cs = 1;
+      g.B = Wt; g.b_rs = T.t; g.b_cs = 1;
+      g.C = tmp; g.c_rs = T.t;
+      TNT_TRY(zgemm(c, g));
+      k_copy_strided<<<gridn(B.mq * T.t), 256, 0, st>>>(tmp, B.mq, T.t, T.t, Yt, B.k);
+      c->launches++;
+    }
+  }
+  TNT_CHECK_LAUNCH(c);
+  k_cand_sigma<<<(unsigned)bl.size(), 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  c->ws.top = top;
+  return TNT_OK;
+}
+}  // namespace
 
 int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq,
                    const int64_t* h_cq, int side, int renorm, z* U, z* X, double* h_S,
@@ -361,10 +509,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   // candidates per block: its leading min(rank, chi_max) values (all of them for the
   // 1-norm error, which cannot be completed from |M|_F)
   const bool all_values = (P.trunc_type == TNT_TRUNC_1NORM);
-  struct Blk {
-    int64_t q, mq, nq, g, r, k;
-    int64_t roff, coff, moff, goff, xoff;
-  };
+
   bool complete = true;
   std::vector<Blk> bl;
   std::vector<int64_t> rows_all, cols_all;
@@ -532,6 +677,7 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   }
   k_cand_sigma<<<nb, 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
   c->launches++;
+  TNT_TRY(refine_tails(c, side, bl, Vp, Xp, d_cb, d_unscale, d_sig, ntot_vals));
   // ---- global order and the four rules
   {
     size_t smem = (size_t)P2 * (sizeof(double) + 2 * sizeof(int));

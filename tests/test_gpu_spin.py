@@ -269,3 +269,40 @@ def test_spin1_table1_first_sweep_matches_oracle(ctx, precision):
     off = np.abs(Eu - Eu_ref) > 1e-6 * np.abs(Eu_ref)
     first = int(np.argmax(off)) if off.any() else -1
     assert abs(E - g["E_sweep0"]) <= 1e-5 * abs(g["E_sweep0"]), (E, g["E_sweep0"], first)
+
+
+def test_spin1_tebd_chi1000_sampled_gate(ctx):
+    """One Trotter gate of the Table 2 workload at its bond dimension (spin-1 Heisenberg, dt =
+    0.05, chi_max = 1000, truncation error 1e-10, S^z_total = +1, seeded random MPS with the
+    Gaussian sector profile), on a 15-site chain whose middle bonds are at chi = 1000: the
+    GPU (centre moved to bond 7 by exact SVD moves through tnt_tebd_gate) against the FP64
+    oracle's canonical form and gate on the same state.  A random state's Schmidt spectrum
+    is flat, so chi_max = 1000 cuts it (truncation error ~1e-2 on both sides): compared are
+    every kept Schmidt value (normalised by the state norm) to 1e-12, the truncation errors
+    to 1e-8 relative, and the bond dimension."""
+    from oracle import dmrg as od
+    Ls, two_s, chi, dt, err, bond = 15, 2, 1000, 0.05, 1e-10, 7
+    N = Ls * two_s // 2 + 1
+    A, q = synth.random_charged_mps(synth.rng(0), Ls, two_s + 1, N, chi, "gauss", 2.0)
+    hs = [ospin.bond_hamiltonian(two_s, 1.0, 1.0, 0.0, *bh.bond_weights(Ls, j + 1))
+          for j in range(Ls - 1)]
+    G = bh.gate(hs[bond], dt)
+    Ao, qo = od.right_canonicalize([a.copy() for a in A], [c.copy() for c in q])
+    ev = otebd.Tebd.from_bond_hamiltonians(Ao, qo, hs, dt, TruncParams(chi_max=chi, err_tol=err))
+    ev.apply_gate(bond, G, True)
+    Bo = ev.A[bond + 1]
+    S_ref = np.linalg.svd(Bo.reshape(Bo.shape[0], -1), compute_uv=False)
+    ctx.set_params(chi_max=chi, trunc_err=err, trunc_abs=-1.0, trunc_rel=1e-16, trunc_type=0)
+    try:
+        mps = ctx.mps_create(A, q, chi_cap=chi)
+        tb = ctx.tebd_create_bonds(mps, hs, dt)
+        n2 = mps.norm2()
+        tr = tb.gate(bond, G, +1)
+        assert tb.centre() == bond + 1
+        B = mps.site(bond + 1)
+    finally:
+        ctx.set_params(chi_max=1 << 40, trunc_err=1e-8)
+    S = np.linalg.svd(B.reshape(B.shape[0], -1), compute_uv=False) / np.sqrt(n2)
+    assert len(S) == len(S_ref) == tr["chi"]
+    assert np.abs(S - S_ref).max() <= 1e-12, np.abs(S - S_ref).max()
+    assert abs(tr["err"] - ev.eps_sum) <= 1e-8 * ev.eps_sum, (tr["err"], ev.eps_sum)
