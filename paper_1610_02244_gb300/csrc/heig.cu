@@ -36,15 +36,19 @@ __device__ __forceinline__ void zsub_mul_conj(z& x, z a, z b) {
   x.y = fma(-a.y, b.x, fma(a.x, b.y, x.y));
 }
 
-// block-wide sum; valid in every thread on return
+// block-wide sum; valid in every thread on return.  The warp sums are combined by a
+// butterfly over one warp's lanes (every warp the same order, so every thread gets the
+// same bits): five FP64 adds per thread, where a loop over the warp sums in every thread
+// cost one add per warp per thread (the FP64 pipe is the scarce unit on GB300)
 __device__ double block_sum_all(double v, double* sh) {
   v = warp_sum_d(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double r = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  double r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   return r;
 }
 
@@ -56,8 +60,9 @@ __device__ double block_max_all(double v, double* sh) {
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double r = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
+  double r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
   return r;
 }
 
@@ -131,40 +136,63 @@ __device__ bool grid_barrier(const TriArgs& a) {
   return s_ok != 0;
 }
 
+// Block-wide sum, valid in thread 0 only (warp 0 combines the warp sums).
+__device__ double block_sum0(double v, double* sh) {
+  v = warp_sum_d(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0;
+  if (w == 0) r = warp_sum_d((l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0);
+  return r;
+}
+
+// Householder reflector of a row x (the part below the diagonal of a column of a Hermitian
+// matrix, conjugated): alpha = conj(x_0), xn2 = sum_{r>0} |x_r|^2.  H = I - tau v v^H with
+// v = (1, conj(x_r) scale, ...) maps conj(x) to beta e_1, beta real.  Computed by one thread:
+// a full-block FP64 square root and three divisions cost more FP64-pipe issue slots on
+// GB300 than the vector work of a short column.
+struct Refl {
+  z tau, scale;
+  double beta;
+};
+__device__ Refl refl_params(z alpha, double xn2, bool empty) {
+  Refl R;
+  if (empty || (xn2 == 0.0 && alpha.y == 0.0)) {
+    R.tau = zmk(0, 0);
+    R.beta = alpha.x;
+    R.scale = zmk(0, 0);
+  } else {
+    const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+    R.beta = alpha.x >= 0 ? -nrm : nrm;
+    R.tau = zmk((R.beta - alpha.x) / R.beta, -alpha.y / R.beta);
+    const z den = zmk(alpha.x - R.beta, alpha.y);  // scale = 1 / (alpha - beta)
+    const double dd = den.x * den.x + den.y * den.y;
+    R.scale = zmk(den.x / dd, -den.y / dd);
+  }
+  return R;
+}
+
 // Reflector from x_r = conj(row[r]), r < m (row already in the workspace): v (length m,
 // v[0] = 1), tau, beta with H^H x = beta e_1.  Every thread of the block returns the same
 // tau and beta.
 __device__ void make_reflector(const z* row, int64_t m, z* v, z* tau_out, double* beta_out,
                                double* sh) {
-  __shared__ double s_xn2;
+  __shared__ Refl s_refl;
   double acc = 0;
   for (int64_t r = 1 + threadIdx.x; r < m; r += blockDim.x) {
     const z x = row[r];
     acc = fma(x.x, x.x, fma(x.y, x.y, acc));
   }
-  acc = block_sum_all(acc, sh);
-  if (threadIdx.x == 0) s_xn2 = acc;
+  acc = block_sum0(acc, sh);
+  if (threadIdx.x == 0) s_refl = refl_params(m > 0 ? zconj(row[0]) : zmk(0, 0), acc, m == 0);
   __syncthreads();
-  const double xn2 = s_xn2;
-  const z alpha = m > 0 ? zconj(row[0]) : zmk(0, 0);
-  double beta;
-  z t, scale;
-  if (m == 0 || (xn2 == 0.0 && alpha.y == 0.0)) {
-    t = zmk(0, 0);
-    beta = alpha.x;
-    scale = zmk(0, 0);
-  } else {
-    const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-    beta = alpha.x >= 0 ? -nrm : nrm;
-    t = zmk((beta - alpha.x) / beta, -alpha.y / beta);
-    const z den = zmk(alpha.x - beta, alpha.y);  // scale = 1 / (alpha - beta)
-    const double dd = den.x * den.x + den.y * den.y;
-    scale = zmk(den.x / dd, -den.y / dd);
-  }
+  const Refl R = s_refl;
   for (int64_t r = threadIdx.x; r < m; r += blockDim.x)
-    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(row[r]), scale);
-  *tau_out = t;
-  *beta_out = beta;
+    v[r] = (r == 0) ? zmk(1, 0) : zmul(zconj(row[r]), R.scale);
+  *tau_out = R.tau;
+  *beta_out = R.beta;
   __syncthreads();
 }
 
@@ -326,6 +354,234 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- rows in shared memory
+// The same column-by-column reduction for n <= TRI_ROWS_NMAX with each block's rows of the
+// matrix (row g belongs to block g mod nb) resident in its shared memory for the whole
+// reduction: the trailing update and the product with the next reflector touch shared
+// memory only, and per column the global memory carries p (n entries), the per-block
+// partial sums and the one row that is the source of the next reflector.  Entering column
+// j every block holds v_j (v_j(j+1) = 1) and tau_j, and p_j = tau_j T_j v_j with the
+// partial sums of p_j^H v_j is in global memory.  Then
+//   every block, one pass over the columns c > j with its loads issued first:
+//     w_j(c) = p_j(c) + cf v_j(c), cf = -(tau_j / 2) p_j^H v_j, and
+//     x(c) = T_j(j+1, c) - conj(w_j(c)) - w_j(j+1) conj(v_j(c)), row j+1 after the
+//     update, whose entries past j+1 give reflector j+1 (scalars by one thread from the
+//     block sum of |x|^2: the same bits in every block);
+//   each block, its rows g > j+1, each split over TRI_WARPS / (rows) warps:
+//     T <- T - v_j w_j^H - w_j v_j^H and the product with v_{j+1}, giving p_{j+1}(g) and
+//     the block's share of p_{j+1}^H v_{j+1}; the owner of row j+2 also stores that row
+//     in global memory for the next column;
+//   grid barrier.
+// Vectors are indexed by global row.  Per column a block spends 16 FP64 operations per
+// trailing entry on the shared vectors and 12 per entry of its rows.
+constexpr int TRI_ROWS_MAX = 8;         // rows per block
+constexpr int TRI_VEC = 3;              // vector entries per thread
+constexpr int64_t TRI_ROWS_NMAX = 1216; // <= TRI_VEC * TRI_THREADS; (8 + 3) n entries fit
+
+// Rows g >= lo of this block (rows[i] = row b + nb i, R of them): with UPD,
+// T(g, c) -= v(g) conj(w(c)) + w(g) conj(v(c)) for c >= lo (the row g == lo also to grow);
+// then p(g) = tq sum_{c >= lo} T(g, c) q(c) to pout[g] and the block's sum of
+// conj(p(g)) q(g) to *partout.
+template <bool UPD>
+__device__ void rows_pass(z* rows, int R, int b, int nb, int64_t n, int64_t lo, const z* v,
+                          const z* w, const z* q, z tq, z* pout, z* partout, z* grow,
+                          double (*s_pr)[TRI_WARPS], double (*s_pi)[TRI_WARPS]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = (lo > b) ? (int)((lo - b + nb - 1) / nb) : 0;
+  const int ract = R - i0;
+  if (ract > 0) {
+    const int wpr = TRI_WARPS / ract;
+    const int ri = warp / wpr, sub = warp - ri * wpr;
+    if (ri < ract) {
+      const int i = i0 + ri;
+      const int64_t g = b + (int64_t)nb * i;
+      z* rw = rows + (int64_t)i * n;
+      z vr = zmk(0, 0), wr = zmk(0, 0);
+      if (UPD) {
+        vr = v[g];
+        wr = w[g];
+      }
+      z* gout = (UPD && g == lo) ? grow : nullptr;
+      double sr = 0, si = 0;
+      const int64_t stride = 32 * (int64_t)wpr;
+#pragma unroll 2
+      for (int64_t c = lo + sub * 32 + lane; c < n; c += stride) {
+        z x = rw[c];
+        if (UPD) {
+          zsub_mul_conj(x, vr, w[c]);
+          zsub_mul_conj(x, wr, v[c]);
+          rw[c] = x;
+          if (gout) gout[c] = x;
+        }
+        const z y = q[c];
+        sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+        si = fma(x.x, y.y, fma(x.y, y.x, si));
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) {
+        s_pr[ri][sub] = sr;
+        s_pi[ri][sub] = si;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double pr = 0, pi = 0;
+    if (lane < ract) {
+      const int wpr = TRI_WARPS / ract;
+      double sr = 0, si = 0;
+      for (int u = 0; u < wpr; ++u) {
+        sr += s_pr[lane][u];
+        si += s_pi[lane][u];
+      }
+      const int64_t g = b + (int64_t)nb * (i0 + lane);
+      const z pv = zmul(tq, zmk(sr, si));
+      pout[g] = pv;
+      const z qq = q[g];
+      pr = pv.x * qq.x + pv.y * qq.y;
+      pi = pv.x * qq.y - pv.y * qq.x;
+    }
+    pr = warp_sum_d(pr);
+    pi = warp_sum_d(pi);
+    if (lane == 0) *partout = zmk(pr, pi);
+  }
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag_rows(TriArgs a) {
+  extern __shared__ z sm_tri[];
+  __shared__ double sh[32];
+  __shared__ double s_pr[TRI_ROWS_MAX][TRI_WARPS], s_pi[TRI_ROWS_MAX][TRI_WARPS];
+  __shared__ z s_cf, s_alpha;
+  __shared__ Refl s_refl;
+  const int64_t n = a.n;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rmax = (int)((n + nb - 1) / nb);
+  const int R = (b < n) ? (int)((n - b + nb - 1) / nb) : 0;
+  z* rows = sm_tri;
+  z* sv = rows + (int64_t)rmax * n;  // v_j
+  z* sw = sv + n;                    // w_j
+  z* sv2 = sw + n;                   // v_{j+1}
+  for (int i = 0; i < R; ++i) {
+    const z* src = a.G + (b + (int64_t)nb * i) * n;
+    for (int64_t c = tid; c < n; c += TRI_THREADS) rows[(int64_t)i * n + c] = __ldcg(src + c);
+  }
+  z t;
+  {  // reflector 0 from row 0, then p_0 = tau_0 T v_0 over the owned rows
+    z x[TRI_VEC];
+    double acc = 0;
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {
+      const int64_t c = 1 + tid + (int64_t)k * TRI_THREADS;
+      x[k] = c < n ? __ldcg(a.G + c) : zmk(0, 0);
+      if (c >= 2 && c < n) acc = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, acc));
+    }
+    acc = block_sum0(acc, sh);
+    if (tid == 0) {  // thread 0 holds column 1
+      const Refl rf = refl_params(zconj(x[0]), acc, n < 2);
+      s_refl = rf;
+      if (b == 0) {
+        a.tau[0] = rf.tau;
+        a.d[0] = __ldcg(a.G).x;
+        if (n > 1) a.e[0] = rf.beta;
+      }
+    }
+    __syncthreads();
+    const Refl rf = s_refl;
+    t = rf.tau;
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {
+      const int64_t c = 1 + tid + (int64_t)k * TRI_THREADS;
+      if (c < n) {
+        const z vc = (c == 1) ? zmk(1, 0) : zmul(zconj(x[k]), rf.scale);
+        sv[c] = vc;
+        if (b == 0) a.Hv[c - 1] = vc;
+      }
+    }
+    __syncthreads();
+    rows_pass<false>(rows, R, b, nb, n, 1, sv, sw, sv, t, a.p, a.part + b, nullptr, s_pr, s_pi);
+  }
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    if (!grid_barrier(a)) return;
+    const z* pj = a.p + (j & 1) * n;
+    z* pn = a.p + ((j + 1) & 1) * n;
+    const z* partj = a.part + (j & 1) * nb;
+    z* partn = a.part + ((j + 1) & 1) * nb;
+    const z* grow = a.G + (j + 1) * n;
+    z pc[TRI_VEC], rc[TRI_VEC];
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {
+      const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
+      pc[k] = c < n ? __ldcg(pj + c) : zmk(0, 0);
+      rc[k] = c < n ? __ldcg(grow + c) : zmk(0, 0);
+    }
+    const z p1 = __ldcg(pj + j + 1);
+    if (warp == 0) {  // the nb partials, loaded by 32 lanes at once and summed by shuffles
+      double sa = 0, sb = 0;
+      for (int q = lane; q < nb; q += 32) {
+        const z pq = __ldcg(partj + q);
+        sa += pq.x;
+        sb += pq.y;
+      }
+      sa = warp_sum_d(sa);
+      sb = warp_sum_d(sb);
+      if (lane == 0) {
+        const z ts = zmul(t, zmk(sa, sb));
+        s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+      }
+    }
+    __syncthreads();
+    const z cf = s_cf;
+    const z w1 = zmk(p1.x + cf.x, p1.y + cf.y);  // w_j(j+1), as v_j(j+1) = 1
+    double acc = 0;
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {
+      const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
+      if (c < n) {
+        const z vv = sv[c];
+        const z wv = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pc[k].x)),
+                         fma(cf.x, vv.y, fma(cf.y, vv.x, pc[k].y)));
+        sw[c] = wv;
+        z x = zmk(rc[k].x - wv.x, rc[k].y + wv.y);
+        zsub_mul_conj(x, w1, vv);
+        rc[k] = x;
+        if (c >= j + 3) acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+        if (c == j + 2) s_alpha = zconj(x);
+      }
+    }
+    acc = block_sum0(acc, sh);
+    const int64_t m2 = n - j - 2;  // length of reflector j+1
+    if (tid == 0) {                // thread 0 holds column j+1
+      const Refl rf = refl_params(m2 > 0 ? s_alpha : zmk(0, 0), acc, m2 <= 0);
+      s_refl = rf;
+      if (b == 0) {
+        a.tau[j + 1] = rf.tau;
+        a.d[j + 1] = rc[0].x;
+        if (m2 > 0) a.e[j + 1] = rf.beta;
+      }
+    }
+    __syncthreads();
+    const Refl rf = s_refl;
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {
+      const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
+      if (c >= j + 2 && c < n) {
+        const z vc = (c == j + 2) ? zmk(1, 0) : zmul(zconj(rc[k]), rf.scale);
+        sv2[c] = vc;
+        if (b == 0) a.Hv[(j + 1) * n + (c - j - 2)] = vc;
+      }
+    }
+    __syncthreads();
+    rows_pass<true>(rows, R, b, nb, n, j + 2, sv, sw, sv2, rf.tau, pn, partn + b,
+                    a.G + (j + 2) * n, s_pr, s_pi);
+    z* tmp = sv;
+    sv = sv2;
+    sv2 = tmp;
+    t = rf.tau;
+  }
+}
+
 // ---------------------------------------------------------------- one block per CTA
 // The same Householder reduction for many small Hermitian blocks (the charge blocks of a
 // truncated SVD), one CTA per block and all blocks in one launch: no grid barrier, the
@@ -343,15 +599,67 @@ struct CtaBlk {
   int n;
 };
 
+// Rows g >= lo of A (one warp per row): with UPD, T(g, c) -= v(g) conj(w(c)) + w(g) conj(v(c))
+// for c >= lo; p(g) = tq sum_{c >= lo} T(g, c) q(c); each warp's sum of conj(p(g)) q(g) to
+// s_part[.][warp].
+template <bool UPD>
+__device__ void cta_rows_pass(z* A, int64_t n, int64_t lo, const z* v, const z* w, const z* q,
+                              z tq, z* p, double (*s_part)[TRI_CTA_THREADS / 32]) {
+  constexpr int NW = TRI_CTA_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double pr = 0, pi = 0;
+  for (int64_t g = lo + warp; g < n; g += NW) {
+    z* row = A + g * n;
+    z vr = zmk(0, 0), wr = zmk(0, 0);
+    if (UPD) {
+      vr = v[g];
+      wr = w[g];
+    }
+    double sr = 0, si = 0;
+    for (int64_t c = lo + lane; c < n; c += 32) {
+      z x = row[c];
+      if (UPD) {
+        zsub_mul_conj(x, vr, w[c]);
+        zsub_mul_conj(x, wr, v[c]);
+        row[c] = x;
+      }
+      const z y = q[c];
+      sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
+      si = fma(x.x, y.y, fma(x.y, y.x, si));
+    }
+    sr = warp_sum_d(sr);
+    si = warp_sum_d(si);
+    if (lane == 0) {
+      const z pv = zmul(tq, zmk(sr, si));
+      p[g] = pv;
+      const z qq = q[g];
+      pr += pv.x * qq.x + pv.y * qq.y;
+      pi += pv.x * qq.y - pv.y * qq.x;
+    }
+  }
+  if (lane == 0) {
+    s_part[0][warp] = pr;
+    s_part[1][warp] = pi;
+  }
+}
+
+// Column j: entering, v_j and p_j = tau_j T_j v_j are in shared memory with the warps'
+// partial sums of p_j^H v_j.  One pass over the columns c > j gives w_j and row j+1 after
+// the update (x), whose entries past j+1 give reflector j+1 (stored in row j+1 of the
+// block, which is read no more); then one pass over the rows g > j+1 updates them and
+// forms p_{j+1} (the trailing block is read and written once per column).  Vectors are
+// indexed by row of the block; one entry per thread (n <= TRI_CTA_MAX = threads).
 __global__ void __launch_bounds__(TRI_CTA_THREADS) k_tridiag_cta(z* __restrict__ G,
                                                                  const CtaBlk* __restrict__ blks,
                                                                  double* __restrict__ dAll,
                                                                  double* __restrict__ eAll,
                                                                  z* __restrict__ tauAll) {
-  __shared__ z v[TRI_CTA_MAX], w[TRI_CTA_MAX];
+  constexpr int NW = TRI_CTA_THREADS / 32;
+  __shared__ z s_v[TRI_CTA_MAX], s_v2[TRI_CTA_MAX], s_w[TRI_CTA_MAX], s_p[TRI_CTA_MAX];
   __shared__ double sh[32];
-  __shared__ double shr[TRI_CTA_THREADS / 32], shi[TRI_CTA_THREADS / 32];
-  __shared__ z s_cf;
+  __shared__ double s_part[2][NW];
+  __shared__ z s_cf, s_alpha;
+  __shared__ Refl s_refl;
   const CtaBlk B = blks[blockIdx.x];
   const int64_t n = B.n;
   z* A = G + B.goff;
@@ -359,76 +667,87 @@ __global__ void __launch_bounds__(TRI_CTA_THREADS) k_tridiag_cta(z* __restrict__
   double* e = eAll + B.off;
   z* tau = tauAll + B.off;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int NW = TRI_CTA_THREADS / 32;
-  for (int64_t j = 0; j + 1 < n; ++j) {
-    const int64_t m = n - j - 1;
-    z t;
-    double beta;
-    make_reflector(A + j * n + j + 1, m, v, &t, &beta, sh);
+  z* v = s_v;
+  z* v2 = s_v2;
+  z t;
+  {  // reflector 0 from row 0 (thread tid holds column 1 + tid), kept in row 0
+    const int64_t c = 1 + tid;
+    const z x = c < n ? A[c] : zmk(0, 0);
+    double acc = (c >= 2 && c < n) ? fma(x.x, x.x, x.y * x.y) : 0.0;
+    acc = block_sum0(acc, sh);
     if (tid == 0) {
-      d[j] = A[j * n + j].x;
-      e[j] = beta;
-      tau[j] = t;
-    }
-    // p = t T v over the trailing rows (one warp per row), then s = p^H v
-    double pr = 0, pi = 0;
-    for (int64_t r = warp; r < m; r += NW) {
-      const z* row = A + (j + 1 + r) * n + j + 1;
-      double sr = 0, si = 0;
-      for (int64_t c = lane; c < m; c += 32) {
-        const z x = row[c], y = v[c];
-        sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
-        si = fma(x.x, y.y, fma(x.y, y.x, si));
-      }
-      sr = warp_sum_d(sr);
-      si = warp_sum_d(si);
-      if (lane == 0) {
-        const z pv = zmul(t, zmk(sr, si));
-        w[r] = pv;
-        const z vr = v[r];
-        pr += pv.x * vr.x + pv.y * vr.y;
-        pi += pv.x * vr.y - pv.y * vr.x;
-      }
-    }
-    if (lane == 0) {
-      shr[warp] = pr;
-      shi[warp] = pi;
+      const Refl rf = refl_params(zconj(x), acc, n < 2);
+      s_refl = rf;
+      tau[0] = rf.tau;
+      d[0] = A[0].x;
+      if (n > 1) e[0] = rf.beta;
     }
     __syncthreads();
-    if (tid == 0) {
-      double sa = 0, sb = 0;
-      for (int q = 0; q < NW; ++q) {
-        sa += shr[q];
-        sb += shi[q];
+    const Refl rf = s_refl;
+    t = rf.tau;
+    if (c < n) {
+      const z vc = (c == 1) ? zmk(1, 0) : zmul(zconj(x), rf.scale);
+      v[c] = vc;
+      A[c - 1] = vc;
+    }
+    __syncthreads();
+    cta_rows_pass<false>(A, n, 1, v, s_w, v, t, s_p, s_part);
+  }
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    __syncthreads();
+    const int64_t c = j + 1 + tid;
+    z pc = zmk(0, 0), rc = zmk(0, 0);
+    if (c < n) {
+      pc = s_p[c];
+      rc = A[(j + 1) * n + c];
+    }
+    const z p1 = s_p[j + 1];
+    if (warp == 0) {
+      double sa = lane < NW ? s_part[0][lane] : 0.0;
+      double sb = lane < NW ? s_part[1][lane] : 0.0;
+      sa = warp_sum_d(sa);
+      sb = warp_sum_d(sb);
+      if (lane == 0) {
+        const z ts = zmul(t, zmk(sa, sb));
+        s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
       }
-      const z ts = zmul(t, zmk(sa, sb));
-      s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
     }
     __syncthreads();
     const z cf = s_cf;
-    for (int64_t r = tid; r < m; r += TRI_CTA_THREADS) {  // w = p - t/2 (p^H v) v
-      const z pv = w[r], vv = v[r];
-      w[r] = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pv.x)), fma(cf.x, vv.y, fma(cf.y, vv.x, pv.y)));
+    const z w1 = zmk(p1.x + cf.x, p1.y + cf.y);  // w_j(j+1), as v_j(j+1) = 1
+    z x = zmk(0, 0);
+    double acc = 0;
+    if (c < n) {
+      const z vv = v[c];
+      const z wv = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pc.x)), fma(cf.x, vv.y, fma(cf.y, vv.x, pc.y)));
+      s_w[c] = wv;
+      x = zmk(rc.x - wv.x, rc.y + wv.y);
+      zsub_mul_conj(x, w1, vv);
+      if (c >= j + 3) acc = fma(x.x, x.x, x.y * x.y);
+      if (c == j + 2) s_alpha = zconj(x);
+    }
+    acc = block_sum0(acc, sh);
+    const int64_t m2 = n - j - 2;
+    if (tid == 0) {  // thread 0 holds column j+1
+      const Refl rf = refl_params(m2 > 0 ? s_alpha : zmk(0, 0), acc, m2 <= 0);
+      s_refl = rf;
+      tau[j + 1] = rf.tau;
+      d[j + 1] = x.x;
+      if (m2 > 0) e[j + 1] = rf.beta;
     }
     __syncthreads();
-    // T <- T - v w^H - w v^H
-    for (int64_t r = warp; r < m; r += NW) {
-      z* row = A + (j + 1 + r) * n + j + 1;
-      const z vr = v[r], wr = w[r];
-      for (int64_t c = lane; c < m; c += 32) {
-        z x = row[c];
-        zsub_mul_conj(x, vr, w[c]);
-        zsub_mul_conj(x, wr, v[c]);
-        row[c] = x;
-      }
+    const Refl rf = s_refl;
+    if (c >= j + 2 && c < n) {
+      const z vc = (c == j + 2) ? zmk(1, 0) : zmul(zconj(x), rf.scale);
+      v2[c] = vc;
+      A[(j + 1) * n + (c - j - 2)] = vc;
     }
     __syncthreads();
-    for (int64_t c = tid; c < m; c += TRI_CTA_THREADS) A[j * n + c] = v[c];
-    __syncthreads();
-  }
-  if (tid == 0) {
-    d[n - 1] = A[(n - 1) * n + n - 1].x;
-    tau[n - 1] = zmk(0, 0);
+    cta_rows_pass<true>(A, n, j + 2, v, s_w, v2, rf.tau, s_p, s_part);
+    z* tmp = v;
+    v = v2;
+    v2 = tmp;
+    t = rf.tau;
   }
 }
 
@@ -1029,22 +1348,42 @@ int heig_top(Ctx* c, z* G, int64_t n, int64_t k, z* U, int64_t ldu, double* ev) 
     // multiply-add, two rank-2 updates of the trailing block and its matrix-vector product)
     ProfScope ps(c, "heig_tridiag", 16.0 / 3.0 * nn * nn * nn);
     const size_t tri_smem = 4 * TRI_CACHE * sizeof(z);
-    static int nsm = 0, occ = 0;
+    static int nsm = 0, occ = 0, rows_dyn_max = 0;
     if (!nsm) {
       TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_persistent,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem));
       TNT_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
       TNT_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_persistent,
                                                                     TRI_THREADS, tri_smem));
+      int optin = 0;
+      cudaFuncAttributes fa{};
+      TNT_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+      TNT_CUDA_TRY(c, cudaFuncGetAttributes(&fa, k_tridiag_rows));
+      rows_dyn_max = optin - (int)fa.sharedSizeBytes;
+      TNT_CUDA_TRY(c, cudaFuncSetAttribute(k_tridiag_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           rows_dyn_max));
     }
     if (occ < 1) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal kernel cannot be resident");
     TNT_CUDA_TRY(c, cudaMemsetAsync(bar, 0, 256, st));
     TriArgs ta{G, n, Hv, tau, d, e, p, part, (unsigned*)bar, (int*)(bar + 16), c->d_status,
                gws};
     void* args[] = {&ta};
-    const int nb = std::min(nsm, TRI_MAX_BLOCKS);
-    TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
-                                                dim3(TRI_THREADS), args, tri_smem, st));
+    // rows resident in shared memory when each block's share and the three vectors fit
+    const int nbr = (int)std::min<int64_t>(std::min(nsm, TRI_MAX_BLOCKS), n);
+    const int64_t rmax = (n + nbr - 1) / nbr;
+    const size_t rows_smem = (size_t)(rmax + 3) * n * sizeof(z);
+    int occ_rows = 0;
+    if (n <= TRI_ROWS_NMAX && rmax <= TRI_ROWS_MAX && rows_smem <= (size_t)rows_dyn_max)
+      TNT_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rows, k_tridiag_rows,
+                                                                    TRI_THREADS, rows_smem));
+    if (occ_rows >= 1) {
+      TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_rows, dim3(nbr),
+                                                  dim3(TRI_THREADS), args, rows_smem, st));
+    } else {
+      const int nb = std::min(nsm, TRI_MAX_BLOCKS);
+      TNT_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_tridiag_persistent, dim3(nb),
+                                                  dim3(TRI_THREADS), args, tri_smem, st));
+    }
     c->launches += 1;
   }
   {
