@@ -518,13 +518,15 @@ def run_ours(args, ws, rank, local):
 
 # kernel class -> (bound, what its work counts).  The library sums, per launch, the
 # algorithmic work: useful complex-product FLOPs (8 M N K; the split-TF32 repeats are not
-# counted) for the GEMM classes, FP64 FLOPs for the eigensolver and for the Lanczos dot
+# counted) for the GEMM classes, FP64 FLOPs for the eigensolver and for the FP64 Lanczos dot
 # products and updates (on GB300 their 4 FP64 FMAs per complex element outrun HBM), bytes
-# read plus written for the memory-bound conversion kernels.
+# read plus written for the memory-bound kernels (conversions, and the FP32-arithmetic
+# Gram-Schmidt passes of the split-TF32 phase).
 CLASSES = {
     "cgemm_tf32x3": ("tensor", "flop"), "zgemm_f64": ("alu", "flop"), "op_apply": ("alu", "flop"),
     "op_mixed": ("hbm", "byte"), "split_theta": ("hbm", "byte"), "multidot": ("alu", "flop"),
-    "multiaxpy": ("alu", "flop"), "multidot_cond": ("alu", None), "multiaxpy_cond": ("alu", None), "heig_tridiag": ("alu", "flop"),
+    "multiaxpy": ("alu", "flop"), "multidot_cond": ("alu", None), "multiaxpy_cond": ("alu", None),
+    "multidot32": ("hbm", "byte"), "multiaxpy32": ("hbm", "byte"), "heig_tridiag": ("alu", "flop"),
     "heig_tridiag_eig": ("alu", None), "heig_backtransform": ("alu", "flop"),
     "cgemm_grouped": ("tensor", "flop"), "zgemm_grouped": ("alu", "flop"),
     "u1_wop": ("hbm", "byte"), "u1_pack_theta": ("hbm", "byte"), "u1_gather": ("hbm", "byte"),
@@ -536,7 +538,15 @@ OZ_TENSOR_PER_USEFUL = 45.0  # slice pairs per complex product: 45 x 4 real MMAs
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture per kernel class, valid while the class's source file is unchanged: class ->
 # (bytes per launch, source file under csrc/, sha256 prefix of that file, capture).
-TRAFFIC = {}
+TRAFFIC = {
+    # both launches of one matvec (T1 = L theta: 22.78 + 1.90 MB; y = T3 R^T: 71.63 + 3.22 MB),
+    # averaged: profiles/cgemm_tf32x3_heff_cfg2.md
+    "cgemm_tf32x3": (49.76e6, "tc_mixed.cu", "663aa2b421eecc8c", "ncu, bench.py update step"),
+    # two launches per update: the 1024-row Gram block (16.93 MB, ncu; the matrix read once)
+    # and the ~231-row tail block (its entries x the same 16.1 B per entry: 0.86 MB), averaged:
+    # profiles/tridiag_rows_gram1024.md
+    "heig_tridiag": (8.9e6, "heig.cu", "6808812dfa05a999", "ncu, svd_large_block_cfg2_shape"),
+}
 
 
 def traffic_for(cls):
@@ -661,7 +671,8 @@ def run_grouped(args, ws, rank, local):
     # kernel classes (plain launches so each is timed with events)
     per_class = {}
     for cls in ("cgemm_grouped", "zgemm_grouped", "u1_wop", "u1_pack_theta", "u1_gather",
-                "multidot", "multiaxpy", "multidot_cond", "multiaxpy_cond"):
+                "multidot", "multiaxpy", "multidot_cond", "multiaxpy_cond", "multidot32",
+                "multiaxpy32"):
         ctx.profile_select(cls)
         x.copy_(x0)
         solve()

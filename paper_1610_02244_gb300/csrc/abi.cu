@@ -362,6 +362,14 @@ int tnt_ctx_create_with_allocator(int device, void* stream, const tnt_allocator*
 int tnt_ctx_destroy(tnt_ctx* ctx) {
   if (!ctx) return TNT_E_INVALID;
   cudaStreamSynchronize(ctx->c.stream);
+  if (ctx->c.side) {
+    cudaStreamSynchronize(ctx->c.side);
+    cudaStreamDestroy(ctx->c.side);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(ctx->c.ev_main[i]);
+      cudaEventDestroy(ctx->c.ev_side[i]);
+    }
+  }
   for (auto& e : ctx->c.prof_ev) cudaEventDestroy(e);
   dev_free(ctx->c.dalloc, ctx->c.ws.base);
   if (ctx->c.h_pinned) cudaFreeHost(ctx->c.h_pinned);

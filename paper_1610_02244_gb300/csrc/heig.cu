@@ -359,40 +359,72 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_persistent(TriArgs a) {
 // matrix (row g belongs to block g mod nb) resident in its shared memory for the whole
 // reduction: the trailing update and the product with the next reflector touch shared
 // memory only, and per column the global memory carries p (n entries), the per-block
-// partial sums and the one row that is the source of the next reflector.  Entering column
-// j every block holds v_j (v_j(j+1) = 1) and tau_j, and p_j = tau_j T_j v_j with the
-// partial sums of p_j^H v_j is in global memory.  Then
-//   every block, one pass over the columns c > j with its loads issued first:
-//     w_j(c) = p_j(c) + cf v_j(c), cf = -(tau_j / 2) p_j^H v_j, and
-//     x(c) = T_j(j+1, c) - conj(w_j(c)) - w_j(j+1) conj(v_j(c)), row j+1 after the
-//     update, whose entries past j+1 give reflector j+1 (scalars by one thread from the
-//     block sum of |x|^2: the same bits in every block);
-//   each block, its rows g > j+1, each split over TRI_WARPS / (rows) warps:
-//     T <- T - v_j w_j^H - w_j v_j^H and the product with v_{j+1}, giving p_{j+1}(g) and
-//     the block's share of p_{j+1}^H v_{j+1}; the owner of row j+2 also stores that row
-//     in global memory for the next column;
+// partial sums and the one row that is the source of the next reflector.
+// Reflector j is v_j = (1, conj(x_c) s_j for c > j+1) with x row j of the updated matrix
+// and s_j its scale; p_j = tau_j T_j v_j is formed without v_j as
+// tau_j (T(g, j+1) + s_j sum_{c > j+1} T(g, c) conj(x_c)), so that the reflector's
+// scalars (a block sum and one thread's square root and divisions) are computed while the
+// rows are updated, and v_j is written out at the start of the next column.  Entering
+// column j every block holds x (in sx, the entry j+1 zeroed), tau_j and s_j, and p_j with
+// the per-block partial sums of p_j^H v_j is in global memory:
+//   every block, one pass over the columns c > j with its loads issued first: v_j(c);
+//     w_j(c) = p_j(c) + cf v_j(c), cf = -(tau_j / 2) p_j^H v_j; and
+//     x'(c) = T_j(j+1, c) - conj(w_j(c)) - w_j(j+1) conj(v_j(c)), row j+1 after the
+//     update (v_j(j+1) = 1), into sx, with the sum of |x'(c)|^2 over c > j+2;
+//   each block, its rows g > j+1 of T_j, split evenly over its warps (a warp spans at most
+//     two rows): T <- T - v_j w_j^H - w_j v_j^H and sum_c T(g, c) conj(x'(c)); the owner
+//     of row j+2 also stores it in global memory for the next column;
+//   warp 0: reflector j+1 (alpha = conj(x'(j+2))), then p_{j+1}(g) for the block's rows
+//     and the block's share of p_{j+1}^H v_{j+1};
 //   grid barrier.
 // Vectors are indexed by global row.  Per column a block spends 16 FP64 operations per
 // trailing entry on the shared vectors and 12 per entry of its rows.
 constexpr int TRI_ROWS_MAX = 8;         // rows per block
+static_assert(TRI_WARPS == 16, "the flattened row split divides by 16 with shifts");
 constexpr int TRI_VEC = 3;              // vector entries per thread
 constexpr int64_t TRI_ROWS_NMAX = 1216; // <= TRI_VEC * TRI_THREADS; (8 + 3) n entries fit
 
-// Rows g >= lo of this block (rows[i] = row b + nb i, R of them): with UPD,
-// T(g, c) -= v(g) conj(w(c)) + w(g) conj(v(c)) for c >= lo (the row g == lo also to grow);
-// then p(g) = tq sum_{c >= lo} T(g, c) q(c) to pout[g] and the block's sum of
-// conj(p(g)) q(g) to *partout.
+// (a, b) summed over the warp with five FP64 adds (the two sums share each step); every
+// lane returns both
+__device__ __forceinline__ void warp_sum_pair(double& a, double& b) {
+  const bool up = (threadIdx.x & 16) != 0;
+  double v = (up ? b : a) + __shfl_xor_sync(0xffffffffu, up ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  a = __shfl_sync(0xffffffffu, v, 0);
+  b = __shfl_sync(0xffffffffu, v, 16);
+}
+
+struct RowsShared {
+  double br[TRI_WARPS][2], bi[TRI_WARPS][2];  // per warp, per row segment: sum T conj(x)
+  double nrm[TRI_WARPS];                       // per warp: sum |x|^2
+  Refl rf;                                     // reflector of the column being finished
+  z cf, alpha;
+};
+
+// Rows g >= lo of this block (rows[i] = row b + nb i, R of them), flattened over
+// (row, column) and split evenly over the warps: with UPD,
+// T(g, c) -= v(g) conj(w(c)) + w(g) conj(v(c)) for c >= lo (the row g == lo also to
+// grow); the sum over c >= lo of T(g, c) conj(x(c)) into S.br/bi[warp][segment].
 template <bool UPD>
-__device__ void rows_pass(z* rows, int R, int b, int nb, int64_t n, int64_t lo, const z* v,
-                          const z* w, const z* q, z tq, z* pout, z* partout, z* grow,
-                          double (*s_pr)[TRI_WARPS], double (*s_pi)[TRI_WARPS]) {
+__device__ void rows_update(z* rows, int R, int b, int nb, int64_t n, int64_t lo,
+                            const z* v, const z* w, const z* x, z* grow, RowsShared& S) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = (lo > b) ? (int)((lo - b + nb - 1) / nb) : 0;
-  const int ract = R - i0;
-  if (ract > 0) {
-    const int wpr = TRI_WARPS / ract;
-    const int ri = warp / wpr, sub = warp - ri * wpr;
-    if (ri < ract) {
+  const int ract = R - i0 > 0 ? R - i0 : 0;
+  // warp w covers [f0, f1) of the flattened (row, column) range, f0 = ract L w / 16, and
+  // starts in row floor(ract w / 16) (exact: floor(floor(x) / L) = floor(x / L)); all in
+  // 32-bit multiplies and shifts (ract L <= 8 * 1216)
+  const unsigned L = (unsigned)(n - lo), total = (unsigned)ract * L;
+  const unsigned f0 = (total * (unsigned)warp) >> 4, f1 = (total * (unsigned)(warp + 1)) >> 4;
+  const int r0 = (ract * warp) >> 4;
+#pragma unroll
+  for (int seg = 0; seg < 2; ++seg) {
+    double sr = 0, si = 0;
+    const int ri = r0 + seg;  // row of this segment
+    const int64_t s0 = (seg == 0) ? (int64_t)f0 - (int64_t)ri * L : 0;
+    const int64_t s1 = min((int64_t)L, (int64_t)f1 - (int64_t)ri * L);
+    if (ri < ract && s0 < s1) {
       const int i = i0 + ri;
       const int64_t g = b + (int64_t)nb * i;
       z* rw = rows + (int64_t)i * n;
@@ -402,58 +434,73 @@ __device__ void rows_pass(z* rows, int R, int b, int nb, int64_t n, int64_t lo, 
         wr = w[g];
       }
       z* gout = (UPD && g == lo) ? grow : nullptr;
-      double sr = 0, si = 0;
-      const int64_t stride = 32 * (int64_t)wpr;
 #pragma unroll 2
-      for (int64_t c = lo + sub * 32 + lane; c < n; c += stride) {
-        z x = rw[c];
+      for (int64_t c = lo + s0 + lane; c < lo + s1; c += 32) {
+        z t = rw[c];
         if (UPD) {
-          zsub_mul_conj(x, vr, w[c]);
-          zsub_mul_conj(x, wr, v[c]);
-          rw[c] = x;
-          if (gout) gout[c] = x;
+          zsub_mul_conj(t, vr, w[c]);
+          zsub_mul_conj(t, wr, v[c]);
+          rw[c] = t;
+          if (gout) gout[c] = t;
         }
-        const z y = q[c];
-        sr = fma(x.x, y.x, fma(-x.y, y.y, sr));
-        si = fma(x.x, y.y, fma(x.y, y.x, si));
-      }
-      sr = warp_sum_d(sr);
-      si = warp_sum_d(si);
-      if (lane == 0) {
-        s_pr[ri][sub] = sr;
-        s_pi[ri][sub] = si;
+        const z y = x[c];  // t conj(y)
+        sr = fma(t.x, y.x, fma(t.y, y.y, sr));
+        si = fma(t.y, y.x, fma(-t.x, y.y, si));
       }
     }
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double pr = 0, pi = 0;
-    if (lane < ract) {
-      const int wpr = TRI_WARPS / ract;
-      double sr = 0, si = 0;
-      for (int u = 0; u < wpr; ++u) {
-        sr += s_pr[lane][u];
-        si += s_pi[lane][u];
-      }
-      const int64_t g = b + (int64_t)nb * (i0 + lane);
-      const z pv = zmul(tq, zmk(sr, si));
-      pout[g] = pv;
-      const z qq = q[g];
-      pr = pv.x * qq.x + pv.y * qq.y;
-      pi = pv.x * qq.y - pv.y * qq.x;
+    warp_sum_pair(sr, si);
+    if (lane == 0) {
+      S.br[warp][seg] = sr;
+      S.bi[warp][seg] = si;
     }
-    pr = warp_sum_d(pr);
-    pi = warp_sum_d(pi);
-    if (lane == 0) *partout = zmk(pr, pi);
   }
+}
+
+// Warp 0 after rows_update: reflector from (alpha, the block's sum of |x|^2 in S.nrm) for
+// the column whose trailing block starts at lo; p(g) = tau (T(g, lo) + s sum) for the
+// block's rows g >= lo into pout, the block's sum of conj(p(g)) v(g) into *partout
+// (v(lo) = 1, v(c) = conj(x(c)) s).  Lane 0 returns the reflector in S.rf.
+__device__ void rows_finish(const z* rows, int R, int b, int nb, int64_t n, int64_t lo,
+                            const z* x, bool empty, z* pout, z* partout, RowsShared& S) {
+  const int lane = threadIdx.x & 31;
+  double nr = lane < TRI_WARPS ? S.nrm[lane] : 0.0;
+  nr = warp_sum_d(nr);
+  if (lane == 0) S.rf = refl_params(empty ? zmk(0, 0) : S.alpha, nr, empty);
+  __syncwarp();
+  const Refl rf = S.rf;
+  const int i0 = (lo > b) ? (int)((lo - b + nb - 1) / nb) : 0;
+  const int ract = R - i0 > 0 ? R - i0 : 0;
+  const unsigned L = (unsigned)(n - lo), total = (unsigned)ract * L;
+  double pr = 0, pi = 0;
+  if (lane < ract) {
+    double sr = 0, si = 0;
+    for (int w = 0; w < TRI_WARPS; ++w) {  // the warps whose range meets row `lane`, in order
+      const unsigned f0 = (total * (unsigned)w) >> 4, f1 = (total * (unsigned)(w + 1)) >> 4;
+      const int r0 = (ract * w) >> 4;
+      if (f0 < f1 && r0 == lane) {
+        sr += S.br[w][0];
+        si += S.bi[w][0];
+      } else if (f0 < f1 && r0 + 1 == lane && f1 > (unsigned)lane * L) {
+        sr += S.br[w][1];
+        si += S.bi[w][1];
+      }
+    }
+    const int64_t g = b + (int64_t)nb * (i0 + lane);
+    const z t0 = rows[(int64_t)(i0 + lane) * n + lo];
+    const z q = zmk(t0.x + rf.scale.x * sr - rf.scale.y * si, t0.y + rf.scale.x * si + rf.scale.y * sr);
+    const z pv = zmul(rf.tau, q);
+    pout[g] = pv;
+    const z vg = (g == lo) ? zmk(1, 0) : zmul(zconj(x[g]), rf.scale);
+    pr = pv.x * vg.x + pv.y * vg.y;
+    pi = pv.x * vg.y - pv.y * vg.x;
+  }
+  warp_sum_pair(pr, pi);
+  if (lane == 0) *partout = zmk(pr, pi);
 }
 
 __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_rows(TriArgs a) {
   extern __shared__ z sm_tri[];
-  __shared__ double sh[32];
-  __shared__ double s_pr[TRI_ROWS_MAX][TRI_WARPS], s_pi[TRI_ROWS_MAX][TRI_WARPS];
-  __shared__ z s_cf, s_alpha;
-  __shared__ Refl s_refl;
+  __shared__ RowsShared S;
   const int64_t n = a.n;
   const int nb = gridDim.x, b = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -462,54 +509,46 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_rows(TriArgs a) {
   z* rows = sm_tri;
   z* sv = rows + (int64_t)rmax * n;  // v_j
   z* sw = sv + n;                    // w_j
-  z* sv2 = sw + n;                   // v_{j+1}
+  z* sx = sw + n;                    // x of the next reflector (its first entry zeroed)
   for (int i = 0; i < R; ++i) {
     const z* src = a.G + (b + (int64_t)nb * i) * n;
     for (int64_t c = tid; c < n; c += TRI_THREADS) rows[(int64_t)i * n + c] = __ldcg(src + c);
   }
-  z t;
-  {  // reflector 0 from row 0, then p_0 = tau_0 T v_0 over the owned rows
-    z x[TRI_VEC];
+  {  // reflector 0 from row 0 (columns 1..n-1), and p_0
     double acc = 0;
 #pragma unroll
     for (int k = 0; k < TRI_VEC; ++k) {
       const int64_t c = 1 + tid + (int64_t)k * TRI_THREADS;
-      x[k] = c < n ? __ldcg(a.G + c) : zmk(0, 0);
-      if (c >= 2 && c < n) acc = fma(x[k].x, x[k].x, fma(x[k].y, x[k].y, acc));
-    }
-    acc = block_sum0(acc, sh);
-    if (tid == 0) {  // thread 0 holds column 1
-      const Refl rf = refl_params(zconj(x[0]), acc, n < 2);
-      s_refl = rf;
-      if (b == 0) {
-        a.tau[0] = rf.tau;
-        a.d[0] = __ldcg(a.G).x;
-        if (n > 1) a.e[0] = rf.beta;
-      }
-    }
-    __syncthreads();
-    const Refl rf = s_refl;
-    t = rf.tau;
-#pragma unroll
-    for (int k = 0; k < TRI_VEC; ++k) {
-      const int64_t c = 1 + tid + (int64_t)k * TRI_THREADS;
       if (c < n) {
-        const z vc = (c == 1) ? zmk(1, 0) : zmul(zconj(x[k]), rf.scale);
-        sv[c] = vc;
-        if (b == 0) a.Hv[c - 1] = vc;
+        const z xc = __ldcg(a.G + c);
+        if (c == 1) S.alpha = zconj(xc);
+        else acc = fma(xc.x, xc.x, fma(xc.y, xc.y, acc));
+        sx[c] = (c == 1) ? zmk(0, 0) : xc;
       }
     }
+    acc = warp_sum_d(acc);
+    if (lane == 0) S.nrm[warp] = acc;
     __syncthreads();
-    rows_pass<false>(rows, R, b, nb, n, 1, sv, sw, sv, t, a.p, a.part + b, nullptr, s_pr, s_pi);
+    rows_update<false>(rows, R, b, nb, n, 1, sv, sw, sx, nullptr, S);
+    __syncthreads();
+    if (warp == 0) {
+      rows_finish(rows, R, b, nb, n, 1, sx, n < 2, a.p, a.part + b, S);
+      if (b == 0 && lane == 0) {
+        a.tau[0] = S.rf.tau;
+        a.d[0] = __ldcg(a.G).x;
+        if (n > 1) a.e[0] = S.rf.beta;
+      }
+    }
   }
   for (int64_t j = 0; j + 1 < n; ++j) {
     if (!grid_barrier(a)) return;
+    const Refl rf = S.rf;  // reflector j
     const z* pj = a.p + (j & 1) * n;
     z* pn = a.p + ((j + 1) & 1) * n;
     const z* partj = a.part + (j & 1) * nb;
     z* partn = a.part + ((j + 1) & 1) * nb;
     const z* grow = a.G + (j + 1) * n;
-    z pc[TRI_VEC], rc[TRI_VEC];
+    z pc[TRI_VEC], rc[TRI_VEC], vc[TRI_VEC];
 #pragma unroll
     for (int k = 0; k < TRI_VEC; ++k) {
       const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
@@ -524,61 +563,61 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_rows(TriArgs a) {
         sa += pq.x;
         sb += pq.y;
       }
-      sa = warp_sum_d(sa);
-      sb = warp_sum_d(sb);
+      warp_sum_pair(sa, sb);
       if (lane == 0) {
-        const z ts = zmul(t, zmk(sa, sb));
-        s_cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+        const z ts = zmul(rf.tau, zmk(sa, sb));
+        S.cf = zmk(-0.5 * ts.x, -0.5 * ts.y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TRI_VEC; ++k) {  // v_j, written out for the back-transformation
+      const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
+      if (c < n) {
+        vc[k] = (c == j + 1) ? zmk(1, 0) : zmul(zconj(sx[c]), rf.scale);
+        sv[c] = vc[k];
+        if (b == 0) a.Hv[j * n + (c - j - 1)] = vc[k];
       }
     }
     __syncthreads();
-    const z cf = s_cf;
+    const z cf = S.cf;
     const z w1 = zmk(p1.x + cf.x, p1.y + cf.y);  // w_j(j+1), as v_j(j+1) = 1
     double acc = 0;
+    double d1 = 0;
 #pragma unroll
     for (int k = 0; k < TRI_VEC; ++k) {
       const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
       if (c < n) {
-        const z vv = sv[c];
+        const z vv = vc[k];
         const z wv = zmk(fma(cf.x, vv.x, fma(-cf.y, vv.y, pc[k].x)),
                          fma(cf.x, vv.y, fma(cf.y, vv.x, pc[k].y)));
         sw[c] = wv;
-        z x = zmk(rc[k].x - wv.x, rc[k].y + wv.y);
-        zsub_mul_conj(x, w1, vv);
-        rc[k] = x;
-        if (c >= j + 3) acc = fma(x.x, x.x, fma(x.y, x.y, acc));
-        if (c == j + 2) s_alpha = zconj(x);
+        z xn = zmk(rc[k].x - wv.x, rc[k].y + wv.y);
+        zsub_mul_conj(xn, w1, vv);
+        if (c == j + 1) {
+          d1 = xn.x;
+        } else if (c == j + 2) {
+          S.alpha = zconj(xn);
+          sx[c] = zmk(0, 0);
+        } else {
+          acc = fma(xn.x, xn.x, fma(xn.y, xn.y, acc));
+          sx[c] = xn;
+        }
       }
     }
-    acc = block_sum0(acc, sh);
-    const int64_t m2 = n - j - 2;  // length of reflector j+1
-    if (tid == 0) {                // thread 0 holds column j+1
-      const Refl rf = refl_params(m2 > 0 ? s_alpha : zmk(0, 0), acc, m2 <= 0);
-      s_refl = rf;
-      if (b == 0) {
-        a.tau[j + 1] = rf.tau;
-        a.d[j + 1] = rc[0].x;
-        if (m2 > 0) a.e[j + 1] = rf.beta;
-      }
-    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) S.nrm[warp] = acc;
     __syncthreads();
-    const Refl rf = s_refl;
-#pragma unroll
-    for (int k = 0; k < TRI_VEC; ++k) {
-      const int64_t c = j + 1 + tid + (int64_t)k * TRI_THREADS;
-      if (c >= j + 2 && c < n) {
-        const z vc = (c == j + 2) ? zmk(1, 0) : zmul(zconj(rc[k]), rf.scale);
-        sv2[c] = vc;
-        if (b == 0) a.Hv[(j + 1) * n + (c - j - 2)] = vc;
+    rows_update<true>(rows, R, b, nb, n, j + 2, sv, sw, sx, a.G + (j + 2) * n, S);
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t m2 = n - j - 2;  // length of reflector j+1
+      rows_finish(rows, R, b, nb, n, j + 2, sx, m2 <= 0, pn, partn + b, S);
+      if (b == 0 && lane == 0) {  // thread 0 holds column j+1
+        a.tau[j + 1] = S.rf.tau;
+        a.d[j + 1] = d1;
+        if (m2 > 0) a.e[j + 1] = S.rf.beta;
       }
     }
-    __syncthreads();
-    rows_pass<true>(rows, R, b, nb, n, j + 2, sv, sw, sv2, rf.tau, pn, partn + b,
-                    a.G + (j + 2) * n, s_pr, s_pi);
-    z* tmp = sv;
-    sv = sv2;
-    sv2 = tmp;
-    t = rf.tau;
   }
 }
 
@@ -1462,8 +1501,6 @@ int heig_small_blocks(Ctx* c, z* G, const std::vector<SmallEig>& blocks, z* U, d
       z* X = (step == 0 ? U0 : U1) + B.yo;                      // n x k, ld k
       z* Xn = (step == 0) ? U1 + B.yo : U + b.goff;             // next X
       const int64_t ldn = (step == 0) ? b.k : b.n;
-      z* Sb = S;  // offset filled below
-      (void)Sb;
       NsTask ts{b.k, b.k, b.n, X, 1, b.k, X, b.k, 1, nullptr, b.k, 1, 1};
       NsTask tx{b.n, b.k, b.k, X, b.k, 1, nullptr, b.k, 1, Xn, ldn, 0, 0};
       ht.push_back(ts);

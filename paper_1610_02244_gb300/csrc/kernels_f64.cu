@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "tnt_internal.cuh"
+#include "f32conv.cuh"
 
 namespace tnt {
 
@@ -309,6 +310,10 @@ namespace {
 constexpr int RB = 608;       // 4 blocks per SM (152 SMs): enough loads in flight for HBM
 constexpr int RT = 256;
 constexpr int KB = 8;         // vectors per multidot pass
+// multidot's grid: 2 blocks per SM.  Each thread ends with 2 KV sums to reduce (five
+// shuffle-adds each, on the FP64 pipe); at 4 blocks per SM a 2^20-element vector gave a
+// thread only ~7 elements and the reduction rivalled the dot products themselves
+constexpr int RB_DOT = 304;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -501,6 +506,271 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm(const z* __restrict__ V, 
   }
 }
 
+// ---------------------------------------------------------------- FP32-arithmetic passes
+// The Gram-Schmidt passes of a Lanczos phase whose matvec is split TF32 (relative error
+// about 2^-22): the FP64 vectors are read as they are and multiplied in FP32 with FP32
+// sums per thread, warp and block; the sums over blocks, the subtraction from w and w
+// itself stay FP64, so cancellation in w - V c does not amplify the FP32 rounding (the
+// update's error is u_32 |V c|, like a matvec error of that size).  An SM retires 64 FP32
+// FMAs per clock against 2 FP64 FMAs on GB300: these passes are bound by HBM, where the
+// FP64 forms are bound by the FP64 pipe.  Conversions between the widths are integer bit
+// operations on the IEEE-754 layouts (f32conv.cuh), so that no FP64-pipe instruction
+// enters the element loop.
+// The last CTA's sums of nv values over nb blocks (partials[v * nb + b], FP64) into
+// out[v]: thread t < per nv (per the largest power of two <= RT / nv) adds blocks
+// t / nv, t / nv + per, ... of value t % nv, then a fixed tree over the per copies.
+// Deterministic, and a handful of FP64 adds per thread (a serial FP64 chain costs the
+// FP64 pipe's full issue time per step).
+__device__ void last_cta_sum(const double* __restrict__ partials, int nv, int nb,
+                             double* __restrict__ out) {
+  __shared__ double sp[RT];
+  const int t = threadIdx.x;
+  int per = 1;
+  while (2 * per * nv <= RT) per *= 2;
+  double r = 0;
+  if (t < per * nv)
+    for (int b = t / nv; b < nb; b += per) r += __ldcg(partials + (int64_t)(t % nv) * nb + b);
+  sp[t] = r;
+  __syncthreads();
+  for (int h = per / 2; h >= 1; h >>= 1) {
+    if (t < h * nv) sp[t] += sp[t + h * nv];
+    __syncthreads();
+  }
+  if (t < nv) out[t] = sp[t];
+}
+
+template <int KV>
+__global__ void __launch_bounds__(RT) k_multidot32(const z* __restrict__ V, int64_t ld,
+                                                   const z* __restrict__ w, int64_t n,
+                                                   double* __restrict__ partial,
+                                                   unsigned* __restrict__ counter,
+                                                   z* __restrict__ out) {
+  float ar[KV], ai[KV];
+#pragma unroll
+  for (int v = 0; v < KV; ++v) ar[v] = ai[v] = 0.f;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const z xd = w[e];
+    z u[KV];
+#pragma unroll
+    for (int v = 0; v < KV; ++v) u[v] = V[(int64_t)v * ld + e];
+    const float xr = f32_of(xd.x), xi = f32_of(xd.y);
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {  // conj(u) x
+      const float ur = f32_of(u[v].x), ui = f32_of(u[v].y);
+      ar[v] = fmaf(ur, xr, fmaf(ui, xi, ar[v]));
+      ai[v] = fmaf(ur, xi, fmaf(-ui, xr, ai[v]));
+    }
+  }
+  __shared__ float shp[RT / 32][2 * KV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < KV; ++v) {
+    ar[v] = warp_sum_f(ar[v]);
+    ai[v] = warp_sum_f(ai[v]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {
+      shp[wid][2 * v] = ar[v];
+      shp[wid][2 * v + 1] = ai[v];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * KV) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) t += shp[q][threadIdx.x];
+    partial[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = f64_of(t);
+    __threadfence();
+  }
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  last_cta_sum(partial, 2 * KV, (int)gridDim.x, (double*)out);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+void launch_multidot32(int kv, dim3 g, dim3 b, cudaStream_t st, const z* V, int64_t ld,
+                       const z* w, int64_t n, double* partial, unsigned* cnt, z* out) {
+  switch (kv) {
+    case 1: k_multidot32<1><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 2: k_multidot32<2><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 3: k_multidot32<3><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 4: k_multidot32<4><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 5: k_multidot32<5><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 6: k_multidot32<6><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    case 7: k_multidot32<7><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+    default: k_multidot32<8><<<g, b, 0, st>>>(V, ld, w, n, partial, cnt, out); break;
+  }
+}
+
+// w[e] -= sum_v coef[v] V_v[e] (the sum in FP32, the subtraction in FP64); the last CTA
+// writes |w|^2 (FP32 per block, FP64 over blocks)
+__global__ void __launch_bounds__(RT) k_multiaxpy_norm32(const z* __restrict__ V, int64_t ld,
+                                                         int k, const z* __restrict__ coef,
+                                                         z* __restrict__ w, int64_t n,
+                                                         double* __restrict__ partial,
+                                                         unsigned* __restrict__ counter,
+                                                         double* __restrict__ norm2_out) {
+  __shared__ float2 sc[64];
+  __shared__ float shw[RT / 32];
+  for (int t = threadIdx.x; t < k; t += blockDim.x)
+    sc[t] = make_float2(f32_of(coef[t].x), f32_of(coef[t].y));
+  __syncthreads();
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  float acc = 0.f;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    float sr = 0.f, si = 0.f;
+    int v = 0;
+    for (; v + 8 <= k; v += 8) {
+      z u[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u[q] = V[(int64_t)(v + q) * ld + e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 cv = sc[v + q];
+        const float ur = f32_of(u[q].x), ui = f32_of(u[q].y);
+        sr = fmaf(cv.x, ur, fmaf(-cv.y, ui, sr));
+        si = fmaf(cv.x, ui, fmaf(cv.y, ur, si));
+      }
+    }
+    for (; v < k; ++v) {
+      const z u = V[(int64_t)v * ld + e];
+      const float2 cv = sc[v];
+      const float ur = f32_of(u.x), ui = f32_of(u.y);
+      sr = fmaf(cv.x, ur, fmaf(-cv.y, ui, sr));
+      si = fmaf(cv.x, ui, fmaf(cv.y, ur, si));
+    }
+    z x = w[e];
+    x.x -= f64_of(sr);
+    x.y -= f64_of(si);
+    w[e] = x;
+    const float xr = f32_of(x.x), xi = f32_of(x.y);
+    acc = fmaf(xr, xr, fmaf(xi, xi, acc));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  acc = warp_sum_f(acc);
+  if (lane == 0) shw[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) t += shw[q];
+    partial[blockIdx.x] = f64_of(t);
+    __threadfence();
+  }
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  last_cta_sum(partial, 1, (int)gridDim.x, norm2_out);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// The update of the first Gram-Schmidt pass and the dot products of the second in one
+// pass over the basis: w[e] -= sum_v coef[v] V_v[e] (FP32 sum, FP64 subtraction), then
+// dots[v] = sum_e conj(V_v[e]) w[e] with the updated w (element e's term needs only
+// element e), and |w|^2.  The basis entries of an element are converted once and kept in
+// registers for both, so the pass reads V once where two passes read it twice.  KB2 is a
+// compile-time bound on k (8, 16 or 32).
+template <int KB2>
+__global__ void __launch_bounds__(RT) k_multiaxpy_dot32(const z* __restrict__ V, int64_t ld, int k,
+                                                        const z* __restrict__ coef,
+                                                        z* __restrict__ w, int64_t n,
+                                                        double* __restrict__ partial,
+                                                        unsigned* __restrict__ counter,
+                                                        z* __restrict__ dots_out,
+                                                        double* __restrict__ norm2_out) {
+  __shared__ float2 sc[KB2];
+  __shared__ float shp[RT / 32][2 * KB2 + 1];
+  for (int t = threadIdx.x; t < k; t += blockDim.x)
+    sc[t] = make_float2(f32_of(coef[t].x), f32_of(coef[t].y));
+  __syncthreads();
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  float dr[KB2], di[KB2], acc = 0.f;
+#pragma unroll
+  for (int v = 0; v < KB2; ++v) dr[v] = di[v] = 0.f;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    float ur[KB2], ui[KB2];
+#pragma unroll
+    for (int v = 0; v < KB2; ++v) {
+      if (v < k) {
+        const z u = V[(int64_t)v * ld + e];
+        ur[v] = f32_of(u.x);
+        ui[v] = f32_of(u.y);
+      } else {
+        ur[v] = ui[v] = 0.f;
+      }
+    }
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int v = 0; v < KB2; ++v) {
+      const float2 cv = (v < k) ? sc[v] : make_float2(0.f, 0.f);
+      sr = fmaf(cv.x, ur[v], fmaf(-cv.y, ui[v], sr));
+      si = fmaf(cv.x, ui[v], fmaf(cv.y, ur[v], si));
+    }
+    z x = w[e];
+    x.x -= f64_of(sr);
+    x.y -= f64_of(si);
+    w[e] = x;
+    const float xr = f32_of(x.x), xi = f32_of(x.y);
+    acc = fmaf(xr, xr, fmaf(xi, xi, acc));
+#pragma unroll
+    for (int v = 0; v < KB2; ++v) {  // conj(u) x
+      dr[v] = fmaf(ur[v], xr, fmaf(ui[v], xi, dr[v]));
+      di[v] = fmaf(ur[v], xi, fmaf(-ui[v], xr, di[v]));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < KB2; ++v) {
+    if (v < k) {
+      dr[v] = warp_sum_f(dr[v]);
+      di[v] = warp_sum_f(di[v]);
+    }
+  }
+  acc = warp_sum_f(acc);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < KB2; ++v) {
+      shp[wid][2 * v] = dr[v];
+      shp[wid][2 * v + 1] = di[v];
+    }
+    shp[wid][2 * KB2] = acc;
+  }
+  __syncthreads();
+  const int nv = 2 * k;  // partial rows: the 2 k dot components, then the norm
+  for (int t = threadIdx.x; t <= nv; t += blockDim.x) {
+    const int col = (t < nv) ? t : 2 * KB2;
+    float r = 0.f;
+#pragma unroll
+    for (int q = 0; q < RT / 32; ++q) r += shp[q][col];
+    partial[(int64_t)t * gridDim.x + blockIdx.x] = f64_of(r);
+  }
+  __threadfence();
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  last_cta_sum(partial, nv, (int)gridDim.x, (double*)dots_out);
+  __syncthreads();
+  last_cta_sum(partial + (int64_t)nv * gridDim.x, 1, (int)gridDim.x, norm2_out);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 __global__ void k_reduce_real(const double* __restrict__ partial, int nb,
                               double* __restrict__ out, const int* __restrict__ skip) {
   if (skip && *skip) return;  // out keeps its previous value
@@ -540,7 +810,7 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
   // partial sums live in scratch only until the next launch on the same stream, so the
   // region is handed back immediately (stream order serialises its reuse)
   const size_t top = c->ws.top;
-  z* partial = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)KB * RB));
+  z* partial = (z*)ws_alloc(c, ws_round(sizeof(z) * (size_t)KB * RB_DOT));
   c->ws.top = top;
   if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot)");
   for (int v0 = 0; v0 < k; v0 += KB) {
@@ -548,7 +818,7 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
     // FP64 FLOPs (complex MAC = 8); a pass the device may skip is profiled apart, with no
     // work claimed (the host cannot know whether it ran)
     ProfScope ps(c, d_skip ? "multidot_cond" : "multidot", d_skip ? 0.0 : 8.0 * (double)kv * (double)n);
-    launch_multidot(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip,
+    launch_multidot(kv, RB_DOT, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial, d_skip,
                     c->d_count, d_dots + v0);
     c->launches += 1;
   }
@@ -568,6 +838,64 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
                  d_skip ? 0.0 : (8.0 * (double)k + 4.0) * (double)n);  // FP64 FLOPs
     k_multiaxpy_norm<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, d_skip,
                                                c->d_count + 1, d_norm2);
+  }
+  c->launches += 1;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_multidot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots) {
+  if (k <= 0) return TNT_OK;
+  const size_t top = c->ws.top;
+  // four CTAs per SM: bound by HBM, these need the loads of more threads in flight than
+  // the FP64 form (whose two CTAs per SM already saturate the FP64 pipe)
+  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * 2 * (size_t)KB * RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multidot32)");
+  for (int v0 = 0; v0 < k; v0 += KB) {
+    const int kv = (k - v0 < KB) ? (k - v0) : KB;
+    ProfScope ps(c, "multidot32", 16.0 * (double)(kv + 1) * (double)n);  // bytes read
+    launch_multidot32(kv, RB, RT, c->stream, V + (int64_t)v0 * ld, ld, w, n, partial,
+                      c->d_count, d_dots + v0);
+    c->launches += 1;
+  }
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_multiaxpy_norm_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                           int64_t n, double* d_norm2) {
+  if (k > 64) return set_err(c, TNT_E_UNSUPPORTED, "multiaxpy with k=%d > 64", k);
+  const size_t top = c->ws.top;
+  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy32)");
+  {
+    ProfScope ps(c, "multiaxpy32", 16.0 * ((double)k + 2.0) * (double)n);  // bytes moved
+    k_multiaxpy_norm32<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial,
+                                                 c->d_count + 1, d_norm2);
+  }
+  c->launches += 1;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int vec_multiaxpy_dot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                          int64_t n, z* d_dots, double* d_norm2) {
+  if (k < 1 || k > 32) return set_err(c, TNT_E_UNSUPPORTED, "multiaxpy_dot with k=%d outside [1, 32]", k);
+  const size_t top = c->ws.top;
+  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * (2 * 32 + 1) * (size_t)RB));
+  c->ws.top = top;
+  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy_dot32)");
+  {
+    // bytes: the k basis vectors and w read, w written
+    ProfScope ps(c, "multiaxpy32", 16.0 * ((double)k + 2.0) * (double)n);
+    if (k <= 8)
+      k_multiaxpy_dot32<8><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
+    else if (k <= 16)
+      k_multiaxpy_dot32<16><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
+    else
+      k_multiaxpy_dot32<32><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
   }
   c->launches += 1;
   TNT_CHECK_LAUNCH(c);
@@ -769,6 +1097,25 @@ int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, d
   k_tridiag_lowest<<<1, 32, 0, c->stream>>>(d_alpha, d_beta, k, d_out, d_y, nullptr);
   c->launches++;
   TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int tridiag_lowest_on(Ctx* c, cudaStream_t st, const double* d_alpha, const double* d_beta, int k,
+                      double* d_out, double* d_y) {
+  if (k < 1 || k > 64) return set_err(c, TNT_E_UNSUPPORTED, "tridiagonal size %d", k);
+  k_tridiag_lowest<<<1, 32, 0, st>>>(d_alpha, d_beta, k, d_out, d_y, nullptr);
+  c->launches++;
+  TNT_CHECK_LAUNCH(c);
+  return TNT_OK;
+}
+
+int side_stream(Ctx* c) {
+  if (c->side) return TNT_OK;
+  TNT_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    TNT_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_main[i], cudaEventDisableTiming));
+    TNT_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_side[i], cudaEventDisableTiming));
+  }
   return TNT_OK;
 }
 

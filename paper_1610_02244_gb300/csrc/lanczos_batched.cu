@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "heff_plan.cuh"
+#include "f32conv.cuh"
 
 namespace tnt {
 
@@ -134,6 +135,112 @@ __global__ void __launch_bounds__(ST) k_saxpy_norm(const z* __restrict__ V, int6
   if (threadIdx.x == 0) partial[b] = s;
 }
 
+// The same two passes in FP32 arithmetic on the FP64 vectors (the products, the sums per
+// thread, warp and chunk; FP64 sums over a problem's chunks and FP64 subtraction from w):
+// for the Gram-Schmidt passes of a split-TF32 phase, whose matvec error (~2^-22) is above
+// this rounding, and which in FP64 are bound by GB300's FP64 pipe
+template <int KV>
+__global__ void __launch_bounds__(ST) k_sdot32(const z* __restrict__ V, int64_t ld,
+                                               const z* __restrict__ w, const int64_t* __restrict__ ch,
+                                               int nch, z* __restrict__ partial,
+                                               const int* __restrict__ skip) {
+  const int b = blockIdx.x;
+  const int p = (int)ch[3 * b];
+  if (skip[p]) return;
+  float ar[KV], ai[KV];
+#pragma unroll
+  for (int v = 0; v < KV; ++v) ar[v] = ai[v] = 0.f;
+  for (int64_t e = ch[3 * b + 1] + threadIdx.x; e < ch[3 * b + 2]; e += blockDim.x) {
+    const z xd = w[e];
+    z u[KV];
+#pragma unroll
+    for (int v = 0; v < KV; ++v) u[v] = V[(int64_t)v * ld + e];
+    const float xr = f32_of(xd.x), xi = f32_of(xd.y);
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {  // conj(u) x
+      const float ur = f32_of(u[v].x), ui = f32_of(u[v].y);
+      ar[v] = fmaf(ur, xr, fmaf(ui, xi, ar[v]));
+      ai[v] = fmaf(ur, xi, fmaf(-ui, xr, ai[v]));
+    }
+  }
+  __shared__ float shp[ST / 32][2 * KV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < KV; ++v) {
+    ar[v] = warp_sum_f(ar[v]);
+    ai[v] = warp_sum_f(ai[v]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < KV; ++v) {
+      shp[wid][2 * v] = ar[v];
+      shp[wid][2 * v + 1] = ai[v];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * KV) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < ST / 32; ++q) t += shp[q][threadIdx.x];
+    ((double*)(partial + (int64_t)(threadIdx.x >> 1) * nch + b))[threadIdx.x & 1] = f64_of(t);
+  }
+}
+
+__global__ void __launch_bounds__(ST) k_saxpy_norm32(const z* __restrict__ V, int64_t ld, int k,
+                                                     const z* __restrict__ coef, z* __restrict__ w,
+                                                     const int64_t* __restrict__ ch,
+                                                     double* __restrict__ partial,
+                                                     const int* __restrict__ skip) {
+  const int b = blockIdx.x;
+  const int p = (int)ch[3 * b];
+  if (skip[p]) return;
+  __shared__ float2 sc[KMAX];
+  __shared__ float shw[ST / 32];
+  for (int t = threadIdx.x; t < k; t += blockDim.x)
+    sc[t] = make_float2(f32_of(coef[p * KMAX + t].x), f32_of(coef[p * KMAX + t].y));
+  __syncthreads();
+  float acc = 0.f;
+  for (int64_t e = ch[3 * b + 1] + threadIdx.x; e < ch[3 * b + 2]; e += blockDim.x) {
+    float sr = 0.f, si = 0.f;
+    int v = 0;
+    for (; v + 8 <= k; v += 8) {
+      z u[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u[q] = V[(int64_t)(v + q) * ld + e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 cv = sc[v + q];
+        const float ur = f32_of(u[q].x), ui = f32_of(u[q].y);
+        sr = fmaf(cv.x, ur, fmaf(-cv.y, ui, sr));
+        si = fmaf(cv.x, ui, fmaf(cv.y, ur, si));
+      }
+    }
+    for (; v < k; ++v) {
+      const z u = V[(int64_t)v * ld + e];
+      const float2 cv = sc[v];
+      const float ur = f32_of(u.x), ui = f32_of(u.y);
+      sr = fmaf(cv.x, ur, fmaf(-cv.y, ui, sr));
+      si = fmaf(cv.x, ui, fmaf(cv.y, ur, si));
+    }
+    z x = w[e];
+    x.x -= f64_of(sr);
+    x.y -= f64_of(si);
+    w[e] = x;
+    const float xr = f32_of(x.x), xi = f32_of(x.y);
+    acc = fmaf(xr, xr, fmaf(xi, xi, acc));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  acc = warp_sum_f(acc);
+  if (lane == 0) shw[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < ST / 32; ++q) t += shw[q];
+    partial[b] = f64_of(t);
+  }
+}
+
 __global__ void __launch_bounds__(ST) k_snorm2(const z* __restrict__ x, const int64_t* __restrict__ ch,
                                                double* __restrict__ partial, const int* __restrict__ skip) {
   const int b = blockIdx.x;
@@ -227,6 +334,20 @@ void sdot_kv(int kv, int nch, cudaStream_t st, const z* V, int64_t ld, const z* 
   }
 }
 
+void sdot32_kv(int kv, int nch, cudaStream_t st, const z* V, int64_t ld, const z* w,
+               const int64_t* ch, z* part, const int* skip) {
+  switch (kv) {
+    case 1: k_sdot32<1><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 2: k_sdot32<2><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 3: k_sdot32<3><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 4: k_sdot32<4><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 5: k_sdot32<5><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 6: k_sdot32<6><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    case 7: k_sdot32<7><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+    default: k_sdot32<8><<<nch, ST, 0, st>>>(V, ld, w, ch, nch, part, skip); break;
+  }
+}
+
 // device scratch of one batched solve
 struct BScratch {
   int P = 0, nch = 0;
@@ -248,12 +369,17 @@ struct BScratch {
 };
 
 // dots[p][v] = <B_v | w> over problem p for v < k, B_v = basis + v * n
-int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, const int* skip) {
+// (f32: FP32 arithmetic, the Gram-Schmidt passes of a split-TF32 phase)
+int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, const int* skip,
+          bool f32 = false) {
   for (int v0 = 0; v0 < k; v0 += SKB) {
     const int kv = std::min(SKB, k - v0);
-    {
-      ProfScope ps(c, skip == s.frozen || skip == s.none ? "multidot" : "multidot_cond",
-                   skip == s.frozen || skip == s.none ? 8.0 * (double)kv * (double)s.n : 0.0);
+    const bool all = skip == s.frozen || skip == s.none;
+    if (f32) {
+      ProfScope ps(c, all ? "multidot32" : "multidot_cond", all ? 16.0 * (double)(kv + 1) * (double)s.n : 0.0);
+      sdot32_kv(kv, s.nch, c->stream, basis + (int64_t)v0 * s.n, s.n, w, s.ch, s.part, skip);
+    } else {
+      ProfScope ps(c, all ? "multidot" : "multidot_cond", all ? 8.0 * (double)kv * (double)s.n : 0.0);
       sdot_kv(kv, s.nch, c->stream, basis + (int64_t)v0 * s.n, s.n, w, s.ch, s.part, skip);
     }
     k_sreduce_dots<<<s.P, 256, 0, c->stream>>>(s.part, s.nch, s.first, kv, v0, dots_out, skip);
@@ -263,10 +389,14 @@ int sdots(Ctx* c, BScratch& s, const z* basis, int k, const z* w, z* dots_out, c
   return TNT_OK;
 }
 int saxpy(Ctx* c, BScratch& s, int k, const z* coef, z* w, double* norm2, const int* skip,
-          const int* kper = nullptr) {
-  {
-    ProfScope ps(c, skip == s.frozen || skip == s.none ? "multiaxpy" : "multiaxpy_cond",
-                 skip == s.frozen || skip == s.none ? (8.0 * (double)k + 4.0) * (double)s.n : 0.0);
+          const int* kper = nullptr, bool f32 = false) {
+  const bool all = skip == s.frozen || skip == s.none;
+  if (f32 && !kper) {
+    ProfScope ps(c, all ? "multiaxpy32" : "multiaxpy_cond", all ? 16.0 * ((double)k + 2.0) * (double)s.n : 0.0);
+    k_saxpy_norm32<<<s.nch, ST, 0, c->stream>>>(s.V, s.n, k, coef, w, s.ch, s.rpart, skip);
+  } else {
+    ProfScope ps(c, all ? "multiaxpy" : "multiaxpy_cond",
+                 all ? (8.0 * (double)k + 4.0) * (double)s.n : 0.0);
     k_saxpy_norm<<<s.nch, ST, 0, c->stream>>>(s.V, s.n, k, coef, w, s.ch, s.rpart, skip, kper);
   }
   k_sreduce_real<<<s.P, 256, 0, c->stream>>>(s.rpart, s.first, norm2, skip);
@@ -290,12 +420,17 @@ int snormalize(Ctx* c, BScratch& s, const z* x, z* y, const double* norm2, const
 
 // Krylov cycles for every problem not yet done (done[p] on entry: skip entirely).
 // x: in start vectors, out Ritz vectors of the problems that ran.
+// resid_only: a split-TF32 phase that an FP64 continuation follows stops on the residual
+// test alone (as in the single-problem solver)
 int cycles(Ctx* c, const MatVec& A, BScratch& s, z* x, int precision, int max_matvec,
-           std::vector<int>& done, std::vector<tnt_lanczos_result>& res) {
+           std::vector<int>& done, std::vector<tnt_lanczos_result>& res, bool resid_only = false) {
   const tnt_params& P = c->params;
   const int cap = P.krylov_cap, NP = s.P;
   const double u = (precision == TNT_PREC_MIXED) ? std::ldexp(1.0, -22) : std::ldexp(1.0, -52);
   const double tol = P.lanczos_tol, rtol = std::max(tol, 10.0 * u);
+  // Gram-Schmidt in FP32 arithmetic while the matvec is split TF32 (the Ritz vectors are
+  // assembled in FP64)
+  const bool f32_gs = (precision == TNT_PREC_MIXED);
   std::vector<int> frozen(done), total((size_t)NP, 0), kk((size_t)NP, 0), conv((size_t)NP, 0);
   std::vector<double> E((size_t)NP, 0), Eprev((size_t)NP, 0), resid((size_t)NP, 0);
   std::vector<int> have_prev((size_t)NP, 0);
@@ -317,12 +452,12 @@ int cycles(Ctx* c, const MatVec& A, BScratch& s, z* x, int precision, int max_ma
     for (; k < cap; ++k) {
       TNT_TRY(A.apply(c, s.V + (int64_t)k * s.n, s.w, precision));
       ++mv;
-      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.dots, s.frozen));
-      TNT_TRY(saxpy(c, s, k + 1, s.dots, s.w, s.n2, s.frozen));
+      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.dots, s.frozen, f32_gs));
+      TNT_TRY(saxpy(c, s, k + 1, s.dots, s.w, s.n2, s.frozen, nullptr, f32_gs));
       k_sscalars<<<(NP + 63) / 64, 64, 0, c->stream>>>(s.dots, k, s.n2, s.alpha, s.beta, s.tri + 2 * NP, NP, s.frozen);
       c->launches += 1;
-      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.coef, s.frozen));  // second pass, always
-      TNT_TRY(saxpy(c, s, k + 1, s.coef, s.w, s.n2, s.frozen));
+      TNT_TRY(sdots(c, s, s.V, k + 1, s.w, s.coef, s.frozen, f32_gs));  // second pass, always
+      TNT_TRY(saxpy(c, s, k + 1, s.coef, s.w, s.n2, s.frozen, nullptr, f32_gs));
       k_sscalars<<<(NP + 63) / 64, 64, 0, c->stream>>>(s.dots, k, s.n2, s.alpha, s.beta, s.tri + 2 * NP, NP, s.frozen);
       c->launches++;
       TNT_TRY(tridiag_lowest_batched(c, s.alpha, s.beta, k + 1, s.tri, s.y, NP, s.frozen));
@@ -338,7 +473,7 @@ int cycles(Ctx* c, const MatVec& A, BScratch& s, z* x, int precision, int max_ma
         E[(size_t)p] = e;
         resid[(size_t)p] = bk * yk;
         kk[(size_t)p] = k + 1;
-        bool cv = have_prev[(size_t)p] && std::fabs(e - Eprev[(size_t)p]) <= tol * std::fabs(e) &&
+        bool cv = (resid_only || (have_prev[(size_t)p] && std::fabs(e - Eprev[(size_t)p]) <= tol * std::fabs(e))) &&
                   resid[(size_t)p] <= rtol * std::fabs(e);
         if (bk <= rtol * std::fabs(e) * 1e-3 || bk == 0.0) cv = true;
         have_prev[(size_t)p] = 1;
@@ -462,7 +597,8 @@ int lanczos_batched(Ctx* c, const MatVec& A, const std::vector<int64_t>& off, z*
   out->assign((size_t)NP, tnt_lanczos_result{});
   std::vector<int> done((size_t)NP, 0);
   const int prec = Pm.precision;
-  TNT_TRY(cycles(c, A, s, x, prec, Pm.lanczos_maxit, done, *out));
+  TNT_TRY(cycles(c, A, s, x, prec, Pm.lanczos_maxit, done, *out,
+                 prec == TNT_PREC_MIXED && c->fp64_finish));
   if (prec == TNT_PREC_MIXED) {
     // win-back: one FP64 grouped matvec for all problems, Rayleigh quotients and residuals
     TNT_TRY(A.apply(c, x, s.w, TNT_PREC_FP64));

@@ -19,11 +19,13 @@
 // GEMM's own rounding bound.  Complex products take four real MMAs per k step
 // (re+ += Ar Br, re- += Ai Bi, im += Ar Bi + Ai Br; re = re+ - re- in FP64).
 //
-// Kernel: persistent, one CTA per SM over (output tile, level group) items, 128 x 128 or
-// 128 x 64 tiles; warp 0 issues TMA loads of the slice planes (3-D maps [plane][row][k],
-// 64-byte swizzle), warp 1 the MMAs into three TMEM accumulators, warps 2..5 convert each
-// (chunk, level) accumulator and add it to the item's FP64 partial tile, handing TMEM back
-// through an mbarrier; a second kernel adds the two level groups.  All waits bounded.
+// Kernel: persistent, one CTA per SM over (output tile, level group, K split) items,
+// 128 x 128 or 128 x 64 tiles (K is split only when the tiles alone would leave most SMs
+// idle, as for the 256 x 256 products of a truncated SVD); warp 0 issues TMA loads of the
+// slice planes (3-D maps [plane][row][k], 64-byte swizzle), warp 1 the MMAs into three
+// TMEM accumulators, warps 2..5 convert each (chunk, level) accumulator and add it to the
+// item's FP64 partial tile, handing TMEM back through an mbarrier; a second kernel adds the
+// partial outputs in a fixed order.  All waits bounded.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -61,7 +63,8 @@ struct OzArgs {
   int64_t M, N, Kp;
   int ntm, ntn;       // tiles along M and N
   int nchunk;         // K chunks of OZ_KC
-  z* P;               // two FP64 partial outputs, [group][M][N]
+  int ks;             // K splits: split s takes chunks [s nchunk / ks, (s+1) nchunk / ks)
+  z* P;               // 2 ks FP64 partial outputs, [split][group][M][N]
   const double* sA;   // row scales (powers of two)
   const double* sB;   // column scales
   int* status;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = g.ntm * g.ntn;
-  const int nitems = 2 * ntiles;  // (tile, level group)
+  const int nitems = 2 * ntiles * g.ks;  // (tile, level group, K split)
   const int kb_total = (int)(g.Kp / 16);
   const int kb_chunk = OZ_KC / 16;
 
@@ -122,10 +125,11 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     uint32_t it = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
-      const int t = w % ntiles, grp = w / ntiles;
+      const int t = w % ntiles, grp = (w / ntiles) & 1, sp = w / (2 * ntiles);
       const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * BN;
       const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
-      for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
+      const int ch0 = sp * g.nchunk / g.ks, ch1 = (sp + 1) * g.nchunk / g.ks;
+      for (int ch = ch0; ch < ch1 && !stop; ++ch) {
         const int kb0 = ch * kb_chunk, kb1 = min(kb_total, kb0 + kb_chunk);
         for (int l = l0; l <= l1 && !stop; ++l) {
           int p0, p1;
@@ -165,9 +169,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     uint32_t it = 0, sub = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
-      const int grp = w / ntiles;
+      const int grp = (w / ntiles) & 1, sp = w / (2 * ntiles);
       const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
-      for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
+      const int ch0 = sp * g.nchunk / g.ks, ch1 = (sp + 1) * g.nchunk / g.ks;
+      for (int ch = ch0; ch < ch1 && !stop; ++ch) {
         const int kb0 = ch * kb_chunk, kb1 = min(kb_total, kb0 + kb_chunk);
         for (int l = l0; l <= l1 && !stop; ++l) {
           int p0, p1;
@@ -220,13 +225,14 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     uint32_t sub = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < nitems && !stop; w += gridDim.x) {
-      const int t = w % ntiles, grp = w / ntiles;
+      const int t = w % ntiles, grp = (w / ntiles) & 1, sp = w / (2 * ntiles);
       const int m0 = (t / g.ntn) * 128, n0 = (t % g.ntn) * BN;
       const int l0 = grp ? OZ_GROUP_SPLIT + 1 : 2, l1 = grp ? OZ_S + 1 : OZ_GROUP_SPLIT;
       const int64_t gm = (int64_t)m0 + row;
       const double sa = (gm < g.M) ? g.sA[gm] : 0.0;
-      z* Cg = g.P + (int64_t)grp * g.M * g.N;
-      for (int ch = 0; ch < g.nchunk && !stop; ++ch) {
+      z* Cg = g.P + (int64_t)(grp + 2 * sp) * g.M * g.N;
+      const int ch0 = sp * g.nchunk / g.ks, ch1 = (sp + 1) * g.nchunk / g.ks;
+      for (int ch = ch0; ch < ch1 && !stop; ++ch) {
         for (int l = l0; l <= l1; ++l) {
           if (*abort_flag || !mbar_wait(accf, sub & 1, g.status)) {
             *abort_flag = 1;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const double lv = ldexp(sa, -l * OZ_BETA);
-          const bool first = (ch == 0 && l == l0);
+          const bool first = (ch == ch0 && l == l0);
           for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t r[32], s[32], u[32];
             tmem_ld32(tmem + lane_addr + c0, r);
@@ -278,12 +284,15 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
 }
 
 // C = P[0] + P[1], the two level groups, in a fixed order
-__global__ void k_oz_finish(const z* __restrict__ P, int64_t M, int64_t N, z* __restrict__ C,
-                            int64_t ldc) {
+__global__ void k_oz_finish(const z* __restrict__ P, int np, int64_t M, int64_t N,
+                            z* __restrict__ C, int64_t ldc) {
   const int64_t total = M * N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x)
-    C[(e / N) * ldc + e % N] = zadd(P[e], P[total + e]);
+       e += (int64_t)gridDim.x * blockDim.x) {
+    z acc = P[e];
+    for (int i = 1; i < np; ++i) acc = zadd(acc, P[(int64_t)i * total + e]);
+    C[(e / N) * ldc + e % N] = acc;
+  }
 }
 
 // ---------------------------------------------------------------- scales and slices
@@ -346,10 +355,11 @@ int64_t rup16(int64_t x) { return (x + 15) / 16 * 16; }
 
 }  // namespace
 
-size_t ozgemm_scratch_bytes(int64_t M, int64_t N, int64_t K) {
+size_t ozgemm_scratch_bytes(int64_t M, int64_t N, int64_t K, int ks) {
   const int64_t Kp = rup16(K);
   return ws_round(sizeof(float) * OZ_PLANES * M * Kp) + ws_round(sizeof(float) * OZ_PLANES * N * Kp) +
-         ws_round(sizeof(double) * M) + ws_round(sizeof(double) * N) + ws_round(sizeof(z) * 2 * M * N) + 4096;
+         ws_round(sizeof(double) * M) + ws_round(sizeof(double) * N) +
+         ws_round(sizeof(z) * 2 * (size_t)ks * M * N) + 4096;
 }
 
 bool ozgemm_eligible(const Ctx* c, const ZGemm& g) {
@@ -378,7 +388,23 @@ int launch_oz(Ctx* c, const CUtensorMap& tA, const CUtensorMap& tB, const OzArgs
 // capture)
 int ozgemm(Ctx* c, const ZGemm& g) {
   const int64_t M = g.M, N = g.N, K = g.K, Kp = rup16(K);
-  const size_t need = ozgemm_scratch_bytes(M, N, K);
+  static int sm = 0;
+  if (!sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sm < 1) sm = 152;
+  }
+  const int ntm = (int)((M + 127) / 128);
+  // N tile 64 when 128-wide tiles would leave SMs idle; split K when even the 64-wide
+  // (tile, level group) items leave most SMs idle (a 256 x 256 product makes 16), keeping
+  // the partial outputs within 256 MB
+  const int bn = (2LL * ntm * ((N + 127) / 128) < 2LL * sm) ? 64 : 128;
+  const int ntn = (int)((N + bn - 1) / bn);
+  const int nchunk = (int)((Kp + OZ_KC - 1) / OZ_KC);
+  int ks = 1;
+  if (2LL * ntm * ntn < sm) ks = (int)std::min<int64_t>(nchunk, std::max<int64_t>(1, sm / (2LL * ntm * ntn)));
+  while (ks > 1 && 32.0 * ks * (double)M * (double)N > 256e6) --ks;
+  const size_t need = ozgemm_scratch_bytes(M, N, K, ks);
   if (need > c->oz_cap) {
     TNT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     dev_free(c->dalloc, c->oz_buf);
@@ -408,21 +434,14 @@ int ozgemm(Ctx* c, const ZGemm& g) {
   }
   c->launches += 4;
   TNT_CHECK_LAUNCH(c);
-  static int sm = 0;
-  if (!sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sm < 1) sm = 152;
-  }
   OzArgs a;
   a.M = M;
   a.N = N;
   a.Kp = Kp;
-  a.nchunk = (int)((Kp + OZ_KC - 1) / OZ_KC);
-  a.ntm = (int)((M + 127) / 128);
-  // N tile 64 when 128-wide tiles would leave SMs idle
-  const int bn = (2LL * a.ntm * ((N + 127) / 128) < 2LL * sm) ? 64 : 128;
-  a.ntn = (int)((N + bn - 1) / bn);
+  a.nchunk = nchunk;
+  a.ks = ks;
+  a.ntm = ntm;
+  a.ntn = ntn;
   a.P = P;
   a.sA = sA;
   a.sB = sB;
@@ -430,11 +449,11 @@ int ozgemm(Ctx* c, const ZGemm& g) {
   CUtensorMap tA, tB;
   TNT_TRY(tma_map_planes_n(c, &tA, Ap, M, Kp, 128, OZ_PLANES));
   TNT_TRY(tma_map_planes_n(c, &tB, Bp, N, Kp, bn, OZ_PLANES));
-  const int nitems = 2 * a.ntm * a.ntn;
+  const int nitems = 2 * a.ntm * a.ntn * ks;
   {
     ProfScope ps(c, "oz_gemm", 8.0 * (double)M * (double)N * (double)K);
     TNT_TRY(bn == 64 ? launch_oz<64>(c, tA, tB, a, nitems, sm) : launch_oz<128>(c, tA, tB, a, nitems, sm));
-    k_oz_finish<<<ogrid(M * N), 256, 0, c->stream>>>(P, M, N, g.C, g.c_rs);
+    k_oz_finish<<<ogrid(M * N), 256, 0, c->stream>>>(P, 2 * ks, M, N, g.C, g.c_rs);
   }
   c->launches += 2;
   TNT_CHECK_LAUNCH(c);

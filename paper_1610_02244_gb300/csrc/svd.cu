@@ -32,33 +32,31 @@ struct CandBlock {
   int by_row;     // 1: sigma_k = |row k|, 0: |column k|
 };
 
-__global__ void k_cand_sigma(const z* __restrict__ X, const CandBlock* __restrict__ cb,
-                             const double* __restrict__ unscale, double* __restrict__ sig) {
-  const CandBlock b = cb[blockIdx.x];
-  const double us = unscale[blockIdx.x];
-  __shared__ double sh[256];
-  for (int k = 0; k < b.r; ++k) {
-    double acc = 0;
-    if (b.by_row) {
-      for (int64_t c = threadIdx.x; c < b.cols; c += blockDim.x) {
-        z v = X[b.xoff + (int64_t)k * b.cols + c];
-        acc = fma(v.x, v.x, fma(v.y, v.y, acc));
-      }
-    } else {
-      for (int64_t i = threadIdx.x; i < b.rows; i += blockDim.x) {
-        z v = X[b.xoff + i * b.cols + k];
-        acc = fma(v.x, v.x, fma(v.y, v.y, acc));
-      }
+// sigma of every candidate, one warp each: blockIdx.y is the charge block, the CTA's
+// eight warps take candidates 8 blockIdx.x ..; the sum of |.|^2 over the candidate's row
+// (by_row) or column of X, times the block's unscale
+__global__ void __launch_bounds__(256) k_cand_sigma(const z* __restrict__ X,
+                                                    const CandBlock* __restrict__ cb,
+                                                    const double* __restrict__ unscale,
+                                                    double* __restrict__ sig) {
+  const CandBlock b = cb[blockIdx.y];
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= b.r) return;
+  double acc = 0;
+  if (b.by_row) {
+    for (int64_t c = lane; c < b.cols; c += 32) {
+      const z v = X[b.xoff + (int64_t)k * b.cols + c];
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
     }
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-      __syncthreads();
+  } else {
+    for (int64_t i = lane; i < b.rows; i += 32) {
+      const z v = X[b.xoff + i * b.cols + k];
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
     }
-    if (threadIdx.x == 0) sig[b.vbase + k] = sqrt(sh[0]) * us;
-    __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) sig[b.vbase + k] = sqrt(acc) * unscale[blockIdx.y];
 }
 
 // Each gathered block M_q is scaled by the power of two 2^-e_q that brings max |Re|, |Im|
@@ -66,27 +64,40 @@ __global__ void k_cand_sigma(const z* __restrict__ X, const CandBlock* __restric
 // the normal range whatever the sector's weight (a sector of theta far from the mean
 // filling can hold entries many orders below the rest, whose squares would underflow).
 // unscale[q] = 2^e_q multiplies every quantity read back from the scaled block.
-__global__ void k_block_scale(z* __restrict__ Mp, const int64_t* __restrict__ boff,
-                              const int64_t* __restrict__ bsize, double* __restrict__ unscale) {
-  __shared__ double sh[32];
-  const int64_t off = boff[blockIdx.x], cnt = bsize[blockIdx.x];
-  double mx = 0;
-  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+// The scale needs only the largest exponent field of the block's entries (a normal x with
+// biased exponent e has frexp exponent e - 1022): an integer maximum over the high words,
+// taken by as many CTAs per block as its size needs (the maximum does not depend on the
+// order), then the scaling by 2^-e_q across the GPU.  A block whose entries are all zero,
+// subnormal or non-finite is left unscaled.
+__global__ void k_block_maxexp(const z* __restrict__ Mp, const int64_t* __restrict__ boff,
+                               const int64_t* __restrict__ bsize, unsigned* __restrict__ mexp) {
+  const int q = blockIdx.y;
+  const int64_t off = boff[q], cnt = bsize[q];
+  unsigned mx = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const z v = Mp[off + i];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned ex = ((unsigned)__double2hiint(v.x) >> 20) & 0x7ffu;
+    const unsigned ey = ((unsigned)__double2hiint(v.y) >> 20) & 0x7ffu;
+    mx = max(mx, max(ex, ey));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  mx = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
-  int ex = 0;
-  if (mx > 0 && isfinite(mx)) frexp(mx, &ex);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(mexp + q, mx);
+}
+__global__ void k_block_apply(z* __restrict__ Mp, const int64_t* __restrict__ boff,
+                              const int64_t* __restrict__ bsize, const unsigned* __restrict__ mexp,
+                              double* __restrict__ unscale) {
+  const int q = blockIdx.y;
+  const unsigned e = mexp[q];
+  const int ex = (e == 0u || e == 2047u) ? 0 : (int)e - 1022;
+  if (blockIdx.x == 0 && threadIdx.x == 0) unscale[q] = ldexp(1.0, ex);
+  if (ex == 0) return;
   const double sc = ldexp(1.0, -ex);
-  if (threadIdx.x == 0) unscale[blockIdx.x] = ldexp(1.0, ex);
-  if (ex != 0)
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) Mp[off + i] = zscale(Mp[off + i], sc);
+  const int64_t off = boff[q], cnt = bsize[q];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Mp[off + i] = zscale(Mp[off + i], sc);
 }
 
 // dst[r * ldd + c] = src[r * lds + c], r < rows, c < cols
@@ -348,6 +359,50 @@ struct Blk {
 // eps |M|; U_t <- U_t W (V_t <- V_t W) and X_t <- W^H X_t (Y_t <- Y_t W) rotate the
 // candidates within the tail subspace, keeping them orthonormal, and the projection norms
 // are taken again.
+// Blocks of up to 256 rows are reduced either together, one CTA (one SM) each, or one by
+// one by the cooperative kernel across the GPU.  On one SM a block costs about
+// 1.3e-9 n^3 s (its 4 n^3 FP64 FMAs at two per clock, plus per-column overhead); across
+// the GPU about 15 us per column, plus 6.4e-12 n^3 s of FP64 work and 0.5 ms for its own
+// eigenvalue, vector and back-transformation launches.  The batch takes as long as its
+// largest block, or its total over the SMs.  The largest blocks move to the cooperative
+// path while that shortens the estimate: a lone 256-row block (the tail of a truncated
+// SVD whose spectrum falls fast) takes about 4 ms there against about 20 ms on one SM.
+std::vector<char> route_coop(const std::vector<int64_t>& ns, int nsm) {
+  auto t_cta = [](double n) { return 1.3e-9 * n * n * n; };
+  auto t_coop = [](double n) { return 15e-6 * n + 6.4e-12 * n * n * n + 5e-4; };
+  std::vector<int> ord(ns.size());
+  for (size_t i = 0; i < ns.size(); ++i) ord[i] = (int)i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return ns[(size_t)a] > ns[(size_t)b]; });
+  auto batch = [&](size_t from) {  // the one-CTA batch over ord[from..]
+    double mx = 0, sum = 0;
+    for (size_t i = from; i < ord.size(); ++i) {
+      const double t = t_cta((double)ns[(size_t)ord[i]]);
+      mx = std::max(mx, t);
+      sum += t;
+    }
+    return std::max(mx, sum / std::max(1, nsm));
+  };
+  double best = batch(0), acc = 0;
+  size_t moved = 0;
+  for (size_t i = 0; i < ord.size(); ++i) {
+    acc += t_coop((double)ns[(size_t)ord[i]]);
+    const double cand = acc + batch(i + 1);
+    if (cand < best) {
+      best = cand;
+      moved = i + 1;
+    }
+  }
+  std::vector<char> coop(ns.size(), 0);
+  for (size_t i = 0; i < moved; ++i) coop[(size_t)ord[i]] = 1;
+  return coop;
+}
+
+int sm_count(Ctx* c) {
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) nsm = 1;
+  return nsm;
+}
+
 constexpr double TAIL_REL = 1e-4;
 
 struct TailBlk {
@@ -413,12 +468,17 @@ int refine_tails(Ctx* c, int side, const std::vector<Blk>& bl, z* Vp, z* Xp,
   }
   // eigenvectors of every tail Gram matrix (all of them, descending)
   {
+    std::vector<int64_t> ns;
+    for (const TailBlk& T : tb) ns.push_back(T.t <= 256 ? T.t : 0);
+    const std::vector<char> coop = route_coop(ns, sm_count(c));
     std::vector<SmallEig> small;
-    for (const TailBlk& T : tb)
-      if (T.t <= 256) small.push_back(SmallEig{T.toff, T.t, T.t});
+    for (size_t i = 0; i < tb.size(); ++i)
+      if (tb[i].t <= 256 && !coop[i]) small.push_back(SmallEig{tb[i].toff, tb[i].t, tb[i].t});
     TNT_TRY(heig_small_blocks(c, H, small, W, ev));
-    for (const TailBlk& T : tb)
-      if (T.t > 256) TNT_TRY(heig_top(c, H + T.toff, T.t, T.t, W + T.toff, T.t, ev));
+    for (size_t i = 0; i < tb.size(); ++i) {
+      const TailBlk& T = tb[i];
+      if (T.t > 256 || coop[i]) TNT_TRY(heig_top(c, H + T.toff, T.t, T.t, W + T.toff, T.t, ev));
+    }
   }
   // rotate the tail candidates within their subspace
   for (const TailBlk& T : tb) {
@@ -457,7 +517,11 @@ int refine_tails(Ctx* c, int side, const std::vector<Blk>& bl, z* Vp, z* Xp,
     }
   }
   TNT_CHECK_LAUNCH(c);
-  k_cand_sigma<<<(unsigned)bl.size(), 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
+  {
+    int64_t rmax = 1;
+    for (const Blk& B : bl) rmax = std::max<int64_t>(rmax, B.k);
+    k_cand_sigma<<<dim3((unsigned)((rmax + 7) / 8), (unsigned)bl.size()), 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
+  }
   c->launches++;
   TNT_CHECK_LAUNCH(c);
   c->ws.top = top;
@@ -571,8 +635,9 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
   double* d_ev = (double*)ws_alloc(c, ws_round(sizeof(double) * 8192));
   double* d_tot = (double*)ws_alloc(c, ws_round(sizeof(double)));
   double* d_unscale = (double*)ws_alloc(c, ws_round(sizeof(double) * nb));
+  unsigned* d_mexp = (unsigned*)ws_alloc(c, ws_round(sizeof(unsigned) * nb));
   int64_t* d_boff = (int64_t*)ws_alloc(c, ws_round(sizeof(int64_t) * 2 * nb));
-  if (!d_unscale || !d_boff) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
+  if (!d_unscale || !d_mexp || !d_boff) return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
   if (!d_rows || !d_cols || !Mp || !Gp || !Vp || !Xp || !d_sig || !d_blk || !d_loc || !d_sig_s ||
       !d_blk_s || !d_loc_s || !d_sel || !d_cb || !d_goff || !d_gdim || !d_ev || !d_tot)
     return set_err(c, TNT_E_ALLOC, "scratch exhausted (svd)");
@@ -617,8 +682,15 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     TNT_TRY(gather2d(c, M, n, d_rows + B.roff, B.mq, d_cols + B.coff, B.nq, Mp + B.moff, B.nq, 0));
   }
   TNT_TRY(vec_norm2(c, Mp, mtot, d_tot));
-  k_block_scale<<<nb, 256, 0, st>>>(Mp, d_boff, d_boff + nb, d_unscale);
-  c->launches++;
+  {
+    int64_t mxcnt = 1;
+    for (int b = 0; b < nb; ++b) mxcnt = std::max<int64_t>(mxcnt, (int64_t)bl[b].mq * bl[b].nq);
+    const unsigned per = (unsigned)std::min<int64_t>(64, (mxcnt + 4095) / 4096);  // CTAs per block
+    TNT_CUDA_TRY(c, cudaMemsetAsync(d_mexp, 0, sizeof(unsigned) * nb, st));
+    k_block_maxexp<<<dim3(per, nb), 256, 0, st>>>(Mp, d_boff, d_boff + nb, d_mexp);
+    k_block_apply<<<dim3(per, nb), 256, 0, st>>>(Mp, d_boff, d_boff + nb, d_mexp, d_unscale);
+    c->launches += 2;
+  }
   TNT_CHECK_LAUNCH(c);
   for (int b = 0; b < nb; ++b) {
     const Blk& B = bl[b];
@@ -642,14 +714,18 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     TNT_TRY(herm_mirror(c, Gp + B.goff, B.g));
   }
   // ---- eigensolves: blocks up to 256 rows reduced together (one CTA each, one launch),
-  // larger ones one by one across the whole GPU
+  // larger ones, and small ones that would hold the batch back (route_coop), one by one
+  // across the whole GPU
   {
+    std::vector<int64_t> ns;
+    for (int b = 0; b < nb; ++b) ns.push_back(bl[b].g <= 256 ? bl[b].g : 0);
+    const std::vector<char> coop = route_coop(ns, sm_count(c));
     std::vector<SmallEig> small;
     for (int b = 0; b < nb; ++b)
-      if (bl[b].g <= 256) small.push_back(SmallEig{bl[b].goff, bl[b].g, bl[b].k});
+      if (bl[b].g <= 256 && !coop[(size_t)b]) small.push_back(SmallEig{bl[b].goff, bl[b].g, bl[b].k});
     TNT_TRY(heig_small_blocks(c, Gp, small, Vp, d_ev));
     for (int b = 0; b < nb; ++b) {
-      if (bl[b].g <= 256) continue;
+      if (bl[b].g <= 256 && !coop[(size_t)b]) continue;
       const Blk& B = bl[b];
       if (B.g > 8192) return set_err(c, TNT_E_UNSUPPORTED, "SVD block of dim %lld > 8192", (long long)B.g);
       TNT_TRY(heig_top(c, Gp + B.goff, B.g, B.k, Vp + B.goff, B.g, d_ev));
@@ -675,7 +751,11 @@ int svd_trunc_impl(Ctx* c, const z* M, int64_t m, int64_t n, const int64_t* h_rq
     }
     TNT_TRY(zgemm(c, g));
   }
-  k_cand_sigma<<<nb, 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
+  {
+    int64_t rmax = 1;
+    for (int b = 0; b < nb; ++b) rmax = std::max<int64_t>(rmax, bl[b].k);
+    k_cand_sigma<<<dim3((unsigned)((rmax + 7) / 8), (unsigned)nb), 256, 0, st>>>(Xp, d_cb, d_unscale, d_sig);
+  }
   c->launches++;
   TNT_TRY(refine_tails(c, side, bl, Vp, Xp, d_cb, d_unscale, d_sig, ntot_vals));
   // ---- global order and the four rules

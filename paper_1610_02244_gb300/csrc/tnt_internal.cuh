@@ -87,6 +87,10 @@ struct Ctx {
   bool fp64_finish = false;
   void* oz_buf = nullptr;
   size_t oz_cap = 0;
+  // second stream for the Lanczos T_k eigenproblem, one Krylov step behind the vector
+  // work on `stream`, and the events that order the two (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_main[2] = {nullptr, nullptr}, ev_side[2] = {nullptr, nullptr};
 };
 
 // Records CUDA events around the launches of one kernel class when that class is
@@ -196,6 +200,15 @@ int vec_multidot(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z
 // which case w and d_norm2 keep their values
 int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
                        int64_t n, double* d_norm2, const int* d_skip = nullptr);
+// The same two passes with FP32 arithmetic on the FP64 vectors (FP64 sums over blocks, FP64
+// subtraction from w): for a Lanczos phase whose matvec error is already ~2^-22.
+int vec_multidot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots);
+int vec_multiaxpy_norm_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                           int64_t n, double* d_norm2);
+// w -= sum_i coef[i] V_i, then d_dots[i] = <V_i | w> with the updated w and d_norm2 = |w|^2,
+// in one pass (k <= 32): the first pass's update and the second pass's products
+int vec_multiaxpy_dot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
+                          int64_t n, z* d_dots, double* d_norm2);
 // y = x * (1 / sqrt(*d_norm2))  (d_norm2 on device); if x == y scales in place
 int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2);
 int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2);
@@ -205,6 +218,11 @@ int vec_dot(Ctx* c, const z* x, const z* y, int64_t n, z* d_dot);
 // writes out[0] = E, out[1] = |y_{k-1}|, and y[0..k-1].
 int tridiag_lowest(Ctx* c, const double* d_alpha, const double* d_beta, int k, double* d_out,
                    double* d_y);
+// The same on stream st (the Lanczos runs it on the context's side stream)
+int tridiag_lowest_on(Ctx* c, cudaStream_t st, const double* d_alpha, const double* d_beta, int k,
+                      double* d_out, double* d_y);
+// Creates the context's side stream and its events on first use
+int side_stream(Ctx* c);
 // the same for nprob problems at once: problem p's alpha, beta, y at p * 64, out at p * 2;
 // problems with d_skip[p] != 0 are left untouched
 int tridiag_lowest_batched(Ctx* c, const double* d_alpha, const double* d_beta, int k,
