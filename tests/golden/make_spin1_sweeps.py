@@ -3,7 +3,7 @@ isotropic spin-1 Heisenberg chain of Sec. 6, Table 1 (L = 101, chi = 200, U(1) i
 S^z_total = 0), from the seeded random start with the Gaussian sector profile (the start
 the DMRG benchmark uses): the energy after each sweep and at each of the 200 updates of the
 last sweep, by which the sweeps have converged.  Calls only the oracle and the seeded input
-generator.  Takes about an hour on eight cores (the first sweep dominates).
+generator.  Takes one to three hours on eight to sixteen cores (the first sweep dominates).
 
     python tests/golden/make_spin1_sweeps.py
 """
