@@ -676,101 +676,6 @@ __global__ void __launch_bounds__(RT) k_multiaxpy_norm32(const z* __restrict__ V
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// The update of the first Gram-Schmidt pass and the dot products of the second in one
-// pass over the basis: w[e] -= sum_v coef[v] V_v[e] (FP32 sum, FP64 subtraction), then
-// dots[v] = sum_e conj(V_v[e]) w[e] with the updated w (element e's term needs only
-// element e), and |w|^2.  The basis entries of an element are converted once and kept in
-// registers for both, so the pass reads V once where two passes read it twice.  KB2 is a
-// compile-time bound on k (8, 16 or 32).
-template <int KB2>
-__global__ void __launch_bounds__(RT) k_multiaxpy_dot32(const z* __restrict__ V, int64_t ld, int k,
-                                                        const z* __restrict__ coef,
-                                                        z* __restrict__ w, int64_t n,
-                                                        double* __restrict__ partial,
-                                                        unsigned* __restrict__ counter,
-                                                        z* __restrict__ dots_out,
-                                                        double* __restrict__ norm2_out) {
-  __shared__ float2 sc[KB2];
-  __shared__ float shp[RT / 32][2 * KB2 + 1];
-  for (int t = threadIdx.x; t < k; t += blockDim.x)
-    sc[t] = make_float2(f32_of(coef[t].x), f32_of(coef[t].y));
-  __syncthreads();
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
-  float dr[KB2], di[KB2], acc = 0.f;
-#pragma unroll
-  for (int v = 0; v < KB2; ++v) dr[v] = di[v] = 0.f;
-  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-    float ur[KB2], ui[KB2];
-#pragma unroll
-    for (int v = 0; v < KB2; ++v) {
-      if (v < k) {
-        const z u = V[(int64_t)v * ld + e];
-        ur[v] = f32_of(u.x);
-        ui[v] = f32_of(u.y);
-      } else {
-        ur[v] = ui[v] = 0.f;
-      }
-    }
-    float sr = 0.f, si = 0.f;
-#pragma unroll
-    for (int v = 0; v < KB2; ++v) {
-      const float2 cv = (v < k) ? sc[v] : make_float2(0.f, 0.f);
-      sr = fmaf(cv.x, ur[v], fmaf(-cv.y, ui[v], sr));
-      si = fmaf(cv.x, ui[v], fmaf(cv.y, ur[v], si));
-    }
-    z x = w[e];
-    x.x -= f64_of(sr);
-    x.y -= f64_of(si);
-    w[e] = x;
-    const float xr = f32_of(x.x), xi = f32_of(x.y);
-    acc = fmaf(xr, xr, fmaf(xi, xi, acc));
-#pragma unroll
-    for (int v = 0; v < KB2; ++v) {  // conj(u) x
-      dr[v] = fmaf(ur[v], xr, fmaf(ui[v], xi, dr[v]));
-      di[v] = fmaf(ur[v], xi, fmaf(-ui[v], xr, di[v]));
-    }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < KB2; ++v) {
-    if (v < k) {
-      dr[v] = warp_sum_f(dr[v]);
-      di[v] = warp_sum_f(di[v]);
-    }
-  }
-  acc = warp_sum_f(acc);
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < KB2; ++v) {
-      shp[wid][2 * v] = dr[v];
-      shp[wid][2 * v + 1] = di[v];
-    }
-    shp[wid][2 * KB2] = acc;
-  }
-  __syncthreads();
-  const int nv = 2 * k;  // partial rows: the 2 k dot components, then the norm
-  for (int t = threadIdx.x; t <= nv; t += blockDim.x) {
-    const int col = (t < nv) ? t : 2 * KB2;
-    float r = 0.f;
-#pragma unroll
-    for (int q = 0; q < RT / 32; ++q) r += shp[q][col];
-    partial[(int64_t)t * gridDim.x + blockIdx.x] = f64_of(r);
-  }
-  __threadfence();
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  last_cta_sum(partial, nv, (int)gridDim.x, (double*)dots_out);
-  __syncthreads();
-  last_cta_sum(partial + (int64_t)nv * gridDim.x, 1, (int)gridDim.x, norm2_out);
-  if (threadIdx.x == 0) *counter = 0u;
-}
-
 __global__ void k_reduce_real(const double* __restrict__ partial, int nb,
                               double* __restrict__ out, const int* __restrict__ skip) {
   if (skip && *skip) return;  // out keeps its previous value
@@ -874,28 +779,6 @@ int vec_multiaxpy_norm_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coe
     ProfScope ps(c, "multiaxpy32", 16.0 * ((double)k + 2.0) * (double)n);  // bytes moved
     k_multiaxpy_norm32<<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial,
                                                  c->d_count + 1, d_norm2);
-  }
-  c->launches += 1;
-  TNT_CHECK_LAUNCH(c);
-  return TNT_OK;
-}
-
-int vec_multiaxpy_dot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
-                          int64_t n, z* d_dots, double* d_norm2) {
-  if (k < 1 || k > 32) return set_err(c, TNT_E_UNSUPPORTED, "multiaxpy_dot with k=%d outside [1, 32]", k);
-  const size_t top = c->ws.top;
-  double* partial = (double*)ws_alloc(c, ws_round(sizeof(double) * (2 * 32 + 1) * (size_t)RB));
-  c->ws.top = top;
-  if (!partial) return set_err(c, TNT_E_ALLOC, "scratch exhausted (multiaxpy_dot32)");
-  {
-    // bytes: the k basis vectors and w read, w written
-    ProfScope ps(c, "multiaxpy32", 16.0 * ((double)k + 2.0) * (double)n);
-    if (k <= 8)
-      k_multiaxpy_dot32<8><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
-    else if (k <= 16)
-      k_multiaxpy_dot32<16><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
-    else
-      k_multiaxpy_dot32<32><<<RB, RT, 0, c->stream>>>(V, ld, k, d_coef, w, n, partial, c->d_count + 1, d_dots, d_norm2);
   }
   c->launches += 1;
   TNT_CHECK_LAUNCH(c);

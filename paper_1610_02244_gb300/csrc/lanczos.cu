@@ -137,13 +137,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
       z* vk = V + (int64_t)k * n;
       TNT_TRY(A.apply(c, vk, w, precision));
       ++total;
-      // (FP32 passes with up to 32 vectors: pass 1's update and pass 2's products share one
-      // pass over the basis)
-      const bool fuse = f32_gs && k + 1 <= 32;
-      if (fuse) {
-        TNT_TRY(vec_multidot_f32(c, V, n, k + 1, w, n, dots));
-        TNT_TRY(vec_multiaxpy_dot_f32(c, V, n, k + 1, dots, w, n, coef, norm2));
-      } else if (f32_gs) {
+      if (f32_gs) {
         TNT_TRY(vec_multidot_f32(c, V, n, k + 1, w, n, dots));
         TNT_TRY(vec_multiaxpy_norm_f32(c, V, n, k + 1, dots, w, n, norm2));
       } else {
@@ -152,9 +146,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
       }
       k_lz_scalars<<<1, 32, 0, c->stream>>>(dots, k, norm2, alpha, beta);  // alpha_k from pass 1
       c->launches += 1;
-      if (fuse) {
-        TNT_TRY(vec_multiaxpy_norm_f32(c, V, n, k + 1, coef, w, n, norm2));
-      } else if (f32_gs) {
+      if (f32_gs) {
         TNT_TRY(vec_multidot_f32(c, V, n, k + 1, w, n, coef));
         TNT_TRY(vec_multiaxpy_norm_f32(c, V, n, k + 1, coef, w, n, norm2));
       } else {

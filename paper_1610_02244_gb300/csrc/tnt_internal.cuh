@@ -205,10 +205,6 @@ int vec_multiaxpy_norm(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z
 int vec_multidot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* w, int64_t n, z* d_dots);
 int vec_multiaxpy_norm_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
                            int64_t n, double* d_norm2);
-// w -= sum_i coef[i] V_i, then d_dots[i] = <V_i | w> with the updated w and d_norm2 = |w|^2,
-// in one pass (k <= 32): the first pass's update and the second pass's products
-int vec_multiaxpy_dot_f32(Ctx* c, const z* V, int64_t ld, int k, const z* d_coef, z* w,
-                          int64_t n, z* d_dots, double* d_norm2);
 // y = x * (1 / sqrt(*d_norm2))  (d_norm2 on device); if x == y scales in place
 int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2);
 int vec_norm2(Ctx* c, const z* x, int64_t n, double* d_norm2);
