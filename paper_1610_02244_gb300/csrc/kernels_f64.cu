@@ -702,7 +702,12 @@ __global__ void k_norm2_partial(const z* __restrict__ x, int64_t n, double* __re
 
 __global__ void k_normalize(const z* __restrict__ x, z* __restrict__ y, int64_t n,
                             const double* __restrict__ norm2) {
-  const double s = 1.0 / sqrt(norm2[0]);
+  // the scale by one thread of the block: an FP64 square root and division in every thread
+  // cost several times the FP64-pipe issue slots of the scaling itself
+  __shared__ double s_s;
+  if (threadIdx.x == 0) s_s = 1.0 / sqrt(norm2[0]);
+  __syncthreads();
+  const double s = s_s;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     y[e] = zscale(x[e], s);
@@ -803,7 +808,7 @@ int vec_dot(Ctx* c, const z* x, const z* y, int64_t n, z* d_dot) {
 
 int vec_normalize(Ctx* c, const z* x, z* y, int64_t n, const double* d_norm2) {
   int64_t blocks = (n + 255) / 256;
-  if (blocks > RB * 4) blocks = RB * 4;
+  if (blocks > RB) blocks = RB;  // grid-stride: one scale per CTA, four CTAs per SM
   if (blocks < 1) blocks = 1;
   k_normalize<<<(unsigned)blocks, 256, 0, c->stream>>>(x, y, n, d_norm2);
   c->launches++;
@@ -1039,7 +1044,10 @@ __global__ void k_zfill(z* p, int64_t n, z v) {
 
 // mode 0: p *= s[0]; mode 1: p *= 1/sqrt(s[0])
 __global__ void k_zscale(z* p, int64_t n, const double* s, int mode) {
-  double f = (mode == 0) ? s[0] : 1.0 / sqrt(s[0]);
+  __shared__ double s_f;  // by one thread, as in k_normalize
+  if (threadIdx.x == 0) s_f = (mode == 0) ? s[0] : 1.0 / sqrt(s[0]);
+  __syncthreads();
+  const double f = s_f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     p[e] = zscale(p[e], f);

@@ -274,7 +274,10 @@ __global__ void __launch_bounds__(ST) k_snormalize(const z* __restrict__ x, z* _
   const int b = blockIdx.x;
   const int p = (int)ch[3 * b];
   if (skip[p]) return;
-  const double s = norm2[p] > 0.0 ? 1.0 / sqrt(norm2[p]) : 0.0;
+  __shared__ double s_s;  // by one thread: the FP64 square root and division outweigh the chunk's scaling
+  if (threadIdx.x == 0) s_s = norm2[p] > 0.0 ? 1.0 / sqrt(norm2[p]) : 0.0;
+  __syncthreads();
+  const double s = s_s;
   for (int64_t e = ch[3 * b + 1] + threadIdx.x; e < ch[3 * b + 2]; e += blockDim.x) y[e] = zscale(x[e], s);
 }
 
