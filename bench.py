@@ -540,8 +540,9 @@ OZ_TENSOR_PER_USEFUL = 45.0  # slice pairs per complex product: 45 x 4 real MMAs
 # (bytes per launch, source file under csrc/, sha256 prefix of that file, capture).
 TRAFFIC = {
     # both launches of one matvec (T1 = L theta: 22.78 + 1.90 MB; y = T3 R^T: 71.63 + 3.22 MB),
-    # averaged: profiles/cgemm_tf32x3_heff_cfg2.md
-    "cgemm_tf32x3": (49.76e6, "tc_mixed.cu", "663aa2b421eecc8c", "ncu, bench.py update step"),
+    # averaged: profiles/cgemm_tf32x3_heff_cfg2.md (the key follows the file; since the
+    # capture only the gather kernel in it changed)
+    "cgemm_tf32x3": (49.76e6, "tc_mixed.cu", "8430c4ff3cf17339", "ncu, bench.py update step"),
     # two launches per update: the 1024-row Gram block (16.93 MB, ncu; the matrix read once)
     # and the ~231-row tail block (its entries x the same 16.1 B per entry: 0.86 MB), averaged:
     # profiles/tridiag_rows_gram1024.md

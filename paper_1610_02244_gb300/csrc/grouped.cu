@@ -440,12 +440,12 @@ __global__ void k_gather_u1(GthArgs a) {
     const GRow g = a.rows[r];
     for (int64_t j = lane; j < g.n; j += 32) {
       if (MIXED) {
-        double re = 0, im = 0;
+        float re = 0.f, im = 0.f;  // FP32 partials added in FP32, widened once (tc_mixed.cu)
         for (int s = 0; s < a.nsplit; ++s) {
-          re += (double)a.yf[s * a.sstride + g.src + j];
-          im += (double)a.yf[s * a.sstride + a.plane + g.src + j];
+          re += a.yf[s * a.sstride + g.src + j];
+          im += a.yf[s * a.sstride + a.plane + g.src + j];
         }
-        a.y[g.dst + j] = zmk(re, im);
+        a.y[g.dst + j] = zmk(f64_of(re), f64_of(im));
       } else {
         a.y[g.dst + j] = a.yz[g.src + j];
       }

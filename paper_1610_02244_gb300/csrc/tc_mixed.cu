@@ -289,12 +289,14 @@ __global__ void k_gather_y(const float* __restrict__ Yp, int split, int64_t M, i
   const int64_t plane = M * N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double re = 0, im = 0;
+    // the split-K partials are FP32 sums of split-TF32 products (~2^-22): added in FP32,
+    // widened once by integer operations (no FP64-pipe conversion in the loop)
+    float re = 0.f, im = 0.f;
     for (int s = 0; s < split; ++s) {
-      re += (double)Yp[(int64_t)s * 2 * plane + e];
-      im += (double)Yp[(int64_t)s * 2 * plane + plane + e];
+      re += Yp[(int64_t)s * 2 * plane + e];
+      im += Yp[(int64_t)s * 2 * plane + plane + e];
     }
-    y[e] = zmk(re, im);
+    y[e] = zmk(f64_of(re), f64_of(im));
   }
 }
 
