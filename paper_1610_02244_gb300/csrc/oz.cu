@@ -300,52 +300,75 @@ __global__ void k_oz_finish(const z* __restrict__ P, int np, int64_t M, int64_t 
 // one warp per row of a strided operand X[i * rs + k * cs]
 __global__ void k_oz_row_scale(const z* __restrict__ X, int64_t rows, int64_t K, int64_t rs,
                                int64_t cs, double* __restrict__ sc) {
+  // by integer operations on the exponent fields (no FP64-pipe comparisons): the largest
+  // field mx of the row gives 2^(mx - 1023) <= max < 2^(mx - 1022), so sc = 2^(mx - 1022),
+  // the frexp exponent of the maximum; a row of subnormals gets 2^-1022, a zero row 1
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < rows;
        i += (int64_t)((gridDim.x * blockDim.x) >> 5)) {
-    double m = 0;
+    unsigned mx = 0, nz = 0;
     for (int64_t k = lane; k < K; k += 32) {
       const z v = X[i * rs + k * cs];
-      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned hr = (unsigned)__double2hiint(v.x), hi = (unsigned)__double2hiint(v.y);
+      mx = max(mx, max((hr >> 20) & 0x7ffu, (hi >> 20) & 0x7ffu));
+      nz |= (hr & 0x7fffffffu) | (unsigned)__double2loint(v.x) | (hi & 0x7fffffffu) |
+            (unsigned)__double2loint(v.y);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      nz |= __shfl_xor_sync(0xffffffffu, nz, o);
+    }
     if (lane == 0) {
-      int e = 0;
-      if (m > 0) {
-        frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
-      }
-      sc[i] = m > 0 ? ldexp(1.0, e) : 1.0;
+      double r = 1.0;
+      if (mx > 0) r = __hiloint2double((int)((mx + 1u) << 20), 0);  // 2^(mx - 1022)
+      else if (nz) r = __hiloint2double(1 << 20, 0);                  // 2^-1022
+      sc[i] = r;
     }
   }
 }
 
 // slice planes: out[2(p-1) + (0 re | 1 im)][i][k] = p-th integer slice of X_ik / sc[i],
 // i < rows, k < Kp (zero for k >= K); X[i * rs + k * cs], conjugated if conj
+static_assert(OZ_S * OZ_BETA == 54, "the fixed-point form holds 54 bits");
+// F = floor(|v| / sc 2^54) for sc = 2^esc > |v|: the mantissa shifted (exact)
+__device__ __forceinline__ uint64_t oz_fixed(double v, int esc) {
+  const uint64_t u = (uint64_t)__double_as_longlong(v);
+  const int eb = (int)((u >> 52) & 0x7ff);
+  uint64_t mant = u & ((1ull << 52) - 1);
+  if (eb) mant |= 1ull << 52;
+  const int sh = (eb ? eb : 1) - 1021 - esc;  // F = mant 2^sh, F < 2^54
+  if (sh >= 0) return mant << sh;
+  return sh <= -64 ? 0ull : mant >> (-sh);
+}
+
 __global__ void k_oz_slice(const z* __restrict__ X, int64_t rows, int64_t K, int64_t Kp,
                            int64_t rs, int64_t cs, int conj, const double* __restrict__ sc,
                            float* __restrict__ out) {
+  // The p-th slice is the p-th base-2^beta digit of X_ik / sc[i] with its sign: what
+  // repeated multiplication by 2^beta and truncation give (every step exact), taken here
+  // from the fixed-point value F = floor(|X_ik| / sc[i] 2^54) by shifts and masks
   const int64_t plane = rows * Kp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / Kp, k = e % Kp;
-    double tr = 0, ti = 0;
+    uint64_t fr = 0, fi = 0;
+    bool nr = false, ni = false;
     if (k < K) {
       const z v = X[i * rs + k * cs];
-      const double inv = 1.0 / sc[i];  // a power of two: exact
-      tr = v.x * inv;
-      ti = (conj ? -v.y : v.y) * inv;
+      const int esc = (int)(((uint64_t)__double_as_longlong(sc[i]) >> 52) & 0x7ff) - 1023;
+      fr = oz_fixed(v.x, esc);
+      fi = oz_fixed(v.y, esc);
+      nr = __double2hiint(v.x) < 0;
+      ni = (__double2hiint(v.y) < 0) != (conj != 0);
     }
-    const double step = (double)(1 << OZ_BETA);
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) {
-      tr *= step;
-      ti *= step;
-      const double ar = trunc(tr), ai = trunc(ti);
-      tr -= ar;
-      ti -= ai;
-      out[(int64_t)(2 * p) * plane + e] = (float)ar;
-      out[(int64_t)(2 * p + 1) * plane + e] = (float)ai;
+      const int shift = OZ_S * OZ_BETA - OZ_BETA * (p + 1);
+      const float ar = (float)(int)((fr >> shift) & ((1u << OZ_BETA) - 1));
+      const float ai = (float)(int)((fi >> shift) & ((1u << OZ_BETA) - 1));
+      out[(int64_t)(2 * p) * plane + e] = nr ? -ar : ar;
+      out[(int64_t)(2 * p + 1) * plane + e] = ni ? -ai : ai;
     }
   }
 }
