@@ -4,6 +4,7 @@
 //   f32_of: truncation toward zero to 23 mantissa bits; magnitudes below 2^-126 become a
 //           signed zero, magnitudes of 2^128 and above (and non-finite values) infinity.
 //   f64_of: exact; FP32 subnormals become a signed zero.
+//   fixed54: the fixed-point form floor(|v| 2^(54 - esc)) of |v| < 2^esc.
 // The same code compiles for the host, where tests/f32conv_host.cu checks it against the
 // C library's conversions.
 #pragma once
@@ -72,6 +73,18 @@ __host__ __device__ __forceinline__ double f64_of(float f) {
   }
   if (e == 255u) hi = sgn | 0x7ff00000u | (m >> 3);
   return double_of_bits(((uint64_t)hi << 32) | lo);
+}
+
+// F = floor(|v| 2^(54 - esc)) for |v| < 2^esc: the 53-bit mantissa shifted (exact), the
+// fixed-point form whose 6-bit groups are the slices of the FP64-accurate GEMM (oz.cu)
+__host__ __device__ __forceinline__ uint64_t fixed54(double v, int esc) {
+  const uint64_t u = bits_of(v);
+  const int eb = (int)((u >> 52) & 0x7ff);
+  uint64_t mant = u & ((1ull << 52) - 1);
+  if (eb) mant |= 1ull << 52;
+  const int sh = (eb ? eb : 1) - 1021 - esc;  // F = mant 2^sh, F < 2^54
+  if (sh >= 0) return mant << sh;
+  return sh <= -64 ? 0ull : mant >> (-sh);
 }
 
 #ifdef __CUDACC__

@@ -32,6 +32,7 @@
 
 #include "heff_plan.cuh"
 #include "tc_common.cuh"
+#include "f32conv.cuh"
 
 namespace tnt {
 
@@ -331,17 +332,6 @@ __global__ void k_oz_row_scale(const z* __restrict__ X, int64_t rows, int64_t K,
 // slice planes: out[2(p-1) + (0 re | 1 im)][i][k] = p-th integer slice of X_ik / sc[i],
 // i < rows, k < Kp (zero for k >= K); X[i * rs + k * cs], conjugated if conj
 static_assert(OZ_S * OZ_BETA == 54, "the fixed-point form holds 54 bits");
-// F = floor(|v| / sc 2^54) for sc = 2^esc > |v|: the mantissa shifted (exact)
-__device__ __forceinline__ uint64_t oz_fixed(double v, int esc) {
-  const uint64_t u = (uint64_t)__double_as_longlong(v);
-  const int eb = (int)((u >> 52) & 0x7ff);
-  uint64_t mant = u & ((1ull << 52) - 1);
-  if (eb) mant |= 1ull << 52;
-  const int sh = (eb ? eb : 1) - 1021 - esc;  // F = mant 2^sh, F < 2^54
-  if (sh >= 0) return mant << sh;
-  return sh <= -64 ? 0ull : mant >> (-sh);
-}
-
 __global__ void k_oz_slice(const z* __restrict__ X, int64_t rows, int64_t K, int64_t Kp,
                            int64_t rs, int64_t cs, int conj, const double* __restrict__ sc,
                            float* __restrict__ out) {
@@ -357,8 +347,8 @@ __global__ void k_oz_slice(const z* __restrict__ X, int64_t rows, int64_t K, int
     if (k < K) {
       const z v = X[i * rs + k * cs];
       const int esc = (int)(((uint64_t)__double_as_longlong(sc[i]) >> 52) & 0x7ff) - 1023;
-      fr = oz_fixed(v.x, esc);
-      fi = oz_fixed(v.y, esc);
+      fr = fixed54(v.x, esc);
+      fi = fixed54(v.y, esc);
       nr = __double2hiint(v.x) < 0;
       ni = (__double2hiint(v.y) < 0) != (conj != 0);
     }

@@ -1,9 +1,10 @@
-// Host check of the bit-level FP64 <-> FP32 conversions of csrc/f32conv.cuh against the C
-// library's IEEE conversions: f32_of must truncate toward zero (round to nearest, then one
-// step toward zero where that rounded away), give a signed zero below 2^-126 and infinity
-// from 2^128 on; f64_of must be exact on normal floats and give a signed zero for FP32
-// subnormals.  Random magnitudes over the whole FP32 range plus edge values; prints the
-// number of mismatches and exits non-zero on any.
+// Host check of the bit-level conversions of csrc/f32conv.cuh.  Against the C library's
+// IEEE conversions: f32_of must truncate toward zero (round to nearest, then one step
+// toward zero where that rounded away), give a signed zero below 2^-126 and infinity from
+// 2^128 on; f64_of must be exact on normal floats and give a signed zero for FP32
+// subnormals.  Against the FP64 slicing loop of the FP64-accurate GEMM: fixed54's 6-bit
+// groups must be its digits.  Random magnitudes plus edge values; prints the number of
+// mismatches and exits non-zero on any.
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -49,8 +50,37 @@ static int check_f64(float f) {
   return 0;
 }
 
+// fixed54's 6-bit groups against the FP64 loop the slicing of the FP64-accurate GEMM
+// defines: t = |v| / 2^esc, then nine times t *= 64, digit = trunc(t), t -= digit (each
+// step exact)
+static int check_fixed54(double v, int esc) {
+  double t = std::fabs(v) * std::ldexp(1.0, -esc);
+  const uint64_t F = tnt::fixed54(v, esc);
+  for (int p = 0; p < 9; ++p) {
+    t *= 64.0;
+    const double d = std::trunc(t);
+    t -= d;
+    const uint64_t got = (F >> (48 - 6 * p)) & 63u;
+    if ((double)got != d) {
+      std::printf("fixed54(%.17g, %d): digit %d = %llu, expected %.0f\n", v, esc, p + 1,
+                  (unsigned long long)got, d);
+      return 1;
+    }
+  }
+  return 0;
+}
+
 int main() {
   int bad = 0;
+  for (int i = 0; i < 400000; ++i) {  // |v| < 2^esc, esc one to four above v's exponent
+    const uint64_t r = next_u64();
+    const double mant = 1.0 + (double)(r >> 12) * std::ldexp(1.0, -52);
+    const int ex = (int)(next_u64() % 600) - 300;
+    const double v = std::ldexp((r & 1) ? -mant : mant, ex);
+    bad += check_fixed54(v, ex + 1 + (int)(next_u64() % 4));
+  }
+  bad += check_fixed54(0.0, 0) + check_fixed54(-0.0, 5) + check_fixed54(4.9e-324, -1020) +
+         check_fixed54(std::nextafter(1.0, 0.0), 0) + check_fixed54(-0.75, 0);
   const double edges[] = {0.0, -0.0, 1.0, -1.0, 0.5, 3.0, (double)FLT_MIN, -(double)FLT_MIN,
                           std::ldexp(1.0, -127), std::ldexp(1.0, -149), (double)FLT_MAX,
                           std::nextafter((double)FLT_MAX, INFINITY), std::ldexp(1.0, 128),

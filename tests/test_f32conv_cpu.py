@@ -1,7 +1,9 @@
-"""The FP64 <-> FP32 conversions of the FP32-arithmetic Gram-Schmidt passes
-(`csrc/f32conv.cuh`: integer operations on the IEEE-754 layouts, truncation toward zero)
-compiled for the host and checked against the C library's conversions on two million
-random values and the edge cases (`tests/f32conv_host.cu`).  No GPU."""
+"""The bit-level helpers of `csrc/f32conv.cuh`, compiled for the host (`tests/f32conv_host.cu`):
+the FP64 <-> FP32 conversions of the FP32-arithmetic Gram-Schmidt passes and the split-TF32
+operands (integer operations on the IEEE-754 layouts, truncation toward zero) against the
+C library's conversions on two million random values and the edge cases, and the
+fixed-point form whose 6-bit groups are the slices of the FP64-accurate GEMM against the
+FP64 multiply-truncate loop that defines them.  No GPU."""
 import os
 import shutil
 import subprocess
