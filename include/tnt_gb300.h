@@ -55,7 +55,7 @@ enum {
   TNT_E_TIMEOUT = 5,     /* a bounded device-side wait gave up                          */
   TNT_E_BOUNDS = 6,      /* a device-side index check failed                            */
   TNT_E_NAN = 7,         /* a NaN/Inf was detected in a result                          */
-  TNT_E_UNSUPPORTED = 8  /* shape or mode not supported by this build                   */
+  TNT_E_UNSUPPORTED = 8  /* shape or mode not supported by this library                 */
 };
 
 enum { TNT_PREC_FP64 = 0, TNT_PREC_MIXED = 1 };

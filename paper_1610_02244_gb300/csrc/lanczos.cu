@@ -94,7 +94,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
   double E_prev = 0;
   // T_k's lowest eigenpair runs on the side stream one Krylov step behind the vector work:
   // step k's scalars are handed over by an event, its result comes back into pinned slot
-  // k & 1, and the host judges step k - 1 while step k runs.  A solve that converges at
+  // k & 1, and the host checks step k - 1 while step k runs.  A solve that converges at
   // k - 1 has computed one step more than it uses (not counted in n_matvec); the Ritz
   // vector is that of step k - 1, from V[0..k-1] and y of slot (k-1) & 1.
   TNT_TRY(side_stream(c));
@@ -113,7 +113,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
   double E = 0, resid = 0;
   int kk = 0;
   // step j's result: E_j, the residual estimate, and whether the solve may stop there
-  auto judge = [&](int j, bool* cv) -> int {
+  auto check_step = [&](int j, bool* cv) -> int {
     TNT_CUDA_TRY(c, cudaEventSynchronize(c->ev_side[j & 1]));
     const double* h = hp + 4 * (j & 1);
     E = h[0];
@@ -159,7 +159,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
       TNT_TRY(launch_tk(k));
       if (k > 0) {
         bool cv = false;
-        TNT_TRY(judge(k - 1, &cv));
+        TNT_TRY(check_step(k - 1, &cv));
         if (cv) {
           conv = stop = true;
           use = k - 1;
@@ -169,7 +169,7 @@ static int lanczos_cycle_loop(Ctx* c, const MatVec& A, z* theta, int precision,
       }
       if (k + 1 == cap || total >= max_matvec) {
         bool cv = false;
-        TNT_TRY(judge(k, &cv));
+        TNT_TRY(check_step(k, &cv));
         conv = cv;
         stop = cv || total >= max_matvec;
         use = k;
